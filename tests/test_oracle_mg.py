@@ -1,0 +1,194 @@
+"""Pins of the oracle's multigrid and Krylov layer.
+
+Smoothers are pinned against closed forms on diagonal operators (Jacobi and
+Chebyshev polynomials) and against library triangular solves (Gauss-Seidel);
+the coarse solve against a pseudo-inverse; unpreconditioned flexible CG
+against scipy's CG on the equivalent symmetric system; MG and MG-PCG against
+direct solves.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import multigrid as mg
+
+
+def _square(nsub, nlevels, **kw):
+    v, t = W.unit_square()
+    return mg.build_hierarchy(v, t, nsub, nlevels, "dirichlet", opts=mg.MGOptions(**kw))
+
+
+def _ico(nsub, nlevels, **kw):
+    v, t = W.icosahedron()
+    return mg.build_hierarchy(v, t, nsub, nlevels, "gauge", sphere=True, opts=mg.MGOptions(**kw))
+
+
+def _diag_level(lams):
+    n = len(lams)
+    lev = mg.Level(mesh=None, star0=np.ones(n), star1=None, A=None, L=sp.diags(lams).tocsr(),
+                   free=np.ones(n, dtype=bool), diag=np.ones(n))
+    lev.lmax = float(max(lams))
+    return lev
+
+
+def test_jacobi_closed_form_on_diagonal_operator():
+    lams = np.array([0.1, 0.5, 1.0, 1.7])
+    lev = _diag_level(lams)
+    for nu in (1, 2, 3):
+        x = mg.jacobi(lev, np.zeros(4), np.ones(4), 0.7, nu)
+        assert np.allclose(x, (1 - 0.7 * lams) ** nu, rtol=1e-14)
+
+
+def _cheb_T(s, x):
+    return np.cosh(s * np.arccosh(x)) if np.all(x >= 1) else np.cos(s * np.arccos(np.clip(x, -1, 1)))
+
+
+def test_chebyshev_is_scaled_chebyshev_polynomial():
+    # with b = 0 the error after s steps is T_s((theta - lam)/delta) / T_s(theta/delta)
+    lams = np.linspace(0.35, 1.9, 9)
+    lev = _diag_level(lams)
+    lo, hi = 0.3, 1.1
+    a, bb = lo * lev.lmax, hi * lev.lmax
+    theta, delta = (a + bb) / 2, (bb - a) / 2
+    for s in (1, 2, 3, 4):
+        x = mg.chebyshev(lev, np.zeros(len(lams)), np.ones(len(lams)), s, lo, hi)
+        expect = np.array([_cheb_T(s, np.array([(theta - l) / delta]))[0] for l in lams]) / _cheb_T(s, np.array([theta / delta]))[0]
+        assert np.allclose(x, expect, rtol=1e-12, atol=1e-14)
+
+
+def test_gauss_seidel_matches_sequential_sweep():
+    h = _square(2, 2, smoother="gs")
+    lev = h.finest
+    rng = np.random.default_rng(0)
+    b = lev.free * rng.standard_normal(lev.mesh.nv)
+    x0 = lev.free * rng.standard_normal(lev.mesh.nv)
+    got = mg.gauss_seidel(lev, b, x0, 2)
+    L = lev.L.toarray()
+    x = x0.copy()
+    for _ in range(2):
+        for i in range(len(x)):
+            if lev.free[i]:
+                s = sum(L[i, j] * x[j] for j in range(len(x)) if j != i and lev.free[j])
+                x[i] = (b[i] - s) / L[i, i]
+    assert np.allclose(got, x, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("mk", [lambda: _square(3, 2, smoother="mcgs"), lambda: _ico(2, 2, smoother="mcgs")])
+def test_multicolour_gs_is_gs_in_colour_order(mk):
+    h = mk()
+    lev = h.finest
+    col = lev.colors
+    for a, b in lev.mesh.edges:
+        assert col[a] != col[b]
+    rng = np.random.default_rng(1)
+    b = lev.free * rng.standard_normal(lev.mesh.nv)
+    x0 = lev.free * rng.standard_normal(lev.mesh.nv)
+    got = mg.mc_gauss_seidel(lev, b, x0, 1)
+    perm = np.lexsort((np.arange(len(col)), col))
+    F = sp.diags(lev.free.astype(float))
+    Lf = (F @ lev.L @ F).tocsr() + sp.diags((~lev.free).astype(float))
+    Lp = Lf[perm][:, perm]
+    lo = sp.tril(Lp, 0).tocsr()
+    up = sp.triu(Lp, 1).tocsr()
+    xp = spla.spsolve_triangular(lo, (lev.free * b)[perm] - up @ x0[perm], lower=True)
+    expect = np.empty_like(xp)
+    expect[perm] = xp
+    assert np.allclose(got, lev.free * expect, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("mk", [lambda: _square(4, 1), lambda: _ico(3, 1)])
+def test_power_iteration_bounds_lambda_max(mk):
+    h = mk()
+    lev = h.finest
+    idx = np.flatnonzero(lev.free)
+    DL = (sp.diags(1.0 / lev.diag[idx]) @ lev.L[idx][:, idx]).toarray()
+    true = np.max(np.linalg.eigvals(DL).real)
+    assert lev.lmax <= true * (1 + 1e-12)
+    assert lev.lmax > 0.9 * true
+
+
+def test_gauge_coarse_solve_is_pseudo_inverse():
+    h = _ico(1, 1)
+    lev = h.finest
+    b = mg.prepare_rhs(h, W.uniform_field(lev.mesh.nv, 7))
+    x = mg.coarse_solve(h, lev, b)
+    A = lev.A.toarray()
+    xp = np.linalg.pinv(A) @ (lev.star0 * b)
+    assert np.allclose(x, mg.project_mean_zero(lev, xp), atol=1e-12)
+    assert abs(mg.star0_mean(lev, x)) < 1e-14
+
+
+def test_dirichlet_coarse_solve_single_unknown():
+    # 3x3 vertices, one interior unknown: *0 = 1/4, L_ii = 4 / h^2 with h = 1/2
+    h = _square(1, 1)
+    lev = h.finest
+    b = np.ones(lev.mesh.nv)
+    x = mg.coarse_solve(h, lev, b)
+    assert np.count_nonzero(x) == 1
+    assert np.isclose(x[lev.free][0], 1.0 / 16.0, rtol=1e-15)
+
+
+def test_unpreconditioned_flexible_cg_is_cg():
+    # CG on L in the *0 inner product == CG on A x = *0 b in the Euclidean one
+    h = _square(3, 1)
+    lev = h.finest
+    b = mg.prepare_rhs(h, W.uniform_field(lev.mesh.nv, 3))
+    idx = np.flatnonzero(lev.free)
+    A = lev.A[idx][:, idx]
+    iters = []
+    spla.cg(A, lev.star0[idx] * b[idx], rtol=1e-30, maxiter=6, callback=lambda xk: iters.append(xk.copy()))
+    for k in range(1, 6):
+        res = mg.pcg_solve(h, b, 0.0, k, precondition=False)
+        assert np.allclose(res.x[idx], iters[k - 1], rtol=1e-9, atol=1e-12)
+
+
+def test_single_level_cycle_is_direct_solve():
+    h = _ico(2, 1)
+    lev = h.finest
+    b = mg.prepare_rhs(h, W.uniform_field(lev.mesh.nv, 4))
+    x = mg.vcycle(h, b, np.zeros_like(b))
+    assert np.allclose(x, mg.direct_solve(h, b), atol=1e-12)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "gs", "mcgs"])
+@pytest.mark.parametrize("which", ["square", "ico"])
+def test_mg_and_pcg_reach_direct_solution(smoother, which):
+    h = _square(5, 4, smoother=smoother) if which == "square" else _ico(3, 3, smoother=smoother)
+    lev = h.finest
+    b = W.uniform_field(lev.mesh.nv, 11)
+    xs = mg.direct_solve(h, b)
+    r1 = mg.mg_solve(h, b, 1e-10, 60)
+    r2 = mg.pcg_solve(h, b, 1e-10, 60)
+    for r in (r1, r2):
+        assert r.rel_res <= 1e-10
+        assert mg.star0_norm(lev, r.x - xs) / mg.star0_norm(lev, xs) < 1e-8
+    band = {"jacobi": 0.35, "chebyshev": 0.3, "gs": 0.2, "mcgs": 0.2}[smoother]
+    assert mg.convergence_factor(r1.history) < band
+    assert r2.iters <= r1.iters
+
+
+def test_config1_standalone_mg_matches_closed_form():
+    # unit square x5, 5-level V(2,2), Dirichlet 0, RHS -Delta of sin(pi x) sin(pi y), to 1e-10
+    h = _square(5, 5)
+    lev = h.finest
+    assert [l.mesh.nv for l in h.levels] == [9, 25, 81, 289, 1089]
+    r = mg.mg_solve(h, W.rhs_sin_square(lev.mesh.verts), 1e-10, 100)
+    hh = 1.0 / 32
+    lam11 = 8.0 / hh ** 2 * math.sin(math.pi * hh / 2) ** 2
+    u_h = 2 * math.pi ** 2 / lam11 * W.u_sin_square(lev.mesh.verts)
+    assert r.rel_res <= 1e-10
+    assert mg.star0_norm(lev, r.x - u_h) / mg.star0_norm(lev, u_h) < 1e-9
+
+
+def test_w_cycle_converges_faster_than_v():
+    hv = _square(5, 5)
+    hw = _square(5, 5, gamma=2)
+    b = W.uniform_field(hv.finest.mesh.nv, 12)
+    rv = mg.mg_solve(hv, b, 1e-10, 60)
+    rw = mg.mg_solve(hw, b, 1e-10, 60)
+    assert rw.iters <= rv.iters
+    assert np.allclose(rw.x, rv.x, atol=1e-9 * np.abs(rv.x).max())
