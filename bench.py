@@ -1,0 +1,419 @@
+"""Benchmark: Poisson solves/s to 1e-8 relative residual on the icosphere x8 mesh.
+
+Workload (the configuration the headline metric is quoted on): unit
+icosphere subdivided 8 times with midpoints projected to radius 1
+(655,362 vertices, 1,310,720 triangles), 7 multigrid levels (162 ... 655,362
+vertices), constant-nullspace gauge, right-hand side = sum of real spherical
+harmonics of degree 1..16 with N(0,1) coefficients (seed 1), flexible
+MG-preconditioned CG with FP32 V-cycles inside the FP64 outer iteration, to
+relative residual 1e-8.  One step = one complete solve with b resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs independent replicas of the solve on its own
+GPU (the solve has no data-parallel split); `value` is the total solves/s of
+all ranks over the slowest rank's time.  `--impl reference` times the FP64
+CPU oracle on the host (rank 0 only) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Poisson solves/s to 1e-8 rel. residual; V-cycle MDOF/s; HBM GB/s vs peak"
+NSUB, NLEVELS, TOL, SEED = 8, 7, 1e-8, 1
+WORKLOAD = "icosphere_l8_gauge_sh16_mgpcg_1e-8"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+# Algorithmic bytes per row of each kernel kind (K = stencil slots per row,
+# FP32 cycle vectors / FP64 outer vectors, int32 columns).  A gathered vector
+# is counted once per row (its entries are reused from cache by neighbours).
+def bytes_per_row(kind, K, mixed, cheb):
+    f = 4 if mixed else 8  # cycle precision
+    if kind == "smooth0":
+        return K * f + f + f + (f if cheb else 0)
+    if kind == "smooth":
+        # with nu = 2 each Chebyshev step reads or writes one direction vector
+        return K * 4 + K * f + 3 * f + (f if cheb else 0)
+    if kind == "residual":
+        return K * 4 + K * f + 3 * f
+    if kind == "spmv64":
+        return K * 4 + K * 8 + 8 + 8 + 8 + 1
+    if kind == "update":
+        return 8 + 8 + 16 + 16 + (4 if mixed else 0)
+    if kind == "zdots":
+        return f + 8 + 8 + 8 + 8 + 1  # z, zn write, *0, r, z_old, free flag
+    if kind == "pupd":
+        return 8 + 1 + 8 + 16
+    return None
+
+
+def restrict_bytes(n_f, n_c, K, f):
+    return n_c * K * 4 + n_f * f + n_c * f
+
+
+def prolong_bytes(n_f, n_c, f):
+    return 2 * n_f * f + (n_f - n_c) * 8 + n_c * f
+
+
+def kernel_bytes(entry, hier, mixed, cheb):
+    """Algorithmic bytes moved by one launch of a profiled kernel."""
+    lvl = entry["level"]
+    n = entry["rows"]
+    K = hier.ell_width[lvl]
+    f = 4 if mixed else 8
+    kind = entry["kind"]
+    if kind == "restrict":
+        return restrict_bytes(n, hier.nv[lvl - 1], K, f)
+    if kind == "prolong":
+        return prolong_bytes(n, hier.nv[lvl - 1], f)
+    per = bytes_per_row(kind, K, mixed, cheb)
+    return None if per is None else per * n
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernels_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "solver.cu"):
+        with open(os.path.join(ROOT, "paper_2508_12501_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, if it was taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernels_hash") != kernels_hash():
+        return None
+    ent = d.get("kernels", {}).get(kind)
+    return None if ent is None else float(ent["dram_bytes_per_launch"])
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu is not None:
+                cmd += ["-i", str(self.gpu)]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() in ("active", "1"):
+                        reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# oracle arm / CPU baseline
+# ----------------------------------------------------------------------------
+
+def oracle_setup(smoother="chebyshev"):
+    from oracle import multigrid as omg
+    v, t = W.icosahedron()
+    oh = omg.build_hierarchy(v, t, NSUB, NLEVELS, "gauge", sphere=True, opts=omg.MGOptions(smoother=smoother))
+    b = W.sh_sum(oh.finest.mesh.verts, W.sh_coefficients(SEED))
+    return oh, b
+
+
+def oracle_time(oh, b, nsolve):
+    from oracle import multigrid as omg
+    ts = []
+    res = None
+    for _ in range(nsolve):
+        t0 = time.perf_counter()
+        res = omg.pcg_solve(oh, b, TOL, 100)
+        ts.append(time.perf_counter() - t0)
+    return ts, res
+
+
+def cpu_cores_used():
+    # the oracle is numpy/scipy on one process; sparse products are single-threaded
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return 1
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    oh, b = oracle_setup(args.smoother)
+    oracle_time(oh, b, args.warmup)
+    ts, res = oracle_time(oh, b, args.steps)
+    tot = sum(ts)
+    value = args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nv": oh.finest.mesh.nv, "levels": NLEVELS, "solver": "oracle flexible MG-PCG",
+                   "parallelism": "host, 1 process"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": f"{args.steps} complete oracle solves of the full workload ({res.iters} iterations each)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "iters": res.iters, "rel_res": res.rel_res,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--smoother", default="chebyshev", choices=["jacobi", "chebyshev"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-all-levels", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    import paper_2508_12501_gb300 as P
+
+    v, t = W.icosahedron()
+    h = P.Hierarchy(P.Mesh(v, t), NSUB, NLEVELS, bc="gauge", sphere=True, smoother=args.smoother)
+    n = h.n
+    b_host = W.sh_sum(h.table(-1, "verts"), W.sh_coefficients(SEED))
+    b = torch.as_tensor(b_host, device=dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    def timed_solves(k, mode, profile=0):
+        if profile:
+            h.profile(profile)
+        evs = []
+        st = None
+        launches = 0
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = h.solve(b, x, solver="mgpcg", mode=mode, tol=TOL)
+            e1.record(stream)
+            evs.append((e0, e1))
+            launches += st.launches
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(c) for a, c in evs]
+        prof = h.profile_read() if profile else None
+        if profile:
+            h.profile(0)
+        return ms, st, launches, prof
+
+    # warm-up (builds the iteration graphs)
+    for _ in range(args.warmup):
+        h.solve(b, x, solver="mgpcg", mode=args.mode, tol=TOL)
+        h.solve(b, x, solver="mgpcg", mode="f64", tol=TOL)
+    barrier()
+
+    gpu_idx = None
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        ids = [s for s in cvd.split(",") if s.strip()]
+        gpu_idx = ids[local] if local < len(ids) else None
+    else:
+        gpu_idx = local
+    clocks = ClockSampler(gpu_idx)
+    clocks.start()
+
+    # ---- timed region: K solves, L2 flushed before each, CUDA events per solve
+    barrier()
+    ms, st, launches, _ = timed_solves(args.steps, args.mode)
+    barrier()
+    clk = clocks.stop()
+    tot_s = sum(ms) / 1e3
+    x_mixed = x.clone()
+    if world > 1:
+        tt = torch.tensor([tot_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_s = float(tt.item())
+    value = args.steps * world / tot_s
+
+    # ---- plain FP64 form of the same solve (speedup at equal accuracy)
+    ms64, st64, _, _ = timed_solves(args.steps, "f64")
+    x_f64 = x.clone()
+    v64 = args.steps / (sum(ms64) / 1e3)
+
+    # ---- live per-kernel timing of the same solves (event pairs on the solve stream)
+    _, _, _, prof = timed_solves(args.steps, args.mode, profile=2 if args.profile_all_levels else 1)
+    mixed = args.mode == "mixed"
+    cheb = args.smoother == "chebyshev"
+    rows = []
+    for e in prof or []:
+        by = kernel_bytes(e, h, mixed, cheb)
+        avg = e["total_ms"] / max(1, e["launches"])
+        rows.append(dict(e, avg_ms=avg, bytes=by, gbs=(by / (avg * 1e-3) / 1e9) if by else None))
+    top = max(rows, key=lambda r: r["total_ms"]) if rows else None
+    peak, peak_src = peaks()
+    roof = None
+    if top and top["bytes"]:
+        tr = ncu_traffic(top["kind"])
+        roof = {"bound": "hbm", "kernel": f"{top['kind']} (level {top['level']}, {top['rows']} rows)",
+                "achieved": top["gbs"], "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": top["gbs"] / peak, "traffic": tr, "algorithmic_bytes": top["bytes"],
+                "avg_launch_ms": top["avg_ms"], "share_of_profiled_time": top["total_ms"] / sum(r["total_ms"] for r in rows)}
+
+    # ---- V-cycle throughput: back-to-back FP32 cycles
+    xb = torch.zeros(n, dtype=torch.float32, device=dev)
+    bb = b.float()
+    for _ in range(3):
+        h.vcycle(bb, xb)
+    ncyc = 20
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ncyc):
+        h.vcycle(bb, xb)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    vc_ms = e0.elapsed_time(e1) / ncyc
+    mdofs = n / (vc_ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers
+    b_pin = torch.as_tensor(b_host).pin_memory()
+    for _ in range(2):
+        h.solve(b_pin, solver="mgpcg", mode=args.mode, tol=TOL)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        xh, _ = h.solve(b_pin, solver="mgpcg", mode=args.mode, tol=TOL)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": args.steps * world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n, "note": "wall clock, includes one 256 MB L2 flush per step"}
+
+    # accuracy of the mixed result against the plain FP64 GPU result (*0 norm)
+    s0 = torch.as_tensor(h.table(-1, "star0"), device=dev)
+    d = x_mixed - x_f64
+    err = float(torch.sqrt((s0 * d * d).sum() / (s0 * x_f64 * x_f64).sum()))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oh, ob = oracle_setup(args.smoother)
+        ts, ores = oracle_time(oh, ob, 5)
+        cpu = {"value": len(ts) / sum(ts), "unit": "solves/s", "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"5 complete FP64 oracle MG-PCG solves of the full workload ({ores.iters} iterations each), "
+                         f"hierarchy build excluded"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nv": n, "levels": NLEVELS, "smoother": args.smoother,
+                       "cycle": "V(2,2)", "mode": args.mode, "tol": TOL,
+                       "l2": "256 MB buffer written before every step (flush)", "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "iters": st.iters, "rel_res": st.rel_res, "fp64_solves_per_s": v64, "fp64_iters": st64.iters,
+            "speedup_vs_fp64": value / world / v64, "mixed_vs_fp64_rel_err_star0": err,
+            "vcycle_ms": vc_ms, "vcycle_mdof_s": mdofs,
+            "kernels": [{k: (round(v_, 6) if isinstance(v_, float) else v_) for k, v_ in r.items()} for r in rows],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

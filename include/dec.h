@@ -1,0 +1,257 @@
+/*
+ * dec.h -- C ABI of libdec: geometric multigrid for the DEC 0-form Laplacian
+ * on triangle meshes nested by 1->4 midpoint subdivision, on one GB300 GPU.
+ *
+ * The operator is L = *0^-1 d0^T *1 d0 (Sec. 3.1.1, Eq. hodge0-laplacian,
+ * with the sign chosen so that L is positive semidefinite: L = -Delta_0).
+ * Interpolation is the matrix of the subdivision map and restriction its
+ * row-normalized transpose (Sec. 2.2.1).  Solvers: standalone multigrid and
+ * multigrid-preconditioned CG (Sec. 3.1.2), in plain FP64 or with FP32
+ * V-cycles inside an FP64 outer iteration.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status (DEC_OK = 0 on success).  On
+ *     failure dec_last_error() returns a message for the calling thread.
+ *   - Host arrays (double*, int32_t*) passed to *_create / *_build are
+ *     copied; the caller keeps ownership.
+ *   - Vector arguments of the compute calls are DEVICE pointers on the
+ *     device that was current when the hierarchy was built; the caller owns
+ *     them.  They are enqueued on `stream` (a cudaStream_t, 0 = legacy
+ *     default stream); the call returns after enqueueing unless stated.
+ *   - Vertex vectors are in the library's vertex order, which is the order
+ *     produced by the subdivision itself: the coarse vertices keep their ids
+ *     and the midpoint of coarse edge e gets id n_coarse + e.  With k > 1
+ *     right-hand sides a vector is interleaved: value j of vertex v at
+ *     [v * k + j].
+ *   - A handle may be used by one thread / one stream at a time.
+ */
+#ifndef DEC_H
+#define DEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dec_mesh dec_mesh;
+typedef struct dec_mg dec_mg;
+typedef struct CUstream_st *dec_stream_t; /* same type as cudaStream_t */
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    DEC_OK = 0,
+    DEC_ERR_ARG = 1,           /* bad argument (null pointer, size, enum)          */
+    DEC_ERR_MESH = 2,          /* mesh violates the simplicial-complex definition  */
+    DEC_ERR_CUDA = 3,          /* a CUDA runtime call failed                        */
+    DEC_ERR_OOM = 4,           /* host or device allocation failed                  */
+    DEC_ERR_NOT_CONVERGED = 5, /* maxit reached; the output holds the last iterate  */
+    DEC_ERR_NONFINITE = 6      /* NaN or Inf met in the input or in the iteration   */
+};
+
+/* ---- enums ------------------------------------------------------------- */
+/* dec_mg_build flags: DEC_SPHERE_PROJECT pushes new midpoints to the unit
+ * sphere; DEC_HOST_ONLY builds the host tables only (no device memory, no
+ * CUDA call) so they can be inspected with dec_mg_info / dec_mg_copy_table;
+ * compute calls on such a handle return DEC_ERR_ARG. */
+enum { DEC_SPHERE_PROJECT = 1u, DEC_HOST_ONLY = 2u };
+enum { DEC_BC_DIRICHLET = 0, DEC_BC_GAUGE = 1 };
+enum { DEC_F64 = 0, DEC_F32 = 1 };           /* precision of a single operator call */
+enum { DEC_SMOOTH_JACOBI = 0, DEC_SMOOTH_CHEBYSHEV = 1, DEC_SMOOTH_MCGS = 2 };
+enum { DEC_SOLVER_MG = 0, DEC_SOLVER_MGPCG = 1, DEC_SOLVER_CG = 2 };
+enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1 };
+
+/* Multigrid options.  dec_mg_default_opts() fills the defaults:
+ * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
+ * [0.3, 1.1] * lambda_max(D^-1 L) with lambda_max from 10 power iterations,
+ * gamma = 1 (V-cycle; 2 gives a W-cycle). */
+typedef struct dec_mg_opts {
+    int smoother;
+    int nu1, nu2;
+    double omega;
+    double cheby_lo, cheby_hi;
+    int power_iters;
+    int gamma;
+} dec_mg_opts;
+
+/* Solver options.  dec_solve_default_opts(): MG-PCG, mixed precision,
+ * tol = 1e-8, maxit = 100, no warm start, convergence checked every
+ * iteration. */
+typedef struct dec_solve_opts {
+    int solver;       /* DEC_SOLVER_*                                           */
+    int mode;         /* DEC_MODE_F64 or DEC_MODE_MIXED                           */
+    double tol;       /* stop when ||b - L x||_2 / ||b||_2 <= tol (free vertices) */
+    int maxit;        /* outer iterations                                         */
+    int warm_start;   /* nonzero: x holds the initial guess on entry              */
+    int check_every;  /* host reads the residual every this many iterations (>=1) */
+} dec_solve_opts;
+
+typedef struct dec_stats {
+    int iters;        /* outer iterations taken                                  */
+    double rel_res;   /* final relative residual (recurrence value for PCG)      */
+    double rel_res0;  /* relative residual of the initial guess                  */
+    int64_t launches; /* libdec kernels launched by this call (graph nodes included) */
+} dec_stats;
+
+typedef struct dec_mg_info_t {
+    int nlevels;          /* levels in the hierarchy, 0 = coarsest                */
+    int64_t nv[16];       /* vertices per level                                   */
+    int64_t ne[16];       /* edges per level                                      */
+    int64_t nt[16];       /* triangles per level                                  */
+    int ell_width[16];    /* stored stencil slots per vertex per level            */
+    double lmax[16];      /* power-iteration lambda_max(D^-1 L) per level         */
+    int ncolors[16];      /* greedy colour count per level (multicolour GS)       */
+    int bc;               /* DEC_BC_*                                             */
+    int dim;              /* coordinate dimension of the vertices (2 or 3)        */
+    size_t device_bytes;  /* device memory held by the handle                     */
+} dec_mg_info_t;
+
+/* What dec_mg_copy_table copies (host output, element type in brackets). */
+enum {
+    DEC_TABLE_VERTS = 0,   /* [nv * dim] double, vertex coordinates               */
+    DEC_TABLE_TRIS = 1,    /* [nt * 3] int32, triangles                           */
+    DEC_TABLE_EDGES = 2,   /* [ne * 2] int32, (lo, hi), lexicographic             */
+    DEC_TABLE_STAR0 = 3,   /* [nv] double, circumcentric dual areas               */
+    DEC_TABLE_STAR1 = 4,   /* [ne] double, dual/primal length ratios (scaled)     */
+    DEC_TABLE_FREE = 5,    /* [nv] int32, 1 = unknown, 0 = Dirichlet vertex       */
+    DEC_TABLE_PARENTS = 6, /* [ne(level) * 2] int32, parents of level+1 midpoints */
+    DEC_TABLE_COLORS = 7   /* [nv] int32, greedy colour of each vertex            */
+};
+
+/* ---- errors, defaults --------------------------------------------------- */
+const char *dec_last_error(void);
+void dec_mg_default_opts(dec_mg_opts *opts);
+void dec_solve_default_opts(dec_solve_opts *opts);
+
+/* ---- meshes (host only; no GPU needed) ----------------------------------
+ * dec_mesh_create: an embedded 2-simplicial complex (Sec. 2.1, Def. of an
+ * embedded simplicial complex): nv points of dimension dim (2 or 3, row
+ * major [nv * dim]) and nt triangles ([nt * 3] vertex ids).  Edges are
+ * enumerated once as (lo, hi), lo < hi, in lexicographic order.
+ * Errors: DEC_ERR_ARG for null pointers or sizes out of range (nv, nt >= 1,
+ * nv < 2^31); DEC_ERR_MESH for an index out of range, a triangle repeating a
+ * vertex, two triangles on the same vertex set, a vertex in no triangle or
+ * an edge in more than two triangles.  *out is owned by the caller and
+ * released with dec_mesh_destroy. */
+int dec_mesh_create(const double *verts, int64_t nv, int dim,
+                    const int32_t *tris, int64_t nt, dec_mesh **out);
+void dec_mesh_destroy(dec_mesh *mesh);
+/* Sizes and coordinate dimension of a mesh.  Any output pointer may be null. */
+int dec_mesh_sizes(const dec_mesh *mesh, int64_t *nv, int64_t *ne, int64_t *nt, int *dim);
+/* dec_mesh_refine: nsub successive 1->4 midpoint subdivisions (Sec. 2.2.1,
+ * binary subdivision) on the host.  Coarse ids are kept; the midpoint of
+ * coarse edge e is n_coarse + e; triangle t = (a,b,c) becomes
+ * 4t+0 = (a,m_ab,m_ca), 4t+1 = (m_ab,b,m_bc), 4t+2 = (m_ca,m_bc,c),
+ * 4t+3 = (m_ab,m_bc,m_ca).  flags & DEC_SPHERE_PROJECT pushes each new
+ * midpoint to the unit sphere.  *out is a new mesh owned by the caller. */
+int dec_mesh_refine(const dec_mesh *mesh, int nsub, uint32_t flags, dec_mesh **out);
+/* Copy DEC_TABLE_VERTS / TRIS / EDGES / STAR0 / STAR1 of a mesh to host memory.
+ * STAR0 and STAR1 are the circumcentric Hodge stars (Sec. 3.1.1). */
+int dec_mesh_copy_table(const dec_mesh *mesh, int what, void *host_out);
+
+/* ---- hierarchy ------------------------------------------------------------
+ * dec_mg_build: subdivide `base` nsub times and keep the finest nlevels
+ * meshes as the multigrid hierarchy (nlevels in 1..min(nsub+1, 16)).  The
+ * operator L = *0^-1 d0^T *1 d0 is rediscretized on every level (Sec. 3.1.1,
+ * last paragraph).  bc = DEC_BC_DIRICHLET fixes boundary vertices to 0;
+ * DEC_BC_GAUGE treats the constants as the nullspace and works with
+ * *0-weighted mean-zero vectors.  star1_scale (host, nullable, one value per
+ * finest edge) multiplies *1 on the finest level.  opts may be null
+ * (defaults).  Builds on the host, then uploads every table to the current
+ * CUDA device.  Errors: DEC_ERR_ARG, DEC_ERR_MESH (also: a free vertex whose
+ * diagonal is not positive, or a coarsest level above 8192 unknowns),
+ * DEC_ERR_CUDA, DEC_ERR_OOM.  Release with dec_mg_destroy. */
+int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t flags,
+                 const double *star1_scale, const dec_mg_opts *opts, dec_mg **out);
+void dec_mg_destroy(dec_mg *mg);
+int dec_mg_info(const dec_mg *mg, dec_mg_info_t *info);
+/* Copy a host-side table of one level (DEC_TABLE_*) into host_out. */
+int dec_mg_copy_table(const dec_mg *mg, int level, int what, void *host_out);
+
+/* dec_mg_set_star1: replace the finest-level *1 (device pointer, [ne] double,
+ * unscaled final values) and rebuild the finest operator's weights on the
+ * device.  Coarser levels keep their geometric operators. */
+int dec_mg_set_star1(dec_mg *mg, const double *star1, dec_stream_t stream);
+
+/* ---- operator --------------------------------------------------------------
+ * dec_laplace0_apply: y = L_level x (Sec. 3.1.1, Eq. hodge0-laplacian, as
+ * -Delta_0), i.e. y_v = (1 / star0_v) sum_{e=(v,w)} *1_e (x_v - x_w); rows of
+ * Dirichlet vertices are 0.  prec = DEC_F64 (double x, y) or DEC_F32 (float
+ * x, y, weights rounded to float).  k: right-hand sides, interleaved.
+ * x and y must not overlap. */
+int dec_laplace0_apply(const dec_mg *mg, int level, const void *x, void *y, int k,
+                       int prec, dec_stream_t stream);
+/* dec_residual: r = b - L_level x on free vertices, 0 on Dirichlet vertices. */
+int dec_residual(const dec_mg *mg, int level, const void *b, const void *x, void *r, int k,
+                 int prec, dec_stream_t stream);
+
+/* ---- cycles and solves -------------------------------------------------------
+ * dec_mg_vcycle: x <- x + C(b - L x) on the finest level, where C is one
+ * multigrid cycle with zero initial guess: pre-smoothing, residual,
+ * restriction by the row-normalized transpose of the subdivision matrix,
+ * recursion (gamma times), interpolation by the subdivision matrix,
+ * post-smoothing (Sec. 2.2.1; Sec. 3.1.1 last paragraph), and a dense
+ * direct solve on the coarsest level.  prec as for dec_laplace0_apply. */
+int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_stream_t stream);
+
+/* dec_solve: solve L x = b on the finest level to ||b - L x||_2/||b||_2 <= tol
+ * (Sec. 3.1.2).  Standalone multigrid, or flexible CG in the *0 inner
+ * product preconditioned by one cycle (Sec. 3.1.2 cross-comparison), or
+ * plain CG.  DEC_MODE_MIXED runs the cycles in FP32 inside the FP64 outer
+ * iteration (residuals, dot products and updates in FP64).  b and x are
+ * double device vectors of nv(finest) * k entries.  Under DEC_BC_GAUGE, b is
+ * projected to *0-weighted mean zero and so is x.  Synchronizes `stream`
+ * while iterating.  Returns DEC_ERR_NOT_CONVERGED (x holds the last iterate)
+ * or DEC_ERR_NONFINITE; stats may be null. */
+int dec_solve(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts,
+              dec_stats *stats, dec_stream_t stream);
+
+/* dec_solve_backward: adjoint of x = L^-1 b.  Given u = L^-1 b and
+ * grad_u = dJ/du (device, [nv]), solve L mu = *0^-1 grad_u with the same
+ * hierarchy (L^T = d0^T *1 d0 *0^-1 = *0 L *0^-1), then
+ * grad_b = dJ/db = *0 mu and, if grad_star1 is not null,
+ * grad_star1[e] = dJ/d*1_e = -(d0 mu)_e (d0 u)_e on the finest edges. */
+int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double *grad_b,
+                       double *grad_star1, const dec_solve_opts *opts, dec_stats *stats,
+                       dec_stream_t stream);
+
+/* ---- live kernel timing ------------------------------------------------------
+ * dec_mg_profile: enable = 1 records a CUDA event pair around every launch of
+ * the finest level inside the repeated part of dec_solve (the captured
+ * iteration), enable = 2 around the launches of every level, 0 turns it off.
+ * Events are recorded on the solve's stream, so each pair brackets exactly one
+ * kernel.  Enabling clears the counters.  While enabled, dec_solve reads the
+ * events after every iteration (check_every is treated as 1); the iteration
+ * in which the solve converges is not counted.
+ * dec_mg_profile_read copies up to `max` non-empty (kind, level) totals. */
+enum {
+    DEC_PK_SMOOTH0 = 0, /* first smoothing step from zero                     */
+    DEC_PK_SMOOTH,      /* smoothing step                                      */
+    DEC_PK_RESIDUAL,    /* residual inside the cycle                           */
+    DEC_PK_RESTRICT,    /* restriction (launched on the fine level)            */
+    DEC_PK_PROLONG,     /* interpolation and correction                        */
+    DEC_PK_COARSE,      /* coarsest-level dense solve                          */
+    DEC_PK_SPMV64,      /* outer FP64 operator apply with <p, Lp>              */
+    DEC_PK_UPDATE,      /* outer x, r update with ||r||                        */
+    DEC_PK_ZDOTS,       /* outer preconditioned-vector dot products            */
+    DEC_PK_PUPD,        /* outer search-direction update                       */
+    DEC_PK_MGRES,       /* standalone-MG residual with ||r||                   */
+    DEC_PK_ADD,         /* standalone-MG correction                            */
+    DEC_PK_AUX,         /* set-up kernels of a solve (gauge mean, initial residual) */
+    DEC_PK_COUNT
+};
+typedef struct dec_prof_entry {
+    int kind;          /* DEC_PK_*                                   */
+    int level;         /* hierarchy level of the launch              */
+    int64_t launches;  /* launches timed                             */
+    double total_ms;   /* summed event-to-event time                 */
+    int64_t rows;      /* vertices of that level (units per launch)  */
+} dec_prof_entry;
+int dec_mg_profile(dec_mg *mg, int enable);
+int dec_mg_profile_read(const dec_mg *mg, dec_prof_entry *out, int max, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEC_H */

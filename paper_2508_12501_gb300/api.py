@@ -1,0 +1,273 @@
+"""Python face of libdec: meshes, hierarchies, operator calls, solves, autograd.
+
+Everything here is argument marshalling around the C ABI of include/dec.h:
+shapes, dtypes, devices and the current CUDA stream are checked and passed
+through; every arithmetic step runs inside libdec's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import check, lib
+
+SMOOTHERS = {"jacobi": L.DEC_SMOOTH_JACOBI, "chebyshev": L.DEC_SMOOTH_CHEBYSHEV, "mcgs": L.DEC_SMOOTH_MCGS}
+SOLVERS = {"mg": L.DEC_SOLVER_MG, "mgpcg": L.DEC_SOLVER_MGPCG, "cg": L.DEC_SOLVER_CG}
+MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED}
+BCS = {"dirichlet": L.DEC_BC_DIRICHLET, "gauge": L.DEC_BC_GAUGE}
+TABLES = {"verts": L.DEC_TABLE_VERTS, "tris": L.DEC_TABLE_TRIS, "edges": L.DEC_TABLE_EDGES,
+          "star0": L.DEC_TABLE_STAR0, "star1": L.DEC_TABLE_STAR1, "free": L.DEC_TABLE_FREE,
+          "parents": L.DEC_TABLE_PARENTS, "colors": L.DEC_TABLE_COLORS}
+
+
+def _np_ptr(a):
+    return C.c_void_p(a.ctypes.data)
+
+
+class Mesh:
+    """Host mesh (dec_mesh_*): validated triangles and canonical edges."""
+
+    def __init__(self, verts=None, tris=None, _handle=None):
+        if _handle is not None:
+            self._h = _handle
+        else:
+            v = np.ascontiguousarray(verts, dtype=np.float64)
+            t = np.ascontiguousarray(tris, dtype=np.int32)
+            if v.ndim != 2 or t.ndim != 2 or t.shape[1] != 3:
+                raise ValueError("verts must be [nv, dim], tris [nt, 3]")
+            h = C.c_void_p()
+            check(lib.dec_mesh_create(_np_ptr(v), v.shape[0], v.shape[1], _np_ptr(t), t.shape[0], C.byref(h)),
+                  "dec_mesh_create")
+            self._h = h
+        nv, ne, nt, dim = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int()
+        check(lib.dec_mesh_sizes(self._h, C.byref(nv), C.byref(ne), C.byref(nt), C.byref(dim)), "dec_mesh_sizes")
+        self.nv, self.ne, self.nt, self.dim = nv.value, ne.value, nt.value, dim.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.dec_mesh_destroy(h)
+            self._h = None
+
+    def refine(self, nsub, sphere=False):
+        h = C.c_void_p()
+        check(lib.dec_mesh_refine(self._h, int(nsub), L.DEC_SPHERE_PROJECT if sphere else 0, C.byref(h)),
+              "dec_mesh_refine")
+        return Mesh(_handle=h)
+
+    def table(self, what):
+        n = {"verts": self.nv * self.dim, "tris": self.nt * 3, "edges": self.ne * 2,
+             "star0": self.nv, "star1": self.ne}[what]
+        dt = np.float64 if what in ("verts", "star0", "star1") else np.int32
+        out = np.empty(n, dtype=dt)
+        check(lib.dec_mesh_copy_table(self._h, TABLES[what], _np_ptr(out)), "dec_mesh_copy_table")
+        if what == "verts":
+            return out.reshape(self.nv, self.dim)
+        if what in ("tris", "edges"):
+            return out.reshape(-1, 3 if what == "tris" else 2)
+        return out
+
+
+@dataclass
+class SolveStats:
+    iters: int
+    rel_res: float
+    rel_res0: float
+    status: int
+    launches: int = 0
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Hierarchy:
+    """A multigrid hierarchy on the current CUDA device (dec_mg_*)."""
+
+    def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
+                 nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
+                 host_only=False):
+        if not isinstance(mesh, Mesh):
+            raise TypeError("mesh must be a Mesh")
+        o = L.dec_mg_opts()
+        lib.dec_mg_default_opts(C.byref(o))
+        o.smoother = SMOOTHERS[smoother]
+        o.nu1, o.nu2, o.omega = nu1, nu2, omega
+        o.cheby_lo, o.cheby_hi = cheby_lo, cheby_hi
+        o.power_iters, o.gamma = power_iters, gamma
+        flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0)
+        scale = None
+        if star1_scale is not None:
+            scale = np.ascontiguousarray(star1_scale, dtype=np.float64)
+        h = C.c_void_p()
+        self.device = None
+        if not host_only:
+            torch = _torch()
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        check(lib.dec_mg_build(mesh._h, int(nsub), int(nlevels), BCS[bc], flags,
+                               _np_ptr(scale) if scale is not None else None, C.byref(o), C.byref(h)),
+              "dec_mg_build")
+        self._h = h
+        self.bc = bc
+        self.host_only = host_only
+        info = L.dec_mg_info_t()
+        check(lib.dec_mg_info(self._h, C.byref(info)), "dec_mg_info")
+        self.nlevels = info.nlevels
+        self.nv = [info.nv[i] for i in range(self.nlevels)]
+        self.ne = [info.ne[i] for i in range(self.nlevels)]
+        self.nt = [info.nt[i] for i in range(self.nlevels)]
+        self.ell_width = [info.ell_width[i] for i in range(self.nlevels)]
+        self.lmax = [info.lmax[i] for i in range(self.nlevels)]
+        self.ncolors = [info.ncolors[i] for i in range(self.nlevels)]
+        self.dim = info.dim
+        self.device_bytes = info.device_bytes
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.dec_mg_destroy(h)
+            self._h = None
+
+    @property
+    def n(self):
+        return self.nv[-1]
+
+    def table(self, level, what):
+        level = level % self.nlevels
+        nv, ne, nt = self.nv[level], self.ne[level], self.nt[level]
+        n = {"verts": nv * self.dim, "tris": nt * 3, "edges": ne * 2, "parents": ne * 2, "star0": nv,
+             "star1": ne, "free": nv, "colors": nv}[what]
+        dt = np.float64 if what in ("verts", "star0", "star1") else np.int32
+        out = np.empty(n, dtype=dt)
+        check(lib.dec_mg_copy_table(self._h, level, TABLES[what], _np_ptr(out)), "dec_mg_copy_table")
+        if what == "verts":
+            return out.reshape(nv, self.dim)
+        if what == "tris":
+            return out.reshape(nt, 3)
+        if what in ("edges", "parents"):
+            return out.reshape(ne, 2)
+        return out
+
+    # ---- device calls ----------------------------------------------------
+    def _vec(self, t, n, dtypes, name):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} must live on {self.device}")
+        if t.dtype not in dtypes:
+            raise TypeError(f"{name} has dtype {t.dtype}")
+        if t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with {n} entries")
+        return C.c_void_p(t.data_ptr())
+
+    def _stream(self):
+        return C.c_void_p(_torch().cuda.current_stream(self.device).cuda_stream)
+
+    def laplace0_apply(self, x, level=-1, out=None):
+        torch = _torch()
+        level = level % self.nlevels
+        n = self.nv[level]
+        prec = L.DEC_F64 if x.dtype == torch.float64 else L.DEC_F32
+        px = self._vec(x, n, (torch.float64, torch.float32), "x")
+        y = torch.empty_like(x) if out is None else out
+        py = self._vec(y, n, (x.dtype,), "out")
+        check(lib.dec_laplace0_apply(self._h, level, px, py, 1, prec, self._stream()), "dec_laplace0_apply")
+        return y
+
+    def residual(self, b, x, level=-1, out=None):
+        torch = _torch()
+        level = level % self.nlevels
+        n = self.nv[level]
+        prec = L.DEC_F64 if x.dtype == torch.float64 else L.DEC_F32
+        pb = self._vec(b, n, (x.dtype,), "b")
+        px = self._vec(x, n, (torch.float64, torch.float32), "x")
+        r = torch.empty_like(x) if out is None else out
+        pr = self._vec(r, n, (x.dtype,), "out")
+        check(lib.dec_residual(self._h, level, pb, px, pr, 1, prec, self._stream()), "dec_residual")
+        return r
+
+    def vcycle(self, b, x):
+        """x <- x + C(b - L x) in place (one multigrid cycle, precision of x)."""
+        torch = _torch()
+        prec = L.DEC_F64 if x.dtype == torch.float64 else L.DEC_F32
+        pb = self._vec(b, self.n, (x.dtype,), "b")
+        px = self._vec(x, self.n, (torch.float64, torch.float32), "x")
+        check(lib.dec_mg_vcycle(self._h, pb, px, 1, prec, self._stream()), "dec_mg_vcycle")
+        return x
+
+    def _solve_opts(self, solver, mode, tol, maxit, warm_start, check_every):
+        o = L.dec_solve_opts()
+        lib.dec_solve_default_opts(C.byref(o))
+        o.solver = SOLVERS[solver]
+        o.mode = MODES[mode]
+        o.tol = float(tol)
+        o.maxit = int(maxit)
+        o.warm_start = 1 if warm_start else 0
+        o.check_every = int(check_every)
+        return o
+
+    def solve(self, b, x=None, solver="mgpcg", mode="mixed", tol=1e-8, maxit=100, warm_start=False,
+              check_every=1, raise_on_fail=True):
+        """Solve L x = b on the finest level; returns (x, SolveStats).
+
+        b may be a CUDA or a CPU float64 tensor; a CPU input is copied to the
+        device and the result copied back (the host-buffer entry point).
+        """
+        torch = _torch()
+        host = b.device.type == "cpu"
+        if host:
+            b = b.to(self.device, non_blocking=True)
+            if x is not None:
+                x = x.to(self.device, non_blocking=True)
+        if x is None:
+            x = torch.empty_like(b)
+            warm_start = False
+        pb = self._vec(b, self.n, (torch.float64,), "b")
+        px = self._vec(x, self.n, (torch.float64,), "x")
+        o = self._solve_opts(solver, mode, tol, maxit, warm_start, check_every)
+        st = L.dec_stats()
+        rc = lib.dec_solve(self._h, pb, px, 1, C.byref(o), C.byref(st), self._stream())
+        if rc not in (L.DEC_OK, L.DEC_ERR_NOT_CONVERGED) or (raise_on_fail and rc != L.DEC_OK):
+            check(rc, "dec_solve")
+        stats = SolveStats(st.iters, st.rel_res, st.rel_res0, rc, st.launches)
+        if host:
+            x = x.cpu()
+        return x, stats
+
+    def solve_backward(self, u, grad_u, want_star1=True, solver="mgpcg", mode="mixed", tol=1e-8, maxit=100,
+                       check_every=1):
+        """Adjoint of x = L^-1 b: returns (dJ/db, dJ/d*1 or None, SolveStats)."""
+        torch = _torch()
+        pu = self._vec(u, self.n, (torch.float64,), "u")
+        pg = self._vec(grad_u, self.n, (torch.float64,), "grad_u")
+        gb = torch.empty_like(u)
+        gs = torch.empty(self.ne[-1], dtype=torch.float64, device=self.device) if want_star1 else None
+        o = self._solve_opts(solver, mode, tol, maxit, False, check_every)
+        st = L.dec_stats()
+        rc = lib.dec_solve_backward(self._h, pu, pg, C.c_void_p(gb.data_ptr()),
+                                    C.c_void_p(gs.data_ptr()) if gs is not None else None,
+                                    C.byref(o), C.byref(st), self._stream())
+        check(rc, "dec_solve_backward")
+        return gb, gs, SolveStats(st.iters, st.rel_res, st.rel_res0, rc, st.launches)
+
+    def profile(self, enable=1):
+        """Live CUDA-event timing of the solver's kernels (1: finest level, 2: all levels, 0: off)."""
+        check(lib.dec_mg_profile(self._h, int(enable)), "dec_mg_profile")
+
+    def profile_read(self):
+        """List of dicts {kind, level, launches, total_ms, rows} accumulated since profile() was enabled."""
+        buf = (L.dec_prof_entry * 256)()
+        cnt = C.c_int()
+        check(lib.dec_mg_profile_read(self._h, buf, 256, C.byref(cnt)), "dec_mg_profile_read")
+        return [dict(kind=L.PROF_KINDS[e.kind], level=e.level, launches=e.launches, total_ms=e.total_ms,
+                     rows=e.rows) for e in buf[: cnt.value]]
+
+    def set_star1(self, star1):
+        torch = _torch()
+        p = self._vec(star1, self.ne[-1], (torch.float64,), "star1")
+        check(lib.dec_mg_set_star1(self._h, p, self._stream()), "dec_mg_set_star1")

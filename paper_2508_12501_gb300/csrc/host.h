@@ -1,0 +1,89 @@
+// Internal host-side data structures of libdec (mesh, hierarchy levels).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dec.h"
+
+namespace decimpl {
+
+// Thread-local error message set by every failing entry point.
+void set_error(const std::string &msg);
+
+struct Status {
+    int code = DEC_OK;
+    std::string msg;
+    static Status ok() { return Status(); }
+    static Status fail(int c, const std::string &m) {
+        Status s;
+        s.code = c;
+        s.msg = m;
+        return s;
+    }
+    bool good() const { return code == DEC_OK; }
+};
+
+// Embedded 2-simplicial complex: points, triangles, canonical edges.
+struct HostMesh {
+    int dim = 2;
+    int64_t nv = 0, ne = 0, nt = 0;
+    std::vector<double> verts;      // [nv * dim]
+    std::vector<int32_t> tris;      // [nt * 3]
+    std::vector<int32_t> edges;     // [ne * 2] (lo, hi), lexicographic
+    std::vector<int32_t> tri_edges; // [nt * 3] edge of (v0v1, v1v2, v2v0)
+};
+
+// Validates (Sec. 2.1 definition, plus at most two triangles per edge) and
+// enumerates the canonical edges.
+Status build_mesh(std::vector<double> verts, int dim, std::vector<int32_t> tris, HostMesh &out);
+
+// One 1->4 midpoint subdivision; `parents` of fine vertex nc + e is coarse edge e.
+Status subdivide(const HostMesh &coarse, bool sphere, HostMesh &fine);
+
+// Circumcentric diagonal Hodge stars (cotangent formulas).
+void hodge_stars(const HostMesh &m, std::vector<double> &star0, std::vector<double> &star1);
+
+// Vertices on edges that lie in exactly one triangle.
+std::vector<uint8_t> boundary_vertices(const HostMesh &m);
+
+// One level of the hierarchy, host copy.
+struct HostLevel {
+    HostMesh mesh;
+    std::vector<double> star0, star1;
+    std::vector<uint8_t> free_;      // 1 = unknown
+    int K = 0;                       // ELL width (max valence)
+    std::vector<int32_t> col;        // [K * nv] slot-major; padding: col = row
+    std::vector<int32_t> slot_edge;  // [K * nv] edge id of each slot, -1 = padding
+    std::vector<double> w;           // [K * nv] *1_e / *0_v, 0 on Dirichlet rows
+    double lmax = 0.0;
+    std::vector<int32_t> colors;
+    int ncolors = 0;
+};
+
+}  // namespace decimpl
+
+namespace decimpl {
+
+// The whole hierarchy on the host.  levels[0] is the coarsest level used.
+struct HostHierarchy {
+    int bc = DEC_BC_DIRICHLET;
+    bool sphere = false;
+    dec_mg_opts opts{};
+    std::vector<HostLevel> levels;
+    std::vector<std::vector<int32_t>> parents;  // parents[l]: level-l edges = parents of level l+1 midpoints
+    std::vector<double> G;                      // [n0 * n0] coarse solution operator, row-major
+};
+
+Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere,
+                       const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H);
+
+// Rebuild ELL weights of one level from its (possibly new) star1.
+Status level_weights(HostLevel &L, int bc);
+
+// lambda_max(D^-1 L) by power iteration on the free vertices.
+double power_lmax(const HostLevel &L, int iters);
+
+}  // namespace decimpl

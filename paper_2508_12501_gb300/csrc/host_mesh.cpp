@@ -1,0 +1,189 @@
+// Host-side mesh construction: validation, canonical edges, 1->4 midpoint
+// subdivision and the circumcentric Hodge stars.
+//
+// Sec. 2.1 defines the embedded 2-simplicial complex (face maps E->V, T->E,
+// no duplicate simplices, every vertex and edge in a triangle); Sec. 2.2.1
+// describes binary (1->4) subdivision; Sec. 3.1.1 defines *0 (dual-cell
+// areas) and *1 (dual/primal length ratio).  Edges are (lo, hi) with lo < hi
+// in lexicographic order, found by a counting sort on lo.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <numeric>
+
+#include "host.h"
+
+namespace decimpl {
+
+namespace {
+
+struct HalfEdge {
+    int32_t hi;
+    int32_t h;  // 3 * triangle + k
+};
+
+}  // namespace
+
+Status build_mesh(std::vector<double> verts, int dim, std::vector<int32_t> tris, HostMesh &out) {
+    if (dim != 2 && dim != 3) return Status::fail(DEC_ERR_ARG, "dim must be 2 or 3");
+    if (verts.size() % dim != 0 || tris.size() % 3 != 0) return Status::fail(DEC_ERR_ARG, "array sizes");
+    const int64_t nv = (int64_t)verts.size() / dim;
+    const int64_t nt = (int64_t)tris.size() / 3;
+    if (nv < 1 || nt < 1) return Status::fail(DEC_ERR_ARG, "empty mesh");
+    if (nv >= (int64_t)1 << 31 || 3 * nt >= (int64_t)1 << 31) return Status::fail(DEC_ERR_ARG, "mesh too large");
+    for (int64_t i = 0; i < 3 * nt; ++i)
+        if (tris[i] < 0 || tris[i] >= nv) return Status::fail(DEC_ERR_MESH, "triangle vertex index out of range");
+    for (int64_t t = 0; t < nt; ++t) {
+        int32_t a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        if (a == b || b == c || a == c) return Status::fail(DEC_ERR_MESH, "a triangle repeats a vertex");
+    }
+    {  // every vertex in some triangle
+        std::vector<uint8_t> used(nv, 0);
+        for (int64_t i = 0; i < 3 * nt; ++i) used[tris[i]] = 1;
+        for (int64_t v = 0; v < nv; ++v)
+            if (!used[v]) return Status::fail(DEC_ERR_MESH, "a vertex lies in no triangle");
+    }
+    {  // no two triangles on the same vertex set: bucket sorted triples by their smallest vertex
+        std::vector<int64_t> cnt(nv + 1, 0);
+        std::vector<std::array<int32_t, 3>> key(nt);
+        for (int64_t t = 0; t < nt; ++t) {
+            std::array<int32_t, 3> k = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+            std::sort(k.begin(), k.end());
+            key[t] = k;
+            cnt[k[0] + 1]++;
+        }
+        std::partial_sum(cnt.begin(), cnt.end(), cnt.begin());
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        std::vector<std::pair<int32_t, int32_t>> bucket(nt);
+        for (int64_t t = 0; t < nt; ++t) bucket[pos[key[t][0]]++] = {key[t][1], key[t][2]};
+        for (int64_t v = 0; v < nv; ++v) {
+            auto b = bucket.begin() + cnt[v], e = bucket.begin() + cnt[v + 1];
+            std::sort(b, e);
+            if (std::adjacent_find(b, e) != e) return Status::fail(DEC_ERR_MESH, "two triangles share the same vertex set");
+        }
+    }
+    // half-edges bucketed by their low vertex, then sorted by (hi, h) inside each bucket
+    const int64_t nh = 3 * nt;
+    std::vector<int64_t> off(nv + 1, 0);
+    for (int64_t h = 0; h < nh; ++h) {
+        int32_t s = tris[h], d = tris[(h / 3) * 3 + (h % 3 + 1) % 3];
+        off[std::min(s, d) + 1]++;
+    }
+    std::partial_sum(off.begin(), off.end(), off.begin());
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    std::vector<HalfEdge> he(nh);
+    for (int64_t h = 0; h < nh; ++h) {
+        int32_t s = tris[h], d = tris[(h / 3) * 3 + (h % 3 + 1) % 3];
+        he[fill[std::min(s, d)]++] = HalfEdge{std::max(s, d), (int32_t)h};
+    }
+    out.tri_edges.assign(nh, -1);
+    out.edges.clear();
+    out.edges.reserve(nh);  // upper bound 2 * ne <= 2 * nh
+    int32_t ne = 0;
+    for (int64_t v = 0; v < nv; ++v) {
+        auto b = he.begin() + off[v], e = he.begin() + off[v + 1];
+        std::sort(b, e, [](const HalfEdge &x, const HalfEdge &y) { return x.hi != y.hi ? x.hi < y.hi : x.h < y.h; });
+        for (auto it = b; it != e;) {
+            auto jt = it;
+            while (jt != e && jt->hi == it->hi) ++jt;
+            if (jt - it > 2) return Status::fail(DEC_ERR_MESH, "an edge lies in more than two triangles");
+            for (auto k = it; k != jt; ++k) out.tri_edges[k->h] = ne;
+            out.edges.push_back((int32_t)v);
+            out.edges.push_back(it->hi);
+            ++ne;
+            it = jt;
+        }
+    }
+    out.dim = dim;
+    out.nv = nv;
+    out.nt = nt;
+    out.ne = ne;
+    out.verts = std::move(verts);
+    out.tris = std::move(tris);
+    return Status::ok();
+}
+
+Status subdivide(const HostMesh &c, bool sphere, HostMesh &f) {
+    if (sphere && c.dim != 3) return Status::fail(DEC_ERR_ARG, "sphere projection needs 3-D vertices");
+    const int dim = c.dim;
+    const int64_t nc = c.nv, E = c.ne, T = c.nt;
+    if (nc + E >= (int64_t)1 << 31 || 12 * T >= (int64_t)1 << 31) return Status::fail(DEC_ERR_ARG, "refined mesh too large");
+    std::vector<double> fv((nc + E) * dim);
+    std::copy(c.verts.begin(), c.verts.end(), fv.begin());
+    for (int64_t e = 0; e < E; ++e) {
+        const double *pa = &c.verts[(int64_t)c.edges[2 * e] * dim];
+        const double *pb = &c.verts[(int64_t)c.edges[2 * e + 1] * dim];
+        double m[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) m[d] = (pa[d] + pb[d]) * 0.5;
+        if (sphere) {
+            double s = m[0] * m[0] + m[1] * m[1];
+            s = s + m[2] * m[2];
+            double nrm = std::sqrt(s);
+            for (int d = 0; d < 3; ++d) m[d] = m[d] / nrm;
+        }
+        for (int d = 0; d < dim; ++d) fv[(nc + e) * dim + d] = m[d];
+    }
+    std::vector<int32_t> ft(12 * T);
+    for (int64_t t = 0; t < T; ++t) {
+        int32_t a = c.tris[3 * t], b = c.tris[3 * t + 1], cc = c.tris[3 * t + 2];
+        int32_t mab = (int32_t)(nc + c.tri_edges[3 * t]);
+        int32_t mbc = (int32_t)(nc + c.tri_edges[3 * t + 1]);
+        int32_t mca = (int32_t)(nc + c.tri_edges[3 * t + 2]);
+        int32_t *o = &ft[12 * t];
+        o[0] = a;   o[1] = mab;  o[2] = mca;
+        o[3] = mab; o[4] = b;    o[5] = mbc;
+        o[6] = mca; o[7] = mbc;  o[8] = cc;
+        o[9] = mab; o[10] = mbc; o[11] = mca;
+    }
+    return build_mesh(std::move(fv), dim, std::move(ft), f);
+}
+
+void hodge_stars(const HostMesh &m, std::vector<double> &star0, std::vector<double> &star1) {
+    star0.assign(m.nv, 0.0);
+    star1.assign(m.ne, 0.0);
+    const int dim = m.dim;
+    for (int64_t t = 0; t < m.nt; ++t) {
+        double P[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int k = 0; k < 3; ++k)
+            for (int d = 0; d < dim; ++d) P[k][d] = m.verts[(int64_t)m.tris[3 * t + k] * dim + d];
+        for (int k = 0; k < 3; ++k) {
+            // edge k joins corners k and k+1; the opposite corner is k+2
+            const double *A = P[k], *B = P[(k + 1) % 3], *O = P[(k + 2) % 3];
+            double u[3], w[3];
+            for (int d = 0; d < 3; ++d) {
+                u[d] = A[d] - O[d];
+                w[d] = B[d] - O[d];
+            }
+            double dot = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+            double cr;
+            if (dim == 2) {
+                cr = std::fabs(u[0] * w[1] - u[1] * w[0]);
+            } else {
+                double c0 = u[1] * w[2] - u[2] * w[1];
+                double c1 = u[2] * w[0] - u[0] * w[2];
+                double c2 = u[0] * w[1] - u[1] * w[0];
+                cr = std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+            }
+            double cot = dot / cr;
+            double l2 = 0.0;
+            for (int d = 0; d < 3; ++d) l2 += (B[d] - A[d]) * (B[d] - A[d]);
+            star1[m.tri_edges[3 * t + k]] += 0.5 * cot;
+            double c = l2 * cot / 8.0;
+            star0[m.tris[3 * t + k]] += c;
+            star0[m.tris[3 * t + (k + 1) % 3]] += c;
+        }
+    }
+}
+
+std::vector<uint8_t> boundary_vertices(const HostMesh &m) {
+    std::vector<uint8_t> cnt(m.ne, 0), bv(m.nv, 0);
+    for (int64_t i = 0; i < 3 * m.nt; ++i) cnt[m.tri_edges[i]]++;
+    for (int64_t e = 0; e < m.ne; ++e)
+        if (cnt[e] == 1) {
+            bv[m.edges[2 * e]] = 1;
+            bv[m.edges[2 * e + 1]] = 1;
+        }
+    return bv;
+}
+
+}  // namespace decimpl

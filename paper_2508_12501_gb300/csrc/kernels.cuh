@@ -1,0 +1,477 @@
+// sm_103a kernels of the DEC multigrid hot path.
+//
+// Operator rows are stored ELL-style, slot-major: slot k of row i is at
+// [k * n + i] so a warp's loads of one slot are contiguous.  A row computes
+//   s = sum_k w_k (x_i - x_col(k)) = (L x)_i,   d = sum_k w_k = L_ii,
+// with w_k = *1_e / *0_i (Sec. 3.1.1, Eq. hodge0-laplacian as -Delta_0).
+// Dirichlet rows have all weights 0, hence d == 0, which every kernel uses
+// as the "fixed vertex" mask.  Padding slots point at the row with weight 0.
+//
+// Every kernel takes `skip`: when non-null and *skip != 0 the kernel returns
+// at once (used to retire queued iterations after convergence).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace decdev {
+
+constexpr int kThreads = 256;
+constexpr int kMaxRedBlocks = 1024;  // partial-sum slots per reduction
+constexpr int kHist = 1024;          // residual history entries
+
+// Scalars of the outer iteration, resident in device memory.
+struct Scal {
+    double rz;          // <r, z> (*0 inner product)
+    double alpha, beta;
+    double c;           // gauge shift of the current preconditioned vector
+    double bnorm2, rnorm2, rel, rel0;
+    double tol;
+    double star0_sum;   // sum of *0 over free vertices
+    double mean;        // result of the last k_mean
+    int iter, maxit, done, status;  // status: 0 ok, 1 non-finite
+    double hist[kHist];
+};
+
+__device__ __forceinline__ bool skipped(const int *skip) { return skip != nullptr && *skip != 0; }
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// (L x)_i and L_ii for one row.
+template <typename T, int KT>
+__device__ __forceinline__ void row_apply(int i, int n, int K, const int32_t *__restrict__ col,
+                                          const T *__restrict__ w, const T *__restrict__ x, T &s, T &d) {
+    const int Kk = KT > 0 ? KT : K;
+    const T xi = ldg(x + i);
+    s = T(0);
+    d = T(0);
+#pragma unroll
+    for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+        if (KT == 0 && k >= Kk) break;
+        const size_t o = (size_t)k * n + i;
+        const int c = ldg(col + o);
+        const T wk = ldg(w + o);
+        s = fma(wk, xi - ldg(x + c), s);
+        d += wk;
+    }
+}
+
+#define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// y = L x
+template <typename T, int KT>
+__global__ void __launch_bounds__(kThreads) k_apply(int n, int K, const int32_t *__restrict__ col,
+                                                   const T *__restrict__ w, const T *__restrict__ x,
+                                                   T *__restrict__ y, const int *skip) {
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) {
+        T s, d;
+        row_apply<T, KT>(i, n, K, col, w, x, s, d);
+        y[i] = s;
+    }
+}
+
+// r = b - L x on free rows, 0 on fixed rows
+template <typename T, int KT>
+__global__ void __launch_bounds__(kThreads) k_residual(int n, int K, const int32_t *__restrict__ col,
+                                                      const T *__restrict__ w, const T *__restrict__ b,
+                                                      const T *__restrict__ x, T *__restrict__ r,
+                                                      const int *skip) {
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) {
+        T s, d;
+        row_apply<T, KT>(i, n, K, col, w, x, s, d);
+        r[i] = d != T(0) ? ldg(b + i) - s : T(0);
+    }
+}
+
+// One smoothing step from a nonzero iterate:
+//   q = D^-1 (b - L x);  delta = c * d_in + e * q;  x_out = x_in + delta;  d_out = delta.
+// Damped Jacobi: DIN = DOUT = false, e = omega.  Chebyshev: the first step of
+// a smoothing call has DIN = false, later steps DIN = true; DOUT is false on
+// the last step (its direction is never read).
+template <typename T, int KT, bool DIN, bool DOUT>
+__global__ void __launch_bounds__(kThreads) k_smooth(int n, int K, const int32_t *__restrict__ col,
+                                                    const T *__restrict__ w, const T *__restrict__ b,
+                                                    const T *__restrict__ x_in, const T *__restrict__ d_in,
+                                                    T *__restrict__ x_out, T *__restrict__ d_out, T c, T e,
+                                                    const int *skip) {
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) {
+        T s, d;
+        row_apply<T, KT>(i, n, K, col, w, x_in, s, d);
+        T q = d != T(0) ? (ldg(b + i) - s) / d : T(0);
+        T delta = DIN ? fma(c, ldg(d_in + i), e * q) : e * q;
+        x_out[i] = ldg(x_in + i) + delta;
+        if (DOUT) d_out[i] = delta;
+    }
+}
+
+// First smoothing step from x = 0: x_out = e * D^-1 b (and d_out = x_out).
+template <typename T, int KT, bool DOUT>
+__global__ void __launch_bounds__(kThreads) k_smooth0(int n, int K, const T *__restrict__ w,
+                                                     const T *__restrict__ b, T *__restrict__ x_out,
+                                                     T *__restrict__ d_out, T e, const int *skip) {
+    if (skipped(skip)) return;
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(i, n) {
+        T d = T(0);
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            d += ldg(w + (size_t)k * n + i);
+        }
+        T v = d != T(0) ? e * (ldg(b + i) / d) : T(0);
+        x_out[i] = v;
+        if (DOUT) d_out[i] = v;
+    }
+}
+
+// x += e (same precision)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_axpy1(int n, const T *__restrict__ e, T *__restrict__ x,
+                                                   const int *skip) {
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) x[i] += ldg(e + i);
+}
+
+// Restriction by the row-normalized subdivision matrix (Sec. 2.2.1):
+//   b_c[c] = (r_f[c] + 1/2 sum_{midpoints m adjacent to c} r_f[m]) / (1 + deg(c)/2).
+// The fine neighbours of a coarse vertex are exactly the midpoints of its
+// coarse edges, so the fine ELL row c lists them (padding: col == c).
+template <typename T, int KT>
+__global__ void __launch_bounds__(kThreads) k_restrict(int nc, int nf, int Kf, const int32_t *__restrict__ colf,
+                                                      const T *__restrict__ rf, T *__restrict__ bc,
+                                                      const int *skip) {
+    if (skipped(skip)) return;
+    const int Kk = KT > 0 ? KT : Kf;
+    GRID_STRIDE(c, nc) {
+        T acc = T(0);
+        int deg = 0;
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const int j = ldg(colf + (size_t)k * nf + c);
+            if (j != c) {
+                acc += ldg(rf + j);
+                ++deg;
+            }
+        }
+        bc[c] = (ldg(rf + c) + T(0.5) * acc) / (T(1) + T(0.5) * T(deg));
+    }
+}
+
+// Interpolation by the subdivision matrix and correction (Sec. 2.2.1):
+//   x_f[v] += e_c[v] for coarse ids, x_f[nc + m] += (e_c[a] + e_c[b]) / 2 for the midpoint of (a, b).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong(int nc, int nf, const int2 *__restrict__ par,
+                                                     const T *__restrict__ ec, T *__restrict__ xf,
+                                                     const int *skip) {
+    if (skipped(skip)) return;
+    GRID_STRIDE(v, nf) {
+        T add;
+        if (v < nc) {
+            add = ldg(ec + v);
+        } else {
+            const int2 p = ldg(par + (v - nc));
+            add = T(0.5) * (ldg(ec + p.x) + ldg(ec + p.y));
+        }
+        xf[v] += add;
+    }
+}
+
+// Coarsest level: x = G b with the dense precomputed solution operator, one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_coarse(int n0, const T *__restrict__ G, const T *__restrict__ b,
+                                                    T *__restrict__ x, const int *skip) {
+    if (skipped(skip)) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp; r < n0; r += nwarps) {
+        T acc = T(0);
+        for (int j = lane; j < n0; j += 32) acc = fma(ldg(G + (size_t)r * n0 + j), ldg(b + j), acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) x[r] = acc;
+    }
+}
+
+template <typename TD, typename TS>
+__global__ void __launch_bounds__(kThreads) k_cast(int n, const TS *__restrict__ src, TD *__restrict__ dst,
+                                                  const int *skip) {
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) dst[i] = (TD)ldg(src + i);
+}
+
+// x += (double) e
+template <typename TE>
+__global__ void __launch_bounds__(kThreads) k_add(int n, const TE *__restrict__ e, double *__restrict__ x,
+                                                 const int *skip) {
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) x[i] += (double)ldg(e + i);
+}
+
+// ---------------------------------------------------------------------------
+// deterministic block reductions: every block writes its partial sums, the
+// last block to finish adds them in a fixed order and runs the epilogue.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Returns true in every thread of the last block; tot[] then holds the
+// grid-wide sums.  Requires blockDim.x == kThreads and gridDim.x <= kMaxRedBlocks.
+template <int NS>
+__device__ bool grid_reduce(double (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
+    __shared__ double sh[NS][kThreads / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        double x = warp_sum(v[s]);
+        if (lane == 0) sh[s][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            double x = lane < kThreads / 32 ? sh[s][lane] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0) partials[s * kMaxRedBlocks + blockIdx.x] = x;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += __ldcg(partials + s * kMaxRedBlocks + b);
+        acc = warp_sum(acc);
+        __syncthreads();
+        if (lane == 0) sh[s][warp] = acc;
+        __syncthreads();
+        double t = 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) t += sh[s][k];
+        tot[s] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+__device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
+    S->rnorm2 = rnorm2;
+    const bool bad = !isfinite(rnorm2) || !isfinite(S->bnorm2);
+    double rel = bad ? (double)NAN : (S->bnorm2 > 0.0 ? sqrt(rnorm2 / S->bnorm2) : 0.0);
+    S->rel = rel;
+    if (S->iter < kHist) S->hist[S->iter] = rel;
+    if (bad) {
+        S->status = 1;
+        S->done = 1;
+    } else if (rel <= S->tol || S->iter >= S->maxit) {
+        S->done = 1;
+    }
+}
+
+// mean = sum(*0 v) / sum(*0) over free rows (mask: free != 0)
+__global__ void __launch_bounds__(kThreads) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+                                                  const double *__restrict__ v, double *partials, unsigned *counter,
+                                                  Scal *S, const int *skip) {
+    if (skipped(skip)) return;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) if (freev[i]) acc[0] += ldg(star0 + i) * ldg(v + i);
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] / S->star0_sum;
+}
+
+// v -= mean on free rows
+__global__ void __launch_bounds__(kThreads) k_shift(int n, const uint8_t *__restrict__ freev, double *__restrict__ v,
+                                                   const Scal *S, const int *skip) {
+    if (skipped(skip)) return;
+    const double m = S->mean;
+    GRID_STRIDE(i, n) v[i] = freev[i] ? v[i] - m : 0.0;
+}
+
+// Initial residual of the outer iteration: r = b - L x, ||r||^2, ||b||^2 (free rows);
+// also writes the cycle's input rv (cast) when rv != nullptr.
+template <int KT, typename TV>
+__global__ void __launch_bounds__(kThreads) k_outer_init(int n, int K, const int32_t *__restrict__ col,
+                                                        const double *__restrict__ w, const uint8_t *__restrict__ freev,
+                                                        const double *__restrict__ b, const double *__restrict__ x,
+                                                        double *__restrict__ r, TV *__restrict__ rv, double *partials,
+                                                        unsigned *counter, Scal *S) {
+    double acc[2] = {0.0, 0.0};
+    GRID_STRIDE(i, n) {
+        double s, d;
+        row_apply<double, KT>(i, n, K, col, w, x, s, d);
+        double bi = freev[i] ? ldg(b + i) : 0.0;
+        double ri = freev[i] ? bi - s : 0.0;
+        r[i] = ri;
+        if (rv) rv[i] = (TV)ri;
+        acc[0] += ri * ri;
+        acc[1] += bi * bi;
+    }
+    double tot[2];
+    if (grid_reduce<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->bnorm2 = tot[1];
+        S->iter = 0;
+        S->done = 0;
+        S->status = 0;
+        record_residual(S, tot[0]);
+        S->rel0 = S->rel;
+    }
+}
+
+// After a cycle produced z (type TZ): zn = (double) z; sums of *0 z, *0 r zn, *0 r zo, *0 r;
+// epilogue: gauge shift c, new <r,z>, Polak-Ribiere beta.
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+                                                       const TZ *__restrict__ z, double *__restrict__ zn,
+                                                       const double *__restrict__ r, const double *__restrict__ zo,
+                                                       int first, int gauge, double *partials, unsigned *counter,
+                                                       Scal *S, const int *skip) {
+    if (skipped(skip)) return;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    GRID_STRIDE(i, n) {
+        double zi = (double)ldg(z + i);
+        if ((void *)zn != (void *)z) zn[i] = zi;
+        if (freev[i]) {
+            double s0 = ldg(star0 + i), ri = ldg(r + i);
+            acc[0] += s0 * zi;
+            acc[1] += s0 * ri * zi;
+            acc[2] += first ? 0.0 : s0 * ri * ldg(zo + i);
+            acc[3] += s0 * ri;
+        }
+    }
+    double tot[4];
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        double c = gauge ? tot[0] / S->star0_sum : 0.0;
+        double rz_new = tot[1] - c * tot[3];
+        S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
+        S->rz = rz_new;
+        S->c = c;
+    }
+}
+
+// z = zn - c (free rows), p = z + beta p (p = z on the first pass), zo = z.
+__global__ void __launch_bounds__(kThreads) k_pcg_pupd(int n, const uint8_t *__restrict__ freev, const double *__restrict__ zn,
+                                                      double *__restrict__ zo, double *__restrict__ p, int first,
+                                                      const Scal *S, const int *skip) {
+    if (skipped(skip)) return;
+    const double c = S->c, beta = S->beta;
+    GRID_STRIDE(i, n) {
+        double zi = freev[i] ? ldg(zn + i) - c : 0.0;
+        zo[i] = zi;
+        p[i] = first ? zi : fma(beta, p[i], zi);
+    }
+}
+
+// q = L p (free rows), <p, q> -> alpha = <r,z> / <p,q>
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_pcg_spmv(int n, int K, const int32_t *__restrict__ col,
+                                                      const double *__restrict__ w, const double *__restrict__ star0,
+                                                      const uint8_t *__restrict__ freev, const double *__restrict__ p,
+                                                      double *__restrict__ q, double *partials, unsigned *counter,
+                                                      Scal *S, const int *skip) {
+    if (skipped(skip)) return;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) {
+        double s, d;
+        row_apply<double, KT>(i, n, K, col, w, p, s, d);
+        double qi = freev[i] ? s : 0.0;
+        q[i] = qi;
+        acc[0] += ldg(star0 + i) * ldg(p + i) * qi;
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
+}
+
+// x += alpha p, r -= alpha q, rv = (TV) r, ||r||^2 -> convergence test
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
+                                                        double *__restrict__ x, double *__restrict__ r, TV *__restrict__ rv,
+                                                        double *partials, unsigned *counter, Scal *S, const int *skip) {
+    if (skipped(skip)) return;
+    const double a = S->alpha;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) {
+        x[i] = fma(a, ldg(p + i), x[i]);
+        double ri = fma(-a, ldg(q + i), r[i]);
+        r[i] = ri;
+        if (rv) rv[i] = (TV)ri;
+        acc[0] += ri * ri;
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->iter += 1;
+        record_residual(S, tot[0]);
+    }
+}
+
+// Standalone MG / iterative refinement: x += e; r = b - L x; ||r||^2 -> convergence test.
+template <int KT, typename TV>
+__global__ void __launch_bounds__(kThreads) k_mg_residual(int n, int K, const int32_t *__restrict__ col,
+                                                         const double *__restrict__ w, const uint8_t *__restrict__ freev,
+                                                         const double *__restrict__ b, const double *__restrict__ x,
+                                                         double *__restrict__ r, TV *__restrict__ rv, double *partials,
+                                                         unsigned *counter, Scal *S, const int *skip) {
+    if (skipped(skip)) return;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) {
+        double s, d;
+        row_apply<double, KT>(i, n, K, col, w, x, s, d);
+        double ri = freev[i] ? ldg(b + i) - s : 0.0;
+        r[i] = ri;
+        if (rv) rv[i] = (TV)ri;
+        acc[0] += ri * ri;
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->iter += 1;
+        record_residual(S, tot[0]);
+    }
+}
+
+// Gradient with respect to the edge weights: g_e = -(d0 mu)_e (d0 u)_e.
+__global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const int2 *__restrict__ edges, const double *__restrict__ mu,
+                                                       const double *__restrict__ u, double *__restrict__ g) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ab = ldg(edges + e);
+        g[e] = -(ldg(mu + ab.y) - ldg(mu + ab.x)) * (ldg(u + ab.y) - ldg(u + ab.x));
+    }
+}
+
+// y = s0 .* x, or y = x ./ s0 (inverse != 0)
+__global__ void __launch_bounds__(kThreads) k_star0_scale(int n, const double *__restrict__ star0, const double *x,
+                                                         double *y, int inverse) {
+    GRID_STRIDE(i, n) y[i] = inverse ? x[i] / ldg(star0 + i) : x[i] * ldg(star0 + i);
+}
+
+// Finest-level weights from a new *1: w[slot] = *1[edge(slot)] / *0[row] on free rows.
+__global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const int32_t *__restrict__ slot_edge,
+                                                         const double *__restrict__ star1, const double *__restrict__ star0,
+                                                         const uint8_t *__restrict__ freev, double *__restrict__ w64,
+                                                         float *__restrict__ w32) {
+    GRID_STRIDE(i, n) {
+        const double s0 = ldg(star0 + i);
+        for (int k = 0; k < K; ++k) {
+            const size_t o = (size_t)k * n + i;
+            const int e = ldg(slot_edge + o);
+            double wk = (e >= 0 && freev[i]) ? ldg(star1 + e) / s0 : 0.0;
+            w64[o] = wk;
+            w32[o] = (float)wk;
+        }
+    }
+}
+
+}  // namespace decdev

@@ -1,0 +1,850 @@
+// Device orchestration of libdec: hierarchy upload, the multigrid cycle,
+// the outer FP64 iterations (standalone MG / iterative refinement, flexible
+// MG-preconditioned CG, plain CG), the adjoint solve, and their C ABI.
+//
+// The cycle follows Sec. 2.2.1 and Sec. 3.1.1: smoothing, residual,
+// restriction by the row-normalized transpose of the subdivision matrix,
+// recursion, interpolation by the subdivision matrix, smoothing; the
+// coarsest level applies a dense precomputed solution operator.  The outer
+// CG uses the *0 inner product in which L is self-adjoint and the
+// Polak-Ribiere beta because the V-cycle is only approximately symmetric.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "host.h"
+#include "kernels.cuh"
+
+using decimpl::Status;
+using namespace decdev;
+
+const decimpl::HostMesh *dec_mesh_host(const dec_mesh *m);
+
+namespace {
+
+struct DevLevel {
+    int n = 0, K = 0, nc = 0;  // nc: vertex count of the next coarser level
+    int64_t ne = 0;
+    int32_t *col = nullptr;
+    double *w64 = nullptr;
+    float *w32 = nullptr;
+    double *star0 = nullptr;
+    uint8_t *freev = nullptr;
+    int2 *par = nullptr;
+    float *x32[2] = {nullptr, nullptr}, *d32[2] = {nullptr, nullptr}, *r32 = nullptr, *b32 = nullptr;
+    double *x64[2] = {nullptr, nullptr}, *d64[2] = {nullptr, nullptr}, *r64 = nullptr, *b64 = nullptr;
+    // Chebyshev coefficients (c_k, e_k) of one smoothing call of nu1 and nu2 steps
+    std::vector<double> c_pre, e_pre, c_post, e_post;
+};
+
+template <typename T> struct P;
+template <> struct P<float> {
+    static float *x(DevLevel &L, int i) { return L.x32[i]; }
+    static float *d(DevLevel &L, int i) { return L.d32[i]; }
+    static float *r(DevLevel &L) { return L.r32; }
+    static float *b(DevLevel &L) { return L.b32; }
+    static const float *w(const DevLevel &L) { return L.w32; }
+};
+template <> struct P<double> {
+    static double *x(DevLevel &L, int i) { return L.x64[i]; }
+    static double *d(DevLevel &L, int i) { return L.d64[i]; }
+    static double *r(DevLevel &L) { return L.r64; }
+    static double *b(DevLevel &L) { return L.b64; }
+    static const double *w(const DevLevel &L) { return L.w64; }
+};
+
+template <typename F>
+void dispatch_k(int K, F &&f) {
+    if (K == 6)
+        f(std::integral_constant<int, 6>{});
+    else
+        f(std::integral_constant<int, 0>{});
+}
+
+}  // namespace
+
+struct dec_mg {
+    decimpl::HostHierarchy H;
+    int device = 0;
+    int nsm = 152;
+    std::vector<DevLevel> lv;
+    int n0 = 0;
+    double *G64 = nullptr;
+    float *G32 = nullptr;
+    // finest-level extras
+    int32_t *slot_edge = nullptr;
+    int2 *edges = nullptr;
+    // outer-iteration workspace (finest level, FP64)
+    double *ox = nullptr, *orr = nullptr, *op = nullptr, *oq = nullptr, *ozn = nullptr, *ozo = nullptr, *ob = nullptr;
+    double *tmp = nullptr;
+    double *partials = nullptr;
+    unsigned *counter = nullptr;
+    Scal *scal = nullptr;
+    Scal *scal_h = nullptr;  // pinned host mirror
+    double star0_sum = 0.0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graphs[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    bool host_only = false;
+    // live kernel timing (dec_mg_profile)
+    int64_t launches = 0;       // kernels enqueued outside graph capture
+    int64_t graph_kernels[3][2] = {};  // kernel nodes per captured iteration graph
+    int prof = 0;               // 0 off, 1 finest level, 2 all levels
+    bool prof_capture = false;  // true while a profiled iteration graph is being captured
+    bool capturing = false;     // true while any iteration graph is being captured
+    struct Slot {
+        cudaEvent_t a, b;
+        int kind, level;
+    };
+    std::vector<Slot> slots;
+    double prof_ms[DEC_PK_COUNT][16] = {};
+    int64_t prof_n[DEC_PK_COUNT][16] = {};
+};
+
+namespace {
+
+int fail(const Status &s) {
+    decimpl::set_error(s.msg);
+    return s.code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    decimpl::set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return DEC_ERR_CUDA;
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);       \
+    } while (0)
+
+template <typename T>
+int dalloc(dec_mg *mg, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        decimpl::set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? DEC_ERR_OOM : DEC_ERR_CUDA;
+    }
+    mg->allocs.push_back((void *)*p);
+    mg->bytes += count * sizeof(T);
+    return DEC_OK;
+}
+
+template <typename T>
+int upload(dec_mg *mg, T **p, const T *src, size_t count) {
+    int rc = dalloc(mg, p, count);
+    if (rc) return rc;
+    CK(cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return DEC_OK;
+}
+
+void clear_slots(dec_mg *mg);
+void drop_graphs(dec_mg *mg);
+
+void free_all(dec_mg *mg) {
+    drop_graphs(mg);
+    for (void *p : mg->allocs) cudaFree(p);
+    mg->allocs.clear();
+    if (mg->scal_h) cudaFreeHost(mg->scal_h);
+    if (mg->cap) cudaStreamDestroy(mg->cap);
+}
+
+// Brackets one kernel launch with an event pair while the profiled iteration
+// graph is being captured.
+struct ProfScope {
+    dec_mg *mg;
+    cudaStream_t s;
+    int idx = -1;
+    ProfScope(dec_mg *m, int kind, int level, cudaStream_t st) : mg(m), s(st) {
+        if (!mg->capturing) mg->launches += 1;
+        if (!mg->prof_capture) return;
+        if (mg->prof == 1 && level != (int)mg->lv.size() - 1) return;
+        dec_mg::Slot sl{nullptr, nullptr, kind, level};
+        if (cudaEventCreate(&sl.a) != cudaSuccess || cudaEventCreate(&sl.b) != cudaSuccess) return;
+        idx = (int)mg->slots.size();
+        mg->slots.push_back(sl);
+        cudaEventRecord(sl.a, s);
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecord(mg->slots[idx].b, s);
+    }
+};
+
+void clear_slots(dec_mg *mg) {
+    for (auto &sl : mg->slots) {
+        cudaEventDestroy(sl.a);
+        cudaEventDestroy(sl.b);
+    }
+    mg->slots.clear();
+}
+
+void drop_graphs(dec_mg *mg) {
+    for (auto &row : mg->graphs)
+        for (auto &g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    clear_slots(mg);
+}
+
+void accumulate_slots(dec_mg *mg) {
+    for (auto &sl : mg->slots) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sl.a, sl.b) == cudaSuccess) {
+            mg->prof_ms[sl.kind][sl.level] += ms;
+            mg->prof_n[sl.kind][sl.level] += 1;
+        }
+    }
+}
+
+inline int grid_for(const dec_mg *mg, int64_t n) {
+    int64_t g = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)mg->nsm * 8;
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+inline int red_grid(const dec_mg *mg, int64_t n) {
+    int64_t g = (n + kThreads - 1) / kThreads;
+    int64_t cap = std::min<int64_t>(kMaxRedBlocks, (int64_t)mg->nsm * 4);
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+void cheb_coeffs(double lmax, double lo, double hi, int nu, std::vector<double> &c, std::vector<double> &e) {
+    c.clear();
+    e.clear();
+    const double a = lo * lmax, b = hi * lmax;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+    c.push_back(0.0);
+    e.push_back(1.0 / theta);
+    double rho_prev = 1.0 / sigma;
+    for (int k = 1; k < nu; ++k) {
+        double rho = 1.0 / (2.0 * sigma - rho_prev);
+        c.push_back(rho * rho_prev);
+        e.push_back(2.0 * rho / delta);
+        rho_prev = rho;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the cycle
+// ---------------------------------------------------------------------------
+
+// nu smoothing steps on level l; if from_zero the iterate starts at 0.
+// `cur` is the x buffer index holding the iterate on entry/exit.
+template <typename T>
+void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, int &cur, cudaStream_t s,
+            const int *skip) {
+    DevLevel &L = mg->lv[l];
+    const dec_mg_opts &o = mg->H.opts;
+    const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+    const std::vector<double> &cc = post ? L.c_post : L.c_pre;
+    const std::vector<double> &ee = post ? L.e_post : L.e_pre;
+    const int g = grid_for(mg, L.n);
+    const T *w = P<T>::w(L);
+    dispatch_k(L.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        for (int k = 0; k < nu; ++k) {
+            const T e = (T)(cheb ? ee[k] : o.omega);
+            const T c = (T)(cheb ? cc[k] : 0.0);
+            const bool dout = cheb && k + 1 < nu;
+            if (k == 0 && from_zero) {
+                cur = 0;
+                ProfScope ps(mg, DEC_PK_SMOOTH0, l, s);
+                if (dout)
+                    k_smooth0<T, KT, true><<<g, kThreads, 0, s>>>(L.n, L.K, w, b, P<T>::x(L, 0), P<T>::d(L, 0), e, skip);
+                else
+                    k_smooth0<T, KT, false><<<g, kThreads, 0, s>>>(L.n, L.K, w, b, P<T>::x(L, 0), nullptr, e, skip);
+                continue;
+            }
+            const int nxt = 1 - cur;
+            const bool din = cheb && k > 0;
+            T *xi = P<T>::x(L, cur), *xo = P<T>::x(L, nxt);
+            T *di = P<T>::d(L, cur), *dn = P<T>::d(L, nxt);
+            ProfScope ps(mg, DEC_PK_SMOOTH, l, s);
+            if (din && dout)
+                k_smooth<T, KT, true, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, di, xo, dn, c, e, skip);
+            else if (din)
+                k_smooth<T, KT, true, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, di, xo, nullptr, c, e, skip);
+            else if (dout)
+                k_smooth<T, KT, false, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, nullptr, xo, dn, c, e, skip);
+            else
+                k_smooth<T, KT, false, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, nullptr, xo, nullptr, c, e, skip);
+            cur = nxt;
+        }
+    });
+}
+
+// Enqueue one cycle C_l(b) with zero initial guess; returns the level-l
+// buffer that holds the result.
+template <typename T>
+T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
+    DevLevel &L = mg->lv[l];
+    if (l == 0) {
+        const T *G;
+        if constexpr (std::is_same<T, float>::value) G = mg->G32; else G = mg->G64;
+        int g = (int)std::min<int64_t>(mg->nsm * 4, (L.n * 32 + kThreads - 1) / kThreads);
+        ProfScope ps(mg, DEC_PK_COARSE, 0, s);
+        k_coarse<T><<<g, kThreads, 0, s>>>(L.n, G, b, P<T>::x(L, 0), skip);
+        return P<T>::x(L, 0);
+    }
+    const dec_mg_opts &o = mg->H.opts;
+    DevLevel &C = mg->lv[l - 1];
+    int cur = 0;
+    if (o.nu1 > 0)
+        smooth<T>(mg, l, b, o.nu1, true, false, cur, s, skip);
+    else
+        cudaMemsetAsync(P<T>::x(L, 0), 0, sizeof(T) * L.n, s);
+    const int g = grid_for(mg, L.n);
+    const T *w = P<T>::w(L);
+    dispatch_k(L.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        {
+            ProfScope ps(mg, DEC_PK_RESIDUAL, l, s);
+            k_residual<T, KT><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, P<T>::x(L, cur), P<T>::r(L), skip);
+        }
+        {
+            ProfScope ps(mg, DEC_PK_RESTRICT, l, s);
+            k_restrict<T, KT><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
+                                                                    skip);
+        }
+    });
+    T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip);
+    {
+        ProfScope ps(mg, DEC_PK_PROLONG, l, s);
+        k_prolong<T><<<g, kThreads, 0, s>>>(C.n, L.n, L.par, ec, P<T>::x(L, cur), skip);
+    }
+    if (o.nu2 > 0) smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip);
+    return P<T>::x(L, cur);
+}
+
+// ---------------------------------------------------------------------------
+// outer iterations
+// ---------------------------------------------------------------------------
+
+template <typename TV>
+void enqueue_outer_init(dec_mg *mg, TV *rv, cudaStream_t s) {
+    DevLevel &F = mg->lv.back();
+    ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        k_outer_init<KT, TV><<<red_grid(mg, F.n), kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox,
+                                                                    mg->orr, rv, mg->partials, mg->counter, mg->scal);
+    });
+}
+
+void enqueue_mean_shift(dec_mg *mg, double *v, cudaStream_t s, const int *skip) {
+    DevLevel &F = mg->lv.back();
+    const int top = (int)mg->lv.size() - 1;
+    ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
+    k_mean<<<red_grid(mg, F.n), kThreads, 0, s>>>(F.n, F.star0, F.freev, v, mg->partials, mg->counter, mg->scal, skip);
+    k_shift<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.freev, v, mg->scal, skip);
+}
+
+// z <- M r, then the dot products and the new search direction.
+void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStream_t s, const int *skip) {
+    DevLevel &F = mg->lv.back();
+    const int gauge = mg->H.bc == DEC_BC_GAUGE;
+    const int rg = red_grid(mg, F.n);
+    const int top = (int)mg->lv.size() - 1;
+    if (solver == DEC_SOLVER_CG) {
+        ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
+        k_pcg_zdots<double><<<rg, kThreads, 0, s>>>(F.n, F.star0, F.freev, mg->orr, mg->ozn, mg->orr, mg->ozo, first,
+                                                    gauge, mg->partials, mg->counter, mg->scal, skip);
+    } else if (mode == DEC_MODE_MIXED) {
+        float *z = cycle<float>(mg, top, F.b32, s, skip);
+        ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
+        k_pcg_zdots<float><<<rg, kThreads, 0, s>>>(F.n, F.star0, F.freev, z, mg->ozn, mg->orr, mg->ozo, first, gauge,
+                                                   mg->partials, mg->counter, mg->scal, skip);
+    } else {
+        double *z = cycle<double>(mg, top, mg->orr, s, skip);
+        ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
+        k_pcg_zdots<double><<<rg, kThreads, 0, s>>>(F.n, F.star0, F.freev, z, mg->ozn, mg->orr, mg->ozo, first, gauge,
+                                                    mg->partials, mg->counter, mg->scal, skip);
+    }
+    ProfScope ps(mg, DEC_PK_PUPD, top, s);
+    k_pcg_pupd<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.freev, mg->ozn, mg->ozo, mg->op, first ? 1 : 0, mg->scal,
+                                                      skip);
+}
+
+void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
+    DevLevel &F = mg->lv.back();
+    const int *skip = &mg->scal->done;
+    const int rg = red_grid(mg, F.n);
+    const int top = (int)mg->lv.size() - 1;
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        ProfScope ps(mg, DEC_PK_SPMV64, top, s);
+        k_pcg_spmv<KT><<<rg, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.star0, F.freev, mg->op, mg->oq, mg->partials,
+                                               mg->counter, mg->scal, skip);
+    });
+    {
+    ProfScope ps(mg, DEC_PK_UPDATE, top, s);
+    if (mode == DEC_MODE_MIXED && solver != DEC_SOLVER_CG)
+        k_pcg_update<float><<<rg, kThreads, 0, s>>>(F.n, mg->op, mg->oq, mg->ox, mg->orr, F.b32, mg->partials,
+                                                    mg->counter, mg->scal, skip);
+    else
+        k_pcg_update<double><<<rg, kThreads, 0, s>>>(F.n, mg->op, mg->oq, mg->ox, mg->orr, nullptr, mg->partials,
+                                                     mg->counter, mg->scal, skip);
+    }
+    enqueue_precondition(mg, solver, mode, false, s, skip);
+}
+
+void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
+    DevLevel &F = mg->lv.back();
+    const int *skip = &mg->scal->done;
+    const int top = (int)mg->lv.size() - 1;
+    const int rg = red_grid(mg, F.n);
+    if (mode == DEC_MODE_MIXED) {
+        float *e = cycle<float>(mg, top, F.b32, s, skip);
+        {
+            ProfScope ps(mg, DEC_PK_ADD, top, s);
+            k_add<float><<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, e, mg->ox, skip);
+        }
+        dispatch_k(F.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            ProfScope ps(mg, DEC_PK_MGRES, top, s);
+            k_mg_residual<KT, float><<<rg, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox, mg->orr,
+                                                             F.b32, mg->partials, mg->counter, mg->scal, skip);
+        });
+    } else {
+        double *e = cycle<double>(mg, top, mg->orr, s, skip);
+        {
+            ProfScope ps(mg, DEC_PK_ADD, top, s);
+            k_add<double><<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, e, mg->ox, skip);
+        }
+        dispatch_k(F.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            ProfScope ps(mg, DEC_PK_MGRES, top, s);
+            k_mg_residual<KT, double><<<rg, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox, mg->orr,
+                                                              (double *)nullptr, mg->partials, mg->counter, mg->scal,
+                                                              skip);
+        });
+    }
+}
+
+// One iteration of the chosen solver, as a CUDA graph captured on first use.
+int iteration_graph(dec_mg *mg, int solver, int mode, cudaGraphExec_t *out) {
+    cudaGraphExec_t &slot = mg->graphs[solver][mode];
+    if (!slot && mg->prof) {
+        // profiled graphs own the event slots: keep one profiled graph at a time
+        drop_graphs(mg);
+    }
+    if (!slot) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(mg->cap, cudaStreamCaptureModeThreadLocal));
+        mg->prof_capture = mg->prof != 0;
+        mg->capturing = true;
+        if (solver == DEC_SOLVER_MG)
+            enqueue_mg_iteration(mg, mode, mg->cap);
+        else
+            enqueue_pcg_iteration(mg, solver, mode, mg->cap);
+        mg->prof_capture = false;
+        mg->capturing = false;
+        cudaError_t e1 = cudaGetLastError();
+        cudaError_t e2 = cudaStreamEndCapture(mg->cap, &g);
+        if (e1 != cudaSuccess) return cuda_fail(e1, "capture");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int64_t nk = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+        }
+        mg->graph_kernels[solver][mode] = nk;
+        cudaError_t e3 = cudaGraphInstantiate(&slot, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) {
+            slot = nullptr;
+            return cuda_fail(e3, "cudaGraphInstantiate");
+        }
+    }
+    *out = slot;
+    return DEC_OK;
+}
+
+int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po, dec_stats *stats,
+               cudaStream_t s) {
+    dec_solve_opts o;
+    if (po)
+        o = *po;
+    else
+        dec_solve_default_opts(&o);
+    if (o.solver < 0 || o.solver > 2 || (o.mode != DEC_MODE_F64 && o.mode != DEC_MODE_MIXED) || o.maxit < 0 ||
+        o.maxit >= kHist || !(o.tol >= 0.0))
+        return fail(Status::fail(DEC_ERR_ARG, "bad solve options"));
+    if (o.check_every < 1) o.check_every = 1;
+    DevLevel &F = mg->lv.back();
+    const size_t vb = sizeof(double) * F.n;
+    const bool gauge = mg->H.bc == DEC_BC_GAUGE;
+    const bool mixed = o.mode == DEC_MODE_MIXED && o.solver != DEC_SOLVER_CG;
+    const int64_t launches0 = mg->launches;
+    int64_t graph_launches = 0;
+    CK(cudaMemcpyAsync(mg->ob, b, vb, cudaMemcpyDeviceToDevice, s));
+    if (o.warm_start)
+        CK(cudaMemcpyAsync(mg->ox, x, vb, cudaMemcpyDeviceToDevice, s));
+    else
+        CK(cudaMemsetAsync(mg->ox, 0, vb, s));
+    // scalar header (everything before the history)
+    Scal *h = mg->scal_h;
+    std::memset(h, 0, offsetof(Scal, hist));
+    h->tol = o.tol;
+    h->maxit = o.maxit;
+    h->star0_sum = mg->star0_sum;
+    CK(cudaMemcpyAsync(mg->scal, h, offsetof(Scal, hist), cudaMemcpyHostToDevice, s));
+    if (gauge) {
+        enqueue_mean_shift(mg, mg->ob, s, nullptr);
+        if (o.warm_start) enqueue_mean_shift(mg, mg->ox, s, nullptr);
+    }
+    if (mixed)
+        enqueue_outer_init<float>(mg, F.b32, s);
+    else
+        enqueue_outer_init<double>(mg, (double *)nullptr, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int rc = DEC_OK;
+    if (!h->done && o.maxit > 0) {
+        if (o.solver != DEC_SOLVER_MG) enqueue_precondition(mg, o.solver, o.mode, true, s, nullptr);
+        cudaGraphExec_t ge;
+        rc = iteration_graph(mg, o.solver, o.mode, &ge);
+        if (rc) return rc;
+        int launched = 0;
+        const int every = mg->prof ? 1 : o.check_every;
+        while (launched < o.maxit) {
+            int chunk = std::min(every, o.maxit - launched);
+            for (int k = 0; k < chunk; ++k) CK(cudaGraphLaunch(ge, s));
+            graph_launches += chunk;
+            launched += chunk;
+            CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (h->done) break;
+            if (mg->prof) accumulate_slots(mg);
+        }
+    }
+    if (gauge) enqueue_mean_shift(mg, mg->ox, s, nullptr);
+    CK(cudaMemcpyAsync(x, mg->ox, vb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->iters = h->iter;
+        stats->rel_res = h->rel;
+        stats->rel_res0 = h->rel0;
+        stats->launches = (mg->launches - launches0) + graph_launches * mg->graph_kernels[o.solver][o.mode];
+    }
+    if (h->status == 1) return fail(Status::fail(DEC_ERR_NONFINITE, "non-finite residual"));
+    if (!(h->rel <= o.tol)) return fail(Status::fail(DEC_ERR_NOT_CONVERGED, "maxit reached before tol"));
+    return rc;
+}
+
+int check_mg(const dec_mg *mg) {
+    if (!mg) return fail(Status::fail(DEC_ERR_ARG, "null handle"));
+    return DEC_OK;
+}
+
+int check_dev(const dec_mg *mg) {
+    if (!mg) return fail(Status::fail(DEC_ERR_ARG, "null handle"));
+    if (mg->host_only) return fail(Status::fail(DEC_ERR_ARG, "handle was built with DEC_HOST_ONLY"));
+    return DEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t flags, const double *star1_scale,
+                 const dec_mg_opts *opts, dec_mg **out) {
+    if (!base || !out) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    *out = nullptr;
+    if (nsub < 0 || nsub > 14) return fail(Status::fail(DEC_ERR_ARG, "nsub out of range"));
+    dec_mg_opts o;
+    if (opts)
+        o = *opts;
+    else
+        dec_mg_default_opts(&o);
+    if (o.smoother != DEC_SMOOTH_JACOBI && o.smoother != DEC_SMOOTH_CHEBYSHEV)
+        return fail(Status::fail(DEC_ERR_ARG, "smoother not available"));
+    if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma != 1 || o.power_iters < 1 ||
+        !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
+        return fail(Status::fail(DEC_ERR_ARG, "bad multigrid options"));
+    dec_mg *mg = new (std::nothrow) dec_mg;
+    if (!mg) return fail(Status::fail(DEC_ERR_OOM, "host allocation"));
+    int rc = DEC_OK;
+    auto bail = [&](int code) {
+        free_all(mg);
+        delete mg;
+        return code;
+    };
+    try {
+        Status st = decimpl::build_hierarchy(*dec_mesh_host(base), nsub, nlevels, bc, (flags & DEC_SPHERE_PROJECT) != 0,
+                                             star1_scale, o, mg->H);
+        if (!st.good()) return bail(fail(st));
+    } catch (const std::bad_alloc &) {
+        return bail(fail(Status::fail(DEC_ERR_OOM, "host allocation")));
+    }
+    if (flags & DEC_HOST_ONLY) {
+        mg->host_only = true;
+        *out = mg;
+        return DEC_OK;
+    }
+    cudaError_t ce = cudaGetDevice(&mg->device);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
+    cudaDeviceGetAttribute(&mg->nsm, cudaDevAttrMultiProcessorCount, mg->device);
+    ce = cudaStreamCreateWithFlags(&mg->cap, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
+    const int nl = (int)mg->H.levels.size();
+    mg->lv.resize(nl);
+    for (int l = 0; l < nl; ++l) {
+        decimpl::HostLevel &HL = mg->H.levels[l];
+        DevLevel &D = mg->lv[l];
+        D.n = (int)HL.mesh.nv;
+        D.K = HL.K;
+        D.ne = HL.mesh.ne;
+        D.nc = l > 0 ? (int)mg->H.levels[l - 1].mesh.nv : 0;
+        const size_t slots = (size_t)HL.K * D.n;
+        std::vector<float> w32(slots);
+        for (size_t i = 0; i < slots; ++i) w32[i] = (float)HL.w[i];
+        if ((rc = upload(mg, &D.col, HL.col.data(), slots))) return bail(rc);
+        if ((rc = upload(mg, &D.w64, HL.w.data(), slots))) return bail(rc);
+        if ((rc = upload(mg, &D.w32, w32.data(), slots))) return bail(rc);
+        if ((rc = upload(mg, &D.star0, HL.star0.data(), D.n))) return bail(rc);
+        if ((rc = upload(mg, &D.freev, HL.free_.data(), D.n))) return bail(rc);
+        if (l > 0) {
+            const std::vector<int32_t> &par = mg->H.parents[l - 1];
+            if ((rc = upload(mg, &D.par, reinterpret_cast<const int2 *>(par.data()), par.size() / 2))) return bail(rc);
+        }
+        for (int i = 0; i < 2; ++i) {
+            if ((rc = dalloc(mg, &D.x32[i], D.n)) || (rc = dalloc(mg, &D.d32[i], D.n)) ||
+                (rc = dalloc(mg, &D.x64[i], D.n)) || (rc = dalloc(mg, &D.d64[i], D.n)))
+                return bail(rc);
+        }
+        if ((rc = dalloc(mg, &D.r32, D.n)) || (rc = dalloc(mg, &D.b32, D.n)) || (rc = dalloc(mg, &D.r64, D.n)) ||
+            (rc = dalloc(mg, &D.b64, D.n)))
+            return bail(rc);
+        cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu1, 1), D.c_pre, D.e_pre);
+        cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu2, 1), D.c_post, D.e_post);
+    }
+    // coarsest dense operator
+    {
+        mg->n0 = mg->lv[0].n;
+        const std::vector<double> &G = mg->H.G;
+        std::vector<float> G32(G.size());
+        for (size_t i = 0; i < G.size(); ++i) G32[i] = (float)G[i];
+        if ((rc = upload(mg, &mg->G64, G.data(), G.size())) || (rc = upload(mg, &mg->G32, G32.data(), G32.size())))
+            return bail(rc);
+    }
+    // finest extras and outer workspace
+    {
+        decimpl::HostLevel &HF = mg->H.levels.back();
+        const int n = (int)HF.mesh.nv;
+        if ((rc = upload(mg, &mg->slot_edge, HF.slot_edge.data(), HF.slot_edge.size()))) return bail(rc);
+        if ((rc = upload(mg, &mg->edges, reinterpret_cast<const int2 *>(HF.mesh.edges.data()), (size_t)HF.mesh.ne)))
+            return bail(rc);
+        double **vecs[] = {&mg->ox, &mg->orr, &mg->op, &mg->oq, &mg->ozn, &mg->ozo, &mg->ob, &mg->tmp};
+        for (double **v : vecs)
+            if ((rc = dalloc(mg, v, n))) return bail(rc);
+        if ((rc = dalloc(mg, &mg->partials, 8 * kMaxRedBlocks))) return bail(rc);
+        if ((rc = dalloc(mg, &mg->counter, 1))) return bail(rc);
+        if ((rc = dalloc(mg, &mg->scal, 1))) return bail(rc);
+        ce = cudaMemset(mg->counter, 0, sizeof(unsigned));
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
+        ce = cudaMallocHost((void **)&mg->scal_h, sizeof(Scal));
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMallocHost"));
+        double s = 0.0;
+        for (int v = 0; v < n; ++v)
+            if (HF.free_[v]) s += HF.star0[v];
+        mg->star0_sum = s;
+    }
+    ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceSynchronize"));
+    *out = mg;
+    return DEC_OK;
+}
+
+void dec_mg_destroy(dec_mg *mg) {
+    if (!mg) return;
+    free_all(mg);
+    delete mg;
+}
+
+int dec_mg_info(const dec_mg *mg, dec_mg_info_t *info) {
+    if (int rc = check_mg(mg)) return rc;
+    if (!info) return fail(Status::fail(DEC_ERR_ARG, "null info"));
+    std::memset(info, 0, sizeof(*info));
+    info->nlevels = (int)mg->H.levels.size();
+    for (int l = 0; l < info->nlevels; ++l) {
+        const decimpl::HostLevel &L = mg->H.levels[l];
+        info->nv[l] = L.mesh.nv;
+        info->ne[l] = L.mesh.ne;
+        info->nt[l] = L.mesh.nt;
+        info->ell_width[l] = L.K;
+        info->lmax[l] = L.lmax;
+        info->ncolors[l] = L.ncolors;
+    }
+    info->bc = mg->H.bc;
+    info->dim = mg->H.levels.back().mesh.dim;
+    info->device_bytes = mg->bytes;
+    return DEC_OK;
+}
+
+int dec_mg_copy_table(const dec_mg *mg, int level, int what, void *out) {
+    if (int rc = check_mg(mg)) return rc;
+    if (!out || level < 0 || level >= (int)mg->H.levels.size()) return fail(Status::fail(DEC_ERR_ARG, "bad level"));
+    const decimpl::HostLevel &L = mg->H.levels[level];
+    switch (what) {
+        case DEC_TABLE_VERTS: std::memcpy(out, L.mesh.verts.data(), L.mesh.verts.size() * 8); break;
+        case DEC_TABLE_TRIS: std::memcpy(out, L.mesh.tris.data(), L.mesh.tris.size() * 4); break;
+        case DEC_TABLE_EDGES:
+        case DEC_TABLE_PARENTS: std::memcpy(out, L.mesh.edges.data(), L.mesh.edges.size() * 4); break;
+        case DEC_TABLE_STAR0: std::memcpy(out, L.star0.data(), L.star0.size() * 8); break;
+        case DEC_TABLE_STAR1: std::memcpy(out, L.star1.data(), L.star1.size() * 8); break;
+        case DEC_TABLE_FREE: {
+            int32_t *o = (int32_t *)out;
+            for (size_t i = 0; i < L.free_.size(); ++i) o[i] = L.free_[i];
+            break;
+        }
+        case DEC_TABLE_COLORS: std::memcpy(out, L.colors.data(), L.colors.size() * 4); break;
+        default: return fail(Status::fail(DEC_ERR_ARG, "unknown table"));
+    }
+    return DEC_OK;
+}
+
+int dec_mg_set_star1(dec_mg *mg, const double *star1, dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    if (!star1) return fail(Status::fail(DEC_ERR_ARG, "null star1"));
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &F = mg->lv.back();
+    k_set_weights<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.K, mg->slot_edge, star1, F.star0, F.freev, F.w64, F.w32);
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
+
+int dec_laplace0_apply(const dec_mg *mgc, int level, const void *x, void *y, int k, int prec, dec_stream_t stream) {
+    if (int rc = check_dev(mgc)) return rc;
+    dec_mg *mg = const_cast<dec_mg *>(mgc);
+    if (!x || !y || level < 0 || level >= (int)mg->lv.size() || k != 1 || (prec != DEC_F64 && prec != DEC_F32))
+        return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &L = mg->lv[level];
+    dispatch_k(L.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        if (prec == DEC_F64)
+            k_apply<double, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w64, (const double *)x,
+                                                                      (double *)y, nullptr);
+        else
+            k_apply<float, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, (const float *)x,
+                                                                     (float *)y, nullptr);
+    });
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
+
+int dec_residual(const dec_mg *mgc, int level, const void *b, const void *x, void *r, int k, int prec,
+                 dec_stream_t stream) {
+    if (int rc = check_dev(mgc)) return rc;
+    dec_mg *mg = const_cast<dec_mg *>(mgc);
+    if (!b || !x || !r || level < 0 || level >= (int)mg->lv.size() || k != 1 || (prec != DEC_F64 && prec != DEC_F32))
+        return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &L = mg->lv[level];
+    dispatch_k(L.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        if (prec == DEC_F64)
+            k_residual<double, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w64, (const double *)b,
+                                                                         (const double *)x, (double *)r, nullptr);
+        else
+            k_residual<float, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, (const float *)b,
+                                                                        (const float *)x, (float *)r, nullptr);
+    });
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
+
+int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    if (!b || !x || k != 1 || (prec != DEC_F64 && prec != DEC_F32)) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int top = (int)mg->lv.size() - 1;
+    DevLevel &F = mg->lv[top];
+    const int g = grid_for(mg, F.n);
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        if (prec == DEC_F64) {
+            k_residual<double, KT><<<g, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, (const double *)b, (const double *)x,
+                                                          F.b64, nullptr);
+            double *e = cycle<double>(mg, top, F.b64, s, nullptr);
+            k_axpy1<double><<<g, kThreads, 0, s>>>(F.n, e, (double *)x, nullptr);
+        } else {
+            k_residual<float, KT><<<g, kThreads, 0, s>>>(F.n, F.K, F.col, F.w32, (const float *)b, (const float *)x,
+                                                         F.b32, nullptr);
+            float *e = cycle<float>(mg, top, F.b32, s, nullptr);
+            k_axpy1<float><<<g, kThreads, 0, s>>>(F.n, e, (float *)x, nullptr);
+        }
+    });
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
+
+int dec_mg_profile(dec_mg *mg, int enable) {
+    if (int rc = check_dev(mg)) return rc;
+    if (enable < 0 || enable > 2) return fail(Status::fail(DEC_ERR_ARG, "enable must be 0, 1 or 2"));
+    drop_graphs(mg);
+    mg->prof = enable;
+    std::memset(mg->prof_ms, 0, sizeof(mg->prof_ms));
+    std::memset(mg->prof_n, 0, sizeof(mg->prof_n));
+    return DEC_OK;
+}
+
+int dec_mg_profile_read(const dec_mg *mg, dec_prof_entry *out, int max, int *count) {
+    if (int rc = check_dev(mg)) return rc;
+    if (!count || (max > 0 && !out)) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    int c = 0;
+    for (int k = 0; k < DEC_PK_COUNT; ++k)
+        for (int l = 0; l < (int)mg->lv.size(); ++l) {
+            if (mg->prof_n[k][l] == 0) continue;
+            if (c < max) out[c] = dec_prof_entry{k, l, mg->prof_n[k][l], mg->prof_ms[k][l], (int64_t)mg->lv[l].n};
+            ++c;
+        }
+    *count = std::min(c, max);
+    return DEC_OK;
+}
+
+int dec_solve(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts, dec_stats *stats,
+              dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    if (!b || !x || k != 1) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    return solve_impl(mg, b, x, opts, stats, (cudaStream_t)stream);
+}
+
+int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double *grad_b, double *grad_star1,
+                       const dec_solve_opts *opts, dec_stats *stats, dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    if (!u || !grad_u || !grad_b) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &F = mg->lv.back();
+    // L mu = *0^-1 grad_u, solved into grad_b, then grad_b = *0 mu
+    k_star0_scale<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.star0, grad_u, mg->tmp, 1);
+    CK(cudaGetLastError());
+    int rc = solve_impl(mg, mg->tmp, grad_b, opts, stats, s);
+    if (rc != DEC_OK && rc != DEC_ERR_NOT_CONVERGED) return rc;
+    if (grad_star1) {
+        k_edge_grad<<<grid_for(mg, F.ne), kThreads, 0, s>>>(F.ne, mg->edges, grad_b, u, grad_star1);
+    }
+    k_star0_scale<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.star0, grad_b, grad_b, 0);
+    CK(cudaGetLastError());
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances come from the arithmetic.  One operator row sums at most K terms
+w_k (x_i - x_k); reordering that sum changes it by at most ~K eps times
+s_i = sum_k |w_k| (|x_i| + |x_k|), so rows are compared against
+TOL_ROW * eps * s_i (eps = 2^-53 for FP64, 2^-24 for FP32, where the FP32
+weights add one more rounding per term).  Cycles and solves are compared in
+the *0-norm: 1e-12 relative for an FP64 cycle, 2e-5 for an FP32 cycle, and
+for solves the error bound implied by the requested relative residual.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import multigrid as omg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+EPS32 = 2.0 ** -24
+TOL_ROW = 16.0
+
+
+def _lib():
+    import paper_2508_12501_gb300 as P
+    return P
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+CASES = {
+    # name: (base, nsub, nlevels, bc, sphere)
+    "square5": (W.unit_square, 5, 5, "dirichlet", False),
+    "ico5": (W.icosahedron, 5, 4, "gauge", True),
+    "fan3": (W.heptagon_fan, 3, 3, "dirichlet", False),
+    "grid_ragged": (lambda: W.grid_mesh(7, 5, 0.0, 1.3, 0.0, 0.9), 3, 3, "dirichlet", False),
+}
+
+_cache = {}
+
+
+def _pair(name, smoother="jacobi", nu=2):
+    key = (name, smoother, nu)
+    if key not in _cache:
+        P = _lib()
+        base, nsub, nl, bc, sph = CASES[name]
+        v, t = base()
+        h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, nu1=nu, nu2=nu)
+        oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, opts=omg.MGOptions(smoother=smoother, nu1=nu, nu2=nu))
+        _cache[key] = (h, oh)
+    return _cache[key]
+
+
+def _row_scale(lev, x):
+    # s_i = sum_k |w_k| (|x_i| + |x_k|) = (|L| |x|)_i
+    return abs(lev.L) @ np.abs(x)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_laplace0_apply_matches_oracle(name, prec):
+    h, oh = _pair(name)
+    assert h.ell_width[-1] == (7 if name == "fan3" else 6)
+    for l in range(h.nlevels):
+        lev = oh.levels[l]
+        x = W.uniform_field(lev.mesh.nv, 100 + l)
+        if prec == "f32":
+            x = x.astype(np.float32).astype(np.float64)  # exactly representable input
+        y = h.laplace0_apply(_dev(x, torch.float64 if prec == "f64" else torch.float32), level=l).double().cpu().numpy()
+        ref = np.where(lev.free, lev.L @ x, 0.0)
+        eps = EPS64 if prec == "f64" else EPS32
+        bound = TOL_ROW * eps * _row_scale(lev, x) + 1e-300
+        assert np.all(np.abs(y - ref) <= bound), (l, np.max(np.abs(y - ref) / bound))
+
+
+@pytest.mark.parametrize("name", ["square5", "ico5", "fan3"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_residual_matches_oracle(name, prec):
+    h, oh = _pair(name)
+    lev = oh.finest
+    x = W.uniform_field(lev.mesh.nv, 7)
+    b = W.uniform_field(lev.mesh.nv, 8)
+    if prec == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+        b = b.astype(np.float32).astype(np.float64)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    r = h.residual(_dev(b, dt), _dev(x, dt)).double().cpu().numpy()
+    ref = np.where(lev.free, b - lev.L @ x, 0.0)
+    eps = EPS64 if prec == "f64" else EPS32
+    bound = TOL_ROW * eps * (_row_scale(lev, x) + np.abs(b)) + 1e-300
+    assert np.all(np.abs(r - ref) <= bound)
+
+
+def _s0_rel(lev, a, b):
+    return omg.star0_norm(lev, a - b) / omg.star0_norm(lev, b)
+
+
+@pytest.mark.parametrize("name", ["square5", "ico5", "fan3", "grid_ragged"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_one_cycle_matches_oracle(name, smoother, prec):
+    h, oh = _pair(name, smoother)
+    lev = oh.finest
+    b = omg.prepare_rhs(oh, W.uniform_field(lev.mesh.nv, 21))
+    ref = omg.vcycle(oh, b, np.zeros_like(b))
+    dt = torch.float64 if prec == "f64" else torch.float32
+    x = torch.zeros(lev.mesh.nv, dtype=dt, device="cuda")
+    h.vcycle(_dev(b, dt), x)
+    got = x.double().cpu().numpy()
+    tol = 1e-12 if prec == "f64" else 2e-5
+    assert _s0_rel(lev, got, ref) < tol
+    assert np.all(got[~lev.free] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["square5", "ico5", "fan3"])
+@pytest.mark.parametrize("solver", ["mg", "mgpcg", "cg"])
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_solve_matches_oracle(name, solver, mode):
+    h, oh = _pair(name)
+    lev = oh.finest
+    b = W.uniform_field(lev.mesh.nv, 31)
+    tol = 1e-10
+    xs = omg.direct_solve(oh, b)
+    x, st = h.solve(_dev(b), solver=solver, mode=mode, tol=tol, maxit=1000 if solver == "cg" else 100)
+    x = x.cpu().numpy()
+    assert st.status == 0 and st.rel_res <= tol
+    bp = omg.prepare_rhs(oh, b)
+    # the true FP64 residual of the returned iterate, recomputed by the oracle
+    assert omg.rel_residual(lev, bp, x) <= 4 * tol
+    assert _s0_rel(lev, x, xs) < 1e-7
+    if mode == "f64" and solver != "cg":
+        # the same algorithm in the same precision takes the same number of steps
+        ref = omg.mg_solve(oh, b, tol, 100) if solver == "mg" else omg.pcg_solve(oh, b, tol, 100)
+        assert abs(st.iters - ref.iters) <= 1
+    if mode == "f64" and solver == "cg":
+        ref = omg.pcg_solve(oh, b, tol, 1000, precondition=False)
+        assert abs(st.iters - ref.iters) <= max(2, 0.05 * ref.iters)
+
+
+def test_config1_closed_form():
+    # unit square x5, 5-level V(2,2) Jacobi, Dirichlet, -Delta of sin(pi x) sin(pi y), standalone MG to 1e-10
+    h, oh = _pair("square5")
+    lev = oh.finest
+    assert h.nv == [9, 25, 81, 289, 1089]
+    b = W.rhs_sin_square(lev.mesh.verts)
+    x, st = h.solve(_dev(b), solver="mg", mode="f64", tol=1e-10, maxit=100)
+    ref = omg.mg_solve(oh, b, 1e-10, 100)
+    assert st.iters == ref.iters
+    hh = 1.0 / 32
+    lam11 = 8.0 / hh ** 2 * math.sin(math.pi * hh / 2) ** 2
+    u_h = 2 * math.pi ** 2 / lam11 * W.u_sin_square(lev.mesh.verts)
+    assert _s0_rel(lev, x.cpu().numpy(), u_h) < 1e-9
+
+
+def test_host_buffers_and_warm_start():
+    h, oh = _pair("ico5")
+    lev = oh.finest
+    b = torch.as_tensor(W.uniform_field(lev.mesh.nv, 41)).pin_memory()
+    x, st = h.solve(b, tol=1e-9)
+    assert x.device.type == "cpu" and st.rel_res <= 1e-9
+    x2, st2 = h.solve(b.cuda(), x=x.cuda(), warm_start=True, tol=1e-9)
+    assert st2.iters <= 1 and st2.rel_res0 <= 1e-8
+
+
+def test_error_paths():
+    P = _lib()
+    h, oh = _pair("ico5")
+    n = oh.finest.mesh.nv
+    b = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.DecError) as ei:
+        h.solve(b)
+    assert ei.value.code == 6  # DEC_ERR_NONFINITE
+    b = _dev(W.uniform_field(n, 5))
+    x, st = h.solve(b, maxit=1, raise_on_fail=False)
+    assert st.status == 5 and st.iters == 1 and 0 < st.rel_res < st.rel_res0
+    assert torch.isfinite(x).all()
+    z, st = h.solve(torch.zeros(n, dtype=torch.float64, device="cuda"))
+    assert st.iters == 0 and torch.count_nonzero(z) == 0
+    with pytest.raises(TypeError):
+        h.solve(b.float())
+
+
+def test_single_level_hierarchy_is_direct_solve():
+    P = _lib()
+    v, t = W.icosahedron()
+    h = P.Hierarchy(P.Mesh(v, t), 2, 1, bc="gauge", sphere=True)
+    oh = omg.build_hierarchy(v, t, 2, 1, "gauge", sphere=True)
+    b = omg.prepare_rhs(oh, W.uniform_field(h.n, 3))
+    x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+    h.vcycle(_dev(b), x)
+    assert _s0_rel(oh.finest, x.cpu().numpy(), omg.direct_solve(oh, b)) < 1e-12

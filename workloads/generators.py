@@ -26,6 +26,7 @@ __all__ = [
     "porous_initial_T",
     "gaussian_initial_T",
     "random_directions",
+    "heptagon_fan",
     "WORKLOADS",
 ]
 
@@ -218,3 +219,15 @@ WORKLOADS = {
                                 rhs_seed=3, fd_seed=4, tol=1e-8),
     "square_l9_porous": dict(base="unit_square", nsub=9, bc="gauge", T0_seed=0, steps=2000),
 }
+
+
+def heptagon_fan():
+    """A centre vertex joined to 7 points on the unit circle: valence 7 at the centre.
+
+    After subdivision the centre keeps valence 7, so every level has 7
+    stencil slots per row; used to exercise meshes whose valence is not 6.
+    """
+    ang = 2.0 * math.pi * np.arange(7) / 7.0
+    verts = np.concatenate([[[0.0, 0.0]], np.stack([np.cos(ang), np.sin(ang)], axis=1)])
+    tris = np.array([[0, 1 + k, 1 + (k + 1) % 7] for k in range(7)], dtype=np.int32)
+    return verts, tris
