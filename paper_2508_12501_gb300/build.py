@@ -1,13 +1,15 @@
 """Build libdec.so in-tree: host C++ with g++, device code with nvcc for sm_103a.
 
 Run as ``python -m paper_2508_12501_gb300.build`` or call ``build()``.
-Objects go to ``_build/`` next to this file; the shared library is written
-to ``libdec.so`` in this package directory.
+Objects go to ``_build/<machine>/`` next to this file; the shared library is
+written to ``libdec.so`` in this package directory (relinked whenever it is
+missing or older than an object).
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -16,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libdec.so")
 
 HOST_SOURCES = ["host_mesh.cpp", "host_hier.cpp", "capi_host.cpp"]
@@ -71,7 +73,7 @@ def build(verbose=False, force=False):
         for o in outs:
             if o.strip():
                 print(o)
-    if jobs or not os.path.exists(LIB):
+    if jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         _run([nvcc, ARCH, "-shared", "-o", LIB] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"])
     return LIB
 
