@@ -238,6 +238,8 @@ def main():
     ap.add_argument("--smoother", default="chebyshev", choices=["jacobi", "chebyshev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all-levels", action="store_true")
+    ap.add_argument("--only-solves", action="store_true",
+                    help="warm-up and timed solves only (the command line used for the ncu launch list)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -298,7 +300,8 @@ def main():
     # warm-up (builds the iteration graphs)
     for _ in range(args.warmup):
         h.solve(b, x, solver="mgpcg", mode=args.mode, tol=TOL)
-        h.solve(b, x, solver="mgpcg", mode="f64", tol=TOL)
+        if not args.only_solves:
+            h.solve(b, x, solver="mgpcg", mode="f64", tol=TOL)
     barrier()
 
     gpu_idx = None
@@ -323,77 +326,103 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         tot_s = float(tt.item())
     value = args.steps * world / tot_s
+    errors = {}
+    if args.only_solves:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "iters": st.iters,
+                              "gpu_launches": launches, "ms_per_step": 1e3 * tot_s / args.steps}), flush=True)
+        return 0
 
     # ---- plain FP64 form of the same solve (speedup at equal accuracy)
-    ms64, st64, _, _ = timed_solves(args.steps, "f64")
-    x_f64 = x.clone()
-    v64 = args.steps / (sum(ms64) / 1e3)
+    v64, st64, x_f64 = None, None, None
+    try:
+        ms64, st64, _, _ = timed_solves(args.steps, "f64")
+        x_f64 = x.clone()
+        v64 = args.steps / (sum(ms64) / 1e3)
+    except Exception as ex:  # noqa: BLE001
+        errors["fp64"] = repr(ex)
 
     # ---- live per-kernel timing of the same solves (event pairs on the solve stream)
-    _, _, _, prof = timed_solves(args.steps, args.mode, profile=2 if args.profile_all_levels else 1)
     mixed = args.mode == "mixed"
     cheb = args.smoother == "chebyshev"
-    rows = []
-    for e in prof or []:
-        by = kernel_bytes(e, h, mixed, cheb)
-        avg = e["total_ms"] / max(1, e["launches"])
-        rows.append(dict(e, avg_ms=avg, bytes=by, gbs=(by / (avg * 1e-3) / 1e9) if by else None))
-    top = max(rows, key=lambda r: r["total_ms"]) if rows else None
-    peak, peak_src = peaks()
-    roof = None
-    if top and top["bytes"]:
-        tr = ncu_traffic(top["kind"])
-        roof = {"bound": "hbm", "kernel": f"{top['kind']} (level {top['level']}, {top['rows']} rows)",
-                "achieved": top["gbs"], "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": top["gbs"] / peak, "traffic": tr, "algorithmic_bytes": top["bytes"],
-                "avg_launch_ms": top["avg_ms"], "share_of_profiled_time": top["total_ms"] / sum(r["total_ms"] for r in rows)}
+    rows, roof = [], None
+    try:
+        _, _, _, prof = timed_solves(args.steps, args.mode, profile=2 if args.profile_all_levels else 1)
+        for e in prof or []:
+            by = kernel_bytes(e, h, mixed, cheb)
+            avg = e["total_ms"] / max(1, e["launches"])
+            rows.append(dict(e, avg_ms=avg, bytes=by, gbs=(by / (avg * 1e-3) / 1e9) if by else None))
+        top = max(rows, key=lambda r: r["total_ms"]) if rows else None
+        peak, peak_src = peaks()
+        if top and top["bytes"]:
+            tr = ncu_traffic(top["kind"])
+            roof = {"bound": "hbm", "kernel": f"{top['kind']} (level {top['level']}, {top['rows']} rows)",
+                    "achieved": top["gbs"], "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                    "frac": top["gbs"] / peak, "traffic": tr, "algorithmic_bytes": top["bytes"],
+                    "avg_launch_ms": top["avg_ms"],
+                    "share_of_profiled_time": top["total_ms"] / sum(r["total_ms"] for r in rows)}
+    except Exception as ex:  # noqa: BLE001
+        errors["profile"] = repr(ex)
 
     # ---- V-cycle throughput: back-to-back FP32 cycles
-    xb = torch.zeros(n, dtype=torch.float32, device=dev)
-    bb = b.float()
-    for _ in range(3):
-        h.vcycle(bb, xb)
-    ncyc = 20
-    flush.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(ncyc):
-        h.vcycle(bb, xb)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    vc_ms = e0.elapsed_time(e1) / ncyc
-    mdofs = n / (vc_ms * 1e-3) / 1e6
+    vc_ms = mdofs = None
+    try:
+        xb = torch.zeros(n, dtype=torch.float32, device=dev)
+        bb = b.float()
+        for _ in range(3):
+            h.vcycle(bb, xb)
+        ncyc = 20
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ncyc):
+            h.vcycle(bb, xb)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        vc_ms = e0.elapsed_time(e1) / ncyc
+        mdofs = n / (vc_ms * 1e-3) / 1e6
+    except Exception as ex:  # noqa: BLE001
+        errors["vcycle"] = repr(ex)
 
     # ---- end to end through the public API with host buffers
-    b_pin = torch.as_tensor(b_host).pin_memory()
-    for _ in range(2):
-        h.solve(b_pin, solver="mgpcg", mode=args.mode, tol=TOL)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        xh, _ = h.solve(b_pin, solver="mgpcg", mode=args.mode, tol=TOL)
-    torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": args.steps * world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
-           "d2h_bytes_per_step": 8 * n, "note": "wall clock, includes one 256 MB L2 flush per step"}
+    e2e = None
+    try:
+        b_pin = torch.as_tensor(b_host).pin_memory()
+        for _ in range(2):
+            h.solve(b_pin, solver="mgpcg", mode=args.mode, tol=TOL)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            xh, _ = h.solve(b_pin, solver="mgpcg", mode=args.mode, tol=TOL)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": args.steps * world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 8 * n, "note": "wall clock, includes one 256 MB L2 flush per step"}
+    except Exception as ex:  # noqa: BLE001
+        errors["e2e"] = repr(ex)
 
     # accuracy of the mixed result against the plain FP64 GPU result (*0 norm)
-    s0 = torch.as_tensor(h.table(-1, "star0"), device=dev)
-    d = x_mixed - x_f64
-    err = float(torch.sqrt((s0 * d * d).sum() / (s0 * x_f64 * x_f64).sum()))
+    err = None
+    if x_f64 is not None:
+        s0 = torch.as_tensor(h.table(-1, "star0"), device=dev)
+        d = x_mixed - x_f64
+        err = float(torch.sqrt((s0 * d * d).sum() / (s0 * x_f64 * x_f64).sum()))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        oh, ob = oracle_setup(args.smoother)
-        ts, ores = oracle_time(oh, ob, 5)
-        cpu = {"value": len(ts) / sum(ts), "unit": "solves/s", "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": f"5 complete FP64 oracle MG-PCG solves of the full workload ({ores.iters} iterations each), "
-                         f"hierarchy build excluded"}
+        try:
+            oh, ob = oracle_setup(args.smoother)
+            ts, ores = oracle_time(oh, ob, 5)
+            cpu = {"value": len(ts) / sum(ts), "unit": "solves/s", "cores": cpu_cores_used(), "kind": "oracle",
+                   "sample": f"5 complete FP64 oracle MG-PCG solves of the full workload ({ores.iters} iterations "
+                             f"each), hierarchy build excluded"}
+        except Exception as ex:  # noqa: BLE001
+            errors["cpu_baseline"] = repr(ex)
 
     if rank == 0:
         line = {
@@ -404,11 +433,14 @@ def main():
                        "cycle": "V(2,2)", "mode": args.mode, "tol": TOL,
                        "l2": "256 MB buffer written before every step (flush)", "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-            "iters": st.iters, "rel_res": st.rel_res, "fp64_solves_per_s": v64, "fp64_iters": st64.iters,
-            "speedup_vs_fp64": value / world / v64, "mixed_vs_fp64_rel_err_star0": err,
+            "iters": st.iters, "rel_res": st.rel_res, "fp64_solves_per_s": v64,
+            "fp64_iters": st64.iters if st64 else None,
+            "speedup_vs_fp64": (value / world / v64) if v64 else None, "mixed_vs_fp64_rel_err_star0": err,
             "vcycle_ms": vc_ms, "vcycle_mdof_s": mdofs,
             "kernels": [{k: (round(v_, 6) if isinstance(v_, float) else v_) for k, v_ in r.items()} for r in rows],
         }
+        if errors:
+            line["errors"] = errors
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

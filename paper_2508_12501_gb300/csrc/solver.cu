@@ -172,10 +172,11 @@ struct ProfScope {
         if (cudaEventCreate(&sl.a) != cudaSuccess || cudaEventCreate(&sl.b) != cudaSuccess) return;
         idx = (int)mg->slots.size();
         mg->slots.push_back(sl);
-        cudaEventRecord(sl.a, s);
+        // inside stream capture only an "external" record becomes an event-record node
+        cudaEventRecordWithFlags(sl.a, s, cudaEventRecordExternal);
     }
     ~ProfScope() {
-        if (idx >= 0) cudaEventRecord(mg->slots[idx].b, s);
+        if (idx >= 0) cudaEventRecordWithFlags(mg->slots[idx].b, s, cudaEventRecordExternal);
     }
 };
 
@@ -203,6 +204,8 @@ void accumulate_slots(dec_mg *mg) {
         if (cudaEventElapsedTime(&ms, sl.a, sl.b) == cudaSuccess) {
             mg->prof_ms[sl.kind][sl.level] += ms;
             mg->prof_n[sl.kind][sl.level] += 1;
+        } else {
+            (void)cudaGetLastError();  // a failed read must not surface as a later launch error
         }
     }
 }
