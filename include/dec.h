@@ -195,6 +195,34 @@ int dec_residual(const dec_mg *mg, int level, const void *b, const void *x, void
  * direct solve on the coarsest level.  prec as for dec_laplace0_apply. */
 int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_stream_t stream);
 
+/* dec_mg_vcycle_noalloc: the same FP32 cycle as dec_mg_vcycle(prec =
+ * DEC_F32, k = 1), x <- x + C(b - L x), for callers that may not allocate
+ * device memory when they run it.  (The paper has no counterpart: this is a
+ * deployment variant.)  Such callers include runtimes that reserve all device
+ * memory at start-up and forbid later allocation to keep latency and memory
+ * footprint predictable, plug-ins whose host application owns every device
+ * allocation, and code that runs where cudaMalloc is not allowed or would
+ * synchronize the device.  The call allocates nothing: its work vectors live
+ * in one file-scope device array of DEC_NOALLOC_SCRATCH_BYTES (32 MiB) that
+ * every GPU which loads libdec holds until the process exits.  The handle's
+ * tables (built earlier by dec_mg_build) and the caller's b and x (float
+ * device vectors of nv(finest) entries, x updated in place) are the inputs
+ * and outputs.
+ *   - The first call on a device looks up the device address of the array
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the array, which keeps the last call's
+ *     contents; every vector is written before it is read within a call, so
+ *     nothing needs clearing.  Calls whose executions overlap on the GPU (two
+ *     streams, two host threads, two handles) race on the array: serialize
+ *     them.
+ *   - Hierarchies whose six FP32 vectors per level (each rounded up to 256
+ *     bytes) need more than DEC_NOALLOC_SCRATCH_BYTES are rejected with
+ *     DEC_ERR_ARG; 32 MiB covers a finest level of about one million vertices.
+ */
+#define DEC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_stream_t stream);
+
 /* dec_solve: solve L x = b on the finest level to ||b - L x||_2/||b||_2 <= tol
  * (Sec. 3.1.2).  Standalone multigrid, or flexible CG in the *0 inner
  * product preconditioned by one cycle (Sec. 3.1.2 cross-comparison), or

@@ -21,6 +21,7 @@ lib = C.CDLL(LIB_PATH)
 # status codes and enums (mirror include/dec.h)
 DEC_OK, DEC_ERR_ARG, DEC_ERR_MESH, DEC_ERR_CUDA, DEC_ERR_OOM, DEC_ERR_NOT_CONVERGED, DEC_ERR_NONFINITE = range(7)
 DEC_SPHERE_PROJECT, DEC_HOST_ONLY = 1, 2
+DEC_NOALLOC_SCRATCH_BYTES = 32 << 20
 DEC_BC_DIRICHLET, DEC_BC_GAUGE = 0, 1
 DEC_F64, DEC_F32 = 0, 1
 DEC_SMOOTH_JACOBI, DEC_SMOOTH_CHEBYSHEV, DEC_SMOOTH_MCGS = 0, 1, 2
@@ -87,6 +88,7 @@ _SIGS = {
     "dec_solve": (_i, [_p, _p, _p, _i, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_solve_backward": (_i, [_p, _p, _p, _p, _p, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_mg_profile": (_i, [_p, _i]),
+    "dec_mg_vcycle_noalloc": (_i, [_p, _p, _p, _p]),
     "dec_mg_profile_read": (_i, [_p, C.POINTER(dec_prof_entry), _i, C.POINTER(_i)]),
 }
 

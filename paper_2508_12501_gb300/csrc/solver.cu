@@ -13,7 +13,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -851,3 +853,153 @@ int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// dec_mg_vcycle_noalloc: the FP32 cycle of dec_mg_vcycle with its level work
+// vectors taken from one file-scope device array instead of memory that the
+// handle allocated.  For callers that may not allocate device memory at the
+// point where they run the cycle (see include/dec.h).
+// ===========================================================================
+
+// Scratch shared by every call on a device: per level six float vectors
+// (two iterates, two Chebyshev directions, residual, right-hand side), each
+// starting on a 256-byte boundary.
+static __device__ __align__(256) float g_noalloc_scratch[DEC_NOALLOC_SCRATCH_BYTES / sizeof(float)];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, never a device address).
+int noalloc_scratch(float **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(Status::fail(DEC_ERR_ARG, "device index out of range"));
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[dev] = (float *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return DEC_OK;
+}
+
+struct NoallocLevel {
+    float *x[2], *d[2], *r, *b;
+};
+
+inline size_t noalloc_stride(int n) { return ((size_t)n + 63) / 64 * 64; }  // floats, 256-byte multiple
+
+size_t noalloc_floats(const dec_mg *mg) {
+    size_t f = 0;
+    for (const DevLevel &L : mg->lv) f += 6 * noalloc_stride(L.n);
+    return f;
+}
+
+void noalloc_smooth(dec_mg *mg, int l, NoallocLevel &B, const float *b, int nu, bool from_zero, bool post, int &cur,
+                    cudaStream_t s) {
+    DevLevel &L = mg->lv[l];
+    const dec_mg_opts &o = mg->H.opts;
+    const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+    const std::vector<double> &cc = post ? L.c_post : L.c_pre;
+    const std::vector<double> &ee = post ? L.e_post : L.e_pre;
+    const int g = grid_for(mg, L.n);
+    dispatch_k(L.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        for (int k = 0; k < nu; ++k) {
+            const float e = (float)(cheb ? ee[k] : o.omega);
+            const float c = (float)(cheb ? cc[k] : 0.0);
+            const bool dout = cheb && k + 1 < nu;
+            if (k == 0 && from_zero) {
+                cur = 0;
+                if (dout)
+                    k_smooth0<float, KT, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.w32, b, B.x[0], B.d[0], e, nullptr);
+                else
+                    k_smooth0<float, KT, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.w32, b, B.x[0], nullptr, e, nullptr);
+                continue;
+            }
+            const int nxt = 1 - cur;
+            const bool din = cheb && k > 0;
+            if (din && dout)
+                k_smooth<float, KT, true, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], B.d[cur],
+                                                                       B.x[nxt], B.d[nxt], c, e, nullptr);
+            else if (din)
+                k_smooth<float, KT, true, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], B.d[cur],
+                                                                        B.x[nxt], nullptr, c, e, nullptr);
+            else if (dout)
+                k_smooth<float, KT, false, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], nullptr,
+                                                                        B.x[nxt], B.d[nxt], c, e, nullptr);
+            else
+                k_smooth<float, KT, false, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], nullptr,
+                                                                         B.x[nxt], nullptr, c, e, nullptr);
+            cur = nxt;
+        }
+    });
+}
+
+float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const float *b, cudaStream_t s) {
+    DevLevel &L = mg->lv[l];
+    if (l == 0) {
+        int g = (int)std::min<int64_t>(mg->nsm * 4, (L.n * 32 + kThreads - 1) / kThreads);
+        k_coarse<float><<<g, kThreads, 0, s>>>(L.n, mg->G32, b, B[0].x[0], nullptr);
+        return B[0].x[0];
+    }
+    const dec_mg_opts &o = mg->H.opts;
+    DevLevel &C = mg->lv[l - 1];
+    int cur = 0;
+    if (o.nu1 > 0)
+        noalloc_smooth(mg, l, B[l], b, o.nu1, true, false, cur, s);
+    else
+        cudaMemsetAsync(B[l].x[0], 0, sizeof(float) * L.n, s);  // the iterate starts at zero
+    const int g = grid_for(mg, L.n);
+    dispatch_k(L.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        k_residual<float, KT><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B[l].x[cur], B[l].r, nullptr);
+        k_restrict<float, KT><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, B[l].r, B[l - 1].b, nullptr);
+    });
+    float *ec = noalloc_cycle(mg, B, l - 1, B[l - 1].b, s);
+    k_prolong<float><<<g, kThreads, 0, s>>>(C.n, L.n, L.par, ec, B[l].x[cur], nullptr);
+    if (o.nu2 > 0) noalloc_smooth(mg, l, B[l], b, o.nu2, false, true, cur, s);
+    return B[l].x[cur];
+}
+
+}  // namespace
+
+extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    if (!b || !x) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    const size_t need = noalloc_floats(mg) * sizeof(float);
+    if (need > DEC_NOALLOC_SCRATCH_BYTES)
+        return fail(Status::fail(DEC_ERR_ARG, "hierarchy needs " + std::to_string(need) +
+                                                  " bytes of cycle scratch, above the DEC_NOALLOC_SCRATCH_BYTES limit of " +
+                                                  std::to_string((size_t)DEC_NOALLOC_SCRATCH_BYTES)));
+    float *base = nullptr;
+    if (int rc = noalloc_scratch(&base)) return rc;
+    std::vector<NoallocLevel> B(mg->lv.size());
+    float *p = base;
+    for (size_t l = 0; l < mg->lv.size(); ++l) {
+        const size_t st = noalloc_stride(mg->lv[l].n);
+        float **slots[6] = {&B[l].x[0], &B[l].x[1], &B[l].d[0], &B[l].d[1], &B[l].r, &B[l].b};
+        for (float **q : slots) {
+            *q = p;
+            p += st;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int top = (int)mg->lv.size() - 1;
+    DevLevel &F = mg->lv[top];
+    const int g = grid_for(mg, F.n);
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        k_residual<float, KT><<<g, kThreads, 0, s>>>(F.n, F.K, F.col, F.w32, b, x, B[top].b, nullptr);
+    });
+    float *e = noalloc_cycle(mg, B, top, B[top].b, s);
+    k_axpy1<float><<<g, kThreads, 0, s>>>(F.n, e, x, nullptr);
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
