@@ -271,3 +271,57 @@ class Hierarchy:
         torch = _torch()
         p = self._vec(star1, self.ne[-1], (torch.float64,), "star1")
         check(lib.dec_mg_set_star1(self._h, p, self._stream()), "dec_mg_set_star1")
+
+
+def _autograd_function():
+    import torch
+
+    class PoissonSolve(torch.autograd.Function):
+        """u = L(*1)^-1 b with a hand-written backward: one adjoint solve on the same hierarchy.
+
+        forward(b, star1): if star1 is given it becomes the finest-level *1 (dec_mg_set_star1);
+        backward(dJ/du): dec_solve_backward returns dJ/db = *0 mu and dJ/d*1 = -(d0 mu)(d0 u),
+        with L mu = *0^-1 dJ/du.
+        """
+
+        @staticmethod
+        def forward(ctx, b, star1, hier, opts):
+            if star1 is not None:
+                hier.set_star1(star1.detach().contiguous())
+            u, _ = hier.solve(b.detach().contiguous(), **opts)
+            ctx.hier = hier
+            ctx.opts = opts
+            ctx.save_for_backward(u, star1 if star1 is not None else torch.empty(0, device=u.device))
+            ctx.has_star1 = star1 is not None
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            u, star1 = ctx.saved_tensors
+            hier = ctx.hier
+            if ctx.has_star1:
+                hier.set_star1(star1.contiguous())
+            o = {k: v for k, v in ctx.opts.items() if k in ("solver", "mode", "tol", "maxit", "check_every")}
+            want_s1 = ctx.has_star1 and ctx.needs_input_grad[1]
+            gb, gs, _ = hier.solve_backward(u, grad_u.contiguous(), want_star1=want_s1, **o)
+            return gb, (gs if want_s1 else None), None, None
+
+    return PoissonSolve
+
+
+_PS = None
+
+
+def poisson_solve(b, star1=None, hier=None, **opts):
+    """Differentiable solve of L(*1) u = b on `hier`'s finest level (torch.autograd.Function).
+
+    b: float64 CUDA tensor [nv]; star1: optional float64 CUDA tensor [ne] of
+    finest-level *1 values (differentiable); opts: solve options
+    (solver, mode, tol, maxit).  Returns u.
+    """
+    global _PS
+    if hier is None:
+        raise ValueError("hier is required")
+    if _PS is None:
+        _PS = _autograd_function()
+    return _PS.apply(b, star1, hier, opts)

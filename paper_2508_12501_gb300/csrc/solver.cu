@@ -849,6 +849,7 @@ int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double
     }
     k_star0_scale<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.star0, grad_b, grad_b, 0);
     CK(cudaGetLastError());
+    if (stats) stats->launches += grad_star1 ? 3 : 2;
     return rc;
 }
 
