@@ -244,6 +244,56 @@ int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double
                        double *grad_star1, const dec_solve_opts *opts, dec_stats *stats,
                        dec_stream_t stream);
 
+/* ---- porous convection (Sec. 3.2) -------------------------------------------
+ * One explicit step of the DEC porous-convection model of Sec. 3.2.1 with the
+ * constants of Sec. 3.2.2, on the finest level of a DEC_BC_GAUGE hierarchy
+ * (the pressure problem is pure Neumann):
+ *   w   = alpha rho0 (g^flat wedge T),  (g^flat wedge T)_e = g.(x_hi - x_lo) (T_lo + T_hi)/2
+ *   L P = *0^-1 d0^T *1 w              (Delta P = delta w; MG-PCG, warm-started from P)
+ *   q   = -(k/eta) (d0 P - w)
+ *   T  += dt * mask * ( -(1/phi) L_q T - kappa L T ),
+ *         (L_q T)_v = (1/*0_v) sum_{e ni v} (1/2) *1_e (d0 T)_e q_e,
+ * mask = 0 where fixed[v] != 0 (the bc operation of Sec. 3.2.1: top and
+ * bottom rows).  dec_porous_default_params: g = (0, -9.81, 0),
+ * alpha_rho0 = 1/|g|, phi = 0.1, k_eta = 1, kappa = 2 (= Ra^-1 g alpha rho0
+ * k_eta dT y_max / phi with Ra = 1000, dT = 200, y_max = 1), tol = 1e-8,
+ * mixed precision, maxit = 100; dt must be set by the caller (> 0). */
+typedef struct dec_porous_params {
+    double g[3];       /* gravity; the first dim components are used                */
+    double alpha_rho0; /* alpha * rho0; <= 0 selects 1/|g|                          */
+    double phi;        /* porosity                                                   */
+    double k_eta;      /* permeability / viscosity                                   */
+    double kappa;      /* thermal diffusivity lambda / (rho0 c_p)                    */
+    double dt;         /* forward-Euler time step                                    */
+    double tol;        /* relative-residual tolerance of every pressure solve        */
+    int mode;          /* DEC_MODE_F64 or DEC_MODE_MIXED for the pressure solves      */
+    int maxit;         /* MG-PCG iterations per pressure solve                       */
+} dec_porous_params;
+void dec_porous_default_params(dec_porous_params *prm);
+
+/* dec_porous_step: nsteps steps in place.  T, P: double device vectors
+ * [nv(finest)] (P is the warm start on entry and the last pressure on exit);
+ * fixed: uint8 device mask [nv].  checkpoints (nullable, device): receives T
+ * before steps 0, ckpt_every, 2 ckpt_every, ... and after the last step when
+ * nsteps is a multiple of ckpt_every: [(nsteps / ckpt_every + 1) * nv].
+ * stats (nullable): iters = pressure iterations summed over the steps,
+ * rel_res = the largest final pressure residual.  Errors: DEC_ERR_ARG (not a
+ * gauge hierarchy, dt <= 0, null pointers), and the errors of dec_solve.
+ * Synchronizes `stream`. */
+int dec_porous_step(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const dec_porous_params *prm,
+                    int nsteps, double *checkpoints, int ckpt_every, dec_stats *stats, dec_stream_t stream);
+
+/* dec_porous_backward: reverse-mode derivative of T_N = step^N(T_0):
+ * given grad_TN = dF/dT_N, writes grad_T0 = dF/dT_0.  Checkpoints every
+ * ckpt_every steps are kept on the device and each segment is recomputed
+ * forward before it is differentiated (memory: (nsteps/ckpt_every + 2 *
+ * ckpt_every + 8) vectors, allocated inside this call).  Each adjoint step
+ * costs one adjoint pressure solve on the same hierarchy.  Arguments as for
+ * dec_porous_step; T0 and P0 are not modified. */
+int dec_porous_backward(dec_mg *mg, const double *T0, const double *P0, const uint8_t *fixed,
+                        const dec_porous_params *prm, int nsteps, int ckpt_every, const double *grad_TN,
+                        double *grad_T0, dec_stats *stats, dec_stream_t stream);
+
 /* ---- live kernel timing ------------------------------------------------------
  * dec_mg_profile: enable = 1 records a CUDA event pair around every launch of
  * the finest level inside the repeated part of dec_solve (the captured

@@ -57,6 +57,12 @@ PROF_KINDS = ["smooth0", "smooth", "residual", "restrict", "prolong", "coarse", 
               "pupd", "mgres", "add", "aux"]
 
 
+class dec_porous_params(C.Structure):
+    _fields_ = [("g", C.c_double * 3), ("alpha_rho0", C.c_double), ("phi", C.c_double), ("k_eta", C.c_double),
+                ("kappa", C.c_double), ("dt", C.c_double), ("tol", C.c_double), ("mode", C.c_int),
+                ("maxit", C.c_int)]
+
+
 class dec_mg_info_t(C.Structure):
     _fields_ = [("nlevels", C.c_int), ("nv", C.c_int64 * 16), ("ne", C.c_int64 * 16), ("nt", C.c_int64 * 16),
                 ("ell_width", C.c_int * 16), ("lmax", C.c_double * 16), ("ncolors", C.c_int * 16),
@@ -89,6 +95,10 @@ _SIGS = {
     "dec_solve_backward": (_i, [_p, _p, _p, _p, _p, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_mg_profile": (_i, [_p, _i]),
     "dec_mg_vcycle_noalloc": (_i, [_p, _p, _p, _p]),
+    "dec_porous_default_params": (None, [C.POINTER(dec_porous_params)]),
+    "dec_porous_step": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _p, _i, C.POINTER(dec_stats), _p]),
+    "dec_porous_backward": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _i, _p, _p,
+                                 C.POINTER(dec_stats), _p]),
     "dec_mg_profile_read": (_i, [_p, C.POINTER(dec_prof_entry), _i, C.POINTER(_i)]),
 }
 

@@ -267,6 +267,48 @@ class Hierarchy:
         return [dict(kind=L.PROF_KINDS[e.kind], level=e.level, launches=e.launches, total_ms=e.total_ms,
                      rows=e.rows) for e in buf[: cnt.value]]
 
+    # ---- porous convection (Sec. 3.2) ------------------------------------
+    def _porous_params(self, dt, g=(0.0, -9.81, 0.0), alpha_rho0=0.0, phi=0.1, k_eta=1.0, kappa=2.0, tol=1e-8,
+                       mode="mixed", maxit=100):
+        p = L.dec_porous_params()
+        lib.dec_porous_default_params(C.byref(p))
+        for i in range(3):
+            p.g[i] = float(g[i]) if i < len(g) else 0.0
+        p.alpha_rho0, p.phi, p.k_eta, p.kappa, p.dt, p.tol = alpha_rho0, phi, k_eta, kappa, dt, tol
+        p.mode, p.maxit = MODES[mode], maxit
+        return p
+
+    def porous_step(self, T, P, fixed, nsteps, dt, checkpoints=None, ckpt_every=100, **params):
+        """Advance T (and the pressure P) by nsteps explicit porous-convection steps, in place."""
+        torch = _torch()
+        pT = self._vec(T, self.n, (torch.float64,), "T")
+        pP = self._vec(P, self.n, (torch.float64,), "P")
+        pf = self._vec(fixed, self.n, (torch.uint8,), "fixed")
+        pc = None
+        if checkpoints is not None:
+            pc = self._vec(checkpoints, checkpoints.numel(), (torch.float64,), "checkpoints")
+            if checkpoints.numel() < (nsteps // ckpt_every + 1) * self.n:
+                raise ValueError("checkpoints too small")
+        prm = self._porous_params(dt, **params)
+        st = L.dec_stats()
+        check(lib.dec_porous_step(self._h, pT, pP, pf, C.byref(prm), int(nsteps), pc, int(ckpt_every),
+                                  C.byref(st), self._stream()), "dec_porous_step")
+        return SolveStats(st.iters, st.rel_res, st.rel_res0, 0, st.launches)
+
+    def porous_backward(self, T0, P0, fixed, nsteps, grad_TN, dt, ckpt_every=100, **params):
+        """dF/dT0 of T_N = step^N(T0) given dF/dT_N (checkpointed recomputation)."""
+        torch = _torch()
+        args = [self._vec(T0, self.n, (torch.float64,), "T0"), self._vec(P0, self.n, (torch.float64,), "P0"),
+                self._vec(fixed, self.n, (torch.uint8,), "fixed")]
+        pg = self._vec(grad_TN, self.n, (torch.float64,), "grad_TN")
+        out = torch.empty_like(grad_TN)
+        prm = self._porous_params(dt, **params)
+        st = L.dec_stats()
+        check(lib.dec_porous_backward(self._h, *args, C.byref(prm), int(nsteps), int(ckpt_every), pg,
+                                      C.c_void_p(out.data_ptr()), C.byref(st), self._stream()),
+              "dec_porous_backward")
+        return out, SolveStats(st.iters, st.rel_res, st.rel_res0, 0, st.launches)
+
     def set_star1(self, star1):
         torch = _torch()
         p = self._vec(star1, self.ne[-1], (torch.float64,), "star1")

@@ -474,4 +474,141 @@ __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const in
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// porous convection (Sec. 3.2.1), FP64.  pot_v = alpha rho0 g . x_v, so the
+// buoyancy 1-form is w_e = (pot_hi - pot_lo)(T_lo + T_hi)/2 and, with the
+// ELL weight w_k = *1_e / *0_v of the slot joining v to u,
+//   (*0^-1 d0^T *1 w)_v = sum_k w_k (pot_v - pot_u)(T_v + T_u)/2,
+//   q_{v->u} = -k_eta [(P_u - P_v) - (pot_u - pot_v)(T_u + T_v)/2],
+//   (L_q T)_v = sum_k w_k (T_u - T_v) q_{v->u} / 2,   (L T)_v = sum_k w_k (T_v - T_u).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) k_potential(int n, int dim, const double *__restrict__ verts, double g0,
+                                                       double g1, double g2, double arho, double *__restrict__ pot) {
+    GRID_STRIDE(v, n) {
+        const double *x = verts + (size_t)v * dim;
+        double s = g0 * x[0] + g1 * x[1];
+        if (dim == 3) s += g2 * x[2];
+        pot[v] = arho * s;
+    }
+}
+
+// rhs = *0^-1 d0^T *1 w(T)
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_porous_rhs(int n, int K, const int32_t *__restrict__ col,
+                                                        const double *__restrict__ w, const double *__restrict__ T,
+                                                        const double *__restrict__ pot, double *__restrict__ rhs) {
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(v, n) {
+        const double Tv = ldg(T + v), pv = ldg(pot + v);
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + v;
+            const int u = ldg(col + o);
+            s += ldg(w + o) * (pv - ldg(pot + u)) * 0.5 * (Tv + ldg(T + u));
+        }
+        rhs[v] = s;
+    }
+}
+
+// T_out = T + dt * mask * ( -(1/phi) L_q T - kappa L T )
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_porous_update(int n, int K, const int32_t *__restrict__ col,
+                                                           const double *__restrict__ w, const double *__restrict__ T,
+                                                           const double *__restrict__ P, const double *__restrict__ pot,
+                                                           const uint8_t *__restrict__ fixed, double inv_phi,
+                                                           double k_eta, double kappa, double dt,
+                                                           double *__restrict__ T_out) {
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(v, n) {
+        const double Tv = ldg(T + v);
+        if (fixed[v]) {
+            T_out[v] = Tv;
+            continue;
+        }
+        const double Pv = ldg(P + v), pv = ldg(pot + v);
+        double adv = 0.0, dif = 0.0;
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + v;
+            const int u = ldg(col + o);
+            const double wk = ldg(w + o);
+            const double Tu = ldg(T + u);
+            const double q = -k_eta * ((ldg(P + u) - Pv) - (ldg(pot + u) - pv) * 0.5 * (Tu + Tv));
+            adv += wk * 0.5 * (Tu - Tv) * q;
+            dif += wk * (Tv - Tu);
+        }
+        T_out[v] = Tv + dt * (-inv_phi * adv - kappa * dif);
+    }
+}
+
+// Adjoint step, part 1: ms = mu / *0 with mu = dt * mask * lam.
+__global__ void __launch_bounds__(kThreads) k_porous_adj1(int n, const double *__restrict__ lam,
+                                                         const uint8_t *__restrict__ fixed,
+                                                         const double *__restrict__ star0, double dt,
+                                                         double *__restrict__ ms) {
+    GRID_STRIDE(v, n) ms[v] = fixed[v] ? 0.0 : dt * ldg(lam + v) / ldg(star0 + v);
+}
+
+// Adjoint step, part 2 (per vertex v, slots to u, *1_e = w_k *0_v):
+//   out_v  = lam_v - kappa *0_v sum_k w_k (ms_v - ms_u) + sum_k abar_e da_e/dT_v
+//   pbs_v  = (sum_k abar_e da_e/dP_v) / *0_v          (right-hand side of the pressure adjoint)
+// with abar_e = -(ms_v + ms_u)/phi, a_e = *1_e (T_u - T_v) q_{v->u} / 2.
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_porous_adj2(int n, int K, const int32_t *__restrict__ col,
+                                                         const double *__restrict__ w, const double *__restrict__ star0,
+                                                         const double *__restrict__ T, const double *__restrict__ P,
+                                                         const double *__restrict__ pot, const double *__restrict__ lam,
+                                                         const double *__restrict__ ms, double inv_phi, double k_eta,
+                                                         double kappa, double *__restrict__ out,
+                                                         double *__restrict__ pbs) {
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(v, n) {
+        const double Tv = ldg(T + v), Pv = ldg(P + v), pv = ldg(pot + v), mv = ldg(ms + v);
+        const double s0 = ldg(star0 + v);
+        double dif = 0.0, tbar = 0.0, pbar = 0.0;
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + v;
+            const int u = ldg(col + o);
+            const double wk = ldg(w + o);
+            const double Tu = ldg(T + u), dpot = ldg(pot + u) - pv, mu_u = ldg(ms + u);
+            dif += wk * (mv - mu_u);
+            const double q = -k_eta * ((ldg(P + u) - Pv) - dpot * 0.5 * (Tu + Tv));
+            const double abar = -(mv + mu_u) * inv_phi;
+            const double half_s1 = 0.5 * wk * s0;
+            tbar += abar * half_s1 * (-q + (Tu - Tv) * k_eta * dpot * 0.5);
+            pbar += abar * half_s1 * (Tu - Tv) * k_eta;
+        }
+        out[v] = ldg(lam + v) - kappa * s0 * dif + tbar;
+        pbs[v] = pbar / s0;
+    }
+}
+
+// Adjoint step, part 3: out_v += *0_v sum_k w_k (m_u - m_v)(pot_u - pot_v) / 2.
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_porous_adj3(int n, int K, const int32_t *__restrict__ col,
+                                                         const double *__restrict__ w, const double *__restrict__ star0,
+                                                         const double *__restrict__ pot, const double *__restrict__ m,
+                                                         double *__restrict__ out) {
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(v, n) {
+        const double mv = ldg(m + v), pv = ldg(pot + v);
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + v;
+            const int u = ldg(col + o);
+            s += ldg(w + o) * (ldg(m + u) - mv) * (ldg(pot + u) - pv);
+        }
+        out[v] += 0.5 * ldg(star0 + v) * s;
+    }
+}
+
 }  // namespace decdev

@@ -81,6 +81,9 @@ struct dec_mg {
     // finest-level extras
     int32_t *slot_edge = nullptr;
     int2 *edges = nullptr;
+    double *verts = nullptr;  // [n * dim] finest coordinates
+    int dim = 2;
+    double *pot = nullptr, *ptmp = nullptr, *prhs = nullptr;  // porous-step work vectors
     // outer-iteration workspace (finest level, FP64)
     double *ox = nullptr, *orr = nullptr, *op = nullptr, *oq = nullptr, *ozn = nullptr, *ozo = nullptr, *ob = nullptr;
     double *tmp = nullptr;
@@ -657,6 +660,10 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         if ((rc = upload(mg, &mg->slot_edge, HF.slot_edge.data(), HF.slot_edge.size()))) return bail(rc);
         if ((rc = upload(mg, &mg->edges, reinterpret_cast<const int2 *>(HF.mesh.edges.data()), (size_t)HF.mesh.ne)))
             return bail(rc);
+        mg->dim = HF.mesh.dim;
+        if ((rc = upload(mg, &mg->verts, HF.mesh.verts.data(), HF.mesh.verts.size()))) return bail(rc);
+        if ((rc = dalloc(mg, &mg->pot, n)) || (rc = dalloc(mg, &mg->ptmp, n)) || (rc = dalloc(mg, &mg->prhs, n)))
+            return bail(rc);
         double **vecs[] = {&mg->ox, &mg->orr, &mg->op, &mg->oq, &mg->ozn, &mg->ozo, &mg->ob, &mg->tmp};
         for (double **v : vecs)
             if ((rc = dalloc(mg, v, n))) return bail(rc);
@@ -1004,3 +1011,233 @@ extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_s
     CK(cudaGetLastError());
     return DEC_OK;
 }
+
+// ===========================================================================
+// porous convection: forward steps and the checkpointed adjoint (Sec. 3.2)
+// ===========================================================================
+
+namespace {
+
+struct PorousRun {
+    dec_mg *mg;
+    cudaStream_t s;
+    dec_porous_params prm;
+    const uint8_t *fixed;
+    dec_solve_opts so;
+    int64_t iters = 0;
+    double worst = 0.0;
+    int64_t launches = 0;
+};
+
+int porous_check(dec_mg *mg, const dec_porous_params *prm, dec_porous_params &out) {
+    if (int rc = check_dev(mg)) return rc;
+    if (mg->H.bc != DEC_BC_GAUGE) return fail(Status::fail(DEC_ERR_ARG, "porous steps need a DEC_BC_GAUGE hierarchy"));
+    if (prm)
+        out = *prm;
+    else
+        dec_porous_default_params(&out);
+    if (!(out.dt > 0.0) || !(out.phi > 0.0) || !(out.tol >= 0.0) || out.maxit < 1 || out.maxit >= kHist)
+        return fail(Status::fail(DEC_ERR_ARG, "bad porous parameters (dt, phi, tol, maxit)"));
+    if (out.alpha_rho0 <= 0.0) {
+        double gn = std::sqrt(out.g[0] * out.g[0] + out.g[1] * out.g[1] + out.g[2] * out.g[2]);
+        if (!(gn > 0.0)) return fail(Status::fail(DEC_ERR_ARG, "zero gravity with alpha_rho0 <= 0"));
+        out.alpha_rho0 = 1.0 / gn;
+    }
+    return DEC_OK;
+}
+
+void porous_potential(PorousRun &R) {
+    dec_mg *mg = R.mg;
+    DevLevel &F = mg->lv.back();
+    k_potential<<<grid_for(mg, F.n), kThreads, 0, R.s>>>(F.n, mg->dim, mg->verts, R.prm.g[0], R.prm.g[1], R.prm.g[2],
+                                                        R.prm.alpha_rho0, mg->pot);
+    R.launches += 1;
+}
+
+// rhs(T); P <- solve (warm); T_out = update(T_in, P)
+int porous_one_step(PorousRun &R, const double *T_in, double *P, double *T_out) {
+    dec_mg *mg = R.mg;
+    DevLevel &F = mg->lv.back();
+    const int g = grid_for(mg, F.n);
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        k_porous_rhs<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, T_in, mg->pot, mg->prhs);
+    });
+    dec_stats st{};
+    int rc = solve_impl(mg, mg->prhs, P, &R.so, &st, R.s);
+    R.iters += st.iters;
+    R.worst = std::max(R.worst, st.rel_res);
+    R.launches += st.launches + 2;
+    if (rc != DEC_OK) return rc;
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        k_porous_update<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, T_in, P, mg->pot, R.fixed,
+                                                    1.0 / R.prm.phi, R.prm.k_eta, R.prm.kappa, R.prm.dt, T_out);
+    });
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
+
+// lam <- (dT_{n+1}/dT_n)^T lam at the state (T, P) of step n; uses `out`, `ms`, `pbs`, `m` as work vectors.
+int porous_adjoint_step(PorousRun &R, const double *T, const double *P, double *&lam, double *&out, double *ms,
+                        double *pbs, double *m) {
+    dec_mg *mg = R.mg;
+    DevLevel &F = mg->lv.back();
+    const int g = grid_for(mg, F.n);
+    k_porous_adj1<<<g, kThreads, 0, R.s>>>(F.n, lam, R.fixed, F.star0, R.prm.dt, ms);
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        k_porous_adj2<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, F.star0, T, P, mg->pot, lam, ms,
+                                                  1.0 / R.prm.phi, R.prm.k_eta, R.prm.kappa, out, pbs);
+    });
+    dec_solve_opts so = R.so;  // adjoint pressure solve, warm-started from the previous m
+    dec_stats st{};
+    int rc = solve_impl(mg, pbs, m, &so, &st, R.s);
+    R.iters += st.iters;
+    R.worst = std::max(R.worst, st.rel_res);
+    R.launches += st.launches + 3;
+    if (rc != DEC_OK) return rc;
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        k_porous_adj3<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, F.star0, mg->pot, m, out);
+    });
+    CK(cudaGetLastError());
+    std::swap(lam, out);
+    return DEC_OK;
+}
+
+void porous_stats(const PorousRun &R, dec_stats *stats) {
+    if (!stats) return;
+    stats->iters = (int)std::min<int64_t>(R.iters, INT32_MAX);
+    stats->rel_res = R.worst;
+    stats->rel_res0 = 0.0;
+    stats->launches = R.launches;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dec_porous_default_params(dec_porous_params *p) {
+    if (!p) return;
+    p->g[0] = 0.0;
+    p->g[1] = -9.81;
+    p->g[2] = 0.0;
+    p->alpha_rho0 = 0.0;
+    p->phi = 0.1;
+    p->k_eta = 1.0;
+    p->kappa = 2.0;
+    p->dt = 0.0;
+    p->tol = 1e-8;
+    p->mode = DEC_MODE_MIXED;
+    p->maxit = 100;
+}
+
+int dec_porous_step(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const dec_porous_params *prm, int nsteps,
+                    double *checkpoints, int ckpt_every, dec_stats *stats, dec_stream_t stream) {
+    PorousRun R{mg, (cudaStream_t)stream, {}, fixed, {}};
+    if (int rc = porous_check(mg, prm, R.prm)) return rc;
+    if (!T || !P || !fixed || nsteps < 0 || (checkpoints && ckpt_every < 1))
+        return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    dec_solve_default_opts(&R.so);
+    R.so.mode = R.prm.mode;
+    R.so.tol = R.prm.tol;
+    R.so.maxit = R.prm.maxit;
+    R.so.warm_start = 1;
+    const int n = mg->lv.back().n;
+    const size_t vb = sizeof(double) * n;
+    porous_potential(R);
+    double *cur = T, *other = mg->ptmp;
+    int ck = 0;
+    for (int step = 0; step < nsteps; ++step) {
+        if (checkpoints && step % ckpt_every == 0)
+            CK(cudaMemcpyAsync(checkpoints + (size_t)ck++ * n, cur, vb, cudaMemcpyDeviceToDevice, R.s));
+        if (int rc = porous_one_step(R, cur, P, other)) {
+            porous_stats(R, stats);
+            return rc;
+        }
+        std::swap(cur, other);
+    }
+    if (checkpoints && nsteps % ckpt_every == 0)
+        CK(cudaMemcpyAsync(checkpoints + (size_t)ck * n, cur, vb, cudaMemcpyDeviceToDevice, R.s));
+    if (cur != T) CK(cudaMemcpyAsync(T, cur, vb, cudaMemcpyDeviceToDevice, R.s));
+    CK(cudaStreamSynchronize(R.s));
+    porous_stats(R, stats);
+    return DEC_OK;
+}
+
+int dec_porous_backward(dec_mg *mg, const double *T0, const double *P0, const uint8_t *fixed,
+                        const dec_porous_params *prm, int nsteps, int ckpt_every, const double *grad_TN,
+                        double *grad_T0, dec_stats *stats, dec_stream_t stream) {
+    PorousRun R{mg, (cudaStream_t)stream, {}, fixed, {}};
+    if (int rc = porous_check(mg, prm, R.prm)) return rc;
+    if (!T0 || !P0 || !fixed || !grad_TN || !grad_T0 || nsteps < 0 || ckpt_every < 1)
+        return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    dec_solve_default_opts(&R.so);
+    R.so.mode = R.prm.mode;
+    R.so.tol = R.prm.tol;
+    R.so.maxit = R.prm.maxit;
+    R.so.warm_start = 1;
+    const int n = mg->lv.back().n;
+    const size_t vb = sizeof(double) * n;
+    const int nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    // device work memory for this call: segment-start states, one segment of states, 8 vectors
+    const size_t nvec = (size_t)2 * std::max(nseg, 1) + (size_t)2 * ckpt_every + 8;
+    double *work = nullptr;
+    cudaError_t ce = cudaMalloc(&work, nvec * vb);
+    if (ce != cudaSuccess) return ce == cudaErrorMemoryAllocation ? fail(Status::fail(DEC_ERR_OOM, "cudaMalloc")) : cuda_fail(ce, "cudaMalloc");
+    auto V = [&](size_t i) { return work + i * n; };
+    double *ckT = V(0), *ckP = V(nseg);
+    double *segT = V(2 * (size_t)nseg), *segP = V(2 * (size_t)nseg + ckpt_every);
+    size_t b0 = 2 * (size_t)nseg + 2 * ckpt_every;
+    double *A = V(b0), *B = V(b0 + 1), *Pw = V(b0 + 2), *lam = V(b0 + 3), *out = V(b0 + 4), *ms = V(b0 + 5),
+           *pbs = V(b0 + 6), *m = V(b0 + 7);
+    int rc = DEC_OK;
+    auto done = [&](int code) {
+        cudaStreamSynchronize(R.s);
+        cudaFree(work);
+        porous_stats(R, stats);
+        return code;
+    };
+    // every failure below releases `work` through done()
+#define CKW(call)                                                         \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return done(cuda_fail(_e, #call));         \
+    } while (0)
+    porous_potential(R);
+    // forward pass, keeping the state (T, warm-start P) at each segment start
+    CKW(cudaMemcpyAsync(A, T0, vb, cudaMemcpyDeviceToDevice, R.s));
+    CKW(cudaMemcpyAsync(Pw, P0, vb, cudaMemcpyDeviceToDevice, R.s));
+    for (int step = 0; step < nsteps; ++step) {
+        if (step % ckpt_every == 0) {
+            const int sgi = step / ckpt_every;
+            CKW(cudaMemcpyAsync(ckT + (size_t)sgi * n, A, vb, cudaMemcpyDeviceToDevice, R.s));
+            CKW(cudaMemcpyAsync(ckP + (size_t)sgi * n, Pw, vb, cudaMemcpyDeviceToDevice, R.s));
+        }
+        if ((rc = porous_one_step(R, A, Pw, B))) return done(rc);
+        std::swap(A, B);
+    }
+    CKW(cudaMemcpyAsync(lam, grad_TN, vb, cudaMemcpyDeviceToDevice, R.s));
+    CKW(cudaMemsetAsync(m, 0, vb, R.s));
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int first = sgi * ckpt_every;
+        const int len = std::min(ckpt_every, nsteps - first);
+        CKW(cudaMemcpyAsync(A, ckT + (size_t)sgi * n, vb, cudaMemcpyDeviceToDevice, R.s));
+        CKW(cudaMemcpyAsync(Pw, ckP + (size_t)sgi * n, vb, cudaMemcpyDeviceToDevice, R.s));
+        for (int j = 0; j < len; ++j) {  // recompute the segment: T_n and the pressure P_n of step n
+            CKW(cudaMemcpyAsync(segT + (size_t)j * n, A, vb, cudaMemcpyDeviceToDevice, R.s));
+            if ((rc = porous_one_step(R, A, Pw, B))) return done(rc);
+            CKW(cudaMemcpyAsync(segP + (size_t)j * n, Pw, vb, cudaMemcpyDeviceToDevice, R.s));
+            std::swap(A, B);
+        }
+        for (int j = len - 1; j >= 0; --j)
+            if ((rc = porous_adjoint_step(R, segT + (size_t)j * n, segP + (size_t)j * n, lam, out, ms, pbs, m)))
+                return done(rc);
+    }
+    CKW(cudaMemcpyAsync(grad_T0, lam, vb, cudaMemcpyDeviceToDevice, R.s));
+    return done(DEC_OK);
+#undef CKW
+}
+
+}  // extern "C"
