@@ -59,13 +59,18 @@ enum { DEC_SPHERE_PROJECT = 1u, DEC_HOST_ONLY = 2u };
 enum { DEC_BC_DIRICHLET = 0, DEC_BC_GAUGE = 1 };
 enum { DEC_F64 = 0, DEC_F32 = 1 };           /* precision of a single operator call */
 enum { DEC_SMOOTH_JACOBI = 0, DEC_SMOOTH_CHEBYSHEV = 1, DEC_SMOOTH_MCGS = 2 };
+/* Restriction: DEC_RESTRICT_ROWNORM is the paper's transpose of the
+ * row-normalized subdivision matrix (Sec. 2.2.1); DEC_RESTRICT_STAR0 is the
+ * *0-adjoint of interpolation, r_c = *0c^-1 M(f) *0f r_f, which makes the
+ * cycle self-adjoint in the *0 inner product (an option, not the paper's). */
+enum { DEC_RESTRICT_ROWNORM = 0, DEC_RESTRICT_STAR0 = 1 };
 enum { DEC_SOLVER_MG = 0, DEC_SOLVER_MGPCG = 1, DEC_SOLVER_CG = 2 };
 enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1 };
 
 /* Multigrid options.  dec_mg_default_opts() fills the defaults:
  * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
  * [0.3, 1.1] * lambda_max(D^-1 L) with lambda_max from 10 power iterations,
- * gamma = 1 (V-cycle; 2 gives a W-cycle). */
+ * gamma = 1 (V-cycle; 2 gives a W-cycle), the paper's restriction. */
 typedef struct dec_mg_opts {
     int smoother;
     int nu1, nu2;
@@ -73,6 +78,7 @@ typedef struct dec_mg_opts {
     double cheby_lo, cheby_hi;
     int power_iters;
     int gamma;
+    int restriction;  /* DEC_RESTRICT_* */
 } dec_mg_opts;
 
 /* Solver options.  dec_solve_default_opts(): MG-PCG, mixed precision,

@@ -51,6 +51,7 @@ class MGOptions:
     cheby_hi: float = 1.1
     power_iters: int = 10
     gamma: int = 1                # 1: V-cycle, 2: W-cycle
+    restriction: str = "rownorm"  # rownorm: the paper's; star0: *0-adjoint of interpolation
 
 
 @dataclass
@@ -105,6 +106,16 @@ def restriction(nc, parents):
     M = barycentric_matrix(nc, parents)
     rs = np.asarray(M.sum(axis=1)).ravel()
     return (sp.diags(1.0 / rs) @ M).tocsr()
+
+
+def restriction_star0(nc, parents, star0_c, star0_f):
+    """*0-adjoint of interpolation: r_c = *0c^-1 M(f) *0f r_f, so <R r, e>_*0c = <r, P e>_*0f.
+
+    Not the paper's operator (an option): with it the cycle is self-adjoint in
+    the *0 inner product, as CG's preconditioner needs.
+    """
+    M = barycentric_matrix(nc, parents)
+    return (sp.diags(1.0 / star0_c) @ M @ sp.diags(star0_f)).tocsr()
 
 
 # ----------------------------------------------------------------------------
@@ -192,7 +203,11 @@ def build_hierarchy(verts, tris, nsub, nlevels, bc, sphere=False, star1_scale=No
     for i in range(first, nsub):
         nc = meshes[i].nv
         P.append(interpolation(nc, parents[i]))
-        R.append(restriction(nc, parents[i]))
+        if opts.restriction == "star0":
+            lc, lf = levels[i - first], levels[i - first + 1]
+            R.append(restriction_star0(nc, parents[i], lc.star0, lf.star0))
+        else:
+            R.append(restriction(nc, parents[i]))
     return Hierarchy(levels, P, R, bc, opts)
 
 

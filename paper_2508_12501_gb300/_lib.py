@@ -25,6 +25,7 @@ DEC_NOALLOC_SCRATCH_BYTES = 32 << 20
 DEC_BC_DIRICHLET, DEC_BC_GAUGE = 0, 1
 DEC_F64, DEC_F32 = 0, 1
 DEC_SMOOTH_JACOBI, DEC_SMOOTH_CHEBYSHEV, DEC_SMOOTH_MCGS = 0, 1, 2
+DEC_RESTRICT_ROWNORM, DEC_RESTRICT_STAR0 = 0, 1
 DEC_SOLVER_MG, DEC_SOLVER_MGPCG, DEC_SOLVER_CG = 0, 1, 2
 DEC_MODE_F64, DEC_MODE_MIXED = 0, 1
 (DEC_TABLE_VERTS, DEC_TABLE_TRIS, DEC_TABLE_EDGES, DEC_TABLE_STAR0, DEC_TABLE_STAR1,
@@ -36,7 +37,8 @@ STATUS_NAMES = {0: "DEC_OK", 1: "DEC_ERR_ARG", 2: "DEC_ERR_MESH", 3: "DEC_ERR_CU
 
 class dec_mg_opts(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
-                ("cheby_lo", C.c_double), ("cheby_hi", C.c_double), ("power_iters", C.c_int), ("gamma", C.c_int)]
+                ("cheby_lo", C.c_double), ("cheby_hi", C.c_double), ("power_iters", C.c_int), ("gamma", C.c_int),
+                ("restriction", C.c_int)]
 
 
 class dec_solve_opts(C.Structure):

@@ -18,6 +18,7 @@ SMOOTHERS = {"jacobi": L.DEC_SMOOTH_JACOBI, "chebyshev": L.DEC_SMOOTH_CHEBYSHEV,
 SOLVERS = {"mg": L.DEC_SOLVER_MG, "mgpcg": L.DEC_SOLVER_MGPCG, "cg": L.DEC_SOLVER_CG}
 MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED}
 BCS = {"dirichlet": L.DEC_BC_DIRICHLET, "gauge": L.DEC_BC_GAUGE}
+RESTRICTIONS = {"rownorm": L.DEC_RESTRICT_ROWNORM, "star0": L.DEC_RESTRICT_STAR0}
 TABLES = {"verts": L.DEC_TABLE_VERTS, "tris": L.DEC_TABLE_TRIS, "edges": L.DEC_TABLE_EDGES,
           "star0": L.DEC_TABLE_STAR0, "star1": L.DEC_TABLE_STAR1, "free": L.DEC_TABLE_FREE,
           "parents": L.DEC_TABLE_PARENTS, "colors": L.DEC_TABLE_COLORS}
@@ -90,7 +91,7 @@ class Hierarchy:
 
     def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
-                 host_only=False):
+                 restriction="rownorm", host_only=False):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
         o = L.dec_mg_opts()
@@ -99,6 +100,7 @@ class Hierarchy:
         o.nu1, o.nu2, o.omega = nu1, nu2, omega
         o.cheby_lo, o.cheby_hi = cheby_lo, cheby_hi
         o.power_iters, o.gamma = power_iters, gamma
+        o.restriction = RESTRICTIONS[restriction]
         flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0)
         scale = None
         if star1_scale is not None:

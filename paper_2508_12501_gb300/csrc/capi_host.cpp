@@ -34,6 +34,7 @@ void dec_mg_default_opts(dec_mg_opts *o) {
     o->cheby_hi = 1.1;
     o->power_iters = 10;
     o->gamma = 1;
+    o->restriction = DEC_RESTRICT_ROWNORM;
 }
 
 void dec_solve_default_opts(dec_solve_opts *o) {

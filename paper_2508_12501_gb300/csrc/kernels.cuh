@@ -140,9 +140,12 @@ __global__ void __launch_bounds__(kThreads) k_axpy1(int n, const T *__restrict__
 //   b_c[c] = (r_f[c] + 1/2 sum_{midpoints m adjacent to c} r_f[m]) / (1 + deg(c)/2).
 // The fine neighbours of a coarse vertex are exactly the midpoints of its
 // coarse edges, so the fine ELL row c lists them (padding: col == c).
-template <typename T, int KT>
+// With STAR0 the *0-adjoint of interpolation is applied instead:
+//   b_c[c] = (s_f[c] r_f[c] + 1/2 sum_m s_f[m] r_f[m]) / s_c[c],  s = *0.
+template <typename T, int KT, bool STAR0>
 __global__ void __launch_bounds__(kThreads) k_restrict(int nc, int nf, int Kf, const int32_t *__restrict__ colf,
                                                       const T *__restrict__ rf, T *__restrict__ bc,
+                                                      const T *__restrict__ s0f, const T *__restrict__ s0c,
                                                       const int *skip) {
     if (skipped(skip)) return;
     const int Kk = KT > 0 ? KT : Kf;
@@ -154,11 +157,14 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int nc, int nf, int Kf, c
             if (KT == 0 && k >= Kk) break;
             const int j = ldg(colf + (size_t)k * nf + c);
             if (j != c) {
-                acc += ldg(rf + j);
+                acc += STAR0 ? ldg(s0f + j) * ldg(rf + j) : ldg(rf + j);
                 ++deg;
             }
         }
-        bc[c] = (ldg(rf + c) + T(0.5) * acc) / (T(1) + T(0.5) * T(deg));
+        if (STAR0)
+            bc[c] = (ldg(s0f + c) * ldg(rf + c) + T(0.5) * acc) / ldg(s0c + c);
+        else
+            bc[c] = (ldg(rf + c) + T(0.5) * acc) / (T(1) + T(0.5) * T(deg));
     }
 }
 

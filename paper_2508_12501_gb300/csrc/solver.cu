@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -36,6 +37,7 @@ struct DevLevel {
     double *w64 = nullptr;
     float *w32 = nullptr;
     double *star0 = nullptr;
+    float *star0_32 = nullptr;
     uint8_t *freev = nullptr;
     int2 *par = nullptr;
     float *x32[2] = {nullptr, nullptr}, *d32[2] = {nullptr, nullptr}, *r32 = nullptr, *b32 = nullptr;
@@ -51,6 +53,7 @@ template <> struct P<float> {
     static float *r(DevLevel &L) { return L.r32; }
     static float *b(DevLevel &L) { return L.b32; }
     static const float *w(const DevLevel &L) { return L.w32; }
+    static const float *s0(const DevLevel &L) { return L.star0_32; }
 };
 template <> struct P<double> {
     static double *x(DevLevel &L, int i) { return L.x64[i]; }
@@ -58,6 +61,7 @@ template <> struct P<double> {
     static double *r(DevLevel &L) { return L.r64; }
     static double *b(DevLevel &L) { return L.b64; }
     static const double *w(const DevLevel &L) { return L.w64; }
+    static const double *s0(const DevLevel &L) { return L.star0; }
 };
 
 template <typename F>
@@ -322,8 +326,12 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
         }
         {
             ProfScope ps(mg, DEC_PK_RESTRICT, l, s);
-            k_restrict<T, KT><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
-                                                                    skip);
+            if (o.restriction == DEC_RESTRICT_STAR0)
+                k_restrict<T, KT, true><<<grid_for(mg, C.n), kThreads, 0, s>>>(
+                    C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C), P<T>::s0(L), P<T>::s0(C), skip);
+            else
+                k_restrict<T, KT, false><<<grid_for(mg, C.n), kThreads, 0, s>>>(
+                    C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C), nullptr, nullptr, skip);
         }
     });
     T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip);
@@ -552,7 +560,12 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         stats->rel_res0 = h->rel0;
         stats->launches = (mg->launches - launches0) + graph_launches * mg->graph_kernels[o.solver][o.mode];
     }
-    if (h->status == 1) return fail(Status::fail(DEC_ERR_NONFINITE, "non-finite residual"));
+    if (h->status == 1) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "non-finite residual at iteration %d (||b||^2 = %.3e, last rel = %.3e, rz = %.3e)",
+                 h->iter, h->bnorm2, h->iter > 0 ? h->hist[std::min(h->iter - 1, kHist - 1)] : 0.0, h->rz);
+        return fail(Status::fail(DEC_ERR_NONFINITE, buf));
+    }
     if (!(h->rel <= o.tol)) return fail(Status::fail(DEC_ERR_NOT_CONVERGED, "maxit reached before tol"));
     return rc;
 }
@@ -584,6 +597,8 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         dec_mg_default_opts(&o);
     if (o.smoother != DEC_SMOOTH_JACOBI && o.smoother != DEC_SMOOTH_CHEBYSHEV)
         return fail(Status::fail(DEC_ERR_ARG, "smoother not available"));
+    if (o.restriction != DEC_RESTRICT_ROWNORM && o.restriction != DEC_RESTRICT_STAR0)
+        return fail(Status::fail(DEC_ERR_ARG, "unknown restriction"));
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma != 1 || o.power_iters < 1 ||
         !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad multigrid options"));
@@ -628,6 +643,10 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         if ((rc = upload(mg, &D.w64, HL.w.data(), slots))) return bail(rc);
         if ((rc = upload(mg, &D.w32, w32.data(), slots))) return bail(rc);
         if ((rc = upload(mg, &D.star0, HL.star0.data(), D.n))) return bail(rc);
+        {
+            std::vector<float> s32(HL.star0.begin(), HL.star0.end());
+            if ((rc = upload(mg, &D.star0_32, s32.data(), D.n))) return bail(rc);
+        }
         if ((rc = upload(mg, &D.freev, HL.free_.data(), D.n))) return bail(rc);
         if (l > 0) {
             const std::vector<int32_t> &par = mg->H.parents[l - 1];
@@ -968,7 +987,12 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         k_residual<float, KT><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B[l].x[cur], B[l].r, nullptr);
-        k_restrict<float, KT><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, B[l].r, B[l - 1].b, nullptr);
+        if (o.restriction == DEC_RESTRICT_STAR0)
+            k_restrict<float, KT, true><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, B[l].r, B[l - 1].b,
+                                                                              L.star0_32, C.star0_32, nullptr);
+        else
+            k_restrict<float, KT, false><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, B[l].r,
+                                                                               B[l - 1].b, nullptr, nullptr, nullptr);
     });
     float *ec = noalloc_cycle(mg, B, l - 1, B[l - 1].b, s);
     k_prolong<float><<<g, kThreads, 0, s>>>(C.n, L.n, L.par, ec, B[l].x[cur], nullptr);
@@ -1065,6 +1089,7 @@ int porous_one_step(PorousRun &R, const double *T_in, double *P, double *T_out) 
     });
     dec_stats st{};
     int rc = solve_impl(mg, mg->prhs, P, &R.so, &st, R.s);
+    if (rc != DEC_OK) decimpl::set_error("pressure solve: " + std::string(dec_last_error()));
     R.iters += st.iters;
     R.worst = std::max(R.worst, st.rel_res);
     R.launches += st.launches + 2;
@@ -1093,6 +1118,7 @@ int porous_adjoint_step(PorousRun &R, const double *T, const double *P, double *
     dec_solve_opts so = R.so;  // adjoint pressure solve, warm-started from the previous m
     dec_stats st{};
     int rc = solve_impl(mg, pbs, m, &so, &st, R.s);
+    if (rc != DEC_OK) decimpl::set_error("adjoint pressure solve: " + std::string(dec_last_error()));
     R.iters += st.iters;
     R.worst = std::max(R.worst, st.rel_res);
     R.launches += st.launches + 3;
@@ -1232,8 +1258,10 @@ int dec_porous_backward(dec_mg *mg, const double *T0, const double *P0, const ui
             std::swap(A, B);
         }
         for (int j = len - 1; j >= 0; --j)
-            if ((rc = porous_adjoint_step(R, segT + (size_t)j * n, segP + (size_t)j * n, lam, out, ms, pbs, m)))
+            if ((rc = porous_adjoint_step(R, segT + (size_t)j * n, segP + (size_t)j * n, lam, out, ms, pbs, m))) {
+                decimpl::set_error("adjoint step " + std::to_string(first + j) + ": " + std::string(dec_last_error()));
                 return done(rc);
+            }
     }
     CKW(cudaMemcpyAsync(grad_T0, lam, vb, cudaMemcpyDeviceToDevice, R.s));
     return done(DEC_OK);

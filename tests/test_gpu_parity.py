@@ -44,14 +44,16 @@ CASES = {
 _cache = {}
 
 
-def _pair(name, smoother="jacobi", nu=2):
-    key = (name, smoother, nu)
+def _pair(name, smoother="jacobi", nu=2, restriction="rownorm"):
+    key = (name, smoother, nu, restriction)
     if key not in _cache:
         P = _lib()
         base, nsub, nl, bc, sph = CASES[name]
         v, t = base()
-        h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, nu1=nu, nu2=nu)
-        oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, opts=omg.MGOptions(smoother=smoother, nu1=nu, nu2=nu))
+        h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, nu1=nu, nu2=nu,
+                        restriction=restriction)
+        oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph,
+                                 opts=omg.MGOptions(smoother=smoother, nu1=nu, nu2=nu, restriction=restriction))
         _cache[key] = (h, oh)
     return _cache[key]
 
@@ -103,8 +105,9 @@ def _s0_rel(lev, a, b):
 @pytest.mark.parametrize("name", ["square5", "ico5", "fan3", "grid_ragged"])
 @pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_one_cycle_matches_oracle(name, smoother, prec):
-    h, oh = _pair(name, smoother)
+@pytest.mark.parametrize("restriction", ["rownorm", "star0"])
+def test_one_cycle_matches_oracle(name, smoother, prec, restriction):
+    h, oh = _pair(name, smoother, restriction=restriction)
     lev = oh.finest
     b = omg.prepare_rhs(oh, W.uniform_field(lev.mesh.nv, 21))
     ref = omg.vcycle(oh, b, np.zeros_like(b))

@@ -22,6 +22,11 @@ def _square(nsub, nlevels, **kw):
     return mg.build_hierarchy(v, t, nsub, nlevels, "dirichlet", opts=mg.MGOptions(**kw))
 
 
+def _square_gauge(nsub, nlevels, **kw):
+    v, t = W.unit_square()
+    return mg.build_hierarchy(v, t, nsub, nlevels, "gauge", opts=mg.MGOptions(**kw))
+
+
 def _ico(nsub, nlevels, **kw):
     v, t = W.icosahedron()
     return mg.build_hierarchy(v, t, nsub, nlevels, "gauge", sphere=True, opts=mg.MGOptions(**kw))
@@ -192,3 +197,33 @@ def test_w_cycle_converges_faster_than_v():
     rw = mg.mg_solve(hw, b, 1e-10, 60)
     assert rw.iters <= rv.iters
     assert np.allclose(rw.x, rv.x, atol=1e-9 * np.abs(rv.x).max())
+
+
+@pytest.mark.parametrize("which", ["square", "ico"])
+def test_star0_restriction_is_adjoint_of_interpolation(which):
+    # <R r, e>_{*0 coarse} = <r, P e>_{*0 fine}, and on a uniform interior vertex it equals the paper's R
+    if which == "square":
+        h = _square(4, 2, restriction="star0"); hp = _square(4, 2)
+    else:
+        h = _ico(3, 2, restriction="star0"); hp = _ico(3, 2)
+    c, f = h.levels[0], h.levels[1]
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(f.mesh.nv)
+    e = rng.standard_normal(c.mesh.nv)
+    lhs = np.sum(c.star0 * (h.R[0] @ r) * e)
+    rhs = np.sum(f.star0 * r * (h.P[0] @ e))
+    assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + np.sum(np.abs(c.star0 * e)) * np.abs(r).max())
+    if which == "square":
+        xy = c.mesh.verts
+        inner = (xy[:, 0] > 0) & (xy[:, 0] < 1) & (xy[:, 1] > 0) & (xy[:, 1] < 1)
+        assert np.allclose((h.R[0] @ r)[inner], (hp.R[0] @ r)[inner], rtol=1e-13, atol=1e-14)
+
+
+def test_star0_restriction_keeps_pcg_stable_on_boundary_data():
+    # data concentrated next to the boundary: the paper's R gives a non-symmetric preconditioner there
+    h = _square_gauge(6, 5, restriction="star0")
+    lev = h.finest
+    y = lev.mesh.verts[:, 1]
+    b = np.where(np.abs(y - (1 - 1.0 / 64)) < 1e-12, W.uniform_field(lev.mesh.nv, 9) * 1e5, 0.0)
+    r = mg.pcg_solve(h, b, 1e-10, 60)
+    assert r.rel_res <= 1e-10 and r.iters < 20
