@@ -52,13 +52,14 @@ def bytes_per_row(kind, K, mixed, cheb):
     if kind == "residual":
         return K * 4 + K * f + 3 * f
     if kind == "spmv64":
-        return K * 4 + K * 8 + 8 + 8 + 8 + 1
+        return K * 4 + K * 8 + 8 + 8 + 8  # col, w64, p_i, q, *0
     if kind == "update":
         return 8 + 8 + 16 + 16 + (4 if mixed else 0)
     if kind == "zdots":
-        return f + 8 + 8 + 8 + 8 + 1  # z, zn write, *0, r, z_old, free flag
+        # mixed: *0 (f32), free, z, r32, z_old (f32); f64: z, zn write, *0, r, z_old, free
+        return (4 + 1 + 4 + 4 + 4) if mixed else (8 + 8 + 8 + 8 + 8 + 1)
     if kind == "pupd":
-        return 8 + 1 + 8 + 16
+        return (1 + 4 + 4 + 16) if mixed else (8 + 1 + 8 + 16)
     return None
 
 

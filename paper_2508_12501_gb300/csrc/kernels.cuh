@@ -17,7 +17,7 @@
 namespace decdev {
 
 constexpr int kThreads = 256;
-constexpr int kMaxRedBlocks = 1024;  // partial-sum slots per reduction
+constexpr int kMaxRedBlocks = 2048;  // partial-sum slots per reduction
 constexpr int kHist = 1024;          // residual history entries
 
 // Scalars of the outer iteration, resident in device memory.
@@ -30,8 +30,17 @@ struct Scal {
     double star0_sum;   // sum of *0 over free vertices
     double mean;        // result of the last k_mean
     int iter, maxit, done, status;  // status: 0 ok, 1 non-finite
+    int loops, max_loops;           // device-side iteration loop: executions and hard cap
     double hist[kHist];
 };
+
+// Programmatic dependent launch: let the next kernel in the stream start its
+// launch now, then wait until the previous kernel has finished and its writes
+// are visible.  Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 __device__ __forceinline__ bool skipped(const int *skip) { return skip != nullptr && *skip != 0; }
 
@@ -64,6 +73,7 @@ template <typename T, int KT>
 __global__ void __launch_bounds__(kThreads) k_apply(int n, int K, const int32_t *__restrict__ col,
                                                    const T *__restrict__ w, const T *__restrict__ x,
                                                    T *__restrict__ y, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) {
         T s, d;
@@ -78,6 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, int K, const int32
                                                       const T *__restrict__ w, const T *__restrict__ b,
                                                       const T *__restrict__ x, T *__restrict__ r,
                                                       const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) {
         T s, d;
@@ -97,6 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth(int n, int K, const int32_t
                                                     const T *__restrict__ x_in, const T *__restrict__ d_in,
                                                     T *__restrict__ x_out, T *__restrict__ d_out, T c, T e,
                                                     const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) {
         T s, d;
@@ -113,6 +125,7 @@ template <typename T, int KT, bool DOUT>
 __global__ void __launch_bounds__(kThreads) k_smooth0(int n, int K, const T *__restrict__ w,
                                                      const T *__restrict__ b, T *__restrict__ x_out,
                                                      T *__restrict__ d_out, T e, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     const int Kk = KT > 0 ? KT : K;
     GRID_STRIDE(i, n) {
@@ -132,6 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth0(int n, int K, const T *__r
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_axpy1(int n, const T *__restrict__ e, T *__restrict__ x,
                                                    const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) x[i] += ldg(e + i);
 }
@@ -147,6 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int nc, int nf, int Kf, c
                                                       const T *__restrict__ rf, T *__restrict__ bc,
                                                       const T *__restrict__ s0f, const T *__restrict__ s0c,
                                                       const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     const int Kk = KT > 0 ? KT : Kf;
     GRID_STRIDE(c, nc) {
@@ -174,6 +189,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong(int nc, int nf, const int2 *__restrict__ par,
                                                      const T *__restrict__ ec, T *__restrict__ xf,
                                                      const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(v, nf) {
         T add;
@@ -191,6 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(int nc, int nf, const int2
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coarse(int n0, const T *__restrict__ G, const T *__restrict__ b,
                                                     T *__restrict__ x, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -207,6 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse(int n0, const T *__restrict
 template <typename TD, typename TS>
 __global__ void __launch_bounds__(kThreads) k_cast(int n, const TS *__restrict__ src, TD *__restrict__ dst,
                                                   const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) dst[i] = (TD)ldg(src + i);
 }
@@ -215,6 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_cast(int n, const TS *__restrict__
 template <typename TE>
 __global__ void __launch_bounds__(kThreads) k_add(int n, const TE *__restrict__ e, double *__restrict__ x,
                                                  const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) x[i] += (double)ldg(e + i);
 }
@@ -230,17 +249,25 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Returns true in every thread of the last block; tot[] then holds the
 // grid-wide sums.  Requires blockDim.x == kThreads and gridDim.x <= kMaxRedBlocks.
-template <int NS>
-__device__ bool grid_reduce(double (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
+// The per-thread values (type TV) are summed across the warp in TV; warp sums
+// are then combined in double, so FP32 partials cost no FP64 instructions per thread.
+template <int NS, typename TV>
+__device__ bool grid_reduce(TV (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
     __shared__ double sh[NS][kThreads / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        double x = warp_sum(v[s]);
-        if (lane == 0) sh[s][warp] = x;
+        TV x = warp_sum(v[s]);
+        if (lane == 0) sh[s][warp] = (double)x;
     }
     __syncthreads();
     if (warp == 0) {
@@ -293,16 +320,18 @@ __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
 __global__ void __launch_bounds__(kThreads) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                   const double *__restrict__ v, double *partials, unsigned *counter,
                                                   Scal *S, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     double acc[1] = {0.0};
     GRID_STRIDE(i, n) if (freev[i]) acc[0] += ldg(star0 + i) * ldg(v + i);
     double tot[1];
-    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] / S->star0_sum;
+    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] / S->star0_sum;
 }
 
 // v -= mean on free rows
 __global__ void __launch_bounds__(kThreads) k_shift(int n, const uint8_t *__restrict__ freev, double *__restrict__ v,
                                                    const Scal *S, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     const double m = S->mean;
     GRID_STRIDE(i, n) v[i] = freev[i] ? v[i] - m : 0.0;
@@ -316,6 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_init(int n, int K, const int
                                                         const double *__restrict__ b, const double *__restrict__ x,
                                                         double *__restrict__ r, TV *__restrict__ rv, double *partials,
                                                         unsigned *counter, Scal *S) {
+    pdl_prologue();
     double acc[2] = {0.0, 0.0};
     GRID_STRIDE(i, n) {
         double s, d;
@@ -328,7 +358,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_init(int n, int K, const int
         acc[1] += bi * bi;
     }
     double tot[2];
-    if (grid_reduce<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<2, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->bnorm2 = tot[1];
         S->iter = 0;
         S->done = 0;
@@ -346,6 +376,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__r
                                                        const double *__restrict__ r, const double *__restrict__ zo,
                                                        int first, int gauge, double *partials, unsigned *counter,
                                                        Scal *S, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     GRID_STRIDE(i, n) {
@@ -360,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__r
         }
     }
     double tot[4];
-    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<4, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
         double c = gauge ? tot[0] / S->star0_sum : 0.0;
         double rz_new = tot[1] - c * tot[3];
         S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
@@ -373,6 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__r
 __global__ void __launch_bounds__(kThreads) k_pcg_pupd(int n, const uint8_t *__restrict__ freev, const double *__restrict__ zn,
                                                       double *__restrict__ zo, double *__restrict__ p, int first,
                                                       const Scal *S, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     const double c = S->c, beta = S->beta;
     GRID_STRIDE(i, n) {
@@ -389,6 +421,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(int n, int K, const int32
                                                       const uint8_t *__restrict__ freev, const double *__restrict__ p,
                                                       double *__restrict__ q, double *partials, unsigned *counter,
                                                       Scal *S, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     double acc[1] = {0.0};
     GRID_STRIDE(i, n) {
@@ -399,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(int n, int K, const int32
         acc[0] += ldg(star0 + i) * ldg(p + i) * qi;
     }
     double tot[1];
-    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
+    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
 }
 
 // x += alpha p, r -= alpha q, rv = (TV) r, ||r||^2 -> convergence test
@@ -407,6 +440,7 @@ template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
                                                         double *__restrict__ x, double *__restrict__ r, TV *__restrict__ rv,
                                                         double *partials, unsigned *counter, Scal *S, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     const double a = S->alpha;
     double acc[1] = {0.0};
@@ -418,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, const double *__
         acc[0] += ri * ri;
     }
     double tot[1];
-    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->iter += 1;
         record_residual(S, tot[0]);
     }
@@ -431,6 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_mg_residual(int n, int K, const in
                                                          const double *__restrict__ b, const double *__restrict__ x,
                                                          double *__restrict__ r, TV *__restrict__ rv, double *partials,
                                                          unsigned *counter, Scal *S, const int *skip) {
+    pdl_prologue();
     if (skipped(skip)) return;
     double acc[1] = {0.0};
     GRID_STRIDE(i, n) {
@@ -442,15 +477,171 @@ __global__ void __launch_bounds__(kThreads) k_mg_residual(int n, int K, const in
         acc[0] += ri * ri;
     }
     double tot[1];
-    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->iter += 1;
         record_residual(S, tot[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Outer-iteration kernels with few FP64 instructions per row.  GB300 issues
+// FP64 at a small fraction of its FP32 rate.  The operator apply keeps the
+// difference form sum_k w_k (x_i - x_k) -- for smooth x the differences are
+// exact, whereas the diagonal form L_ii x_i - sum_k w_k x_k cancels and
+// limits the attainable residual -- but drops the FP64 diagonal sum: fixed
+// rows have all weights 0 and come out 0 without a mask.  In mixed
+// precision the dot products that steer alpha, beta, the gauge shift and the
+// stopping test use FP32 copies, FP32 products and FP32 warp sums (combined
+// in FP64 across warps and blocks).  The x and r updates stay FP64.
+// ---------------------------------------------------------------------------
+
+template <int KT>
+__device__ __forceinline__ double row_apply_nod(int i, int n, int K, const int32_t *__restrict__ col,
+                                                const double *__restrict__ w, const double *__restrict__ x) {
+    const int Kk = KT > 0 ? KT : K;
+    const double xi = ldg(x + i);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+        if (KT == 0 && k >= Kk) break;
+        const size_t o = (size_t)k * n + i;
+        s = fma(ldg(w + o), xi - ldg(x + ldg(col + o)), s);
+    }
+    return s;
+}
+
+// q = L p, <p, q> (*0) -> alpha
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_pcg_spmv_d(int n, int K, const int32_t *__restrict__ col,
+                                                        const double *__restrict__ w,
+                                                        const double *__restrict__ star0, const double *__restrict__ p,
+                                                        double *__restrict__ q, double *partials, unsigned *counter,
+                                                        Scal *S, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) {
+        const double qi = row_apply_nod<KT>(i, n, K, col, w, p);
+        q[i] = qi;
+        acc[0] = fma(ldg(star0 + i) * ldg(p + i), qi, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
+}
+
+// x += alpha p, r -= alpha q (FP64), r32 = (float) r, ||r||^2 from r32
+__global__ void __launch_bounds__(kThreads) k_pcg_update_m(int n, const double *__restrict__ p,
+                                                          const double *__restrict__ q, double *__restrict__ x,
+                                                          double *__restrict__ r, float *__restrict__ r32,
+                                                          double *partials, unsigned *counter, Scal *S,
+                                                          const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const double a = S->alpha;
+    float acc[1] = {0.f};
+    GRID_STRIDE(i, n) {
+        x[i] = fma(a, ldg(p + i), x[i]);
+        const double ri = fma(-a, ldg(q + i), r[i]);
+        r[i] = ri;
+        const float rf = (float)ri;
+        r32[i] = rf;
+        acc[0] = fmaf(rf, rf, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1, float>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->iter += 1;
+        record_residual(S, tot[0]);
+    }
+}
+
+// FP32 dot products of the preconditioned vector z (cycle output) with r32 and the previous z.
+__global__ void __launch_bounds__(kThreads) k_pcg_zdots_m(int n, const float *__restrict__ s032,
+                                                         const uint8_t *__restrict__ freev, const float *__restrict__ z,
+                                                         const float *__restrict__ r32, const float *__restrict__ zo,
+                                                         int first, int gauge, double *partials, unsigned *counter,
+                                                         Scal *S, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    GRID_STRIDE(i, n) {
+        if (freev[i]) {
+            const float s0 = ldg(s032 + i), zi = ldg(z + i), ri = ldg(r32 + i);
+            const float sr = s0 * ri;
+            acc[0] = fmaf(s0, zi, acc[0]);
+            acc[1] = fmaf(sr, zi, acc[1]);
+            if (!first) acc[2] = fmaf(sr, ldg(zo + i), acc[2]);
+            acc[3] += sr;
+        }
+    }
+    double tot[4];
+    if (grid_reduce<4, float>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        double c = gauge ? tot[0] / S->star0_sum : 0.0;
+        double rz_new = tot[1] - c * tot[3];
+        S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
+        S->rz = rz_new;
+        S->c = c;
+    }
+}
+
+// z = z - c (free rows, FP32), zo = z, p = z + beta p (FP64)
+__global__ void __launch_bounds__(kThreads) k_pcg_pupd_m(int n, const uint8_t *__restrict__ freev,
+                                                        const float *__restrict__ z, float *__restrict__ zo,
+                                                        double *__restrict__ p, int first, const Scal *S,
+                                                        const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const float c = (float)S->c;
+    const double beta = S->beta;
+    GRID_STRIDE(i, n) {
+        const float zi = freev[i] ? ldg(z + i) - c : 0.f;
+        zo[i] = zi;
+        p[i] = first ? (double)zi : fma(beta, p[i], (double)zi);
+    }
+}
+
+// Standalone MG / iterative refinement (mixed): r = b - L x; r32; ||r||^2 in FP32.
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_mg_residual_m(int n, int K, const int32_t *__restrict__ col,
+                                                           const double *__restrict__ w,
+                                                           const uint8_t *__restrict__ freev,
+                                                           const double *__restrict__ b, const double *__restrict__ x,
+                                                           double *__restrict__ r, float *__restrict__ r32,
+                                                           double *partials, unsigned *counter, Scal *S,
+                                                           const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    float acc[1] = {0.f};
+    GRID_STRIDE(i, n) {
+        const double s = row_apply_nod<KT>(i, n, K, col, w, x);
+        const double ri = freev[i] ? ldg(b + i) - s : 0.0;
+        r[i] = ri;
+        const float rf = (float)ri;
+        r32[i] = rf;
+        acc[0] = fmaf(rf, rf, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1, float>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->iter += 1;
+        record_residual(S, tot[0]);
+    }
+}
+
+// Body-end kernel of the device-side iteration loop (a while node of the
+// solve graph): repeat while the solve is not done, and never more than
+// max_loops times, so the loop ends even if no kernel ever sets `done`.
+__global__ void k_loop_ctrl(cudaGraphConditionalHandle h, Scal *S) {
+    pdl_prologue();
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        S->loops += 1;
+        const bool more = !S->done && S->loops < S->max_loops;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
     }
 }
 
 // Gradient with respect to the edge weights: g_e = -(d0 mu)_e (d0 u)_e.
 __global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const int2 *__restrict__ edges, const double *__restrict__ mu,
                                                        const double *__restrict__ u, double *__restrict__ g) {
+    pdl_prologue();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
         const int2 ab = ldg(edges + e);
         g[e] = -(ldg(mu + ab.y) - ldg(mu + ab.x)) * (ldg(u + ab.y) - ldg(u + ab.x));
@@ -460,6 +651,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const int2 *
 // y = s0 .* x, or y = x ./ s0 (inverse != 0)
 __global__ void __launch_bounds__(kThreads) k_star0_scale(int n, const double *__restrict__ star0, const double *x,
                                                          double *y, int inverse) {
+    pdl_prologue();
     GRID_STRIDE(i, n) y[i] = inverse ? x[i] / ldg(star0 + i) : x[i] * ldg(star0 + i);
 }
 
@@ -468,6 +660,7 @@ __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const in
                                                          const double *__restrict__ star1, const double *__restrict__ star0,
                                                          const uint8_t *__restrict__ freev, double *__restrict__ w64,
                                                          float *__restrict__ w32) {
+    pdl_prologue();
     GRID_STRIDE(i, n) {
         const double s0 = ldg(star0 + i);
         for (int k = 0; k < K; ++k) {
@@ -492,6 +685,7 @@ __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const in
 
 __global__ void __launch_bounds__(kThreads) k_potential(int n, int dim, const double *__restrict__ verts, double g0,
                                                        double g1, double g2, double arho, double *__restrict__ pot) {
+    pdl_prologue();
     GRID_STRIDE(v, n) {
         const double *x = verts + (size_t)v * dim;
         double s = g0 * x[0] + g1 * x[1];
@@ -505,6 +699,7 @@ template <int KT>
 __global__ void __launch_bounds__(kThreads) k_porous_rhs(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w, const double *__restrict__ T,
                                                         const double *__restrict__ pot, double *__restrict__ rhs) {
+    pdl_prologue();
     const int Kk = KT > 0 ? KT : K;
     GRID_STRIDE(v, n) {
         const double Tv = ldg(T + v), pv = ldg(pot + v);
@@ -528,6 +723,7 @@ __global__ void __launch_bounds__(kThreads) k_porous_update(int n, int K, const 
                                                            const uint8_t *__restrict__ fixed, double inv_phi,
                                                            double k_eta, double kappa, double dt,
                                                            double *__restrict__ T_out) {
+    pdl_prologue();
     const int Kk = KT > 0 ? KT : K;
     GRID_STRIDE(v, n) {
         const double Tv = ldg(T + v);
@@ -557,6 +753,7 @@ __global__ void __launch_bounds__(kThreads) k_porous_adj1(int n, const double *_
                                                          const uint8_t *__restrict__ fixed,
                                                          const double *__restrict__ star0, double dt,
                                                          double *__restrict__ ms) {
+    pdl_prologue();
     GRID_STRIDE(v, n) ms[v] = fixed[v] ? 0.0 : dt * ldg(lam + v) / ldg(star0 + v);
 }
 
@@ -572,6 +769,7 @@ __global__ void __launch_bounds__(kThreads) k_porous_adj2(int n, int K, const in
                                                          const double *__restrict__ ms, double inv_phi, double k_eta,
                                                          double kappa, double *__restrict__ out,
                                                          double *__restrict__ pbs) {
+    pdl_prologue();
     const int Kk = KT > 0 ? KT : K;
     GRID_STRIDE(v, n) {
         const double Tv = ldg(T + v), Pv = ldg(P + v), pv = ldg(pot + v), mv = ldg(ms + v);
@@ -602,6 +800,7 @@ __global__ void __launch_bounds__(kThreads) k_porous_adj3(int n, int K, const in
                                                          const double *__restrict__ w, const double *__restrict__ star0,
                                                          const double *__restrict__ pot, const double *__restrict__ m,
                                                          double *__restrict__ out) {
+    pdl_prologue();
     const int Kk = KT > 0 ? KT : K;
     GRID_STRIDE(v, n) {
         const double mv = ldg(m + v), pv = ldg(pot + v);

@@ -90,6 +90,7 @@ struct dec_mg {
     double *pot = nullptr, *ptmp = nullptr, *prhs = nullptr;  // porous-step work vectors
     // outer-iteration workspace (finest level, FP64)
     double *ox = nullptr, *orr = nullptr, *op = nullptr, *oq = nullptr, *ozn = nullptr, *ozo = nullptr, *ob = nullptr;
+    float *zo32 = nullptr;     // previous preconditioned vector (mixed precision)
     double *tmp = nullptr;
     double *partials = nullptr;
     unsigned *counter = nullptr;
@@ -98,9 +99,14 @@ struct dec_mg {
     double star0_sum = 0.0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graphs[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    // whole iteration loop on the device: a while node around one iteration
+    cudaGraphExec_t loops[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    bool no_device_loop = false;  // set if the driver refuses conditional nodes
+    int64_t loop_kernels[3][2] = {};  // kernel nodes in one pass of a loop body
     std::vector<void *> allocs;
     size_t bytes = 0;
     bool host_only = false;
+    bool pdl = true;  // programmatic dependent launch between consecutive kernels
     // live kernel timing (dec_mg_profile)
     int64_t launches = 0;       // kernels enqueued outside graph capture
     int64_t graph_kernels[3][2] = {};  // kernel nodes per captured iteration graph
@@ -204,6 +210,12 @@ void drop_graphs(dec_mg *mg) {
                 cudaGraphExecDestroy(g);
                 g = nullptr;
             }
+    for (auto &row : mg->loops)
+        for (auto &g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
     clear_slots(mg);
 }
 
@@ -219,6 +231,24 @@ void accumulate_slots(dec_mg *mg) {
     }
 }
 
+// Every kernel goes through here: a plain launch, or one with programmatic
+// stream serialization (PDL) so that consecutive kernels overlap their launch
+// latency; inside stream capture this becomes a programmatic graph edge.
+template <typename... KArgs, typename... Args>
+inline void launch(const dec_mg *mg, void (*kernel)(KArgs...), int grid, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = mg->pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 inline int grid_for(const dec_mg *mg, int64_t n) {
     int64_t g = (n + kThreads - 1) / kThreads;
     int64_t cap = (int64_t)mg->nsm * 8;
@@ -227,7 +257,7 @@ inline int grid_for(const dec_mg *mg, int64_t n) {
 
 inline int red_grid(const dec_mg *mg, int64_t n) {
     int64_t g = (n + kThreads - 1) / kThreads;
-    int64_t cap = std::min<int64_t>(kMaxRedBlocks, (int64_t)mg->nsm * 4);
+    int64_t cap = std::min<int64_t>(kMaxRedBlocks, (int64_t)mg->nsm * 8);
     return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
@@ -273,9 +303,9 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
                 cur = 0;
                 ProfScope ps(mg, DEC_PK_SMOOTH0, l, s);
                 if (dout)
-                    k_smooth0<T, KT, true><<<g, kThreads, 0, s>>>(L.n, L.K, w, b, P<T>::x(L, 0), P<T>::d(L, 0), e, skip);
+                    launch(mg, k_smooth0<T, KT, true>, g, s, L.n, L.K, w, b, P<T>::x(L, 0), P<T>::d(L, 0), e, skip);
                 else
-                    k_smooth0<T, KT, false><<<g, kThreads, 0, s>>>(L.n, L.K, w, b, P<T>::x(L, 0), nullptr, e, skip);
+                    launch(mg, k_smooth0<T, KT, false>, g, s, L.n, L.K, w, b, P<T>::x(L, 0), nullptr, e, skip);
                 continue;
             }
             const int nxt = 1 - cur;
@@ -284,13 +314,13 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
             T *di = P<T>::d(L, cur), *dn = P<T>::d(L, nxt);
             ProfScope ps(mg, DEC_PK_SMOOTH, l, s);
             if (din && dout)
-                k_smooth<T, KT, true, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, di, xo, dn, c, e, skip);
+                launch(mg, k_smooth<T, KT, true, true>, g, s, L.n, L.K, L.col, w, b, xi, di, xo, dn, c, e, skip);
             else if (din)
-                k_smooth<T, KT, true, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, di, xo, nullptr, c, e, skip);
+                launch(mg, k_smooth<T, KT, true, false>, g, s, L.n, L.K, L.col, w, b, xi, di, xo, nullptr, c, e, skip);
             else if (dout)
-                k_smooth<T, KT, false, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, nullptr, xo, dn, c, e, skip);
+                launch(mg, k_smooth<T, KT, false, true>, g, s, L.n, L.K, L.col, w, b, xi, nullptr, xo, dn, c, e, skip);
             else
-                k_smooth<T, KT, false, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, xi, nullptr, xo, nullptr, c, e, skip);
+                launch(mg, k_smooth<T, KT, false, false>, g, s, L.n, L.K, L.col, w, b, xi, nullptr, xo, nullptr, c, e, skip);
             cur = nxt;
         }
     });
@@ -306,7 +336,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
         if constexpr (std::is_same<T, float>::value) G = mg->G32; else G = mg->G64;
         int g = (int)std::min<int64_t>(mg->nsm * 4, (L.n * 32 + kThreads - 1) / kThreads);
         ProfScope ps(mg, DEC_PK_COARSE, 0, s);
-        k_coarse<T><<<g, kThreads, 0, s>>>(L.n, G, b, P<T>::x(L, 0), skip);
+        launch(mg, k_coarse<T>, g, s, L.n, G, b, P<T>::x(L, 0), skip);
         return P<T>::x(L, 0);
     }
     const dec_mg_opts &o = mg->H.opts;
@@ -322,22 +352,22 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
         constexpr int KT = decltype(kt)::value;
         {
             ProfScope ps(mg, DEC_PK_RESIDUAL, l, s);
-            k_residual<T, KT><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, w, b, P<T>::x(L, cur), P<T>::r(L), skip);
+            launch(mg, k_residual<T, KT>, g, s, L.n, L.K, L.col, w, b, P<T>::x(L, cur), P<T>::r(L), skip);
         }
         {
             ProfScope ps(mg, DEC_PK_RESTRICT, l, s);
             if (o.restriction == DEC_RESTRICT_STAR0)
-                k_restrict<T, KT, true><<<grid_for(mg, C.n), kThreads, 0, s>>>(
+                launch(mg, k_restrict<T, KT, true>, grid_for(mg, C.n), s, 
                     C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C), P<T>::s0(L), P<T>::s0(C), skip);
             else
-                k_restrict<T, KT, false><<<grid_for(mg, C.n), kThreads, 0, s>>>(
+                launch(mg, k_restrict<T, KT, false>, grid_for(mg, C.n), s, 
                     C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C), nullptr, nullptr, skip);
         }
     });
     T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip);
     {
         ProfScope ps(mg, DEC_PK_PROLONG, l, s);
-        k_prolong<T><<<g, kThreads, 0, s>>>(C.n, L.n, L.par, ec, P<T>::x(L, cur), skip);
+        launch(mg, k_prolong<T>, g, s, C.n, L.n, L.par, ec, P<T>::x(L, cur), skip);
     }
     if (o.nu2 > 0) smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip);
     return P<T>::x(L, cur);
@@ -353,7 +383,7 @@ void enqueue_outer_init(dec_mg *mg, TV *rv, cudaStream_t s) {
     ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        k_outer_init<KT, TV><<<red_grid(mg, F.n), kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox,
+        launch(mg, k_outer_init<KT, TV>, red_grid(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox,
                                                                     mg->orr, rv, mg->partials, mg->counter, mg->scal);
     });
 }
@@ -362,8 +392,8 @@ void enqueue_mean_shift(dec_mg *mg, double *v, cudaStream_t s, const int *skip) 
     DevLevel &F = mg->lv.back();
     const int top = (int)mg->lv.size() - 1;
     ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
-    k_mean<<<red_grid(mg, F.n), kThreads, 0, s>>>(F.n, F.star0, F.freev, v, mg->partials, mg->counter, mg->scal, skip);
-    k_shift<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.freev, v, mg->scal, skip);
+    launch(mg, k_mean, red_grid(mg, F.n), s, F.n, F.star0, F.freev, v, mg->partials, mg->counter, mg->scal, skip);
+    launch(mg, k_shift, grid_for(mg, F.n), s, F.n, F.freev, v, mg->scal, skip);
 }
 
 // z <- M r, then the dot products and the new search direction.
@@ -374,21 +404,29 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
     const int top = (int)mg->lv.size() - 1;
     if (solver == DEC_SOLVER_CG) {
         ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
-        k_pcg_zdots<double><<<rg, kThreads, 0, s>>>(F.n, F.star0, F.freev, mg->orr, mg->ozn, mg->orr, mg->ozo, first,
+        launch(mg, k_pcg_zdots<double>, rg, s, F.n, F.star0, F.freev, mg->orr, mg->ozn, mg->orr, mg->ozo, first,
                                                     gauge, mg->partials, mg->counter, mg->scal, skip);
     } else if (mode == DEC_MODE_MIXED) {
+        // z (FP32 cycle output) and r32 feed FP32 dot products; p is updated in FP64
         float *z = cycle<float>(mg, top, F.b32, s, skip);
-        ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
-        k_pcg_zdots<float><<<rg, kThreads, 0, s>>>(F.n, F.star0, F.freev, z, mg->ozn, mg->orr, mg->ozo, first, gauge,
-                                                   mg->partials, mg->counter, mg->scal, skip);
+        {
+            ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
+            launch(mg, k_pcg_zdots_m, rg, s, F.n, (const float *)F.star0_32, (const uint8_t *)F.freev, (const float *)z,
+                   (const float *)F.b32, (const float *)mg->zo32, first ? 1 : 0, gauge, mg->partials, mg->counter,
+                   mg->scal, skip);
+        }
+        ProfScope ps(mg, DEC_PK_PUPD, top, s);
+        launch(mg, k_pcg_pupd_m, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
+               mg->op, first ? 1 : 0, (const Scal *)mg->scal, skip);
+        return;
     } else {
         double *z = cycle<double>(mg, top, mg->orr, s, skip);
         ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
-        k_pcg_zdots<double><<<rg, kThreads, 0, s>>>(F.n, F.star0, F.freev, z, mg->ozn, mg->orr, mg->ozo, first, gauge,
+        launch(mg, k_pcg_zdots<double>, rg, s, F.n, F.star0, F.freev, z, mg->ozn, mg->orr, mg->ozo, first, gauge,
                                                     mg->partials, mg->counter, mg->scal, skip);
     }
     ProfScope ps(mg, DEC_PK_PUPD, top, s);
-    k_pcg_pupd<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.freev, mg->ozn, mg->ozo, mg->op, first ? 1 : 0, mg->scal,
+    launch(mg, k_pcg_pupd, grid_for(mg, F.n), s, F.n, F.freev, mg->ozn, mg->ozo, mg->op, first ? 1 : 0, mg->scal,
                                                       skip);
 }
 
@@ -400,16 +438,16 @@ void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         ProfScope ps(mg, DEC_PK_SPMV64, top, s);
-        k_pcg_spmv<KT><<<rg, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.star0, F.freev, mg->op, mg->oq, mg->partials,
-                                               mg->counter, mg->scal, skip);
+        launch(mg, k_pcg_spmv_d<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
+               (const double *)F.star0, (const double *)mg->op, mg->oq, mg->partials, mg->counter, mg->scal, skip);
     });
     {
     ProfScope ps(mg, DEC_PK_UPDATE, top, s);
     if (mode == DEC_MODE_MIXED && solver != DEC_SOLVER_CG)
-        k_pcg_update<float><<<rg, kThreads, 0, s>>>(F.n, mg->op, mg->oq, mg->ox, mg->orr, F.b32, mg->partials,
-                                                    mg->counter, mg->scal, skip);
+        launch(mg, k_pcg_update_m, rg, s, F.n, (const double *)mg->op, (const double *)mg->oq, mg->ox, mg->orr, F.b32,
+               mg->partials, mg->counter, mg->scal, skip);
     else
-        k_pcg_update<double><<<rg, kThreads, 0, s>>>(F.n, mg->op, mg->oq, mg->ox, mg->orr, nullptr, mg->partials,
+        launch(mg, k_pcg_update<double>, rg, s, F.n, mg->op, mg->oq, mg->ox, mg->orr, nullptr, mg->partials,
                                                      mg->counter, mg->scal, skip);
     }
     enqueue_precondition(mg, solver, mode, false, s, skip);
@@ -424,24 +462,25 @@ void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
         float *e = cycle<float>(mg, top, F.b32, s, skip);
         {
             ProfScope ps(mg, DEC_PK_ADD, top, s);
-            k_add<float><<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, e, mg->ox, skip);
+            launch(mg, k_add<float>, grid_for(mg, F.n), s, F.n, e, mg->ox, skip);
         }
         dispatch_k(F.K, [&](auto kt) {
             constexpr int KT = decltype(kt)::value;
             ProfScope ps(mg, DEC_PK_MGRES, top, s);
-            k_mg_residual<KT, float><<<rg, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox, mg->orr,
-                                                             F.b32, mg->partials, mg->counter, mg->scal, skip);
+            launch(mg, k_mg_residual_m<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
+                   (const uint8_t *)F.freev, (const double *)mg->ob,
+                   (const double *)mg->ox, mg->orr, F.b32, mg->partials, mg->counter, mg->scal, skip);
         });
     } else {
         double *e = cycle<double>(mg, top, mg->orr, s, skip);
         {
             ProfScope ps(mg, DEC_PK_ADD, top, s);
-            k_add<double><<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, e, mg->ox, skip);
+            launch(mg, k_add<double>, grid_for(mg, F.n), s, F.n, e, mg->ox, skip);
         }
         dispatch_k(F.K, [&](auto kt) {
             constexpr int KT = decltype(kt)::value;
             ProfScope ps(mg, DEC_PK_MGRES, top, s);
-            k_mg_residual<KT, double><<<rg, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox, mg->orr,
+            launch(mg, k_mg_residual<KT, double>, rg, s, F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox, mg->orr,
                                                               (double *)nullptr, mg->partials, mg->counter, mg->scal,
                                                               skip);
         });
@@ -491,6 +530,70 @@ int iteration_graph(dec_mg *mg, int solver, int mode, cudaGraphExec_t *out) {
     return DEC_OK;
 }
 
+// The whole iteration loop as one graph: while (!done && loops < max_loops) { iteration }.
+int loop_graph(dec_mg *mg, int solver, int mode, cudaGraphExec_t *out) {
+    cudaGraphExec_t &slot = mg->loops[solver][mode];
+    if (slot) {
+        *out = slot;
+        return DEC_OK;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hnd;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNode_t node;
+    cudaGraphNodeParams np = {};
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hnd;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        mg->no_device_loop = true;
+        return DEC_ERR_CUDA;
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(mg->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        mg->capturing = true;
+        if (solver == DEC_SOLVER_MG)
+            enqueue_mg_iteration(mg, mode, mg->cap);
+        else
+            enqueue_pcg_iteration(mg, solver, mode, mg->cap);
+        launch(mg, k_loop_ctrl, 1, mg->cap, hnd, mg->scal);
+        mg->capturing = false;
+        cudaError_t e1 = cudaGetLastError();
+        e = cudaStreamEndCapture(mg->cap, &body);
+        if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) {
+        size_t nn = 0;
+        cudaGraphGetNodes(body, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(body, nodes.data(), &nn);
+        int64_t nk = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+        }
+        mg->loop_kernels[solver][mode] = nk;
+        e = cudaGraphInstantiate(&slot, g, 0);
+    }
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        slot = nullptr;
+        (void)cudaGetLastError();
+        mg->no_device_loop = true;
+        return DEC_ERR_CUDA;
+    }
+    *out = slot;
+    return DEC_OK;
+}
+
 int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po, dec_stats *stats,
                cudaStream_t s) {
     dec_solve_opts o;
@@ -518,6 +621,7 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     std::memset(h, 0, offsetof(Scal, hist));
     h->tol = o.tol;
     h->maxit = o.maxit;
+    h->max_loops = o.maxit + 1;
     h->star0_sum = mg->star0_sum;
     CK(cudaMemcpyAsync(mg->scal, h, offsetof(Scal, hist), cudaMemcpyHostToDevice, s));
     if (gauge) {
@@ -529,9 +633,23 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     else
         enqueue_outer_init<double>(mg, (double *)nullptr, s);
     CK(cudaGetLastError());
+    int rc = DEC_OK;
+    // Default: the iteration loop runs on the device (one graph with a while
+    // node) and the host waits once at the end.  With live profiling, or if
+    // conditional nodes are unavailable, the host relaunches one iteration at
+    // a time and reads the residual in between.
+    cudaGraphExec_t lg = nullptr;
+    if (!mg->prof && !mg->no_device_loop && o.maxit > 0) {
+        if (loop_graph(mg, o.solver, o.mode, &lg) != DEC_OK) lg = nullptr;
+    }
+    int64_t loop_runs = 0;
+    if (lg) {
+        if (o.solver != DEC_SOLVER_MG) enqueue_precondition(mg, o.solver, o.mode, true, s, &mg->scal->done);
+        CK(cudaGraphLaunch(lg, s));
+        loop_runs = 1;
+    } else {
     CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    int rc = DEC_OK;
     if (!h->done && o.maxit > 0) {
         if (o.solver != DEC_SOLVER_MG) enqueue_precondition(mg, o.solver, o.mode, true, s, nullptr);
         cudaGraphExec_t ge;
@@ -550,15 +668,18 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
             if (mg->prof) accumulate_slots(mg);
         }
     }
+    }
     if (gauge) enqueue_mean_shift(mg, mg->ox, s, nullptr);
     CK(cudaMemcpyAsync(x, mg->ox, vb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     if (stats) {
         stats->iters = h->iter;
         stats->rel_res = h->rel;
         stats->rel_res0 = h->rel0;
-        stats->launches = (mg->launches - launches0) + graph_launches * mg->graph_kernels[o.solver][o.mode];
+        stats->launches = (mg->launches - launches0) + graph_launches * mg->graph_kernels[o.solver][o.mode] +
+                          (loop_runs ? (int64_t)h->loops * mg->loop_kernels[o.solver][o.mode] : 0);
     }
     if (h->status == 1) {
         char buf[160];
@@ -686,6 +807,8 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         double **vecs[] = {&mg->ox, &mg->orr, &mg->op, &mg->oq, &mg->ozn, &mg->ozo, &mg->ob, &mg->tmp};
         for (double **v : vecs)
             if ((rc = dalloc(mg, v, n))) return bail(rc);
+        if ((rc = dalloc(mg, &mg->zo32, n))) return bail(rc);
+
         if ((rc = dalloc(mg, &mg->partials, 8 * kMaxRedBlocks))) return bail(rc);
         if ((rc = dalloc(mg, &mg->counter, 1))) return bail(rc);
         if ((rc = dalloc(mg, &mg->scal, 1))) return bail(rc);
@@ -757,7 +880,7 @@ int dec_mg_set_star1(dec_mg *mg, const double *star1, dec_stream_t stream) {
     if (!star1) return fail(Status::fail(DEC_ERR_ARG, "null star1"));
     cudaStream_t s = (cudaStream_t)stream;
     DevLevel &F = mg->lv.back();
-    k_set_weights<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.K, mg->slot_edge, star1, F.star0, F.freev, F.w64, F.w32);
+    launch(mg, k_set_weights, grid_for(mg, F.n), s, F.n, F.K, mg->slot_edge, star1, F.star0, F.freev, F.w64, F.w32);
     CK(cudaGetLastError());
     return DEC_OK;
 }
@@ -772,10 +895,10 @@ int dec_laplace0_apply(const dec_mg *mgc, int level, const void *x, void *y, int
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64)
-            k_apply<double, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w64, (const double *)x,
+            launch(mg, k_apply<double, KT>, grid_for(mg, L.n), s, L.n, L.K, L.col, L.w64, (const double *)x,
                                                                       (double *)y, nullptr);
         else
-            k_apply<float, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, (const float *)x,
+            launch(mg, k_apply<float, KT>, grid_for(mg, L.n), s, L.n, L.K, L.col, L.w32, (const float *)x,
                                                                      (float *)y, nullptr);
     });
     CK(cudaGetLastError());
@@ -793,10 +916,10 @@ int dec_residual(const dec_mg *mgc, int level, const void *b, const void *x, voi
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64)
-            k_residual<double, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w64, (const double *)b,
+            launch(mg, k_residual<double, KT>, grid_for(mg, L.n), s, L.n, L.K, L.col, L.w64, (const double *)b,
                                                                          (const double *)x, (double *)r, nullptr);
         else
-            k_residual<float, KT><<<grid_for(mg, L.n), kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, (const float *)b,
+            launch(mg, k_residual<float, KT>, grid_for(mg, L.n), s, L.n, L.K, L.col, L.w32, (const float *)b,
                                                                         (const float *)x, (float *)r, nullptr);
     });
     CK(cudaGetLastError());
@@ -813,15 +936,15 @@ int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_strea
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64) {
-            k_residual<double, KT><<<g, kThreads, 0, s>>>(F.n, F.K, F.col, F.w64, (const double *)b, (const double *)x,
+            launch(mg, k_residual<double, KT>, g, s, F.n, F.K, F.col, F.w64, (const double *)b, (const double *)x,
                                                           F.b64, nullptr);
             double *e = cycle<double>(mg, top, F.b64, s, nullptr);
-            k_axpy1<double><<<g, kThreads, 0, s>>>(F.n, e, (double *)x, nullptr);
+            launch(mg, k_axpy1<double>, g, s, F.n, e, (double *)x, nullptr);
         } else {
-            k_residual<float, KT><<<g, kThreads, 0, s>>>(F.n, F.K, F.col, F.w32, (const float *)b, (const float *)x,
+            launch(mg, k_residual<float, KT>, g, s, F.n, F.K, F.col, F.w32, (const float *)b, (const float *)x,
                                                          F.b32, nullptr);
             float *e = cycle<float>(mg, top, F.b32, s, nullptr);
-            k_axpy1<float><<<g, kThreads, 0, s>>>(F.n, e, (float *)x, nullptr);
+            launch(mg, k_axpy1<float>, g, s, F.n, e, (float *)x, nullptr);
         }
     });
     CK(cudaGetLastError());
@@ -866,14 +989,14 @@ int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double
     cudaStream_t s = (cudaStream_t)stream;
     DevLevel &F = mg->lv.back();
     // L mu = *0^-1 grad_u, solved into grad_b, then grad_b = *0 mu
-    k_star0_scale<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.star0, grad_u, mg->tmp, 1);
+    launch(mg, k_star0_scale, grid_for(mg, F.n), s, F.n, F.star0, grad_u, mg->tmp, 1);
     CK(cudaGetLastError());
     int rc = solve_impl(mg, mg->tmp, grad_b, opts, stats, s);
     if (rc != DEC_OK && rc != DEC_ERR_NOT_CONVERGED) return rc;
     if (grad_star1) {
-        k_edge_grad<<<grid_for(mg, F.ne), kThreads, 0, s>>>(F.ne, mg->edges, grad_b, u, grad_star1);
+        launch(mg, k_edge_grad, grid_for(mg, F.ne), s, F.ne, mg->edges, grad_b, u, grad_star1);
     }
-    k_star0_scale<<<grid_for(mg, F.n), kThreads, 0, s>>>(F.n, F.star0, grad_b, grad_b, 0);
+    launch(mg, k_star0_scale, grid_for(mg, F.n), s, F.n, F.star0, grad_b, grad_b, 0);
     CK(cudaGetLastError());
     if (stats) stats->launches += grad_star1 ? 3 : 2;
     return rc;
@@ -945,24 +1068,24 @@ void noalloc_smooth(dec_mg *mg, int l, NoallocLevel &B, const float *b, int nu, 
             if (k == 0 && from_zero) {
                 cur = 0;
                 if (dout)
-                    k_smooth0<float, KT, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.w32, b, B.x[0], B.d[0], e, nullptr);
+                    launch(mg, k_smooth0<float, KT, true>, g, s, L.n, L.K, L.w32, b, B.x[0], B.d[0], e, nullptr);
                 else
-                    k_smooth0<float, KT, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.w32, b, B.x[0], nullptr, e, nullptr);
+                    launch(mg, k_smooth0<float, KT, false>, g, s, L.n, L.K, L.w32, b, B.x[0], nullptr, e, nullptr);
                 continue;
             }
             const int nxt = 1 - cur;
             const bool din = cheb && k > 0;
             if (din && dout)
-                k_smooth<float, KT, true, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], B.d[cur],
+                launch(mg, k_smooth<float, KT, true, true>, g, s, L.n, L.K, L.col, L.w32, b, B.x[cur], B.d[cur],
                                                                        B.x[nxt], B.d[nxt], c, e, nullptr);
             else if (din)
-                k_smooth<float, KT, true, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], B.d[cur],
+                launch(mg, k_smooth<float, KT, true, false>, g, s, L.n, L.K, L.col, L.w32, b, B.x[cur], B.d[cur],
                                                                         B.x[nxt], nullptr, c, e, nullptr);
             else if (dout)
-                k_smooth<float, KT, false, true><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], nullptr,
+                launch(mg, k_smooth<float, KT, false, true>, g, s, L.n, L.K, L.col, L.w32, b, B.x[cur], nullptr,
                                                                         B.x[nxt], B.d[nxt], c, e, nullptr);
             else
-                k_smooth<float, KT, false, false><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B.x[cur], nullptr,
+                launch(mg, k_smooth<float, KT, false, false>, g, s, L.n, L.K, L.col, L.w32, b, B.x[cur], nullptr,
                                                                          B.x[nxt], nullptr, c, e, nullptr);
             cur = nxt;
         }
@@ -973,7 +1096,7 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
     DevLevel &L = mg->lv[l];
     if (l == 0) {
         int g = (int)std::min<int64_t>(mg->nsm * 4, (L.n * 32 + kThreads - 1) / kThreads);
-        k_coarse<float><<<g, kThreads, 0, s>>>(L.n, mg->G32, b, B[0].x[0], nullptr);
+        launch(mg, k_coarse<float>, g, s, L.n, mg->G32, b, B[0].x[0], nullptr);
         return B[0].x[0];
     }
     const dec_mg_opts &o = mg->H.opts;
@@ -986,16 +1109,16 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
     const int g = grid_for(mg, L.n);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        k_residual<float, KT><<<g, kThreads, 0, s>>>(L.n, L.K, L.col, L.w32, b, B[l].x[cur], B[l].r, nullptr);
+        launch(mg, k_residual<float, KT>, g, s, L.n, L.K, L.col, L.w32, b, B[l].x[cur], B[l].r, nullptr);
         if (o.restriction == DEC_RESTRICT_STAR0)
-            k_restrict<float, KT, true><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, B[l].r, B[l - 1].b,
+            launch(mg, k_restrict<float, KT, true>, grid_for(mg, C.n), s, C.n, L.n, L.K, L.col, B[l].r, B[l - 1].b,
                                                                               L.star0_32, C.star0_32, nullptr);
         else
-            k_restrict<float, KT, false><<<grid_for(mg, C.n), kThreads, 0, s>>>(C.n, L.n, L.K, L.col, B[l].r,
+            launch(mg, k_restrict<float, KT, false>, grid_for(mg, C.n), s, C.n, L.n, L.K, L.col, B[l].r,
                                                                                B[l - 1].b, nullptr, nullptr, nullptr);
     });
     float *ec = noalloc_cycle(mg, B, l - 1, B[l - 1].b, s);
-    k_prolong<float><<<g, kThreads, 0, s>>>(C.n, L.n, L.par, ec, B[l].x[cur], nullptr);
+    launch(mg, k_prolong<float>, g, s, C.n, L.n, L.par, ec, B[l].x[cur], nullptr);
     if (o.nu2 > 0) noalloc_smooth(mg, l, B[l], b, o.nu2, false, true, cur, s);
     return B[l].x[cur];
 }
@@ -1028,10 +1151,10 @@ extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_s
     const int g = grid_for(mg, F.n);
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        k_residual<float, KT><<<g, kThreads, 0, s>>>(F.n, F.K, F.col, F.w32, b, x, B[top].b, nullptr);
+        launch(mg, k_residual<float, KT>, g, s, F.n, F.K, F.col, F.w32, b, x, B[top].b, nullptr);
     });
     float *e = noalloc_cycle(mg, B, top, B[top].b, s);
-    k_axpy1<float><<<g, kThreads, 0, s>>>(F.n, e, x, nullptr);
+    launch(mg, k_axpy1<float>, g, s, F.n, e, x, nullptr);
     CK(cudaGetLastError());
     return DEC_OK;
 }
@@ -1073,7 +1196,7 @@ int porous_check(dec_mg *mg, const dec_porous_params *prm, dec_porous_params &ou
 void porous_potential(PorousRun &R) {
     dec_mg *mg = R.mg;
     DevLevel &F = mg->lv.back();
-    k_potential<<<grid_for(mg, F.n), kThreads, 0, R.s>>>(F.n, mg->dim, mg->verts, R.prm.g[0], R.prm.g[1], R.prm.g[2],
+    launch(mg, k_potential, grid_for(mg, F.n), R.s, F.n, mg->dim, mg->verts, R.prm.g[0], R.prm.g[1], R.prm.g[2],
                                                         R.prm.alpha_rho0, mg->pot);
     R.launches += 1;
 }
@@ -1085,7 +1208,7 @@ int porous_one_step(PorousRun &R, const double *T_in, double *P, double *T_out) 
     const int g = grid_for(mg, F.n);
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        k_porous_rhs<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, T_in, mg->pot, mg->prhs);
+        launch(mg, k_porous_rhs<KT>, g, R.s, F.n, F.K, F.col, F.w64, T_in, mg->pot, mg->prhs);
     });
     dec_stats st{};
     int rc = solve_impl(mg, mg->prhs, P, &R.so, &st, R.s);
@@ -1096,7 +1219,7 @@ int porous_one_step(PorousRun &R, const double *T_in, double *P, double *T_out) 
     if (rc != DEC_OK) return rc;
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        k_porous_update<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, T_in, P, mg->pot, R.fixed,
+        launch(mg, k_porous_update<KT>, g, R.s, F.n, F.K, F.col, F.w64, T_in, P, mg->pot, R.fixed,
                                                     1.0 / R.prm.phi, R.prm.k_eta, R.prm.kappa, R.prm.dt, T_out);
     });
     CK(cudaGetLastError());
@@ -1109,10 +1232,10 @@ int porous_adjoint_step(PorousRun &R, const double *T, const double *P, double *
     dec_mg *mg = R.mg;
     DevLevel &F = mg->lv.back();
     const int g = grid_for(mg, F.n);
-    k_porous_adj1<<<g, kThreads, 0, R.s>>>(F.n, lam, R.fixed, F.star0, R.prm.dt, ms);
+    launch(mg, k_porous_adj1, g, R.s, F.n, lam, R.fixed, F.star0, R.prm.dt, ms);
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        k_porous_adj2<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, F.star0, T, P, mg->pot, lam, ms,
+        launch(mg, k_porous_adj2<KT>, g, R.s, F.n, F.K, F.col, F.w64, F.star0, T, P, mg->pot, lam, ms,
                                                   1.0 / R.prm.phi, R.prm.k_eta, R.prm.kappa, out, pbs);
     });
     dec_solve_opts so = R.so;  // adjoint pressure solve, warm-started from the previous m
@@ -1125,7 +1248,7 @@ int porous_adjoint_step(PorousRun &R, const double *T, const double *P, double *
     if (rc != DEC_OK) return rc;
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        k_porous_adj3<KT><<<g, kThreads, 0, R.s>>>(F.n, F.K, F.col, F.w64, F.star0, mg->pot, m, out);
+        launch(mg, k_porous_adj3<KT>, g, R.s, F.n, F.K, F.col, F.w64, F.star0, mg->pot, m, out);
     });
     CK(cudaGetLastError());
     std::swap(lam, out);
