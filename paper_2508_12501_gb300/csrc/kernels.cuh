@@ -286,10 +286,21 @@ __device__ bool grid_reduce(TV (&v)[NS], double *partials, unsigned *counter, do
     __syncthreads();
     if (!last) return false;
     __threadfence();
+    // Final pass of the last block: every thread issues all of its partial
+    // loads first (unrolled, predicated), then adds them in a fixed order, so
+    // the tail costs one L2 round trip instead of one per partial.
+    constexpr int kPer = kMaxRedBlocks / kThreads;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
+        double part[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int b = threadIdx.x + j * kThreads;
+            part[j] = b < (int)gridDim.x ? __ldcg(partials + s * kMaxRedBlocks + b) : 0.0;
+        }
         double acc = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += __ldcg(partials + s * kMaxRedBlocks + b);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) acc += part[j];
         acc = warp_sum(acc);
         __syncthreads();
         if (lane == 0) sh[s][warp] = acc;
