@@ -323,7 +323,6 @@ enum {
     DEC_PK_MGRES,       /* standalone-MG residual with ||r||                   */
     DEC_PK_ADD,         /* standalone-MG correction                            */
     DEC_PK_AUX,         /* set-up kernels of a solve (gauge mean, initial residual) */
-    DEC_PK_CCYCLE,      /* all coarse levels of an FP32 cycle in one cluster launch */
     DEC_PK_COUNT
 };
 typedef struct dec_prof_entry {

@@ -56,7 +56,7 @@ class dec_prof_entry(C.Structure):
 
 
 PROF_KINDS = ["smooth0", "smooth", "residual", "restrict", "prolong", "coarse", "spmv64", "update", "zdots",
-              "pupd", "mgres", "add", "aux", "ccycle"]
+              "pupd", "mgres", "add", "aux"]
 
 
 class dec_porous_params(C.Structure):

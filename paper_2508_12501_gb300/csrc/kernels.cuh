@@ -279,14 +279,13 @@ __device__ bool grid_reduce(TV (&v)[NS], double *partials, unsigned *counter, do
         }
     }
     if (threadIdx.x == 0) {
-        // release: this block's partials (written by this thread) become visible
-        // before the count; acquire: the last block then sees every partial
-        unsigned t;
-        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(counter) : "memory");
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return false;
+    __threadfence();
     // Final pass of the last block: every thread issues all of its partial
     // loads first (unrolled, predicated), then adds them in a fixed order, so
     // the tail costs one L2 round trip instead of one per partial.
@@ -329,7 +328,7 @@ __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
 }
 
 // mean = sum(*0 v) / sum(*0) over free rows (mask: free != 0)
-__global__ void __launch_bounds__(kThreads, 8) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+__global__ void __launch_bounds__(kThreads) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                   const double *__restrict__ v, double *partials, unsigned *counter,
                                                   Scal *S, const int *skip) {
     pdl_prologue();
@@ -352,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_shift(int n, const uint8_t *__rest
 // Initial residual of the outer iteration: r = b - L x, ||r||^2, ||b||^2 (free rows);
 // also writes the cycle's input rv (cast) when rv != nullptr.
 template <int KT, typename TV>
-__global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_outer_init(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w, const uint8_t *__restrict__ freev,
                                                         const double *__restrict__ b, const double *__restrict__ x,
                                                         double *__restrict__ r, TV *__restrict__ rv, double *partials,
@@ -383,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const 
 // After a cycle produced z (type TZ): zn = (double) z; sums of *0 z, *0 r zn, *0 r zo, *0 r;
 // epilogue: gauge shift c, new <r,z>, Polak-Ribiere beta.
 template <typename TZ>
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+__global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                        const TZ *__restrict__ z, double *__restrict__ zn,
                                                        const double *__restrict__ r, const double *__restrict__ zo,
                                                        int first, int gauge, double *partials, unsigned *counter,
@@ -428,7 +427,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_pupd(int n, const uint8_t *__r
 
 // q = L p (free rows), <p, q> -> alpha = <r,z> / <p,q>
 template <int KT>
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_pcg_spmv(int n, int K, const int32_t *__restrict__ col,
                                                       const double *__restrict__ w, const double *__restrict__ star0,
                                                       const uint8_t *__restrict__ freev, const double *__restrict__ p,
                                                       double *__restrict__ q, double *partials, unsigned *counter,
@@ -449,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv(int n, int K, const in
 
 // x += alpha p, r -= alpha q, rv = (TV) r, ||r||^2 -> convergence test
 template <typename TV>
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
+__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
                                                         double *__restrict__ x, double *__restrict__ r, TV *__restrict__ rv,
                                                         double *partials, unsigned *counter, Scal *S, const int *skip) {
     pdl_prologue();
@@ -472,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_update(int n, const double 
 
 // Standalone MG / iterative refinement: x += e; r = b - L x; ||r||^2 -> convergence test.
 template <int KT, typename TV>
-__global__ void __launch_bounds__(kThreads, 8) k_mg_residual(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_mg_residual(int n, int K, const int32_t *__restrict__ col,
                                                          const double *__restrict__ w, const uint8_t *__restrict__ freev,
                                                          const double *__restrict__ b, const double *__restrict__ x,
                                                          double *__restrict__ r, TV *__restrict__ rv, double *partials,
@@ -524,7 +523,7 @@ __device__ __forceinline__ double row_apply_nod(int i, int n, int K, const int32
 
 // q = L p, <p, q> (*0) -> alpha
 template <int KT>
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_d(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_pcg_spmv_d(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w,
                                                         const double *__restrict__ star0, const double *__restrict__ p,
                                                         double *__restrict__ q, double *partials, unsigned *counter,
@@ -542,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_d(int n, int K, const 
 }
 
 // x += alpha p, r -= alpha q (FP64), r32 = (float) r, ||r||^2 from r32
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_update_m(int n, const double *__restrict__ p,
+__global__ void __launch_bounds__(kThreads) k_pcg_update_m(int n, const double *__restrict__ p,
                                                           const double *__restrict__ q, double *__restrict__ x,
                                                           double *__restrict__ r, float *__restrict__ r32,
                                                           double *partials, unsigned *counter, Scal *S,
@@ -567,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_m(int n, const doubl
 }
 
 // FP32 dot products of the preconditioned vector z (cycle output) with r32 and the previous z.
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_m(int n, const float *__restrict__ s032,
+__global__ void __launch_bounds__(kThreads) k_pcg_zdots_m(int n, const float *__restrict__ s032,
                                                          const uint8_t *__restrict__ freev, const float *__restrict__ z,
                                                          const float *__restrict__ r32, const float *__restrict__ zo,
                                                          int first, int gauge, double *partials, unsigned *counter,
@@ -613,7 +612,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_pupd_m(int n, const uint8_t *_
 
 // Standalone MG / iterative refinement (mixed): r = b - L x; r32; ||r||^2 in FP32.
 template <int KT>
-__global__ void __launch_bounds__(kThreads, 8) k_mg_residual_m(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_mg_residual_m(int n, int K, const int32_t *__restrict__ col,
                                                            const double *__restrict__ w,
                                                            const uint8_t *__restrict__ freev,
                                                            const double *__restrict__ b, const double *__restrict__ x,
@@ -647,168 +646,6 @@ __global__ void k_loop_ctrl(cudaGraphConditionalHandle h, Scal *S) {
         S->loops += 1;
         const bool more = !S->done && S->loops < S->max_loops;
         cudaGraphSetConditional(h, more ? 1u : 0u);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The coarse end of the cycle in one launch: levels 0..nlev-1 (each at most
-// a few thousand rows) run as phases of a single thread-block cluster,
-// separated by hardware cluster barriers, instead of one launch per
-// operation.  All CTAs of a cluster are co-scheduled and execute the same
-// phase sequence, so every barrier completes.  Vectors written inside the
-// kernel are read with L2-coherent loads (__ldcg), never through the
-// non-coherent read-only path; tables (columns, weights) use __ldg.
-// ---------------------------------------------------------------------------
-
-constexpr int kClusterThreads = 1024;
-constexpr int kClusterMaxLevels = 8;
-constexpr int kMaxNu = 16;
-
-struct ClusterLevel {
-    int n, K;
-    const int32_t *col;
-    const float *w;
-    const float *s0;   // *0 (FP32), for the *0-adjoint restriction
-    const int2 *par;   // parents of this level's midpoints (level > 0)
-    float *x[2], *d[2], *r, *b;
-    float cpre[kMaxNu], epre[kMaxNu], cpost[kMaxNu], epost[kMaxNu];
-};
-
-struct ClusterDesc {
-    int nlev;          // levels 0..nlev-1 are handled by the cluster kernel
-    int nu1, nu2, cheb, star0;
-    float omega;
-    const float *G;    // coarsest solution operator, n0 x n0
-    ClusterLevel L[kClusterMaxLevels];
-};
-
-__device__ __forceinline__ void cluster_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void crow(const ClusterLevel &L, int i, const float *x, float &s, float &d) {
-    const float xi = __ldcg(x + i);
-    s = 0.f;
-    d = 0.f;
-    for (int k = 0; k < L.K; ++k) {
-        const size_t o = (size_t)k * L.n + i;
-        const float wk = __ldg(L.w + o);
-        s = fmaf(wk, xi - __ldcg(x + __ldg(L.col + o)), s);
-        d += wk;
-    }
-}
-
-// nu sweeps on level l; returns the buffer index of the iterate
-__device__ int cluster_smooth(const ClusterDesc &D, int l, const float *b, int nu, bool from_zero, bool post,
-                              int cur, int gtid, int gstride) {
-    const ClusterLevel &L = D.L[l];
-    for (int k = 0; k < nu; ++k) {
-        const float e = D.cheb ? (post ? L.epost[k] : L.epre[k]) : D.omega;
-        const float c = D.cheb ? (post ? L.cpost[k] : L.cpre[k]) : 0.f;
-        const bool dout = D.cheb && k + 1 < nu;
-        if (k == 0 && from_zero) {
-            cur = 0;
-            for (int i = gtid; i < L.n; i += gstride) {
-                float d = 0.f;
-                for (int kk = 0; kk < L.K; ++kk) d += __ldg(L.w + (size_t)kk * L.n + i);
-                const float v = d != 0.f ? e * (__ldcg(b + i) / d) : 0.f;
-                L.x[0][i] = v;
-                if (dout) L.d[0][i] = v;
-            }
-        } else {
-            const int nxt = 1 - cur;
-            const bool din = D.cheb && k > 0;
-            for (int i = gtid; i < L.n; i += gstride) {
-                float s, d;
-                crow(L, i, L.x[cur], s, d);
-                const float q = d != 0.f ? (__ldcg(b + i) - s) / d : 0.f;
-                const float delta = din ? fmaf(c, __ldcg(L.d[cur] + i), e * q) : e * q;
-                L.x[nxt][i] = __ldcg(L.x[cur] + i) + delta;
-                if (dout) L.d[nxt][i] = delta;
-            }
-            cur = nxt;
-        }
-        cluster_barrier();
-    }
-    return cur;
-}
-
-// C(b) on level nlev-1 with zero initial guess; the result lands in
-// D.L[nlev-1].x[final index], which the host computes the same way.
-__global__ void __launch_bounds__(kClusterThreads, 1) k_coarse_cycle(const ClusterDesc *__restrict__ Dp,
-                                                                     const int *skip) {
-    pdl_prologue();
-    if (skipped(skip)) return;  // uniform across the cluster: nothing writes *skip during this kernel
-    const ClusterDesc &D = *Dp;
-    const int nct = (int)(gridDim.x);
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int gstride = nct * blockDim.x;
-    int cur[kClusterMaxLevels];
-    for (int l = D.nlev - 1; l >= 1; --l) {
-        const ClusterLevel &L = D.L[l];
-        const ClusterLevel &C = D.L[l - 1];
-        const float *b = L.b;
-        if (D.nu1 > 0) {
-            cur[l] = cluster_smooth(D, l, b, D.nu1, true, false, 0, gtid, gstride);
-        } else {
-            for (int i = gtid; i < L.n; i += gstride) L.x[0][i] = 0.f;
-            cur[l] = 0;
-            cluster_barrier();
-        }
-        for (int i = gtid; i < L.n; i += gstride) {
-            float s, d;
-            crow(L, i, L.x[cur[l]], s, d);
-            L.r[i] = d != 0.f ? __ldcg(b + i) - s : 0.f;
-        }
-        cluster_barrier();
-        for (int c = gtid; c < C.n; c += gstride) {
-            float acc = 0.f;
-            int deg = 0;
-            for (int k = 0; k < L.K; ++k) {
-                const int j = __ldg(L.col + (size_t)k * L.n + c);
-                if (j != c) {
-                    acc += D.star0 ? __ldg(L.s0 + j) * __ldcg(L.r + j) : __ldcg(L.r + j);
-                    ++deg;
-                }
-            }
-            if (D.star0)
-                C.b[c] = (__ldg(L.s0 + c) * __ldcg(L.r + c) + 0.5f * acc) / __ldg(C.s0 + c);
-            else
-                C.b[c] = (__ldcg(L.r + c) + 0.5f * acc) / (1.f + 0.5f * (float)deg);
-        }
-        cluster_barrier();
-    }
-    {  // coarsest level: x = G b, one warp per row
-        const ClusterLevel &L = D.L[0];
-        const int lane = threadIdx.x & 31;
-        const int gwarp = gtid >> 5, nwarps = gstride >> 5;
-        for (int r = gwarp; r < L.n; r += nwarps) {
-            float acc = 0.f;
-            for (int j = lane; j < L.n; j += 32) acc = fmaf(__ldg(D.G + (size_t)r * L.n + j), __ldcg(L.b + j), acc);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) L.x[0][r] = acc;
-        }
-        cur[0] = 0;
-        cluster_barrier();
-    }
-    for (int l = 1; l < D.nlev; ++l) {
-        const ClusterLevel &L = D.L[l];
-        const ClusterLevel &C = D.L[l - 1];
-        const float *ec = C.x[cur[l - 1]];
-        float *xf = L.x[cur[l]];
-        for (int v = gtid; v < L.n; v += gstride) {
-            float add;
-            if (v < C.n) {
-                add = __ldcg(ec + v);
-            } else {
-                const int2 p = __ldg(L.par + (v - C.n));
-                add = 0.5f * (__ldcg(ec + p.x) + __ldcg(ec + p.y));
-            }
-            xf[v] = __ldcg(xf + v) + add;
-        }
-        cluster_barrier();
-        if (D.nu2 > 0) cur[l] = cluster_smooth(D, l, L.b, D.nu2, false, true, cur[l], gtid, gstride);
     }
 }
 

@@ -107,11 +107,6 @@ struct dec_mg {
     size_t bytes = 0;
     bool host_only = false;
     bool pdl = true;  // programmatic dependent launch between consecutive kernels
-    // coarse levels 0..cl_nlev-1 of the FP32 cycle run as one cluster launch
-    int cl_nlev = 0;
-    int cl_size = 0;
-    int cl_final = 0;  // x buffer index holding the cluster's result on level cl_nlev-1
-    ClusterDesc *cdesc = nullptr;
     // live kernel timing (dec_mg_profile)
     int64_t launches = 0;       // kernels enqueued outside graph capture
     int64_t graph_kernels[3][2] = {};  // kernel nodes per captured iteration graph
@@ -333,34 +328,9 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
 
 // Enqueue one cycle C_l(b) with zero initial guess; returns the level-l
 // buffer that holds the result.
-void launch_coarse_cycle(dec_mg *mg, cudaStream_t s, const int *skip) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)mg->cl_size);
-    cfg.blockDim = dim3(kClusterThreads);
-    cfg.stream = s;
-    cudaLaunchAttribute at[2];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)mg->cl_size;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = mg->pdl ? 2 : 1;
-    cudaLaunchKernelEx(&cfg, k_coarse_cycle, (const ClusterDesc *)mg->cdesc, skip);
-}
-
 template <typename T>
 T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
     DevLevel &L = mg->lv[l];
-    if constexpr (std::is_same<T, float>::value) {
-        if (mg->cl_nlev > 0 && l == mg->cl_nlev - 1) {
-            // b is this level's restriction target (lv[l].b32), which the descriptor points at
-            ProfScope ps(mg, DEC_PK_CCYCLE, l, s);
-            launch_coarse_cycle(mg, s, skip);
-            return L.x32[mg->cl_final];
-        }
-    }
     if (l == 0) {
         const T *G;
         if constexpr (std::is_same<T, float>::value) G = mg->G32; else G = mg->G64;
@@ -822,78 +792,6 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         for (size_t i = 0; i < G.size(); ++i) G32[i] = (float)G[i];
         if ((rc = upload(mg, &mg->G64, G.data(), G.size())) || (rc = upload(mg, &mg->G32, G32.data(), G32.size())))
             return bail(rc);
-    }
-    // coarse levels as one cluster launch (FP32 cycles)
-    {
-        const int top = nl - 1;
-        int cl = 0;
-        while (cl < nl && cl < kClusterMaxLevels && mg->lv[cl].n <= 12288) ++cl;
-        if (cl > top) cl = top;  // keep at least one level above, whose restriction feeds the cluster
-        if (cl >= 2 && o.nu1 <= kMaxNu && o.nu2 <= kMaxNu) {
-            int csize = 0;
-            for (int cs : {16, 8}) {
-                if (cs > 8 && cudaFuncSetAttribute(k_coarse_cycle, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                                  cudaSuccess) {
-                    (void)cudaGetLastError();
-                    continue;
-                }
-                cudaLaunchConfig_t cfg = {};
-                cfg.gridDim = dim3((unsigned)cs);
-                cfg.blockDim = dim3(kClusterThreads);
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeClusterDimension;
-                at[0].val.clusterDim.x = (unsigned)cs;
-                at[0].val.clusterDim.y = 1;
-                at[0].val.clusterDim.z = 1;
-                cfg.attrs = at;
-                cfg.numAttrs = 1;
-                int nclusters = 0;
-                if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_cycle, &cfg) == cudaSuccess && nclusters >= 1) {
-                    csize = cs;
-                    break;
-                }
-                (void)cudaGetLastError();
-            }
-            if (csize > 0) {
-                ClusterDesc hd = {};
-                hd.nlev = cl;
-                hd.nu1 = o.nu1;
-                hd.nu2 = o.nu2;
-                hd.cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
-                hd.star0 = o.restriction == DEC_RESTRICT_STAR0;
-                hd.omega = (float)o.omega;
-                hd.G = mg->G32;
-                for (int l = 0; l < cl; ++l) {
-                    DevLevel &D = mg->lv[l];
-                    ClusterLevel &C = hd.L[l];
-                    C.n = D.n;
-                    C.K = D.K;
-                    C.col = D.col;
-                    C.w = D.w32;
-                    C.s0 = D.star0_32;
-                    C.par = D.par;
-                    C.x[0] = D.x32[0];
-                    C.x[1] = D.x32[1];
-                    C.d[0] = D.d32[0];
-                    C.d[1] = D.d32[1];
-                    C.r = D.r32;
-                    C.b = D.b32;
-                    for (size_t k = 0; k < D.c_pre.size() && k < (size_t)kMaxNu; ++k) {
-                        C.cpre[k] = (float)D.c_pre[k];
-                        C.epre[k] = (float)D.e_pre[k];
-                    }
-                    for (size_t k = 0; k < D.c_post.size() && k < (size_t)kMaxNu; ++k) {
-                        C.cpost[k] = (float)D.c_post[k];
-                        C.epost[k] = (float)D.e_post[k];
-                    }
-                }
-                if ((rc = upload(mg, &mg->cdesc, &hd, 1))) return bail(rc);
-                mg->cl_nlev = cl;
-                mg->cl_size = csize;
-                const int after_pre = o.nu1 > 0 ? (o.nu1 - 1) % 2 : 0;
-                mg->cl_final = (after_pre + o.nu2) % 2;
-            }
-        }
     }
     // finest extras and outer workspace
     {
