@@ -22,145 +22,16 @@
 
 #include "host.h"
 #include "kernels.cuh"
+#include "mg_device.h"
 
 using decimpl::Status;
 using namespace decdev;
+using namespace decimpl;
 
 const decimpl::HostMesh *dec_mesh_host(const dec_mesh *m);
 
-namespace {
-
-struct DevLevel {
-    int n = 0, K = 0, nc = 0;  // nc: vertex count of the next coarser level
-    int64_t ne = 0;
-    int32_t *col = nullptr;
-    double *w64 = nullptr;
-    float *w32 = nullptr;
-    double *star0 = nullptr;
-    float *star0_32 = nullptr;
-    uint8_t *freev = nullptr;
-    int2 *par = nullptr;
-    float *x32[2] = {nullptr, nullptr}, *d32[2] = {nullptr, nullptr}, *r32 = nullptr, *b32 = nullptr;
-    double *x64[2] = {nullptr, nullptr}, *d64[2] = {nullptr, nullptr}, *r64 = nullptr, *b64 = nullptr;
-    // Chebyshev coefficients (c_k, e_k) of one smoothing call of nu1 and nu2 steps
-    std::vector<double> c_pre, e_pre, c_post, e_post;
-};
-
-template <typename T> struct P;
-template <> struct P<float> {
-    static float *x(DevLevel &L, int i) { return L.x32[i]; }
-    static float *d(DevLevel &L, int i) { return L.d32[i]; }
-    static float *r(DevLevel &L) { return L.r32; }
-    static float *b(DevLevel &L) { return L.b32; }
-    static const float *w(const DevLevel &L) { return L.w32; }
-    static const float *s0(const DevLevel &L) { return L.star0_32; }
-};
-template <> struct P<double> {
-    static double *x(DevLevel &L, int i) { return L.x64[i]; }
-    static double *d(DevLevel &L, int i) { return L.d64[i]; }
-    static double *r(DevLevel &L) { return L.r64; }
-    static double *b(DevLevel &L) { return L.b64; }
-    static const double *w(const DevLevel &L) { return L.w64; }
-    static const double *s0(const DevLevel &L) { return L.star0; }
-};
-
-template <typename F>
-void dispatch_k(int K, F &&f) {
-    if (K == 6)
-        f(std::integral_constant<int, 6>{});
-    else
-        f(std::integral_constant<int, 0>{});
-}
-
-}  // namespace
-
-struct dec_mg {
-    decimpl::HostHierarchy H;
-    int device = 0;
-    int nsm = 152;
-    std::vector<DevLevel> lv;
-    int n0 = 0;
-    double *G64 = nullptr;
-    float *G32 = nullptr;
-    // finest-level extras
-    int32_t *slot_edge = nullptr;
-    int2 *edges = nullptr;
-    double *verts = nullptr;  // [n * dim] finest coordinates
-    int dim = 2;
-    double *pot = nullptr, *ptmp = nullptr, *prhs = nullptr;  // porous-step work vectors
-    // outer-iteration workspace (finest level, FP64)
-    double *ox = nullptr, *orr = nullptr, *op = nullptr, *oq = nullptr, *ozn = nullptr, *ozo = nullptr, *ob = nullptr;
-    float *zo32 = nullptr;     // previous preconditioned vector (mixed precision)
-    double *tmp = nullptr;
-    double *partials = nullptr;
-    unsigned *counter = nullptr;
-    Scal *scal = nullptr;
-    Scal *scal_h = nullptr;  // pinned host mirror
-    double star0_sum = 0.0;
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t graphs[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
-    // whole iteration loop on the device: a while node around one iteration
-    cudaGraphExec_t loops[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
-    bool no_device_loop = false;  // set if the driver refuses conditional nodes
-    int64_t loop_kernels[3][2] = {};  // kernel nodes in one pass of a loop body
-    std::vector<void *> allocs;
-    size_t bytes = 0;
-    bool host_only = false;
-    bool pdl = true;  // programmatic dependent launch between consecutive kernels
-    // live kernel timing (dec_mg_profile)
-    int64_t launches = 0;       // kernels enqueued outside graph capture
-    int64_t graph_kernels[3][2] = {};  // kernel nodes per captured iteration graph
-    int prof = 0;               // 0 off, 1 finest level, 2 all levels
-    bool prof_capture = false;  // true while a profiled iteration graph is being captured
-    bool capturing = false;     // true while any iteration graph is being captured
-    struct Slot {
-        cudaEvent_t a, b;
-        int kind, level;
-    };
-    std::vector<Slot> slots;
-    double prof_ms[DEC_PK_COUNT][16] = {};
-    int64_t prof_n[DEC_PK_COUNT][16] = {};
-};
 
 namespace {
-
-int fail(const Status &s) {
-    decimpl::set_error(s.msg);
-    return s.code;
-}
-
-int cuda_fail(cudaError_t e, const char *where) {
-    decimpl::set_error(std::string(where) + ": " + cudaGetErrorString(e));
-    return DEC_ERR_CUDA;
-}
-
-#define CK(call)                                                  \
-    do {                                                          \
-        cudaError_t _e = (call);                                  \
-        if (_e != cudaSuccess) return cuda_fail(_e, #call);       \
-    } while (0)
-
-template <typename T>
-int dalloc(dec_mg *mg, T **p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-    if (e != cudaSuccess) {
-        decimpl::set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        return e == cudaErrorMemoryAllocation ? DEC_ERR_OOM : DEC_ERR_CUDA;
-    }
-    mg->allocs.push_back((void *)*p);
-    mg->bytes += count * sizeof(T);
-    return DEC_OK;
-}
-
-template <typename T>
-int upload(dec_mg *mg, T **p, const T *src, size_t count) {
-    int rc = dalloc(mg, p, count);
-    if (rc) return rc;
-    CK(cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice));
-    return DEC_OK;
-}
 
 void clear_slots(dec_mg *mg);
 void drop_graphs(dec_mg *mg);
@@ -229,36 +100,6 @@ void accumulate_slots(dec_mg *mg) {
             (void)cudaGetLastError();  // a failed read must not surface as a later launch error
         }
     }
-}
-
-// Every kernel goes through here: a plain launch, or one with programmatic
-// stream serialization (PDL) so that consecutive kernels overlap their launch
-// latency; inside stream capture this becomes a programmatic graph edge.
-template <typename... KArgs, typename... Args>
-inline void launch(const dec_mg *mg, void (*kernel)(KArgs...), int grid, cudaStream_t s, Args &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = mg->pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
-inline int grid_for(const dec_mg *mg, int64_t n) {
-    int64_t g = (n + kThreads - 1) / kThreads;
-    int64_t cap = (int64_t)mg->nsm * 8;
-    return (int)std::max<int64_t>(1, std::min(g, cap));
-}
-
-inline int red_grid(const dec_mg *mg, int64_t n) {
-    int64_t g = (n + kThreads - 1) / kThreads;
-    int64_t cap = std::min<int64_t>(kMaxRedBlocks, (int64_t)mg->nsm * 8);
-    return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
 void cheb_coeffs(double lmax, double lo, double hi, int nu, std::vector<double> &c, std::vector<double> &e) {
