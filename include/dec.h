@@ -250,6 +250,46 @@ int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double
                        double *grad_star1, const dec_solve_opts *opts, dec_stats *stats,
                        dec_stream_t stream);
 
+/* ---- batched solves ------------------------------------------------------------
+ * (Not in the paper: solves many right-hand sides on many hierarchies together.)
+ * Each hierarchy's right-hand sides are split into groups of k (a power of
+ * two, kgroup, or the smallest power of two >= the mesh's count when kgroup
+ * = 0) whose vectors are interleaved, value j of vertex v at [v*k + j], so a
+ * neighbour gather reads k contiguous values; every operation of the cycle
+ * is one launch over all groups of all meshes.  The solver is FP32 cycles
+ * inside FP64 iterative refinement, x += C(b - L x), until every right-hand
+ * side has ||b - L x||_2 / ||b||_2 <= tol (Sec. 3.1.2); the refinement
+ * loop runs on the device.  All hierarchies must use the same restriction;
+ * the batch uses its own smoother and sweep count (nu1 = nu2 = nu) with each
+ * hierarchy's Chebyshev interval and lambda_max.  The hierarchies must
+ * outlive the batch and must not be solved concurrently with it. */
+typedef struct dec_batch dec_batch;
+typedef struct dec_batch_opts {
+    int block;    /* threads per block of the batched kernels: 128, 256 or 512 */
+    int kgroup;   /* right-hand sides per interleaved group (power of two <= block), 0: per mesh */
+    int nu;       /* smoothing sweeps before and after the coarse correction, 1..8 */
+    int smoother; /* DEC_SMOOTH_JACOBI or DEC_SMOOTH_CHEBYSHEV */
+} dec_batch_opts;
+typedef struct dec_batch_stats {
+    int iters;          /* refinement passes                                  */
+    double max_rel_res; /* largest final relative residual                     */
+    int64_t launches;   /* libdec kernels launched by the call                 */
+    int64_t dof;        /* finest vertices x right-hand sides over all meshes   */
+} dec_batch_stats;
+void dec_batch_default_opts(dec_batch_opts *opts);
+/* mgs: host array of nmesh hierarchies; nrhs: host array of right-hand-side
+ * counts.  Allocates the batch's device vectors.  Errors: DEC_ERR_ARG,
+ * DEC_ERR_OOM, DEC_ERR_CUDA. */
+int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_batch_opts *opts, dec_batch **out);
+void dec_batch_destroy(dec_batch *batch);
+/* b, x: host arrays of nmesh DEVICE pointers, mesh m's vectors being double
+ * [nv_finest(m) * nrhs(m)] in [v * nrhs + j] order.  Under DEC_BC_GAUGE each
+ * right-hand side is projected to *0-weighted mean zero and so is its
+ * solution.  Synchronizes `stream`.  Errors as for dec_solve. */
+int dec_batch_solve(dec_batch *batch, const double *const *b, double *const *x, double tol, int maxit,
+                    dec_batch_stats *stats, dec_stream_t stream);
+int dec_batch_info(const dec_batch *batch, int *ngroups, int *total_rhs, int64_t *dof, size_t *device_bytes);
+
 /* ---- porous convection (Sec. 3.2) -------------------------------------------
  * One explicit step of the DEC porous-convection model of Sec. 3.2.1 with the
  * constants of Sec. 3.2.2, on the finest level of a DEC_BC_GAUGE hierarchy
@@ -258,7 +298,7 @@ int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double
  *   L P = *0^-1 d0^T *1 w              (Delta P = delta w; MG-PCG, warm-started from P)
  *   q   = -(k/eta) (d0 P - w)
  *   T  += dt * mask * ( -(1/phi) L_q T - kappa L T ),
- *         (L_q T)_v = (1/*0_v) sum_{e ni v} (1/2) *1_e (d0 T)_e q_e,
+ *         (L_q T)_v = (1 / star0_v) sum_{e ni v} (1/2) *1_e (d0 T)_e q_e,
  * mask = 0 where fixed[v] != 0 (the bc operation of Sec. 3.2.1: top and
  * bottom rows).  dec_porous_default_params: g = (0, -9.81, 0),
  * alpha_rho0 = 1/|g|, phi = 0.1, k_eta = 1, kappa = 2 (= Ra^-1 g alpha rho0

@@ -6,7 +6,8 @@ names load the library on first use and raise ImportError if it has not been
 built (``python -m paper_2508_12501_gb300.build``): there is no fallback.
 """
 
-_EXPORTS = {"Hierarchy": "api", "Mesh": "api", "SolveStats": "api", "poisson_solve": "api",
+_EXPORTS = {"Hierarchy": "api", "Mesh": "api", "SolveStats": "api", "poisson_solve": "api", "Batch": "api",
+            "BatchStats": "api",
             "DecError": "_lib"}
 
 __all__ = sorted(_EXPORTS)

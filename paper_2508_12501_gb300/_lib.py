@@ -65,6 +65,14 @@ class dec_porous_params(C.Structure):
                 ("maxit", C.c_int)]
 
 
+class dec_batch_opts(C.Structure):
+    _fields_ = [("block", C.c_int), ("kgroup", C.c_int), ("nu", C.c_int), ("smoother", C.c_int)]
+
+
+class dec_batch_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("max_rel_res", C.c_double), ("launches", C.c_int64), ("dof", C.c_int64)]
+
+
 class dec_mg_info_t(C.Structure):
     _fields_ = [("nlevels", C.c_int), ("nv", C.c_int64 * 16), ("ne", C.c_int64 * 16), ("nt", C.c_int64 * 16),
                 ("ell_width", C.c_int * 16), ("lmax", C.c_double * 16), ("ncolors", C.c_int * 16),
@@ -97,6 +105,11 @@ _SIGS = {
     "dec_solve_backward": (_i, [_p, _p, _p, _p, _p, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_mg_profile": (_i, [_p, _i]),
     "dec_mg_vcycle_noalloc": (_i, [_p, _p, _p, _p]),
+    "dec_batch_default_opts": (None, [C.POINTER(dec_batch_opts)]),
+    "dec_batch_create": (_i, [C.POINTER(_p), C.POINTER(_i), _i, C.POINTER(dec_batch_opts), C.POINTER(_p)]),
+    "dec_batch_destroy": (None, [_p]),
+    "dec_batch_solve": (_i, [_p, C.POINTER(_p), C.POINTER(_p), C.c_double, _i, C.POINTER(dec_batch_stats), _p]),
+    "dec_batch_info": (_i, [_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64), C.POINTER(C.c_size_t)]),
     "dec_porous_default_params": (None, [C.POINTER(dec_porous_params)]),
     "dec_porous_step": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _p, _i, C.POINTER(dec_stats), _p]),
     "dec_porous_backward": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _i, _p, _p,

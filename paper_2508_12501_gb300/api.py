@@ -369,3 +369,62 @@ def poisson_solve(b, star1=None, hier=None, **opts):
     if _PS is None:
         _PS = _autograd_function()
     return _PS.apply(b, star1, hier, opts)
+
+
+@dataclass
+class BatchStats:
+    iters: int
+    max_rel_res: float
+    launches: int
+    dof: int
+    status: int
+
+
+class Batch:
+    """Many right-hand sides on many hierarchies, solved together (dec_batch_*).
+
+    hierarchies: list of Hierarchy on the same device; nrhs: right-hand sides
+    per hierarchy.  Vectors are given per mesh as float64 CUDA tensors of
+    shape [nv, nrhs] (or flat [nv * nrhs]) in row-major order.
+    """
+
+    def __init__(self, hierarchies, nrhs, block=256, kgroup=0, nu=2, smoother="chebyshev"):
+        self.h = list(hierarchies)
+        self.nrhs = [int(k) for k in nrhs]
+        if len(self.h) != len(self.nrhs) or not self.h:
+            raise ValueError("one right-hand-side count per hierarchy")
+        o = L.dec_batch_opts()
+        lib.dec_batch_default_opts(C.byref(o))
+        o.block, o.kgroup, o.nu, o.smoother = block, kgroup, nu, SMOOTHERS[smoother]
+        self.opts = dict(block=block, kgroup=kgroup, nu=nu, smoother=smoother)
+        arr = (C.c_void_p * len(self.h))(*[hh._h.value for hh in self.h])
+        ks = (C.c_int * len(self.h))(*self.nrhs)
+        bh = C.c_void_p()
+        check(lib.dec_batch_create(arr, ks, len(self.h), C.byref(o), C.byref(bh)), "dec_batch_create")
+        self._h = bh
+        ng, nt, dof, nb = C.c_int(), C.c_int(), C.c_int64(), C.c_size_t()
+        check(lib.dec_batch_info(self._h, C.byref(ng), C.byref(nt), C.byref(dof), C.byref(nb)), "dec_batch_info")
+        self.ngroups, self.total_rhs, self.dof, self.device_bytes = ng.value, nt.value, dof.value, nb.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib.dec_batch_destroy(h)
+            self._h = None
+
+    def solve(self, bs, tol=1e-8, maxit=100, raise_on_fail=True):
+        torch = _torch()
+        xs, pb, px = [], [], []
+        for hh, k, b in zip(self.h, self.nrhs, bs):
+            pb.append(hh._vec(b.reshape(-1) if b.is_contiguous() else b, hh.n * k, (torch.float64,), "b"))
+            x = torch.empty(hh.n, k, dtype=torch.float64, device=hh.device) if k > 1 else \
+                torch.empty(hh.n, dtype=torch.float64, device=hh.device)
+            xs.append(x)
+            px.append(C.c_void_p(x.data_ptr()))
+        ab = (C.c_void_p * len(pb))(*[p.value for p in pb])
+        ax = (C.c_void_p * len(px))(*[p.value for p in px])
+        st = L.dec_batch_stats()
+        rc = lib.dec_batch_solve(self._h, ab, ax, float(tol), int(maxit), C.byref(st), self.h[0]._stream())
+        if rc not in (L.DEC_OK, L.DEC_ERR_NOT_CONVERGED) or (raise_on_fail and rc != L.DEC_OK):
+            check(rc, "dec_batch_solve")
+        return xs, BatchStats(st.iters, st.max_rel_res, st.launches, st.dof, rc)

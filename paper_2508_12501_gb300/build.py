@@ -22,7 +22,7 @@ BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libdec.so")
 
 HOST_SOURCES = ["host_mesh.cpp", "host_hier.cpp", "capi_host.cpp"]
-CUDA_SOURCES = ["solver.cu"]
+CUDA_SOURCES = ["solver.cu", "batch.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

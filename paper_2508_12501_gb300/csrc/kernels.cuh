@@ -328,7 +328,7 @@ __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
 }
 
 // mean = sum(*0 v) / sum(*0) over free rows (mask: free != 0)
-__global__ void __launch_bounds__(kThreads) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+static __global__ void __launch_bounds__(kThreads) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                   const double *__restrict__ v, double *partials, unsigned *counter,
                                                   Scal *S, const int *skip) {
     pdl_prologue();
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) k_mean(int n, const double *__restri
 }
 
 // v -= mean on free rows
-__global__ void __launch_bounds__(kThreads) k_shift(int n, const uint8_t *__restrict__ freev, double *__restrict__ v,
+static __global__ void __launch_bounds__(kThreads) k_shift(int n, const uint8_t *__restrict__ freev, double *__restrict__ v,
                                                    const Scal *S, const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__r
 }
 
 // z = zn - c (free rows), p = z + beta p (p = z on the first pass), zo = z.
-__global__ void __launch_bounds__(kThreads) k_pcg_pupd(int n, const uint8_t *__restrict__ freev, const double *__restrict__ zn,
+static __global__ void __launch_bounds__(kThreads) k_pcg_pupd(int n, const uint8_t *__restrict__ freev, const double *__restrict__ zn,
                                                       double *__restrict__ zo, double *__restrict__ p, int first,
                                                       const Scal *S, const int *skip) {
     pdl_prologue();
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv_d(int n, int K, const int
 }
 
 // x += alpha p, r -= alpha q (FP64), r32 = (float) r, ||r||^2 from r32
-__global__ void __launch_bounds__(kThreads) k_pcg_update_m(int n, const double *__restrict__ p,
+static __global__ void __launch_bounds__(kThreads) k_pcg_update_m(int n, const double *__restrict__ p,
                                                           const double *__restrict__ q, double *__restrict__ x,
                                                           double *__restrict__ r, float *__restrict__ r32,
                                                           double *partials, unsigned *counter, Scal *S,
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update_m(int n, const double *
 }
 
 // FP32 dot products of the preconditioned vector z (cycle output) with r32 and the previous z.
-__global__ void __launch_bounds__(kThreads) k_pcg_zdots_m(int n, const float *__restrict__ s032,
+static __global__ void __launch_bounds__(kThreads) k_pcg_zdots_m(int n, const float *__restrict__ s032,
                                                          const uint8_t *__restrict__ freev, const float *__restrict__ z,
                                                          const float *__restrict__ r32, const float *__restrict__ zo,
                                                          int first, int gauge, double *partials, unsigned *counter,
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_zdots_m(int n, const float *__
 }
 
 // z = z - c (free rows, FP32), zo = z, p = z + beta p (FP64)
-__global__ void __launch_bounds__(kThreads) k_pcg_pupd_m(int n, const uint8_t *__restrict__ freev,
+static __global__ void __launch_bounds__(kThreads) k_pcg_pupd_m(int n, const uint8_t *__restrict__ freev,
                                                         const float *__restrict__ z, float *__restrict__ zo,
                                                         double *__restrict__ p, int first, const Scal *S,
                                                         const int *skip) {
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(kThreads) k_mg_residual_m(int n, int K, const 
 // Body-end kernel of the device-side iteration loop (a while node of the
 // solve graph): repeat while the solve is not done, and never more than
 // max_loops times, so the loop ends even if no kernel ever sets `done`.
-__global__ void k_loop_ctrl(cudaGraphConditionalHandle h, Scal *S) {
+static __global__ void k_loop_ctrl(cudaGraphConditionalHandle h, Scal *S) {
     pdl_prologue();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         S->loops += 1;
@@ -650,7 +650,7 @@ __global__ void k_loop_ctrl(cudaGraphConditionalHandle h, Scal *S) {
 }
 
 // Gradient with respect to the edge weights: g_e = -(d0 mu)_e (d0 u)_e.
-__global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const int2 *__restrict__ edges, const double *__restrict__ mu,
+static __global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const int2 *__restrict__ edges, const double *__restrict__ mu,
                                                        const double *__restrict__ u, double *__restrict__ g) {
     pdl_prologue();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -660,14 +660,14 @@ __global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const int2 *
 }
 
 // y = s0 .* x, or y = x ./ s0 (inverse != 0)
-__global__ void __launch_bounds__(kThreads) k_star0_scale(int n, const double *__restrict__ star0, const double *x,
+static __global__ void __launch_bounds__(kThreads) k_star0_scale(int n, const double *__restrict__ star0, const double *x,
                                                          double *y, int inverse) {
     pdl_prologue();
     GRID_STRIDE(i, n) y[i] = inverse ? x[i] / ldg(star0 + i) : x[i] * ldg(star0 + i);
 }
 
 // Finest-level weights from a new *1: w[slot] = *1[edge(slot)] / *0[row] on free rows.
-__global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const int32_t *__restrict__ slot_edge,
+static __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const int32_t *__restrict__ slot_edge,
                                                          const double *__restrict__ star1, const double *__restrict__ star0,
                                                          const uint8_t *__restrict__ freev, double *__restrict__ w64,
                                                          float *__restrict__ w32) {
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const in
 //   (L_q T)_v = sum_k w_k (T_u - T_v) q_{v->u} / 2,   (L T)_v = sum_k w_k (T_v - T_u).
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads) k_potential(int n, int dim, const double *__restrict__ verts, double g0,
+static __global__ void __launch_bounds__(kThreads) k_potential(int n, int dim, const double *__restrict__ verts, double g0,
                                                        double g1, double g2, double arho, double *__restrict__ pot) {
     pdl_prologue();
     GRID_STRIDE(v, n) {
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(kThreads) k_porous_update(int n, int K, const 
 }
 
 // Adjoint step, part 1: ms = mu / *0 with mu = dt * mask * lam.
-__global__ void __launch_bounds__(kThreads) k_porous_adj1(int n, const double *__restrict__ lam,
+static __global__ void __launch_bounds__(kThreads) k_porous_adj1(int n, const double *__restrict__ lam,
                                                          const uint8_t *__restrict__ fixed,
                                                          const double *__restrict__ star0, double dt,
                                                          double *__restrict__ ms) {

@@ -1,0 +1,133 @@
+"""Batched solves (many right-hand sides, uneven meshes) against the oracle.
+
+Each right-hand side of a batch must reach its own relative residual
+(recomputed in FP64 by the oracle's operator) and agree with the oracle's
+direct solution in the *0 norm within the bound that tolerance implies.
+The full-size case is the batched workload: 64 spherical-harmonic right-hand
+sides on the icosphere x7 (163,842 vertices) plus 32 unit squares, 8 each at
+subdivision levels 6-9 (4,225 ... 263,169 vertices), Dirichlet, U[-1,1].
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import multigrid as omg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _mesh(kind, nsub, nl, restriction="rownorm"):
+    import paper_2508_12501_gb300 as P
+    if kind == "ico":
+        v, t = W.icosahedron(); bc, sph = "gauge", True
+    elif kind == "fan":
+        v, t = W.heptagon_fan(); bc, sph = "dirichlet", False
+    else:
+        v, t = W.unit_square(); bc, sph = "dirichlet", False
+    h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, restriction=restriction)
+    oh = omg.build_hierarchy(v, t, nsub, 1, bc, sphere=sph)
+    return h, oh
+
+
+def _rhs(n, k, seed):
+    return np.stack([W.uniform_field(n, seed + j) for j in range(k)], axis=1)
+
+
+def _check(oh, x, b, tol):
+    lev = oh.finest
+    for j in range(b.shape[1]):
+        bj = omg.prepare_rhs(oh, b[:, j])
+        xj = x[:, j]
+        assert omg.rel_residual(lev, bj, xj) <= 4 * tol
+        xs = omg.direct_solve(oh, b[:, j])
+        assert omg.star0_norm(lev, xj - xs) / omg.star0_norm(lev, xs) < 1e-6
+
+
+@pytest.mark.parametrize("kgroup", [0, 1, 2, 4, 8])
+def test_uneven_batch_matches_oracle(kgroup):
+    import paper_2508_12501_gb300 as P
+    cases = [("ico", 4, 3, 5), ("square", 5, 5, 1), ("square", 4, 3, 3), ("fan", 3, 3, 2)]
+    hs, ohs, bs = [], [], []
+    for i, (kind, nsub, nl, k) in enumerate(cases):
+        h, oh = _mesh(kind, nsub, nl)
+        hs.append(h); ohs.append(oh)
+        bs.append(_rhs(h.n, k, 10 * i))
+    B = P.Batch(hs, [c[3] for c in cases], kgroup=kgroup, nu=2)
+    xs, st = B.solve([torch.as_tensor(b, device="cuda") for b in bs], tol=1e-10, maxit=100)
+    assert st.status == 0 and st.max_rel_res <= 1e-10
+    assert st.dof == sum(h.n * c[3] for h, c in zip(hs, cases))
+    for oh, x, b in zip(ohs, xs, bs):
+        _check(oh, x.reshape(len(b), -1).cpu().numpy(), b, 1e-10)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("nu", [1, 3])
+def test_batch_smoother_options(smoother, nu):
+    import paper_2508_12501_gb300 as P
+    h1, o1 = _mesh("square", 5, 4)
+    h2, o2 = _mesh("ico", 3, 2)
+    b1, b2 = _rhs(h1.n, 4, 1), _rhs(h2.n, 2, 2)
+    B = P.Batch([h1, h2], [4, 2], nu=nu, smoother=smoother, block=128)
+    xs, st = B.solve([torch.as_tensor(b1, device="cuda"), torch.as_tensor(b2, device="cuda")], tol=1e-10, maxit=200)
+    assert st.max_rel_res <= 1e-10
+    _check(o1, xs[0].cpu().numpy(), b1, 1e-10)
+    _check(o2, xs[1].cpu().numpy(), b2, 1e-10)
+
+
+def test_batch_error_paths():
+    import paper_2508_12501_gb300 as P
+    h1, _ = _mesh("square", 4, 3)
+    h2, _ = _mesh("square", 4, 3, restriction="star0")
+    with pytest.raises(P.DecError):
+        P.Batch([h1, h2], [1, 1])
+    with pytest.raises(P.DecError):
+        P.Batch([h1], [2], kgroup=3)
+    B = P.Batch([h1], [2])
+    b = torch.zeros(h1.n, 2, dtype=torch.float64, device="cuda")
+    b[5, 1] = float("nan")
+    with pytest.raises(P.DecError) as ei:
+        B.solve([b])
+    assert ei.value.code == 6
+    b = torch.as_tensor(_rhs(h1.n, 2, 3), device="cuda")
+    xs, st = B.solve([b], tol=1e-12, maxit=1, raise_on_fail=False)
+    assert st.status == 5 and st.iters == 1
+
+
+def test_full_batched_workload():
+    import paper_2508_12501_gb300 as P
+    v, t = W.icosahedron()
+    hi = P.Hierarchy(P.Mesh(v, t), 7, 6, bc="gauge", sphere=True)
+    pos = hi.table(-1, "verts")
+    b_ico = np.stack([W.sh_sum(pos, W.sh_coefficients(100 + j)) for j in range(64)], axis=1)
+    hs, ks, bs = [hi], [64], [b_ico]
+    seed = 200
+    vs, ts = W.unit_square()
+    for nsub in (6, 7, 8, 9):
+        hq = P.Hierarchy(P.Mesh(vs, ts), nsub, nsub - 1, bc="dirichlet")
+        for _ in range(8):
+            hs.append(hq); ks.append(1)
+            bs.append(W.uniform_field(hq.n, seed)[:, None]); seed += 1
+    B = P.Batch(hs, ks)
+    assert B.dof == 163842 * 64 + 8 * (4225 + 16641 + 66049 + 263169)
+    xs, st = B.solve([torch.as_tensor(b.reshape(-1), device="cuda") for b in bs], tol=1e-8, maxit=100)
+    assert st.max_rel_res <= 1e-8
+    # every residual, recomputed in FP64 by the oracle operator
+    done = {}
+    for h, b, x in zip(hs, bs, xs):
+        key = id(h)
+        if key not in done:
+            vv, tt = (v, t) if h is hi else (vs, ts)
+            nsub = 7 if h is hi else int(round(np.log2(np.sqrt(h.n) - 1)))
+            done[key] = omg.build_hierarchy(vv, tt, nsub, 1, "gauge" if h is hi else "dirichlet", sphere=h is hi)
+        oh = done[key]
+        xx = x.reshape(h.n, -1).cpu().numpy()
+        for j in range(b.shape[1]):
+            assert omg.rel_residual(oh.finest, omg.prepare_rhs(oh, b[:, j]), xx[:, j]) <= 2e-8
+    # and a few right-hand sides agree with single solves
+    for j in (0, 31, 63):
+        xj, _ = hi.solve(torch.as_tensor(b_ico[:, j], device="cuda"), tol=1e-10)
+        oh = done[id(hi)]
+        a = xs[0][:, j].cpu().numpy()
+        r = xj.cpu().numpy()
+        assert omg.star0_norm(oh.finest, a - r) / omg.star0_norm(oh.finest, r) < 1e-6
