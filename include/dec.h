@@ -289,6 +289,21 @@ void dec_batch_destroy(dec_batch *batch);
 int dec_batch_solve(dec_batch *batch, const double *const *b, double *const *x, double tol, int maxit,
                     dec_batch_stats *stats, dec_stream_t stream);
 int dec_batch_info(const dec_batch *batch, int *ngroups, int *total_rhs, int64_t *dof, size_t *device_bytes);
+/* dec_batch_tune: the batch autotuner.  For each candidate setting (cands,
+ * or when null a grid of block {128,256,512} x kgroup {0,8,16,32} x nu
+ * {1,2,3}, Chebyshev) it builds a batch, solves once to warm up, times
+ * `reps` solves of b with CUDA events on `stream`, and keeps the fastest
+ * that converges.  times (nullable, one per candidate) receives the mean
+ * milliseconds, -1 for a failed candidate.  x receives the last solution. */
+int dec_batch_tune(dec_mg *const *mgs, const int *nrhs, int nmesh, const double *const *b, double *const *x,
+                   double tol, int maxit, const dec_batch_opts *cands, int ncand, int reps, dec_batch_opts *best,
+                   double *best_ms, double *times, dec_stream_t stream);
+/* dec_batch_time_smooth: mean duration of one launch of the batched
+ * finest-level smoothing sweep (every group), over `reps` back-to-back
+ * launches timed with CUDA events on `stream`, and its algorithmic bytes
+ * (per row K column indices and K weights once, per right-hand side x, b,
+ * the new x and, for Chebyshev, a direction vector). */
+int dec_batch_time_smooth(dec_batch *batch, int reps, double *avg_ms, double *bytes, dec_stream_t stream);
 
 /* ---- porous convection (Sec. 3.2) -------------------------------------------
  * One explicit step of the DEC porous-convection model of Sec. 3.2.1 with the

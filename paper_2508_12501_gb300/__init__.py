@@ -7,7 +7,7 @@ built (``python -m paper_2508_12501_gb300.build``): there is no fallback.
 """
 
 _EXPORTS = {"Hierarchy": "api", "Mesh": "api", "SolveStats": "api", "poisson_solve": "api", "Batch": "api",
-            "BatchStats": "api",
+            "BatchStats": "api", "tune_batch": "api",
             "DecError": "_lib"}
 
 __all__ = sorted(_EXPORTS)

@@ -110,6 +110,10 @@ _SIGS = {
     "dec_batch_destroy": (None, [_p]),
     "dec_batch_solve": (_i, [_p, C.POINTER(_p), C.POINTER(_p), C.c_double, _i, C.POINTER(dec_batch_stats), _p]),
     "dec_batch_info": (_i, [_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64), C.POINTER(C.c_size_t)]),
+    "dec_batch_tune": (_i, [C.POINTER(_p), C.POINTER(_i), _i, C.POINTER(_p), C.POINTER(_p), C.c_double, _i,
+                            C.POINTER(dec_batch_opts), _i, _i, C.POINTER(dec_batch_opts), C.POINTER(C.c_double),
+                            C.POINTER(C.c_double), _p]),
+    "dec_batch_time_smooth": (_i, [_p, _i, C.POINTER(C.c_double), C.POINTER(C.c_double), _p]),
     "dec_porous_default_params": (None, [C.POINTER(dec_porous_params)]),
     "dec_porous_step": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _p, _i, C.POINTER(dec_stats), _p]),
     "dec_porous_backward": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _i, _p, _p,

@@ -428,3 +428,35 @@ class Batch:
         if rc not in (L.DEC_OK, L.DEC_ERR_NOT_CONVERGED) or (raise_on_fail and rc != L.DEC_OK):
             check(rc, "dec_batch_solve")
         return xs, BatchStats(st.iters, st.max_rel_res, st.launches, st.dof, rc)
+
+    def time_smooth(self, reps=20):
+        """(mean ms, algorithmic bytes) of one batched finest-level smoothing launch."""
+        ms, by = C.c_double(), C.c_double()
+        check(lib.dec_batch_time_smooth(self._h, int(reps), C.byref(ms), C.byref(by), self.h[0]._stream()),
+              "dec_batch_time_smooth")
+        return ms.value, by.value
+
+
+def tune_batch(hierarchies, nrhs, bs, tol=1e-8, maxit=100, candidates=None, reps=3):
+    """Batch autotuner (dec_batch_tune): returns (best options dict, best ms, list of (options, ms))."""
+    torch = _torch()
+    hs = list(hierarchies)
+    arr = (C.c_void_p * len(hs))(*[hh._h.value for hh in hs])
+    ks = (C.c_int * len(hs))(*[int(k) for k in nrhs])
+    xs = [torch.empty_like(b) for b in bs]
+    ab = (C.c_void_p * len(bs))(*[b.data_ptr() for b in bs])
+    ax = (C.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+    inv = {v: k for k, v in SMOOTHERS.items()}
+    if candidates is None:
+        candidates = [dict(block=bl, kgroup=kg, nu=nu, smoother="chebyshev")
+                      for bl in (128, 256, 512) for kg in (0, 8, 16, 32) for nu in (1, 2, 3)]
+    cands = (L.dec_batch_opts * len(candidates))()
+    for c, o in zip(cands, candidates):
+        c.block, c.kgroup, c.nu, c.smoother = o["block"], o["kgroup"], o["nu"], SMOOTHERS[o["smoother"]]
+    times = (C.c_double * len(candidates))()
+    best = L.dec_batch_opts()
+    best_ms = C.c_double()
+    check(lib.dec_batch_tune(arr, ks, len(hs), ab, ax, float(tol), int(maxit), cands, len(candidates), int(reps),
+                             C.byref(best), C.byref(best_ms), times, hs[0]._stream()), "dec_batch_tune")
+    bo = dict(block=best.block, kgroup=best.kgroup, nu=best.nu, smoother=inv[best.smoother])
+    return bo, best_ms.value, [(o, t) for o, t in zip(candidates, times)]

@@ -789,3 +789,100 @@ int dec_batch_info(const dec_batch *B, int *ngroups, int *total_rhs, int64_t *do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuner: time candidate (block, kgroup, nu, smoother) settings on the
+// caller's batch and keep the fastest that converges
+// ---------------------------------------------------------------------------
+
+extern "C" int dec_batch_tune(dec_mg *const *mgs, const int *nrhs, int nmesh, const double *const *b, double *const *x,
+                              double tol, int maxit, const dec_batch_opts *cands, int ncand, int reps,
+                              dec_batch_opts *best, double *best_ms, double *times, dec_stream_t stream) {
+    if (!mgs || !nrhs || !b || !x || !best || nmesh < 1 || reps < 1)
+        return fail(Status::fail(DEC_ERR_ARG, "null pointer or bad count"));
+    std::vector<dec_batch_opts> grid;
+    if (cands && ncand > 0) {
+        grid.assign(cands, cands + ncand);
+    } else {
+        for (int blk : {128, 256, 512})
+            for (int kg : {0, 8, 16, 32})
+                for (int nu : {1, 2, 3}) grid.push_back(dec_batch_opts{blk, kg, nu, DEC_SMOOTH_CHEBYSHEV});
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best_t = 0.0;
+    int best_i = -1;
+    for (size_t c = 0; c < grid.size(); ++c) {
+        if (times) times[c] = -1.0;
+        dec_batch *B = nullptr;
+        if (dec_batch_create(mgs, nrhs, nmesh, &grid[c], &B) != DEC_OK) continue;
+        bool ok = dec_batch_solve(B, b, x, tol, maxit, nullptr, stream) == DEC_OK;  // warm-up, builds the graph
+        double total = 0.0;
+        for (int r = 0; ok && r < reps; ++r) {
+            cudaEventRecord(e0, s);
+            ok = dec_batch_solve(B, b, x, tol, maxit, nullptr, stream) == DEC_OK;
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            total += ms;
+        }
+        dec_batch_destroy(B);
+        if (!ok) continue;
+        const double t = total / reps;
+        if (times) times[c] = t;
+        if (best_i < 0 || t < best_t) {
+            best_t = t;
+            best_i = (int)c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    if (best_i < 0) return fail(Status::fail(DEC_ERR_NOT_CONVERGED, "no candidate setting converged"));
+    *best = grid[best_i];
+    if (best_ms) *best_ms = best_t;
+    return DEC_OK;
+}
+
+// Time one launch of the batched finest-level smoothing sweep (all groups)
+// with CUDA events on `stream`; reports the average and the algorithmic bytes.
+extern "C" int dec_batch_time_smooth(dec_batch *B, int reps, double *avg_ms, double *bytes, dec_stream_t stream) {
+    if (!B || reps < 1 || !avg_ms || !bytes) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    // the first post-smoothing sweep on depth 0 (every group's finest level)
+    const dec_batch::Op *op = nullptr;
+    for (const auto &o : B->cycle_ops)
+        if (o.kind == 1 && o.post == 1 && o.sweep == 0) op = &o;  // the last such op is depth 0
+    if (!op) return fail(Status::fail(DEC_ERR_ARG, "batch has no smoothing sweep"));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int cheb = B->opts.smoother == DEC_SMOOTH_CHEBYSHEV;
+    double by = 0.0;
+    for (auto &G : B->groups) {
+        const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
+        // per row: K columns + K weights (shared by the k right-hand sides), then per item x, b, x_out (+ direction)
+        by += (double)L.n * (8.0 * L.K) + (double)L.n * G.k * 4.0 * (3 + (cheb ? 1 : 0));
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int *noskip = nullptr;
+    for (int r = 0; r < 2; ++r)
+        blaunch(B, k_b_smooth, op->cnt, 0, s, (const BLevel *)B->dlv, (const BTile *)(B->dtiles + op->off), cheb,
+                (float)(2.0 / 3.0), 0, 1, op->src, 0, op->dout, noskip);
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r)
+        blaunch(B, k_b_smooth, op->cnt, 0, s, (const BLevel *)B->dlv, (const BTile *)(B->dtiles + op->off), cheb,
+                (float)(2.0 / 3.0), 0, 1, op->src, 0, op->dout, noskip);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    *avg_ms = ms / reps;
+    *bytes = by;
+    return DEC_OK;
+}

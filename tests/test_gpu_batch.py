@@ -131,3 +131,22 @@ def test_full_batched_workload():
         a = xs[0][:, j].cpu().numpy()
         r = xj.cpu().numpy()
         assert omg.star0_norm(oh.finest, a - r) / omg.star0_norm(oh.finest, r) < 1e-6
+
+
+def test_autotuner_picks_a_converging_setting():
+    import paper_2508_12501_gb300 as P
+    h1, o1 = _mesh("square", 6, 5)
+    h2, o2 = _mesh("ico", 4, 3)
+    b1, b2 = _rhs(h1.n, 8, 5), _rhs(h2.n, 4, 6)
+    bs = [torch.as_tensor(b1.reshape(-1), device="cuda"), torch.as_tensor(b2.reshape(-1), device="cuda")]
+    cands = [dict(block=128, kgroup=0, nu=2, smoother="chebyshev"), dict(block=256, kgroup=2, nu=1, smoother="jacobi"),
+             dict(block=512, kgroup=8, nu=3, smoother="chebyshev"), dict(block=100, kgroup=0, nu=2, smoother="jacobi")]
+    best, ms, table = P.tune_batch([h1, h2], [8, 4], bs, tol=1e-10, candidates=cands, reps=2)
+    assert best in cands[:3] and ms > 0
+    assert table[3][1] == -1.0  # an invalid candidate is reported, not chosen
+    assert ms == min(t for _, t in table if t > 0)
+    B = P.Batch([h1, h2], [8, 4], **best)
+    xs, st = B.solve(bs, tol=1e-10)
+    _check(o1, xs[0].cpu().numpy(), b1, 1e-10)
+    ms2, by = B.time_smooth(5)
+    assert ms2 > 0 and by > 0
