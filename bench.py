@@ -291,6 +291,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all-levels", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven iteration loop (same kernels; profilers cannot see conditional graphs)")
     ap.add_argument("--only-solves", action="store_true",
                     help="warm-up and timed solves only (the command line used for the ncu launch list)")
     args = ap.parse_args()
@@ -339,7 +341,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, st = h.solve(b, x, solver="mgpcg", mode=mode, tol=TOL)
+            _, st = h.solve(b, x, solver="mgpcg", mode=mode, tol=TOL, host_loop=args.host_loop)
             e1.record(stream)
             evs.append((e0, e1))
             launches += st.launches
@@ -352,7 +354,7 @@ def main():
 
     # warm-up (builds the iteration graphs)
     for _ in range(args.warmup):
-        h.solve(b, x, solver="mgpcg", mode=args.mode, tol=TOL)
+        h.solve(b, x, solver="mgpcg", mode=args.mode, tol=TOL, host_loop=args.host_loop)
         if not args.only_solves:
             h.solve(b, x, solver="mgpcg", mode="f64", tol=TOL)
     barrier()

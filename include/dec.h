@@ -82,15 +82,18 @@ typedef struct dec_mg_opts {
 } dec_mg_opts;
 
 /* Solver options.  dec_solve_default_opts(): MG-PCG, mixed precision,
- * tol = 1e-8, maxit = 100, no warm start, convergence checked every
- * iteration. */
+ * tol = 1e-8, maxit = 100, no warm start, device-side iteration loop. */
 typedef struct dec_solve_opts {
     int solver;       /* DEC_SOLVER_*                                           */
     int mode;         /* DEC_MODE_F64 or DEC_MODE_MIXED                           */
     double tol;       /* stop when ||b - L x||_2 / ||b||_2 <= tol (free vertices) */
     int maxit;        /* outer iterations                                         */
     int warm_start;   /* nonzero: x holds the initial guess on entry              */
-    int check_every;  /* host reads the residual every this many iterations (>=1) */
+    int check_every;  /* with host_loop: host reads the residual every this many iterations */
+    int host_loop;    /* 0: the iteration loop runs on the device (one graph with a while
+                         node, one host wait per solve); 1: the host relaunches a
+                         one-iteration graph and reads the residual in between (same
+                         kernels; for tools that cannot see conditional graphs)   */
 } dec_solve_opts;
 
 typedef struct dec_stats {

@@ -43,7 +43,7 @@ class dec_mg_opts(C.Structure):
 
 class dec_solve_opts(C.Structure):
     _fields_ = [("solver", C.c_int), ("mode", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
-                ("warm_start", C.c_int), ("check_every", C.c_int)]
+                ("warm_start", C.c_int), ("check_every", C.c_int), ("host_loop", C.c_int)]
 
 
 class dec_stats(C.Structure):

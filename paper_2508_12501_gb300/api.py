@@ -202,7 +202,7 @@ class Hierarchy:
         check(lib.dec_mg_vcycle(self._h, pb, px, 1, prec, self._stream()), "dec_mg_vcycle")
         return x
 
-    def _solve_opts(self, solver, mode, tol, maxit, warm_start, check_every):
+    def _solve_opts(self, solver, mode, tol, maxit, warm_start, check_every, host_loop=False):
         o = L.dec_solve_opts()
         lib.dec_solve_default_opts(C.byref(o))
         o.solver = SOLVERS[solver]
@@ -211,10 +211,11 @@ class Hierarchy:
         o.maxit = int(maxit)
         o.warm_start = 1 if warm_start else 0
         o.check_every = int(check_every)
+        o.host_loop = 1 if host_loop else 0
         return o
 
     def solve(self, b, x=None, solver="mgpcg", mode="mixed", tol=1e-8, maxit=100, warm_start=False,
-              check_every=1, raise_on_fail=True):
+              check_every=1, raise_on_fail=True, host_loop=False):
         """Solve L x = b on the finest level; returns (x, SolveStats).
 
         b may be a CUDA or a CPU float64 tensor; a CPU input is copied to the
@@ -231,7 +232,7 @@ class Hierarchy:
             warm_start = False
         pb = self._vec(b, self.n, (torch.float64,), "b")
         px = self._vec(x, self.n, (torch.float64,), "x")
-        o = self._solve_opts(solver, mode, tol, maxit, warm_start, check_every)
+        o = self._solve_opts(solver, mode, tol, maxit, warm_start, check_every, host_loop)
         st = L.dec_stats()
         rc = lib.dec_solve(self._h, pb, px, 1, C.byref(o), C.byref(st), self._stream())
         if rc not in (L.DEC_OK, L.DEC_ERR_NOT_CONVERGED) or (raise_on_fail and rc != L.DEC_OK):

@@ -45,6 +45,7 @@ void dec_solve_default_opts(dec_solve_opts *o) {
     o->maxit = 100;
     o->warm_start = 0;
     o->check_every = 1;
+    o->host_loop = 0;
 }
 
 int dec_mesh_create(const double *verts, int64_t nv, int dim, const int32_t *tris, int64_t nt, dec_mesh **out) {

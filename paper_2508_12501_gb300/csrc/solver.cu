@@ -480,7 +480,7 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     // conditional nodes are unavailable, the host relaunches one iteration at
     // a time and reads the residual in between.
     cudaGraphExec_t lg = nullptr;
-    if (!mg->prof && !mg->no_device_loop && o.maxit > 0) {
+    if (!mg->prof && !mg->no_device_loop && !o.host_loop && o.maxit > 0) {
         if (loop_graph(mg, o.solver, o.mode, &lg) != DEC_OK) lg = nullptr;
     }
     int64_t loop_runs = 0;

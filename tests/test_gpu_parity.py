@@ -197,3 +197,13 @@ def test_single_level_hierarchy_is_direct_solve():
     x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
     h.vcycle(_dev(b), x)
     assert _s0_rel(oh.finest, x.cpu().numpy(), omg.direct_solve(oh, b)) < 1e-12
+
+
+@pytest.mark.parametrize("solver", ["mg", "mgpcg"])
+def test_host_and_device_loops_agree(solver):
+    h, oh = _pair("ico5")
+    b = _dev(W.uniform_field(oh.finest.mesh.nv, 51))
+    x1, s1 = h.solve(b, solver=solver, tol=1e-10)
+    x2, s2 = h.solve(b, solver=solver, tol=1e-10, host_loop=True, check_every=3)
+    assert s1.iters == s2.iters
+    assert torch.equal(x1, x2)  # same kernels in the same order: bitwise equal
