@@ -65,15 +65,70 @@ struct BTile {
 // vector index, i.e. vertex i >> kshift, right-hand side i & (k-1).
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void brow(const BLevel &L, int v, int j, const float *x, float &s, float &d) {
-    const float xi = x[(v << L.kshift) + j];
-    s = 0.f;
+// Per-block path choice: groups whose width k is a multiple of 4 use 16-byte
+// loads of 4 adjacent right-hand sides (one ELL row read per 4 values);
+// other groups use one value per thread.  A tile belongs to one level, so the
+// branch is uniform across the block.
+template <int VW> struct VecT;
+template <> struct VecT<1> {
+    float v[1];
+};
+template <> struct VecT<4> {
+    float v[4];
+};
+
+template <int VW>
+__device__ __forceinline__ VecT<VW> vld(const float *p, int i) {
+    VecT<VW> r;
+    if constexpr (VW == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p + i);
+        r.v[0] = q.x;
+        r.v[1] = q.y;
+        r.v[2] = q.z;
+        r.v[3] = q.w;
+    } else {
+        r.v[0] = p[i];
+    }
+    return r;
+}
+
+template <int VW>
+__device__ __forceinline__ void vst(float *p, int i, const VecT<VW> &a) {
+    if constexpr (VW == 4)
+        *reinterpret_cast<float4 *>(p + i) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+    else
+        p[i] = a.v[0];
+}
+
+// s = sum_q w_q (x_i - x_col(q)), d = sum_q w_q for VW adjacent right-hand sides
+template <int VW>
+__device__ __forceinline__ void brow(const BLevel &L, int v, int j, const float *x, VecT<VW> &s, float &d) {
+    const VecT<VW> xi = vld<VW>(x, (v << L.kshift) + j);
+#pragma unroll
+    for (int c = 0; c < VW; ++c) s.v[c] = 0.f;
     d = 0.f;
     for (int q = 0; q < L.K; ++q) {
         const size_t o = (size_t)q * L.n + v;
         const float wk = __ldg(L.w + o);
-        s = fmaf(wk, xi - x[(__ldg(L.col + o) << L.kshift) + j], s);
+        const VecT<VW> xn = vld<VW>(x, (__ldg(L.col + o) << L.kshift) + j);
+#pragma unroll
+        for (int c = 0; c < VW; ++c) s.v[c] = fmaf(wk, xi.v[c] - xn.v[c], s.v[c]);
         d += wk;
+    }
+}
+
+template <int VW>
+__device__ __forceinline__ void smooth0_body(const BLevel &L, const BTile &t, float e, int dout) {
+    for (int i = t.begin + VW * threadIdx.x; i < t.end; i += VW * blockDim.x) {
+        const int v = i >> L.kshift;
+        float d = 0.f;
+        for (int q = 0; q < L.K; ++q) d += __ldg(L.w + (size_t)q * L.n + v);
+        const VecT<VW> bb = vld<VW>(L.b, i);
+        VecT<VW> val;
+#pragma unroll
+        for (int c = 0; c < VW; ++c) val.v[c] = d != 0.f ? e * (bb.v[c] / d) : 0.f;
+        vst<VW>(L.x[0], i, val);
+        if (dout) vst<VW>(L.d[0], i, val);
     }
 }
 
@@ -84,13 +139,34 @@ __global__ void k_b_smooth0(const BLevel *__restrict__ lv, const BTile *__restri
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
     const float e = cheb ? L.epre[0] : omega;
-    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
-        const int v = i >> L.kshift;
-        float d = 0.f;
-        for (int q = 0; q < L.K; ++q) d += __ldg(L.w + (size_t)q * L.n + v);
-        const float val = d != 0.f ? e * (L.b[i] / d) : 0.f;
-        L.x[0][i] = val;
-        if (dout) L.d[0][i] = val;
+    if ((L.k & 3) == 0)
+        smooth0_body<4>(L, t, e, dout);
+    else
+        smooth0_body<1>(L, t, e, dout);
+}
+
+template <int VW>
+__device__ __forceinline__ void smooth_body(const BLevel &L, const BTile &t, float e, float c, int src, int din,
+                                            int dout) {
+    const int dst = 1 - src;
+    const float *xs = L.x[src];
+    for (int i = t.begin + VW * threadIdx.x; i < t.end; i += VW * blockDim.x) {
+        const int v = i >> L.kshift, j = i & (L.k - 1);
+        VecT<VW> s;
+        float d;
+        brow<VW>(L, v, j, xs, s, d);
+        const VecT<VW> bb = vld<VW>(L.b, i), xo = vld<VW>(xs, i);
+        VecT<VW> dn, xn;
+        VecT<VW> dd;
+        if (din) dd = vld<VW>(L.d[src], i);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            const float q = d != 0.f ? (bb.v[k] - s.v[k]) / d : 0.f;
+            dn.v[k] = din ? fmaf(c, dd.v[k], e * q) : e * q;
+            xn.v[k] = xo.v[k] + dn.v[k];
+        }
+        vst<VW>(L.x[dst], i, xn);
+        if (dout) vst<VW>(L.d[dst], i, dn);
     }
 }
 
@@ -102,16 +178,24 @@ __global__ void k_b_smooth(const BLevel *__restrict__ lv, const BTile *__restric
     const BLevel &L = lv[t.lev];
     const float e = cheb ? (post ? L.epost[sweep] : L.epre[sweep]) : omega;
     const float c = cheb ? (post ? L.cpost[sweep] : L.cpre[sweep]) : 0.f;
-    const int dst = 1 - src;
-    const float *xs = L.x[src];
-    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+    if ((L.k & 3) == 0)
+        smooth_body<4>(L, t, e, c, src, din, dout);
+    else
+        smooth_body<1>(L, t, e, c, src, din, dout);
+}
+
+template <int VW>
+__device__ __forceinline__ void residual_body(const BLevel &L, const BTile &t, int src) {
+    for (int i = t.begin + VW * threadIdx.x; i < t.end; i += VW * blockDim.x) {
         const int v = i >> L.kshift, j = i & (L.k - 1);
-        float s, d;
-        brow(L, v, j, xs, s, d);
-        const float q = d != 0.f ? (L.b[i] - s) / d : 0.f;
-        const float delta = din ? fmaf(c, L.d[src][i], e * q) : e * q;
-        L.x[dst][i] = xs[i] + delta;
-        if (dout) L.d[dst][i] = delta;
+        VecT<VW> s;
+        float d;
+        brow<VW>(L, v, j, L.x[src], s, d);
+        const VecT<VW> bb = vld<VW>(L.b, i);
+        VecT<VW> r;
+#pragma unroll
+        for (int k = 0; k < VW; ++k) r.v[k] = d != 0.f ? bb.v[k] - s.v[k] : 0.f;
+        vst<VW>(L.r, i, r);
     }
 }
 
@@ -121,15 +205,46 @@ __global__ void k_b_residual(const BLevel *__restrict__ lv, const BTile *__restr
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
-    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
-        const int v = i >> L.kshift, j = i & (L.k - 1);
-        float s, d;
-        brow(L, v, j, L.x[src], s, d);
-        L.r[i] = d != 0.f ? L.b[i] - s : 0.f;
-    }
+    if ((L.k & 3) == 0)
+        residual_body<4>(L, t, src);
+    else
+        residual_body<1>(L, t, src);
 }
 
 // tiles range over the coarse items; t.lev is the fine level (the coarse one is t.lev - 1)
+template <int VW>
+__device__ __forceinline__ void restrict_body(const BLevel &L, const BLevel &C, const BTile &t, int star0) {
+    for (int i = t.begin + VW * threadIdx.x; i < t.end; i += VW * blockDim.x) {
+        const int c = i >> L.kshift, j = i & (L.k - 1);
+        VecT<VW> acc;
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc.v[k] = 0.f;
+        int deg = 0;
+        for (int q = 0; q < L.K; ++q) {
+            const int nb = __ldg(L.col + (size_t)q * L.n + c);
+            if (nb != c) {
+                const VecT<VW> rv = vld<VW>(L.r, (nb << L.kshift) + j);
+                const float sw = star0 ? __ldg(L.s0 + nb) : 1.f;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc.v[k] = fmaf(sw, rv.v[k], acc.v[k]);
+                ++deg;
+            }
+        }
+        const VecT<VW> rc = vld<VW>(L.r, (c << L.kshift) + j);
+        VecT<VW> out;
+        if (star0) {
+            const float sc = __ldg(L.s0 + c), inv = 1.f / __ldg(C.s0 + c);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) out.v[k] = (sc * rc.v[k] + 0.5f * acc.v[k]) * inv;
+        } else {
+            const float den = 1.f + 0.5f * (float)deg;
+#pragma unroll
+            for (int k = 0; k < VW; ++k) out.v[k] = (rc.v[k] + 0.5f * acc.v[k]) / den;
+        }
+        vst<VW>(C.b, i, out);
+    }
+}
+
 __global__ void k_b_restrict(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int star0,
                              const int *skip) {
     pdl_prologue();
@@ -137,22 +252,10 @@ __global__ void k_b_restrict(const BLevel *__restrict__ lv, const BTile *__restr
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
     const BLevel &C = lv[t.lev - 1];
-    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
-        const int c = i >> L.kshift, j = i & (L.k - 1);
-        float acc = 0.f;
-        int deg = 0;
-        for (int q = 0; q < L.K; ++q) {
-            const int nb = __ldg(L.col + (size_t)q * L.n + c);
-            if (nb != c) {
-                const float rv = L.r[(nb << L.kshift) + j];
-                acc += star0 ? __ldg(L.s0 + nb) * rv : rv;
-                ++deg;
-            }
-        }
-        const float rc = L.r[(c << L.kshift) + j];
-        C.b[i] = star0 ? (__ldg(L.s0 + c) * rc + 0.5f * acc) / __ldg(C.s0 + c)
-                       : (rc + 0.5f * acc) / (1.f + 0.5f * (float)deg);
-    }
+    if ((L.k & 3) == 0)
+        restrict_body<4>(L, C, t, star0);
+    else
+        restrict_body<1>(L, C, t, star0);
 }
 
 // coarsest level: x = G b for each right-hand side
@@ -170,6 +273,27 @@ __global__ void k_b_coarse(const BLevel *__restrict__ lv, const BTile *__restric
 }
 
 // x_f[dst] += P e_c with e_c the coarser level's cycle result
+template <int VW>
+__device__ __forceinline__ void prolong_body(const BLevel &L, const BLevel &C, const BTile &t, int dst) {
+    const float *ec = C.x[C.res_idx];
+    for (int i = t.begin + VW * threadIdx.x; i < t.end; i += VW * blockDim.x) {
+        const int v = i >> L.kshift, j = i & (L.k - 1);
+        VecT<VW> add;
+        if (v < C.n) {
+            add = vld<VW>(ec, (v << L.kshift) + j);
+        } else {
+            const int2 p = __ldg(L.par + (v - C.n));
+            const VecT<VW> a = vld<VW>(ec, (p.x << L.kshift) + j), b = vld<VW>(ec, (p.y << L.kshift) + j);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) add.v[k] = 0.5f * (a.v[k] + b.v[k]);
+        }
+        VecT<VW> x = vld<VW>(L.x[dst], i);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) x.v[k] += add.v[k];
+        vst<VW>(L.x[dst], i, x);
+    }
+}
+
 __global__ void k_b_prolong(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int dst,
                             const int *skip) {
     pdl_prologue();
@@ -177,18 +301,10 @@ __global__ void k_b_prolong(const BLevel *__restrict__ lv, const BTile *__restri
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
     const BLevel &C = lv[t.lev - 1];
-    const float *ec = C.x[C.res_idx];
-    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
-        const int v = i >> L.kshift, j = i & (L.k - 1);
-        float add;
-        if (v < C.n) {
-            add = ec[(v << L.kshift) + j];
-        } else {
-            const int2 p = __ldg(L.par + (v - C.n));
-            add = 0.5f * (ec[(p.x << L.kshift) + j] + ec[(p.y << L.kshift) + j]);
-        }
-        L.x[dst][i] += add;
-    }
+    if ((L.k & 3) == 0)
+        prolong_body<4>(L, C, t, dst);
+    else
+        prolong_body<1>(L, C, t, dst);
 }
 
 // Per-right-hand-side sums: a thread's items all share j = threadIdx.x & (k-1)
