@@ -277,6 +277,33 @@ def batched_workload(torch, dev, flush, stream, steps):
 
 
 # ----------------------------------------------------------------------------
+# V-cycle convergence factor of each smoother, GPU next to the oracle
+# ----------------------------------------------------------------------------
+
+def convergence_factors(torch, dev):
+    import paper_2508_12501_gb300 as P
+    from oracle import multigrid as omg
+    out = []
+    cases = [("icosphere x6 (40,962 V), gauge", W.icosahedron, 6, 5, "gauge", True),
+             ("unit square x7 (16,641 V), Dirichlet", W.unit_square, 7, 6, "dirichlet", False)]
+    for label, base, nsub, nl, bc, sph in cases:
+        v, t = base()
+        for smoother in ("jacobi", "chebyshev"):
+            for gamma in (1, 2):
+                h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, gamma=gamma)
+                oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph,
+                                         opts=omg.MGOptions(smoother=smoother, gamma=gamma))
+                b = W.uniform_field(h.n, 71)
+                _, st = h.solve(torch.as_tensor(b, device=dev), solver="mg", mode="f64", tol=1e-10, maxit=100)
+                ref = omg.mg_solve(oh, b, 1e-10, 100)
+                out.append({"mesh": label, "smoother": smoother, "cycle": "V(2,2)" if gamma == 1 else "W(2,2)",
+                            "gpu": round((st.rel_res / st.rel_res0) ** (1.0 / st.iters), 4),
+                            "oracle": round(omg.convergence_factor(ref.history), 4),
+                            "gpu_cycles": st.iters, "oracle_cycles": ref.iters})
+    return out
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 
@@ -461,6 +488,13 @@ def main():
     except Exception as ex:  # noqa: BLE001
         errors["e2e"] = repr(ex)
 
+    cfs = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cfs = convergence_factors(torch, dev)
+        except Exception as ex:  # noqa: BLE001
+            errors["convergence_factors"] = repr(ex)
+
     batched = None
     if not args.no_batched:
         try:
@@ -498,7 +532,7 @@ def main():
             "iters": st.iters, "rel_res": st.rel_res, "fp64_solves_per_s": v64,
             "fp64_iters": st64.iters if st64 else None,
             "speedup_vs_fp64": (value / world / v64) if v64 else None, "mixed_vs_fp64_rel_err_star0": err,
-            "vcycle_ms": vc_ms, "vcycle_mdof_s": mdofs, "batched": batched,
+            "vcycle_ms": vc_ms, "vcycle_mdof_s": mdofs, "batched": batched, "convergence_factors": cfs,
             "kernels": [{k: (round(v_, 6) if isinstance(v_, float) else v_) for k, v_ in r.items()} for r in rows],
         }
         if errors:

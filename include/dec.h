@@ -70,7 +70,9 @@ enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1 };
 /* Multigrid options.  dec_mg_default_opts() fills the defaults:
  * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
  * [0.3, 1.1] * lambda_max(D^-1 L) with lambda_max from 10 power iterations,
- * gamma = 1 (V-cycle; 2 gives a W-cycle), the paper's restriction. */
+ * gamma = 1 (V-cycle; 2 gives a W-cycle, up to 4), the paper's restriction.
+ * With gamma > 1 each coarse correction is repeated gamma times,
+ * e <- e + C(b - L e), except on the coarsest level whose solve is exact. */
 typedef struct dec_mg_opts {
     int smoother;
     int nu1, nu2;
@@ -225,6 +227,7 @@ int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_strea
  *     nothing needs clearing.  Calls whose executions overlap on the GPU (two
  *     streams, two host threads, two handles) race on the array: serialize
  *     them.
+ *   - Only V-cycles (gamma = 1); other hierarchies get DEC_ERR_ARG.
  *   - Hierarchies whose six FP32 vectors per level (each rounded up to 256
  *     bytes) need more than DEC_NOALLOC_SCRATCH_BYTES are rejected with
  *     DEC_ERR_ARG; 32 MiB covers a finest level of about one million vertices.

@@ -141,6 +141,14 @@ __global__ void __launch_bounds__(kThreads) k_smooth0(int n, int K, const T *__r
     }
 }
 
+// y = x (same precision)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_copy(int n, const T *__restrict__ x, T *__restrict__ y, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) y[i] = ldg(x + i);
+}
+
 // x += e (same precision)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_axpy1(int n, const T *__restrict__ e, T *__restrict__ x,

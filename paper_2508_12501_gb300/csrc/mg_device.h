@@ -27,6 +27,9 @@ struct DevLevel {
     int2 *par = nullptr;
     float *x32[2] = {nullptr, nullptr}, *d32[2] = {nullptr, nullptr}, *r32 = nullptr, *b32 = nullptr;
     double *x64[2] = {nullptr, nullptr}, *d64[2] = {nullptr, nullptr}, *r64 = nullptr, *b64 = nullptr;
+    // W-cycles (gamma > 1): accumulated coarse correction and the right-hand side of a repeat
+    float *y32 = nullptr, *c32 = nullptr;
+    double *y64 = nullptr, *c64 = nullptr;
     // Chebyshev coefficients (c_k, e_k) of one smoothing call of nu1 and nu2 steps
     std::vector<double> c_pre, e_pre, c_post, e_post;
 };
@@ -39,6 +42,8 @@ template <> struct P<float> {
     static float *b(DevLevel &L) { return L.b32; }
     static const float *w(const DevLevel &L) { return L.w32; }
     static const float *s0(const DevLevel &L) { return L.star0_32; }
+    static float *y(DevLevel &L) { return L.y32; }
+    static float *c(DevLevel &L) { return L.c32; }
 };
 template <> struct P<double> {
     static double *x(DevLevel &L, int i) { return L.x64[i]; }
@@ -47,6 +52,8 @@ template <> struct P<double> {
     static double *b(DevLevel &L) { return L.b64; }
     static const double *w(const DevLevel &L) { return L.w64; }
     static const double *s0(const DevLevel &L) { return L.star0; }
+    static double *y(DevLevel &L) { return L.y64; }
+    static double *c(DevLevel &L) { return L.c64; }
 };
 
 template <typename F>

@@ -206,6 +206,24 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
         }
     });
     T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip);
+    if (o.gamma > 1 && l - 1 > 0) {
+        // W-cycle: repeat the coarse correction gamma times, ec <- ec + C(b_c - L_c ec);
+        // (not on the coarsest level, whose dense solve is exact)
+        const int gc = grid_for(mg, C.n);
+        const T *wc = P<T>::w(C);
+        for (int rep = 1; rep < o.gamma; ++rep) {
+            launch(mg, k_copy<T>, gc, s, C.n, (const T *)ec, P<T>::y(C), skip);
+            dispatch_k(C.K, [&](auto kt) {
+                constexpr int KT = decltype(kt)::value;
+                ProfScope ps(mg, DEC_PK_RESIDUAL, l - 1, s);
+                launch(mg, k_residual<T, KT>, gc, s, C.n, C.K, (const int32_t *)C.col, wc, (const T *)P<T>::b(C),
+                       (const T *)P<T>::y(C), P<T>::c(C), skip);
+            });
+            T *e2 = cycle<T>(mg, l - 1, P<T>::c(C), s, skip);
+            launch(mg, k_axpy1<T>, gc, s, C.n, (const T *)e2, P<T>::y(C), skip);
+            ec = P<T>::y(C);
+        }
+    }
     {
         ProfScope ps(mg, DEC_PK_PROLONG, l, s);
         launch(mg, k_prolong<T>, g, s, C.n, L.n, L.par, ec, P<T>::x(L, cur), skip);
@@ -561,7 +579,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         return fail(Status::fail(DEC_ERR_ARG, "smoother not available"));
     if (o.restriction != DEC_RESTRICT_ROWNORM && o.restriction != DEC_RESTRICT_STAR0)
         return fail(Status::fail(DEC_ERR_ARG, "unknown restriction"));
-    if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma != 1 || o.power_iters < 1 ||
+    if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma < 1 || o.gamma > 4 || o.power_iters < 1 ||
         !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad multigrid options"));
     dec_mg *mg = new (std::nothrow) dec_mg;
@@ -621,6 +639,9 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         }
         if ((rc = dalloc(mg, &D.r32, D.n)) || (rc = dalloc(mg, &D.b32, D.n)) || (rc = dalloc(mg, &D.r64, D.n)) ||
             (rc = dalloc(mg, &D.b64, D.n)))
+            return bail(rc);
+        if (o.gamma > 1 && (((rc = dalloc(mg, &D.y32, D.n))) || (rc = dalloc(mg, &D.c32, D.n)) ||
+                            (rc = dalloc(mg, &D.y64, D.n)) || (rc = dalloc(mg, &D.c64, D.n))))
             return bail(rc);
         cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu1, 1), D.c_pre, D.e_pre);
         cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu2, 1), D.c_post, D.e_post);
@@ -969,6 +990,7 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
 extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_stream_t stream) {
     if (int rc = check_dev(mg)) return rc;
     if (!b || !x) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    if (mg->H.opts.gamma != 1) return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle is a V-cycle (gamma = 1)"));
     const size_t need = noalloc_floats(mg) * sizeof(float);
     if (need > DEC_NOALLOC_SCRATCH_BYTES)
         return fail(Status::fail(DEC_ERR_ARG, "hierarchy needs " + std::to_string(need) +

@@ -207,3 +207,41 @@ def test_host_and_device_loops_agree(solver):
     x2, s2 = h.solve(b, solver=solver, tol=1e-10, host_loop=True, check_every=3)
     assert s1.iters == s2.iters
     assert torch.equal(x1, x2)  # same kernels in the same order: bitwise equal
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["square5", "ico5"])
+def test_w_cycle_matches_oracle(name, prec):
+    P = _lib()
+    base, nsub, nl, bc, sph = CASES[name]
+    v, t = base()
+    h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, gamma=2)
+    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, opts=omg.MGOptions(gamma=2))
+    lev = oh.finest
+    b = omg.prepare_rhs(oh, W.uniform_field(lev.mesh.nv, 61))
+    ref = omg.vcycle(oh, b, np.zeros_like(b))
+    dt = torch.float64 if prec == "f64" else torch.float32
+    x = torch.zeros(lev.mesh.nv, dtype=dt, device="cuda")
+    h.vcycle(_dev(b, dt), x)
+    assert _s0_rel(lev, x.double().cpu().numpy(), ref) < (1e-12 if prec == "f64" else 2e-5)
+    xs, st = h.solve(_dev(W.uniform_field(lev.mesh.nv, 62)), solver="mg", mode="f64", tol=1e-10)
+    ref2 = omg.mg_solve(oh, W.uniform_field(lev.mesh.nv, 62), 1e-10, 100)
+    assert abs(st.iters - ref2.iters) <= 1
+
+
+@pytest.mark.parametrize("name", ["square5", "ico5"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_convergence_factor_matches_oracle(name, smoother, gamma):
+    # standalone MG in FP64: geometric-mean residual reduction per cycle, GPU vs oracle
+    P = _lib()
+    base, nsub, nl, bc, sph = CASES[name]
+    v, t = base()
+    h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, gamma=gamma)
+    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, opts=omg.MGOptions(smoother=smoother, gamma=gamma))
+    b = W.uniform_field(oh.finest.mesh.nv, 71)
+    _, st = h.solve(_dev(b), solver="mg", mode="f64", tol=1e-10, maxit=100)
+    ref = omg.mg_solve(oh, b, 1e-10, 100)
+    cf_gpu = (st.rel_res / st.rel_res0) ** (1.0 / st.iters)
+    cf_ref = omg.convergence_factor(ref.history)
+    assert abs(cf_gpu - cf_ref) <= 0.02, (cf_gpu, cf_ref)
