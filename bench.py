@@ -5,8 +5,11 @@ icosphere subdivided 8 times with midpoints projected to radius 1
 (655,362 vertices, 1,310,720 triangles), 7 multigrid levels (162 ... 655,362
 vertices), constant-nullspace gauge, right-hand side = sum of real spherical
 harmonics of degree 1..16 with N(0,1) coefficients (seed 1), flexible
-MG-preconditioned CG with FP32 V-cycles inside the FP64 outer iteration, to
-relative residual 1e-8.  One step = one complete solve with b resident in HBM.
+MG-preconditioned CG with FP32 V-cycles inside a float-float outer iteration
+(--mode mixed_ff; mixed = FP64 outer iteration, f64 = all FP64), to relative
+residual 1e-8.  One step = one complete solve with b resident in HBM.  The
+line also reports the other two modes and the true FP64 residual of every
+returned solution.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -42,7 +45,9 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # Algorithmic bytes per row of each kernel kind (K = stencil slots per row,
 # FP32 cycle vectors / FP64 outer vectors, int32 columns).  A gathered vector
 # is counted once per row (its entries are reused from cache by neighbours).
-def bytes_per_row(kind, K, mixed, cheb):
+def bytes_per_row(kind, K, mode, cheb):
+    mixed = mode != "f64"
+    ff = mode == "mixed_ff"
     f = 4 if mixed else 8  # cycle precision
     if kind == "smooth0":
         return K * f + f + f + (f if cheb else 0)
@@ -52,13 +57,19 @@ def bytes_per_row(kind, K, mixed, cheb):
     if kind == "residual":
         return K * 4 + K * f + 3 * f
     if kind == "spmv64":
+        if ff:
+            return K * 12 + 4 + 8 + 4  # col, w32 + wlo, p_i (f32), q hi+lo, *0 (f32)
         return K * 4 + K * 8 + 8 + 8 + 8  # col, w64, p_i, q, *0
     if kind == "update":
+        if ff:
+            return 4 + 8 + 16 + 16  # p, q, x and r (hi+lo, read and write)
         return 8 + 8 + 16 + 16 + (4 if mixed else 0)
     if kind == "zdots":
         # mixed: *0 (f32), free, z, r32, z_old (f32); f64: z, zn write, *0, r, z_old, free
         return (4 + 1 + 4 + 4 + 4) if mixed else (8 + 8 + 8 + 8 + 8 + 1)
     if kind == "pupd":
+        if ff:
+            return 1 + 4 + 4 + 8  # free, z, z_old write, p (f32) read and write
         return (1 + 4 + 4 + 16) if mixed else (8 + 1 + 8 + 16)
     return None
 
@@ -71,18 +82,18 @@ def prolong_bytes(n_f, n_c, f):
     return 2 * n_f * f + (n_f - n_c) * 8 + n_c * f
 
 
-def kernel_bytes(entry, hier, mixed, cheb):
+def kernel_bytes(entry, hier, mode, cheb):
     """Algorithmic bytes moved by one launch of a profiled kernel."""
     lvl = entry["level"]
     n = entry["rows"]
     K = hier.ell_width[lvl]
-    f = 4 if mixed else 8
+    f = 4 if mode != "f64" else 8
     kind = entry["kind"]
     if kind == "restrict":
         return restrict_bytes(n, hier.nv[lvl - 1], K, f)
     if kind == "prolong":
         return prolong_bytes(n, hier.nv[lvl - 1], f)
-    per = bytes_per_row(kind, K, mixed, cheb)
+    per = bytes_per_row(kind, K, mode, cheb)
     return None if per is None else per * n
 
 
@@ -313,7 +324,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--mode", default="mixed_ff", choices=["mixed_ff", "mixed", "f64"])
     ap.add_argument("--smoother", default="chebyshev", choices=["jacobi", "chebyshev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all-levels", action="store_true")
@@ -415,33 +426,55 @@ def main():
                               "gpu_launches": launches, "ms_per_step": 1e3 * tot_s / args.steps}), flush=True)
         return 0
 
-    # ---- plain FP64 form of the same solve (speedup at equal accuracy)
-    v64, st64, x_f64 = None, None, None
-    try:
-        ms64, st64, _, _ = timed_solves(args.steps, "f64")
-        x_f64 = x.clone()
-        v64 = args.steps / (sum(ms64) / 1e3)
-    except Exception as ex:  # noqa: BLE001
-        errors["fp64"] = repr(ex)
+    # ---- the other precision modes of the same solve, and the true FP64
+    # residual of every returned solution (dec_residual in FP64)
+    s0v = torch.as_tensor(h.table(-1, "star0"), device=dev)
+    bp = b - (s0v * b).sum() / s0v.sum()  # the gauge projection the solver applies to b
+
+    def true_rel(xv):
+        return float(torch.linalg.vector_norm(h.residual(bp, xv)) / torch.linalg.vector_norm(bp))
+    modes = {args.mode: {"solves_per_s": value / world, "iters": st.iters, "rel_res": st.rel_res,
+                         "true_rel_res": true_rel(x_mixed)}}
+    sols = {args.mode: x_mixed}
+    for m in ("mixed_ff", "mixed", "f64"):
+        if m == args.mode:
+            continue
+        try:
+            for _ in range(2):
+                h.solve(b, x, solver="mgpcg", mode=m, tol=TOL, host_loop=args.host_loop)
+            msm, stm, _, _ = timed_solves(args.steps, m)
+            sols[m] = x.clone()
+            modes[m] = {"solves_per_s": args.steps / (sum(msm) / 1e3), "iters": stm.iters, "rel_res": stm.rel_res,
+                        "true_rel_res": true_rel(sols[m])}
+        except Exception as ex:  # noqa: BLE001
+            errors["mode_" + m] = repr(ex)
+    v64 = modes.get("f64", {}).get("solves_per_s")
+    x_f64 = sols.get("f64")
 
     # ---- live per-kernel timing of the same solves (event pairs on the solve stream)
-    mixed = args.mode == "mixed"
+    mixed = args.mode != "f64"
     cheb = args.smoother == "chebyshev"
     rows, roof = [], None
     try:
         _, _, _, prof = timed_solves(args.steps, args.mode, profile=2 if args.profile_all_levels else 1)
         for e in prof or []:
-            by = kernel_bytes(e, h, mixed, cheb)
+            by = kernel_bytes(e, h, args.mode, cheb)
             avg = e["total_ms"] / max(1, e["launches"])
             rows.append(dict(e, avg_ms=avg, bytes=by, gbs=(by / (avg * 1e-3) / 1e9) if by else None))
         top = max(rows, key=lambda r: r["total_ms"]) if rows else None
         peak, peak_src = peaks()
         if top and top["bytes"]:
             tr = ncu_traffic(top["kind"])
+            avg_ms, by, how = top["avg_ms"], top["bytes"], "event pair around each launch inside the solve graph"
+            if top["kind"] == "smooth":
+                # the same kernel and launch shape, back to back on the solve stream: no event between launches
+                avg_ms, by = h.time_smooth(level=top["level"], reps=200)
+                how = "200 back-to-back launches between two CUDA events on the solve stream"
+            gbs = by / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": f"{top['kind']} (level {top['level']}, {top['rows']} rows)",
-                    "achieved": top["gbs"], "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                    "frac": top["gbs"] / peak, "traffic": tr, "algorithmic_bytes": top["bytes"],
-                    "avg_launch_ms": top["avg_ms"],
+                    "achieved": gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                    "frac": gbs / peak, "traffic": tr, "algorithmic_bytes": by,
+                    "avg_launch_ms": avg_ms, "timing": how, "in_graph_avg_launch_ms": top["avg_ms"],
                     "share_of_profiled_time": top["total_ms"] / sum(r["total_ms"] for r in rows)}
     except Exception as ex:  # noqa: BLE001
         errors["profile"] = repr(ex)
@@ -502,12 +535,13 @@ def main():
         except Exception as ex:  # noqa: BLE001
             errors["batched"] = repr(ex)
 
-    # accuracy of the mixed result against the plain FP64 GPU result (*0 norm)
+    # accuracy of each result against the plain FP64 GPU result (*0 norm)
     err = None
     if x_f64 is not None:
-        s0 = torch.as_tensor(h.table(-1, "star0"), device=dev)
-        d = x_mixed - x_f64
-        err = float(torch.sqrt((s0 * d * d).sum() / (s0 * x_f64 * x_f64).sum()))
+        for m, xm in sols.items():
+            d = xm - x_f64
+            modes[m]["rel_err_star0_vs_f64"] = float(torch.sqrt((s0v * d * d).sum() / (s0v * x_f64 * x_f64).sum()))
+        err = modes[args.mode]["rel_err_star0_vs_f64"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -524,14 +558,16 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed_ff": "f32 (float-float outer)", "mixed": "f32+f64", "f64": "f64"}[args.mode],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "nv": n, "levels": NLEVELS, "smoother": args.smoother,
                        "cycle": "V(2,2)", "mode": args.mode, "tol": TOL,
                        "l2": "256 MB buffer written before every step (flush)", "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-            "iters": st.iters, "rel_res": st.rel_res, "fp64_solves_per_s": v64,
-            "fp64_iters": st64.iters if st64 else None,
-            "speedup_vs_fp64": (value / world / v64) if v64 else None, "mixed_vs_fp64_rel_err_star0": err,
+            "iters": st.iters, "rel_res": st.rel_res, "true_rel_res": modes[args.mode]["true_rel_res"],
+            "modes": modes, "fp64_solves_per_s": v64,
+            "speedup_vs_fp64": (value / world / v64) if v64 else None, "mode_vs_fp64_rel_err_star0": err,
             "vcycle_ms": vc_ms, "vcycle_mdof_s": mdofs, "batched": batched, "convergence_factors": cfs,
             "kernels": [{k: (round(v_, 6) if isinstance(v_, float) else v_) for k, v_ in r.items()} for r in rows],
         }

@@ -65,7 +65,18 @@ enum { DEC_SMOOTH_JACOBI = 0, DEC_SMOOTH_CHEBYSHEV = 1, DEC_SMOOTH_MCGS = 2 };
  * cycle self-adjoint in the *0 inner product (an option, not the paper's). */
 enum { DEC_RESTRICT_ROWNORM = 0, DEC_RESTRICT_STAR0 = 1 };
 enum { DEC_SOLVER_MG = 0, DEC_SOLVER_MGPCG = 1, DEC_SOLVER_CG = 2 };
-enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1 };
+/* Precision of a solve (Sec. 3.1.2 with the mixed-precision pattern):
+ *   DEC_MODE_F64       cycles and outer iteration in FP64;
+ *   DEC_MODE_MIXED     FP32 cycles inside an FP64 outer iteration;
+ *   DEC_MODE_MIXED_FF  FP32 cycles inside a float-float outer iteration
+ *                      (not in the paper): x, r and L p as unevaluated sums
+ *                      of two floats (~48 bits), search directions in FP32,
+ *                      all on the FP32 pipe.  The updated residual tracks
+ *                      b - L x to about 1e-12 of ||b|| on 10^6-vertex meshes,
+ *                      so tolerances down to ~1e-10 are met by the true
+ *                      residual; use DEC_MODE_MIXED or DEC_MODE_F64 below that.
+ * Plain CG (DEC_SOLVER_CG) always runs in FP64. */
+enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1, DEC_MODE_MIXED_FF = 2 };
 
 /* Multigrid options.  dec_mg_default_opts() fills the defaults:
  * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
@@ -87,7 +98,7 @@ typedef struct dec_mg_opts {
  * tol = 1e-8, maxit = 100, no warm start, device-side iteration loop. */
 typedef struct dec_solve_opts {
     int solver;       /* DEC_SOLVER_*                                           */
-    int mode;         /* DEC_MODE_F64 or DEC_MODE_MIXED                           */
+    int mode;         /* DEC_MODE_*                                               */
     double tol;       /* stop when ||b - L x||_2 / ||b||_2 <= tol (free vertices) */
     int maxit;        /* outer iterations                                         */
     int warm_start;   /* nonzero: x holds the initial guess on entry              */
@@ -239,7 +250,8 @@ int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_stream_t str
  * (Sec. 3.1.2).  Standalone multigrid, or flexible CG in the *0 inner
  * product preconditioned by one cycle (Sec. 3.1.2 cross-comparison), or
  * plain CG.  DEC_MODE_MIXED runs the cycles in FP32 inside the FP64 outer
- * iteration (residuals, dot products and updates in FP64).  b and x are
+ * iteration (residuals and updates in FP64); DEC_MODE_MIXED_FF inside a
+ * float-float one (see the DEC_MODE_* enum).  b and x are
  * double device vectors of nv(finest) * k entries.  Under DEC_BC_GAUGE, b is
  * projected to *0-weighted mean zero and so is x.  Synchronizes `stream`
  * while iterating.  Returns DEC_ERR_NOT_CONVERGED (x holds the last iterate)
@@ -333,7 +345,7 @@ typedef struct dec_porous_params {
     double kappa;      /* thermal diffusivity lambda / (rho0 c_p)                    */
     double dt;         /* forward-Euler time step                                    */
     double tol;        /* relative-residual tolerance of every pressure solve        */
-    int mode;          /* DEC_MODE_F64 or DEC_MODE_MIXED for the pressure solves      */
+    int mode;          /* DEC_MODE_* of the pressure solves                           */
     int maxit;         /* MG-PCG iterations per pressure solve                       */
 } dec_porous_params;
 void dec_porous_default_params(dec_porous_params *prm);
@@ -395,6 +407,15 @@ typedef struct dec_prof_entry {
 } dec_prof_entry;
 int dec_mg_profile(dec_mg *mg, int enable);
 int dec_mg_profile_read(const dec_mg *mg, dec_prof_entry *out, int max, int *count);
+/* dec_mg_time_smooth: mean duration of one FP32 smoothing sweep on `level`
+ * (1 .. nlevels-1, or negative from the finest), the same kernel and launch
+ * configuration as the last step of a smoothing call inside the cycle, over
+ * `reps` back-to-back launches timed with CUDA events on `stream` (no events
+ * between launches), and its algorithmic bytes per launch (per row K column
+ * indices and K weights, x_i, b_i, the new x_i and, for Chebyshev, the
+ * direction).  Overwrites that level's FP32 cycle work vectors with zeros
+ * first (a timing call, not a computation). */
+int dec_mg_time_smooth(dec_mg *mg, int level, int reps, double *avg_ms, double *bytes, dec_stream_t stream);
 
 #ifdef __cplusplus
 }

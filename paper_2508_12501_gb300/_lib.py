@@ -27,7 +27,7 @@ DEC_F64, DEC_F32 = 0, 1
 DEC_SMOOTH_JACOBI, DEC_SMOOTH_CHEBYSHEV, DEC_SMOOTH_MCGS = 0, 1, 2
 DEC_RESTRICT_ROWNORM, DEC_RESTRICT_STAR0 = 0, 1
 DEC_SOLVER_MG, DEC_SOLVER_MGPCG, DEC_SOLVER_CG = 0, 1, 2
-DEC_MODE_F64, DEC_MODE_MIXED = 0, 1
+DEC_MODE_F64, DEC_MODE_MIXED, DEC_MODE_MIXED_FF = 0, 1, 2
 (DEC_TABLE_VERTS, DEC_TABLE_TRIS, DEC_TABLE_EDGES, DEC_TABLE_STAR0, DEC_TABLE_STAR1,
  DEC_TABLE_FREE, DEC_TABLE_PARENTS, DEC_TABLE_COLORS) = range(8)
 
@@ -119,6 +119,7 @@ _SIGS = {
     "dec_porous_backward": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _i, _p, _p,
                                  C.POINTER(dec_stats), _p]),
     "dec_mg_profile_read": (_i, [_p, C.POINTER(dec_prof_entry), _i, C.POINTER(_i)]),
+    "dec_mg_time_smooth": (_i, [_p, _i, _i, C.POINTER(C.c_double), C.POINTER(C.c_double), _p]),
 }
 
 for _name, (_res, _args) in _SIGS.items():

@@ -16,7 +16,7 @@ from ._lib import check, lib
 
 SMOOTHERS = {"jacobi": L.DEC_SMOOTH_JACOBI, "chebyshev": L.DEC_SMOOTH_CHEBYSHEV, "mcgs": L.DEC_SMOOTH_MCGS}
 SOLVERS = {"mg": L.DEC_SOLVER_MG, "mgpcg": L.DEC_SOLVER_MGPCG, "cg": L.DEC_SOLVER_CG}
-MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED}
+MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED, "mixed_ff": L.DEC_MODE_MIXED_FF}
 BCS = {"dirichlet": L.DEC_BC_DIRICHLET, "gauge": L.DEC_BC_GAUGE}
 RESTRICTIONS = {"rownorm": L.DEC_RESTRICT_ROWNORM, "star0": L.DEC_RESTRICT_STAR0}
 TABLES = {"verts": L.DEC_TABLE_VERTS, "tris": L.DEC_TABLE_TRIS, "edges": L.DEC_TABLE_EDGES,
@@ -269,6 +269,13 @@ class Hierarchy:
         check(lib.dec_mg_profile_read(self._h, buf, 256, C.byref(cnt)), "dec_mg_profile_read")
         return [dict(kind=L.PROF_KINDS[e.kind], level=e.level, launches=e.launches, total_ms=e.total_ms,
                      rows=e.rows) for e in buf[: cnt.value]]
+
+    def time_smooth(self, level=-1, reps=50):
+        """(mean ms, algorithmic bytes) of one FP32 smoothing launch on `level`, back-to-back launches."""
+        ms, by = C.c_double(), C.c_double()
+        check(lib.dec_mg_time_smooth(self._h, int(level), int(reps), C.byref(ms), C.byref(by), self._stream()),
+              "dec_mg_time_smooth")
+        return ms.value, by.value
 
     # ---- porous convection (Sec. 3.2) ------------------------------------
     def _porous_params(self, dt, g=(0.0, -9.81, 0.0), alpha_rho0=0.0, phi=0.1, k_eta=1.0, kappa=2.0, tol=1e-8,

@@ -29,6 +29,9 @@ struct Scal {
     double tol;
     double star0_sum;   // sum of *0 over free vertices
     double mean;        // result of the last k_mean
+    double scale;       // power-of-two scale of the ff outer iteration (set by k_outer_init)
+    float alpha_hi, alpha_lo;  // alpha as an ff pair
+    float beta_f, c_f;         // beta and the gauge shift rounded to FP32
     int iter, maxit, done, status;  // status: 0 ok, 1 non-finite
     int loops, max_loops;           // device-side iteration loop: executions and hard cap
     double hist[kHist];
@@ -70,7 +73,7 @@ __device__ __forceinline__ void row_apply(int i, int n, int K, const int32_t *__
 
 // y = L x
 template <typename T, int KT>
-__global__ void __launch_bounds__(kThreads) k_apply(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_apply(int n, int K, const int32_t *__restrict__ col,
                                                    const T *__restrict__ w, const T *__restrict__ x,
                                                    T *__restrict__ y, const int *skip) {
     pdl_prologue();
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(int n, int K, const int32_t 
 
 // r = b - L x on free rows, 0 on fixed rows
 template <typename T, int KT>
-__global__ void __launch_bounds__(kThreads) k_residual(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_residual(int n, int K, const int32_t *__restrict__ col,
                                                       const T *__restrict__ w, const T *__restrict__ b,
                                                       const T *__restrict__ x, T *__restrict__ r,
                                                       const int *skip) {
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, int K, const int32
 // a smoothing call has DIN = false, later steps DIN = true; DOUT is false on
 // the last step (its direction is never read).
 template <typename T, int KT, bool DIN, bool DOUT>
-__global__ void __launch_bounds__(kThreads) k_smooth(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_smooth(int n, int K, const int32_t *__restrict__ col,
                                                     const T *__restrict__ w, const T *__restrict__ b,
                                                     const T *__restrict__ x_in, const T *__restrict__ d_in,
                                                     T *__restrict__ x_out, T *__restrict__ d_out, T c, T e,
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth(int n, int K, const int32_t
 
 // First smoothing step from x = 0: x_out = e * D^-1 b (and d_out = x_out).
 template <typename T, int KT, bool DOUT>
-__global__ void __launch_bounds__(kThreads) k_smooth0(int n, int K, const T *__restrict__ w,
+__global__ void __launch_bounds__(kThreads, 8) k_smooth0(int n, int K, const T *__restrict__ w,
                                                      const T *__restrict__ b, T *__restrict__ x_out,
                                                      T *__restrict__ d_out, T e, const int *skip) {
     pdl_prologue();
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth0(int n, int K, const T *__r
 
 // y = x (same precision)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_copy(int n, const T *__restrict__ x, T *__restrict__ y, const int *skip) {
+__global__ void __launch_bounds__(kThreads, 8) k_copy(int n, const T *__restrict__ x, T *__restrict__ y, const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) y[i] = ldg(x + i);
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_copy(int n, const T *__restrict__ 
 
 // x += e (same precision)
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_axpy1(int n, const T *__restrict__ e, T *__restrict__ x,
+__global__ void __launch_bounds__(kThreads, 8) k_axpy1(int n, const T *__restrict__ e, T *__restrict__ x,
                                                    const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_axpy1(int n, const T *__restrict__
 // With STAR0 the *0-adjoint of interpolation is applied instead:
 //   b_c[c] = (s_f[c] r_f[c] + 1/2 sum_m s_f[m] r_f[m]) / s_c[c],  s = *0.
 template <typename T, int KT, bool STAR0>
-__global__ void __launch_bounds__(kThreads) k_restrict(int nc, int nf, int Kf, const int32_t *__restrict__ colf,
+__global__ void __launch_bounds__(kThreads, 8) k_restrict(int nc, int nf, int Kf, const int32_t *__restrict__ colf,
                                                       const T *__restrict__ rf, T *__restrict__ bc,
                                                       const T *__restrict__ s0f, const T *__restrict__ s0c,
                                                       const int *skip) {
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int nc, int nf, int Kf, c
 // Interpolation by the subdivision matrix and correction (Sec. 2.2.1):
 //   x_f[v] += e_c[v] for coarse ids, x_f[nc + m] += (e_c[a] + e_c[b]) / 2 for the midpoint of (a, b).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prolong(int nc, int nf, const int2 *__restrict__ par,
+__global__ void __launch_bounds__(kThreads, 8) k_prolong(int nc, int nf, const int2 *__restrict__ par,
                                                      const T *__restrict__ ec, T *__restrict__ xf,
                                                      const int *skip) {
     pdl_prologue();
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(int nc, int nf, const int2
 
 // Coarsest level: x = G b with the dense precomputed solution operator, one warp per row.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_coarse(int n0, const T *__restrict__ G, const T *__restrict__ b,
+__global__ void __launch_bounds__(kThreads, 8) k_coarse(int n0, const T *__restrict__ G, const T *__restrict__ b,
                                                     T *__restrict__ x, const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse(int n0, const T *__restrict
 }
 
 template <typename TD, typename TS>
-__global__ void __launch_bounds__(kThreads) k_cast(int n, const TS *__restrict__ src, TD *__restrict__ dst,
+__global__ void __launch_bounds__(kThreads, 8) k_cast(int n, const TS *__restrict__ src, TD *__restrict__ dst,
                                                   const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) k_cast(int n, const TS *__restrict__
 
 // x += (double) e
 template <typename TE>
-__global__ void __launch_bounds__(kThreads) k_add(int n, const TE *__restrict__ e, double *__restrict__ x,
+__global__ void __launch_bounds__(kThreads, 8) k_add(int n, const TE *__restrict__ e, double *__restrict__ x,
                                                  const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
@@ -263,41 +266,142 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Returns true in every thread of the last block; tot[] then holds the
-// grid-wide sums.  Requires blockDim.x == kThreads and gridDim.x <= kMaxRedBlocks.
-// The per-thread values (type TV) are summed across the warp in TV; warp sums
-// are then combined in double, so FP32 partials cost no FP64 instructions per thread.
-template <int NS, typename TV>
-__device__ bool grid_reduce(TV (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
-    __shared__ double sh[NS][kThreads / 32];
+// ---------------------------------------------------------------------------
+// Float-float ("ff") arithmetic: a value is the unevaluated sum hi + lo of
+// two floats, |lo| <= ulp(hi)/2, about 48 significant bits, computed on the
+// FP32 pipe.  Built from the error-free transformations TwoSum (Knuth),
+// Fast2Sum (Dekker) and the FMA form of TwoProduct; the _rn intrinsics keep
+// the compiler from contracting or reassociating them.
+// ---------------------------------------------------------------------------
+
+// s + e == a + b exactly
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+
+// s + e == a + b exactly, provided |a| >= |b| or a == 0
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// p + e == a * b exactly
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return make_float2(p, __fmaf_rn(a, b, -p));
+}
+
+// x + y; absolute error about 2^-47 (|x| + |y|)
+__device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
+    const float2 s = two_sum(x.x, y.x);
+    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
+
+// x + b for a float b
+__device__ __forceinline__ float2 ff_add(float2 x, float b) {
+    const float2 s = two_sum(x.x, b);
+    return fast_two_sum(s.x, __fadd_rn(s.y, x.y));
+}
+
+// a * b for an ff a and a float b (unnormalized: |lo| may exceed ulp(hi)/2 slightly)
+__device__ __forceinline__ float2 ff_mul(float2 a, float b) {
+    float2 p = two_prod(a.x, b);
+    p.y = __fmaf_rn(a.y, b, p.y);
+    return p;
+}
+
+// a * b for two ff values (unnormalized, the lo*lo term dropped)
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    float2 p = two_prod(a.x, b.x);
+    p.y = __fmaf_rn(a.x, b.y, p.y);
+    p.y = __fmaf_rn(a.y, b.x, p.y);
+    return p;
+}
+
+// Split a double into an ff pair (FP64 conversions: used at the start and
+// end of a solve and once per thread, never per row inside the iteration).
+__device__ __forceinline__ float2 ff_from(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 u;
+        u.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+        u.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+        v = ff_add(v, u);
+    }
+    return v;
+}
+
+constexpr int kWarps = kThreads / 32;
+
+// Sum over lanes [0, kWarps) of warp 0 (the other lanes hold zeros).
+__device__ __forceinline__ double warps_sum(double v) {
+#pragma unroll
+    for (int o = kWarps / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float2 warps_sum(float2 v) {
+#pragma unroll
+    for (int o = kWarps / 2; o > 0; o >>= 1) {
+        float2 u;
+        u.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+        u.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+        v = ff_add(v, u);
+    }
+    return v;
+}
+
+// Block arrival: true in every thread of the block that arrives last.
+__device__ __forceinline__ bool last_block(unsigned *counter) {
     __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Grid-wide sums.  Returns true in every thread of the last block to finish;
+// thread 0 of that block then holds the sums in tot[].  Requires blockDim.x ==
+// kThreads and gridDim.x <= kMaxRedBlocks.  The last block issues all its
+// partial loads first (one L2 round trip), then adds them in a fixed order,
+// so results do not depend on scheduling.
+//
+// FP64 per-thread values: warp and block sums in FP64.  GB300 issues FP64 at
+// a small fraction of its FP32 rate, so the tail adds only the partials a
+// warp actually holds (a warp-uniform bound) and combines warps over 8 lanes.
+template <int NS>
+__device__ bool grid_reduce(double (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
+    __shared__ double sh[NS][kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        TV x = warp_sum(v[s]);
-        if (lane == 0) sh[s][warp] = (double)x;
+        const double x = warp_sum(v[s]);
+        if (lane == 0) sh[s][warp] = x;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            double x = lane < kThreads / 32 ? sh[s][lane] : 0.0;
-            x = warp_sum(x);
+            const double x = warps_sum(lane < kWarps ? sh[s][lane] : 0.0);
             if (lane == 0) partials[s * kMaxRedBlocks + blockIdx.x] = x;
         }
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned t = atomicAdd(counter, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    // Final pass of the last block: every thread issues all of its partial
-    // loads first (unrolled, predicated), then adds them in a fixed order, so
-    // the tail costs one L2 round trip instead of one per partial.
+    if (!last_block(counter)) return false;
     constexpr int kPer = kMaxRedBlocks / kThreads;
+    const int nj = ((int)gridDim.x - warp * 32 + kThreads - 1) / kThreads;  // rounds with a live lane in this warp
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         double part[kPer];
@@ -306,19 +410,79 @@ __device__ bool grid_reduce(TV (&v)[NS], double *partials, unsigned *counter, do
             const int b = threadIdx.x + j * kThreads;
             part[j] = b < (int)gridDim.x ? __ldcg(partials + s * kMaxRedBlocks + b) : 0.0;
         }
-        double acc = 0.0;
+        double acc = part[0];
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) acc += part[j];
+        for (int j = 1; j < kPer; ++j)
+            if (j < nj) acc += part[j];
         acc = warp_sum(acc);
         __syncthreads();
         if (lane == 0) sh[s][warp] = acc;
         __syncthreads();
-        double t = 0.0;
-        for (int k = 0; k < kThreads / 32; ++k) t += sh[s][k];
-        tot[s] = t;
+        if (warp == 0) {
+            const double t = warps_sum(lane < kWarps ? sh[s][lane] : 0.0);
+            if (lane == 0) tot[s] = t;
+        }
     }
     if (threadIdx.x == 0) *counter = 0u;
     return true;
+}
+
+// FP32 per-thread values: warp, block and grid sums as compensated (ff)
+// sums on the FP32 pipe, so rounding beyond the per-thread FP32 sums is
+// about 2^-47 relative; only thread 0's final hi + lo touches FP64.  The
+// partials buffer holds one ff pair (8 bytes) per block and sum.
+template <int NS>
+__device__ bool grid_reduce(float (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
+    __shared__ float2 sh[NS][kWarps];
+    float2 *part2 = reinterpret_cast<float2 *>(partials);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const float2 x = warp_sum(make_float2(v[s], 0.f));
+        if (lane == 0) sh[s][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const float2 x = warps_sum(lane < kWarps ? sh[s][lane] : make_float2(0.f, 0.f));
+            if (lane == 0) part2[s * kMaxRedBlocks + blockIdx.x] = x;
+        }
+    }
+    if (!last_block(counter)) return false;
+    constexpr int kPer = kMaxRedBlocks / kThreads;
+    const int nj = ((int)gridDim.x - warp * 32 + kThreads - 1) / kThreads;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        float2 pt[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int b = threadIdx.x + j * kThreads;
+            pt[j] = b < (int)gridDim.x ? __ldcg(part2 + s * kMaxRedBlocks + b) : make_float2(0.f, 0.f);
+        }
+        float2 acc = pt[0];
+#pragma unroll
+        for (int j = 1; j < kPer; ++j)
+            if (j < nj) acc = ff_add(acc, pt[j]);
+        acc = warp_sum(acc);
+        __syncthreads();
+        if (lane == 0) sh[s][warp] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            const float2 t = warps_sum(lane < kWarps ? sh[s][lane] : make_float2(0.f, 0.f));
+            if (lane == 0) tot[s] = (double)t.x + (double)t.y;
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// 2^-e with e = floor(log2(rms of b)): the ff outer iteration works on b * scale,
+// whose rms lies in [1, 2) (exact; 1 for b == 0 or non-finite b).
+__device__ __forceinline__ double ff_scale(double bnorm2, int n) {
+    const double ms = bnorm2 / (double)(n > 0 ? n : 1);
+    if (!(ms > 0.0) || !isfinite(ms)) return 1.0;
+    return ldexp(1.0, -(ilogb(ms) >> 1));
 }
 
 __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
@@ -336,7 +500,7 @@ __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
 }
 
 // mean = sum(*0 v) / sum(*0) over free rows (mask: free != 0)
-static __global__ void __launch_bounds__(kThreads) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+static __global__ void __launch_bounds__(kThreads, 8) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                   const double *__restrict__ v, double *partials, unsigned *counter,
                                                   Scal *S, const int *skip) {
     pdl_prologue();
@@ -344,11 +508,11 @@ static __global__ void __launch_bounds__(kThreads) k_mean(int n, const double *_
     double acc[1] = {0.0};
     GRID_STRIDE(i, n) if (freev[i]) acc[0] += ldg(star0 + i) * ldg(v + i);
     double tot[1];
-    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] / S->star0_sum;
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] / S->star0_sum;
 }
 
 // v -= mean on free rows
-static __global__ void __launch_bounds__(kThreads) k_shift(int n, const uint8_t *__restrict__ freev, double *__restrict__ v,
+static __global__ void __launch_bounds__(kThreads, 8) k_shift(int n, const uint8_t *__restrict__ freev, double *__restrict__ v,
                                                    const Scal *S, const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
@@ -359,7 +523,7 @@ static __global__ void __launch_bounds__(kThreads) k_shift(int n, const uint8_t 
 // Initial residual of the outer iteration: r = b - L x, ||r||^2, ||b||^2 (free rows);
 // also writes the cycle's input rv (cast) when rv != nullptr.
 template <int KT, typename TV>
-__global__ void __launch_bounds__(kThreads) k_outer_init(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w, const uint8_t *__restrict__ freev,
                                                         const double *__restrict__ b, const double *__restrict__ x,
                                                         double *__restrict__ r, TV *__restrict__ rv, double *partials,
@@ -377,8 +541,9 @@ __global__ void __launch_bounds__(kThreads) k_outer_init(int n, int K, const int
         acc[1] += bi * bi;
     }
     double tot[2];
-    if (grid_reduce<2, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->bnorm2 = tot[1];
+        S->scale = ff_scale(tot[1], n);
         S->iter = 0;
         S->done = 0;
         S->status = 0;
@@ -390,7 +555,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_init(int n, int K, const int
 // After a cycle produced z (type TZ): zn = (double) z; sums of *0 z, *0 r zn, *0 r zo, *0 r;
 // epilogue: gauge shift c, new <r,z>, Polak-Ribiere beta.
 template <typename TZ>
-__global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+__global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                        const TZ *__restrict__ z, double *__restrict__ zn,
                                                        const double *__restrict__ r, const double *__restrict__ zo,
                                                        int first, int gauge, double *partials, unsigned *counter,
@@ -410,7 +575,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__r
         }
     }
     double tot[4];
-    if (grid_reduce<4, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) {
         double c = gauge ? tot[0] / S->star0_sum : 0.0;
         double rz_new = tot[1] - c * tot[3];
         S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
@@ -420,7 +585,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_zdots(int n, const double *__r
 }
 
 // z = zn - c (free rows), p = z + beta p (p = z on the first pass), zo = z.
-static __global__ void __launch_bounds__(kThreads) k_pcg_pupd(int n, const uint8_t *__restrict__ freev, const double *__restrict__ zn,
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_pupd(int n, const uint8_t *__restrict__ freev, const double *__restrict__ zn,
                                                       double *__restrict__ zo, double *__restrict__ p, int first,
                                                       const Scal *S, const int *skip) {
     pdl_prologue();
@@ -435,7 +600,7 @@ static __global__ void __launch_bounds__(kThreads) k_pcg_pupd(int n, const uint8
 
 // q = L p (free rows), <p, q> -> alpha = <r,z> / <p,q>
 template <int KT>
-__global__ void __launch_bounds__(kThreads) k_pcg_spmv(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv(int n, int K, const int32_t *__restrict__ col,
                                                       const double *__restrict__ w, const double *__restrict__ star0,
                                                       const uint8_t *__restrict__ freev, const double *__restrict__ p,
                                                       double *__restrict__ q, double *partials, unsigned *counter,
@@ -451,12 +616,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(int n, int K, const int32
         acc[0] += ldg(star0 + i) * ldg(p + i) * qi;
     }
     double tot[1];
-    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
 }
 
 // x += alpha p, r -= alpha q, rv = (TV) r, ||r||^2 -> convergence test
 template <typename TV>
-__global__ void __launch_bounds__(kThreads) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
+__global__ void __launch_bounds__(kThreads, 8) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
                                                         double *__restrict__ x, double *__restrict__ r, TV *__restrict__ rv,
                                                         double *partials, unsigned *counter, Scal *S, const int *skip) {
     pdl_prologue();
@@ -471,7 +636,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, const double *__
         acc[0] += ri * ri;
     }
     double tot[1];
-    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->iter += 1;
         record_residual(S, tot[0]);
     }
@@ -479,7 +644,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int n, const double *__
 
 // Standalone MG / iterative refinement: x += e; r = b - L x; ||r||^2 -> convergence test.
 template <int KT, typename TV>
-__global__ void __launch_bounds__(kThreads) k_mg_residual(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_mg_residual(int n, int K, const int32_t *__restrict__ col,
                                                          const double *__restrict__ w, const uint8_t *__restrict__ freev,
                                                          const double *__restrict__ b, const double *__restrict__ x,
                                                          double *__restrict__ r, TV *__restrict__ rv, double *partials,
@@ -496,7 +661,7 @@ __global__ void __launch_bounds__(kThreads) k_mg_residual(int n, int K, const in
         acc[0] += ri * ri;
     }
     double tot[1];
-    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->iter += 1;
         record_residual(S, tot[0]);
     }
@@ -531,7 +696,7 @@ __device__ __forceinline__ double row_apply_nod(int i, int n, int K, const int32
 
 // q = L p, <p, q> (*0) -> alpha
 template <int KT>
-__global__ void __launch_bounds__(kThreads) k_pcg_spmv_d(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_d(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w,
                                                         const double *__restrict__ star0, const double *__restrict__ p,
                                                         double *__restrict__ q, double *partials, unsigned *counter,
@@ -545,11 +710,11 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv_d(int n, int K, const int
         acc[0] = fma(ldg(star0 + i) * ldg(p + i), qi, acc[0]);
     }
     double tot[1];
-    if (grid_reduce<1, double>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
 }
 
 // x += alpha p, r -= alpha q (FP64), r32 = (float) r, ||r||^2 from r32
-static __global__ void __launch_bounds__(kThreads) k_pcg_update_m(int n, const double *__restrict__ p,
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_m(int n, const double *__restrict__ p,
                                                           const double *__restrict__ q, double *__restrict__ x,
                                                           double *__restrict__ r, float *__restrict__ r32,
                                                           double *partials, unsigned *counter, Scal *S,
@@ -567,14 +732,14 @@ static __global__ void __launch_bounds__(kThreads) k_pcg_update_m(int n, const d
         acc[0] = fmaf(rf, rf, acc[0]);
     }
     double tot[1];
-    if (grid_reduce<1, float>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->iter += 1;
         record_residual(S, tot[0]);
     }
 }
 
 // FP32 dot products of the preconditioned vector z (cycle output) with r32 and the previous z.
-static __global__ void __launch_bounds__(kThreads) k_pcg_zdots_m(int n, const float *__restrict__ s032,
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_m(int n, const float *__restrict__ s032,
                                                          const uint8_t *__restrict__ freev, const float *__restrict__ z,
                                                          const float *__restrict__ r32, const float *__restrict__ zo,
                                                          int first, int gauge, double *partials, unsigned *counter,
@@ -593,17 +758,19 @@ static __global__ void __launch_bounds__(kThreads) k_pcg_zdots_m(int n, const fl
         }
     }
     double tot[4];
-    if (grid_reduce<4, float>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) {
         double c = gauge ? tot[0] / S->star0_sum : 0.0;
         double rz_new = tot[1] - c * tot[3];
         S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
         S->rz = rz_new;
         S->c = c;
+        S->beta_f = (float)S->beta;
+        S->c_f = (float)c;
     }
 }
 
 // z = z - c (free rows, FP32), zo = z, p = z + beta p (FP64)
-static __global__ void __launch_bounds__(kThreads) k_pcg_pupd_m(int n, const uint8_t *__restrict__ freev,
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_pupd_m(int n, const uint8_t *__restrict__ freev,
                                                         const float *__restrict__ z, float *__restrict__ zo,
                                                         double *__restrict__ p, int first, const Scal *S,
                                                         const int *skip) {
@@ -620,7 +787,7 @@ static __global__ void __launch_bounds__(kThreads) k_pcg_pupd_m(int n, const uin
 
 // Standalone MG / iterative refinement (mixed): r = b - L x; r32; ||r||^2 in FP32.
 template <int KT>
-__global__ void __launch_bounds__(kThreads) k_mg_residual_m(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, 8) k_mg_residual_m(int n, int K, const int32_t *__restrict__ col,
                                                            const double *__restrict__ w,
                                                            const uint8_t *__restrict__ freev,
                                                            const double *__restrict__ b, const double *__restrict__ x,
@@ -639,9 +806,213 @@ __global__ void __launch_bounds__(kThreads) k_mg_residual_m(int n, int K, const 
         acc[0] = fmaf(rf, rf, acc[0]);
     }
     double tot[1];
-    if (grid_reduce<1, float>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->iter += 1;
         record_residual(S, tot[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Float-float outer iteration (DEC_MODE_MIXED_FF): no FP64 arithmetic per
+// row inside the iteration.  The iterate x, the residual r and q = L p are
+// ff pairs stored as separate hi and lo arrays (r's hi array is the FP32
+// right-hand side of the cycle); the search direction p is FP32.  q is the
+// ff product of the ff weights (w32 + wlo = w64 to ~2^-48) with the exact
+// FP32 differences p_i - p_k, accumulated as a compensated sum, so the
+// updated r tracks b - L x to about 2^-44 of the row terms.  All outer
+// vectors are scaled by the power of two S->scale.
+// ---------------------------------------------------------------------------
+
+// (L p)_i in ff for an FP32 vector p.
+template <int KT>
+__device__ __forceinline__ float2 row_apply_ff(int i, int n, int K, const int32_t *__restrict__ col,
+                                               const float *__restrict__ wh, const float *__restrict__ wl,
+                                               const float *__restrict__ p, float pi) {
+    const int Kk = KT > 0 ? KT : K;
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+        if (KT == 0 && k >= Kk) break;
+        const size_t o = (size_t)k * n + i;
+        const float2 d = two_sum(pi, -ldg(p + ldg(col + o)));
+        const float2 t = ff_mul(make_float2(ldg(wh + o), ldg(wl + o)), d);
+        const float2 u = two_sum(s, t.x);
+        s = u.x;
+        c = __fadd_rn(c, __fadd_rn(u.y, t.y));
+    }
+    return two_sum(s, c);
+}
+
+// (L x)_i in ff for an ff vector x (hi and lo arrays).
+template <int KT>
+__device__ __forceinline__ float2 row_apply_ff2(int i, int n, int K, const int32_t *__restrict__ col,
+                                                const float *__restrict__ wh, const float *__restrict__ wl,
+                                                const float *__restrict__ xh, const float *__restrict__ xl) {
+    const int Kk = KT > 0 ? KT : K;
+    const float xih = ldg(xh + i), xil = ldg(xl + i);
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+        if (KT == 0 && k >= Kk) break;
+        const size_t o = (size_t)k * n + i;
+        const int j = ldg(col + o);
+        float2 d = two_sum(xih, -ldg(xh + j));
+        d = two_sum(d.x, __fadd_rn(d.y, __fsub_rn(xil, ldg(xl + j))));
+        const float2 t = ff_mul(make_float2(ldg(wh + o), ldg(wl + o)), d);
+        const float2 u = two_sum(s, t.x);
+        s = u.x;
+        c = __fadd_rn(c, __fadd_rn(u.y, t.y));
+    }
+    return two_sum(s, c);
+}
+
+// Start of an ff solve: the FP64 x and r of k_outer_init (and b, for
+// standalone MG) -> scaled ff pairs.  x == nullptr means x = 0.
+static __global__ void __launch_bounds__(kThreads, 8) k_ff_split(int n, const double *__restrict__ x,
+                                                      const double *__restrict__ r, const double *__restrict__ b,
+                                                      float *__restrict__ xh, float *__restrict__ xl,
+                                                      float *__restrict__ rh, float *__restrict__ rl,
+                                                      float *__restrict__ bh, float *__restrict__ bl,
+                                                      const Scal *S) {
+    pdl_prologue();
+    const double sc = S->scale;
+    GRID_STRIDE(i, n) {
+        float2 v = x ? ff_from(ldg(x + i) * sc) : make_float2(0.f, 0.f);
+        xh[i] = v.x;
+        xl[i] = v.y;
+        v = ff_from(ldg(r + i) * sc);
+        rh[i] = v.x;
+        rl[i] = v.y;
+        if (bh) {
+            v = ff_from(ldg(b + i) * sc);
+            bh[i] = v.x;
+            bl[i] = v.y;
+        }
+    }
+}
+
+// End of an ff solve: x = (hi + lo) / scale.
+static __global__ void __launch_bounds__(kThreads, 8) k_ff_join(int n, const float *__restrict__ xh,
+                                                     const float *__restrict__ xl, double *__restrict__ x,
+                                                     const Scal *S) {
+    pdl_prologue();
+    const double is = 1.0 / S->scale;
+    GRID_STRIDE(i, n) x[i] = ((double)ldg(xh + i) + (double)ldg(xl + i)) * is;
+}
+
+// z = z - c (free rows), zo = z, p = z + beta p, all FP32.
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_pupd_f(int n, const uint8_t *__restrict__ freev,
+                                                        const float *__restrict__ z, float *__restrict__ zo,
+                                                        float *__restrict__ p, int first, const Scal *S,
+                                                        const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const float c = S->c_f, beta = S->beta_f;
+    GRID_STRIDE(i, n) {
+        const float zi = freev[i] ? ldg(z + i) - c : 0.f;
+        zo[i] = zi;
+        p[i] = first ? zi : fmaf(beta, p[i], zi);
+    }
+}
+
+// q = L p (ff), <p, q>*0 in FP32 products -> alpha = <r,z> / <p,q>
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_ff(int n, int K, const int32_t *__restrict__ col,
+                                                         const float *__restrict__ wh, const float *__restrict__ wl,
+                                                         const float *__restrict__ s032, const float *__restrict__ p,
+                                                         float *__restrict__ qh, float *__restrict__ ql,
+                                                         double *partials, unsigned *counter, Scal *S,
+                                                         const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    float acc[1] = {0.f};
+    GRID_STRIDE(i, n) {
+        const float pi = ldg(p + i);
+        const float2 q = row_apply_ff<KT>(i, n, K, col, wh, wl, p, pi);
+        qh[i] = q.x;
+        ql[i] = q.y;
+        acc[0] = fmaf(ldg(s032 + i) * pi, q.x, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        const double a = S->rz / tot[0];
+        const float2 af = ff_from(a);
+        S->alpha = a;
+        S->alpha_hi = af.x;
+        S->alpha_lo = af.y;
+    }
+}
+
+// x += alpha p, r -= alpha q (ff), ||r||^2 from r's hi part -> convergence test
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_ff(int n, const float *__restrict__ p,
+                                                           const float *__restrict__ qh, const float *__restrict__ ql,
+                                                           float *__restrict__ xh, float *__restrict__ xl,
+                                                           float *__restrict__ rh, float *__restrict__ rl,
+                                                           double *partials, unsigned *counter, Scal *S,
+                                                           const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const float2 a = make_float2(S->alpha_hi, S->alpha_lo);
+    float acc[1] = {0.f};
+    GRID_STRIDE(i, n) {
+        const float2 x = ff_add(make_float2(xh[i], xl[i]), ff_mul(a, ldg(p + i)));
+        xh[i] = x.x;
+        xl[i] = x.y;
+        const float2 aq = ff_mul(a, make_float2(ldg(qh + i), ldg(ql + i)));
+        const float2 r = ff_add(make_float2(rh[i], rl[i]), make_float2(-aq.x, -aq.y));
+        rh[i] = r.x;
+        rl[i] = r.y;
+        acc[0] = fmaf(r.x, r.x, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        const double is = 1.0 / S->scale;
+        S->iter += 1;
+        record_residual(S, tot[0] * is * is);
+    }
+}
+
+// Standalone MG in ff: x += e (FP32 cycle output)
+static __global__ void __launch_bounds__(kThreads, 8) k_add_ff(int n, const float *__restrict__ e,
+                                                    float *__restrict__ xh, float *__restrict__ xl,
+                                                    const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) {
+        const float2 x = ff_add(make_float2(xh[i], xl[i]), ldg(e + i));
+        xh[i] = x.x;
+        xl[i] = x.y;
+    }
+}
+
+// Standalone MG in ff: r = b - L x, ||r||^2 -> convergence test
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 8) k_mg_residual_ff(int n, int K, const int32_t *__restrict__ col,
+                                                            const float *__restrict__ wh, const float *__restrict__ wl,
+                                                            const uint8_t *__restrict__ freev,
+                                                            const float *__restrict__ bh, const float *__restrict__ bl,
+                                                            const float *__restrict__ xh, const float *__restrict__ xl,
+                                                            float *__restrict__ rh, float *__restrict__ rl,
+                                                            double *partials, unsigned *counter, Scal *S,
+                                                            const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    float acc[1] = {0.f};
+    GRID_STRIDE(i, n) {
+        float2 r = make_float2(0.f, 0.f);
+        if (freev[i]) {
+            const float2 s = row_apply_ff2<KT>(i, n, K, col, wh, wl, xh, xl);
+            r = ff_add(make_float2(ldg(bh + i), ldg(bl + i)), make_float2(-s.x, -s.y));
+        }
+        rh[i] = r.x;
+        rl[i] = r.y;
+        acc[0] = fmaf(r.x, r.x, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        const double is = 1.0 / S->scale;
+        S->iter += 1;
+        record_residual(S, tot[0] * is * is);
     }
 }
 
@@ -658,7 +1029,7 @@ static __global__ void k_loop_ctrl(cudaGraphConditionalHandle h, Scal *S) {
 }
 
 // Gradient with respect to the edge weights: g_e = -(d0 mu)_e (d0 u)_e.
-static __global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const int2 *__restrict__ edges, const double *__restrict__ mu,
+static __global__ void __launch_bounds__(kThreads, 8) k_edge_grad(int64_t ne, const int2 *__restrict__ edges, const double *__restrict__ mu,
                                                        const double *__restrict__ u, double *__restrict__ g) {
     pdl_prologue();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -668,7 +1039,7 @@ static __global__ void __launch_bounds__(kThreads) k_edge_grad(int64_t ne, const
 }
 
 // y = s0 .* x, or y = x ./ s0 (inverse != 0)
-static __global__ void __launch_bounds__(kThreads) k_star0_scale(int n, const double *__restrict__ star0, const double *x,
+static __global__ void __launch_bounds__(kThreads, 8) k_star0_scale(int n, const double *__restrict__ star0, const double *x,
                                                          double *y, int inverse) {
     pdl_prologue();
     GRID_STRIDE(i, n) y[i] = inverse ? x[i] / ldg(star0 + i) : x[i] * ldg(star0 + i);
@@ -678,7 +1049,7 @@ static __global__ void __launch_bounds__(kThreads) k_star0_scale(int n, const do
 static __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, const int32_t *__restrict__ slot_edge,
                                                          const double *__restrict__ star1, const double *__restrict__ star0,
                                                          const uint8_t *__restrict__ freev, double *__restrict__ w64,
-                                                         float *__restrict__ w32) {
+                                                         float *__restrict__ w32, float *__restrict__ wlo) {
     pdl_prologue();
     GRID_STRIDE(i, n) {
         const double s0 = ldg(star0 + i);
@@ -686,8 +1057,10 @@ static __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, c
             const size_t o = (size_t)k * n + i;
             const int e = ldg(slot_edge + o);
             double wk = (e >= 0 && freev[i]) ? ldg(star1 + e) / s0 : 0.0;
+            const float wh = (float)wk;
             w64[o] = wk;
-            w32[o] = (float)wk;
+            w32[o] = wh;
+            wlo[o] = (float)(wk - (double)wh);
         }
     }
 }

@@ -21,6 +21,7 @@ struct DevLevel {
     int32_t *col = nullptr;
     double *w64 = nullptr;
     float *w32 = nullptr;
+    float *wlo = nullptr;  // finest level: w64 - w32 rounded to FP32 (ff weights w32 + wlo)
     double *star0 = nullptr;
     float *star0_32 = nullptr;
     uint8_t *freev = nullptr;
@@ -83,6 +84,9 @@ struct dec_mg {
     // outer-iteration workspace (finest level, FP64)
     double *ox = nullptr, *orr = nullptr, *op = nullptr, *oq = nullptr, *ozn = nullptr, *ozo = nullptr, *ob = nullptr;
     float *zo32 = nullptr;     // previous preconditioned vector (mixed precision)
+    // float-float outer iteration: hi/lo arrays of x, r (hi = the finest b32), q, b; FP32 p
+    float *fxh = nullptr, *fxl = nullptr, *frl = nullptr, *fqh = nullptr, *fql = nullptr, *fp = nullptr;
+    float *fbh = nullptr, *fbl = nullptr;
     double *tmp = nullptr;
     double *partials = nullptr;
     unsigned *counter = nullptr;
@@ -90,18 +94,19 @@ struct dec_mg {
     decdev::Scal *scal_h = nullptr;  // pinned host mirror
     double star0_sum = 0.0;
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t graphs[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    // [solver][mode]
+    cudaGraphExec_t graphs[3][3] = {};
     // whole iteration loop on the device: a while node around one iteration
-    cudaGraphExec_t loops[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t loops[3][3] = {};
     bool no_device_loop = false;  // set if the driver refuses conditional nodes
-    int64_t loop_kernels[3][2] = {};  // kernel nodes in one pass of a loop body
+    int64_t loop_kernels[3][3] = {};  // kernel nodes in one pass of a loop body
     std::vector<void *> allocs;
     size_t bytes = 0;
     bool host_only = false;
     bool pdl = true;  // programmatic dependent launch between consecutive kernels
     // live kernel timing (dec_mg_profile)
     int64_t launches = 0;       // kernels enqueued outside graph capture
-    int64_t graph_kernels[3][2] = {};  // kernel nodes per captured iteration graph
+    int64_t graph_kernels[3][3] = {};  // kernel nodes per captured iteration graph
     int prof = 0;               // 0 off, 1 finest level, 2 all levels
     bool prof_capture = false;  // true while a profiled iteration graph is being captured
     bool capturing = false;     // true while any iteration graph is being captured

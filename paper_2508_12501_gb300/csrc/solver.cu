@@ -265,8 +265,9 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
         ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
         launch(mg, k_pcg_zdots<double>, rg, s, F.n, F.star0, F.freev, mg->orr, mg->ozn, mg->orr, mg->ozo, first,
                                                     gauge, mg->partials, mg->counter, mg->scal, skip);
-    } else if (mode == DEC_MODE_MIXED) {
-        // z (FP32 cycle output) and r32 feed FP32 dot products; p is updated in FP64
+    } else if (mode == DEC_MODE_MIXED || mode == DEC_MODE_MIXED_FF) {
+        // z (FP32 cycle output) and r32 feed FP32 dot products; p is updated in
+        // FP64 (mixed) or FP32 (float-float outer iteration)
         float *z = cycle<float>(mg, top, F.b32, s, skip);
         {
             ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
@@ -275,8 +276,12 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
                    mg->scal, skip);
         }
         ProfScope ps(mg, DEC_PK_PUPD, top, s);
-        launch(mg, k_pcg_pupd_m, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
-               mg->op, first ? 1 : 0, (const Scal *)mg->scal, skip);
+        if (mode == DEC_MODE_MIXED_FF)
+            launch(mg, k_pcg_pupd_f, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
+                   mg->fp, first ? 1 : 0, (const Scal *)mg->scal, skip);
+        else
+            launch(mg, k_pcg_pupd_m, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
+                   mg->op, first ? 1 : 0, (const Scal *)mg->scal, skip);
         return;
     } else {
         double *z = cycle<double>(mg, top, mg->orr, s, skip);
@@ -294,6 +299,23 @@ void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
     const int *skip = &mg->scal->done;
     const int rg = red_grid(mg, F.n);
     const int top = (int)mg->lv.size() - 1;
+    if (mode == DEC_MODE_MIXED_FF && solver != DEC_SOLVER_CG) {
+        dispatch_k(F.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            ProfScope ps(mg, DEC_PK_SPMV64, top, s);
+            launch(mg, k_pcg_spmv_ff<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const float *)F.w32,
+                   (const float *)F.wlo, (const float *)F.star0_32, (const float *)mg->fp, mg->fqh, mg->fql,
+                   mg->partials, mg->counter, mg->scal, skip);
+        });
+        {
+            ProfScope ps(mg, DEC_PK_UPDATE, top, s);
+            launch(mg, k_pcg_update_ff, rg, s, F.n, (const float *)mg->fp, (const float *)mg->fqh,
+                   (const float *)mg->fql, mg->fxh, mg->fxl, F.b32, mg->frl, mg->partials, mg->counter, mg->scal,
+                   skip);
+        }
+        enqueue_precondition(mg, solver, mode, false, s, skip);
+        return;
+    }
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         ProfScope ps(mg, DEC_PK_SPMV64, top, s);
@@ -317,7 +339,21 @@ void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
     const int *skip = &mg->scal->done;
     const int top = (int)mg->lv.size() - 1;
     const int rg = red_grid(mg, F.n);
-    if (mode == DEC_MODE_MIXED) {
+    if (mode == DEC_MODE_MIXED_FF) {
+        float *e = cycle<float>(mg, top, F.b32, s, skip);
+        {
+            ProfScope ps(mg, DEC_PK_ADD, top, s);
+            launch(mg, k_add_ff, grid_for(mg, F.n), s, F.n, (const float *)e, mg->fxh, mg->fxl, skip);
+        }
+        dispatch_k(F.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            ProfScope ps(mg, DEC_PK_MGRES, top, s);
+            launch(mg, k_mg_residual_ff<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const float *)F.w32,
+                   (const float *)F.wlo, (const uint8_t *)F.freev, (const float *)mg->fbh, (const float *)mg->fbl,
+                   (const float *)mg->fxh, (const float *)mg->fxl, F.b32, mg->frl, mg->partials, mg->counter,
+                   mg->scal, skip);
+        });
+    } else if (mode == DEC_MODE_MIXED) {
         float *e = cycle<float>(mg, top, F.b32, s, skip);
         {
             ProfScope ps(mg, DEC_PK_ADD, top, s);
@@ -460,14 +496,17 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         o = *po;
     else
         dec_solve_default_opts(&o);
-    if (o.solver < 0 || o.solver > 2 || (o.mode != DEC_MODE_F64 && o.mode != DEC_MODE_MIXED) || o.maxit < 0 ||
+    if (o.solver < 0 || o.solver > 2 || o.mode < DEC_MODE_F64 || o.mode > DEC_MODE_MIXED_FF || o.maxit < 0 ||
         o.maxit >= kHist || !(o.tol >= 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad solve options"));
     if (o.check_every < 1) o.check_every = 1;
     DevLevel &F = mg->lv.back();
     const size_t vb = sizeof(double) * F.n;
     const bool gauge = mg->H.bc == DEC_BC_GAUGE;
-    const bool mixed = o.mode == DEC_MODE_MIXED && o.solver != DEC_SOLVER_CG;
+    // plain CG runs in FP64 whatever the mode
+    if (o.solver == DEC_SOLVER_CG) o.mode = DEC_MODE_F64;
+    const bool mixed = o.mode != DEC_MODE_F64;
+    const bool ff = o.mode == DEC_MODE_MIXED_FF;
     const int64_t launches0 = mg->launches;
     int64_t graph_launches = 0;
     CK(cudaMemcpyAsync(mg->ob, b, vb, cudaMemcpyDeviceToDevice, s));
@@ -491,6 +530,13 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         enqueue_outer_init<float>(mg, F.b32, s);
     else
         enqueue_outer_init<double>(mg, (double *)nullptr, s);
+    if (ff) {
+        ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
+        const bool mg_solver = o.solver == DEC_SOLVER_MG;
+        launch(mg, k_ff_split, grid_for(mg, F.n), s, F.n, o.warm_start ? (const double *)mg->ox : nullptr,
+               (const double *)mg->orr, (const double *)mg->ob, mg->fxh, mg->fxl, F.b32, mg->frl,
+               mg_solver ? mg->fbh : nullptr, mg_solver ? mg->fbl : nullptr, (const Scal *)mg->scal);
+    }
     CK(cudaGetLastError());
     int rc = DEC_OK;
     // Default: the iteration loop runs on the device (one graph with a while
@@ -527,6 +573,11 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
             if (mg->prof) accumulate_slots(mg);
         }
     }
+    }
+    if (ff) {
+        ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
+        launch(mg, k_ff_join, grid_for(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl, mg->ox,
+               (const Scal *)mg->scal);
     }
     if (gauge) enqueue_mean_shift(mg, mg->ox, s, nullptr);
     CK(cudaMemcpyAsync(x, mg->ox, vb, cudaMemcpyDeviceToDevice, s));
@@ -670,6 +721,16 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         for (double **v : vecs)
             if ((rc = dalloc(mg, v, n))) return bail(rc);
         if ((rc = dalloc(mg, &mg->zo32, n))) return bail(rc);
+        float **fvecs[] = {&mg->fxh, &mg->fxl, &mg->frl, &mg->fqh, &mg->fql, &mg->fp, &mg->fbh, &mg->fbl};
+        for (float **v : fvecs)
+            if ((rc = dalloc(mg, v, n))) return bail(rc);
+        {
+            DevLevel &DF = mg->lv.back();
+            const size_t slots = (size_t)HF.K * n;
+            std::vector<float> wlo(slots);
+            for (size_t i = 0; i < slots; ++i) wlo[i] = (float)(HF.w[i] - (double)(float)HF.w[i]);
+            if ((rc = upload(mg, &DF.wlo, wlo.data(), slots))) return bail(rc);
+        }
 
         if ((rc = dalloc(mg, &mg->partials, 8 * kMaxRedBlocks))) return bail(rc);
         if ((rc = dalloc(mg, &mg->counter, 1))) return bail(rc);
@@ -742,7 +803,7 @@ int dec_mg_set_star1(dec_mg *mg, const double *star1, dec_stream_t stream) {
     if (!star1) return fail(Status::fail(DEC_ERR_ARG, "null star1"));
     cudaStream_t s = (cudaStream_t)stream;
     DevLevel &F = mg->lv.back();
-    launch(mg, k_set_weights, grid_for(mg, F.n), s, F.n, F.K, mg->slot_edge, star1, F.star0, F.freev, F.w64, F.w32);
+    launch(mg, k_set_weights, grid_for(mg, F.n), s, F.n, F.K, mg->slot_edge, star1, F.star0, F.freev, F.w64, F.w32, F.wlo);
     CK(cudaGetLastError());
     return DEC_OK;
 }
@@ -834,6 +895,57 @@ int dec_mg_profile_read(const dec_mg *mg, dec_prof_entry *out, int max, int *cou
             ++c;
         }
     *count = std::min(c, max);
+    return DEC_OK;
+}
+
+int dec_mg_time_smooth(dec_mg *mg, int level, int reps, double *avg_ms, double *bytes, dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    const int nl = (int)mg->lv.size();
+    if (level < 0) level += nl;
+    if (reps < 1 || !avg_ms || !bytes || level < 1 || level >= nl)
+        return fail(Status::fail(DEC_ERR_ARG, "bad argument (level must lie above the coarsest)"));
+    DevLevel &L = mg->lv[level];
+    const bool cheb = mg->H.opts.smoother == DEC_SMOOTH_CHEBYSHEV;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = sizeof(float) * L.n;
+    CK(cudaMemsetAsync(L.x32[0], 0, vb, s));
+    CK(cudaMemsetAsync(L.x32[1], 0, vb, s));
+    CK(cudaMemsetAsync(L.d32[0], 0, vb, s));
+    CK(cudaMemsetAsync(L.b32, 0, vb, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int g = grid_for(mg, L.n);
+    const int *noskip = nullptr;
+    // the last step of a smoothing call: reads x, b and (Chebyshev) a direction, writes x
+    auto sweep = [&](int it) {
+        float *xi = L.x32[it & 1], *xo = L.x32[1 - (it & 1)];
+        dispatch_k(L.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            if (cheb)
+                launch(mg, k_smooth<float, KT, true, false>, g, s, L.n, L.K, (const int32_t *)L.col,
+                       (const float *)L.w32, (const float *)L.b32, (const float *)xi, (const float *)L.d32[0], xo,
+                       (float *)nullptr, 0.5f, 0.5f, noskip);
+            else
+                launch(mg, k_smooth<float, KT, false, false>, g, s, L.n, L.K, (const int32_t *)L.col,
+                       (const float *)L.w32, (const float *)L.b32, (const float *)xi, (const float *)nullptr, xo,
+                       (float *)nullptr, 0.f, (float)mg->H.opts.omega, noskip);
+        });
+    };
+    for (int r = 0; r < 3; ++r) sweep(r);
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) sweep(r);
+    cudaEventRecord(e1, s);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return cuda_fail(ce, "dec_mg_time_smooth");
+    CK(cudaGetLastError());
+    *avg_ms = ms / reps;
+    // per row: K column indices and K weights, x_i, b_i, the new x_i (+ the direction)
+    *bytes = (double)L.n * (8.0 * L.K + 4.0 * (3 + (cheb ? 1 : 0)));
     return DEC_OK;
 }
 

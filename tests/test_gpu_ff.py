@@ -1,0 +1,126 @@
+"""Float-float outer iteration (mode "mixed_ff") and the benchmark workload at full size.
+
+The ff outer iteration keeps x, r and q = L p as unevaluated sums of two
+floats (about 48 bits) and the search direction in FP32.  What the oracle can
+check at any size is the property the mode promises: the FP64 relative
+residual ||b - L x|| / ||b|| of the returned x, recomputed on the CPU by the
+oracle's own operator, meets the requested tolerance.  The outer vectors are
+scaled by a power of two, so scaling b by 2^k scales x by exactly 2^k: the
+results are compared bitwise, including a b far below the FP32 range.
+
+The full-size case is the benchmark workload: icosphere x8 (655,362
+vertices), levels 8..2, Chebyshev V(2,2), gauge, a sum of real spherical
+harmonics l = 1..16 (seed 1), MG-PCG to 1e-8, in every precision mode.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mesh as omesh, multigrid as omg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _lib():
+    import paper_2508_12501_gb300 as P
+    return P
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _s0_rel(s0, a, b):
+    d = a - b
+    return float(np.sqrt(np.sum(s0 * d * d) / np.sum(s0 * b * b)))
+
+
+_full = {}
+
+
+def _full_size():
+    if not _full:
+        P = _lib()
+        v, t = W.icosahedron()
+        h = P.Hierarchy(P.Mesh(v, t), 8, 7, bc="gauge", sphere=True, smoother="chebyshev")
+        meshes, _ = omesh.refine(v, t, 8, sphere=True)
+        lev = omg.make_level(meshes[-1], "gauge")
+        b = W.sh_sum(lev.mesh.verts, W.sh_coefficients(1))
+        _full.update(h=h, lev=lev, b=b, bp=omg.project_mean_zero(lev, b))
+    return _full
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed", "mixed_ff"])
+def test_benchmark_workload_true_residual(mode):
+    F = _full_size()
+    h, lev = F["h"], F["lev"]
+    assert h.n == 655362
+    x, st = h.solve(_dev(F["b"]), solver="mgpcg", mode=mode, tol=1e-8)
+    x = x.cpu().numpy()
+    assert st.status == 0 and st.rel_res <= 1e-8 and st.iters <= 10
+    true = omg.rel_residual(lev, F["bp"], x)
+    assert true <= 1e-8, true
+    # the reported (updated) residual tracks the true one
+    assert abs(true - st.rel_res) <= 1e-3 * 1e-8 + 0.05 * st.rel_res
+    assert abs(omg.star0_mean(lev, x)) <= 1e-12 * np.sqrt(np.mean(x * x))
+    F.setdefault("x", {})[mode] = x
+
+
+def test_benchmark_workload_modes_agree():
+    F = _full_size()
+    xs = F.get("x", {})
+    if len(xs) < 3:
+        pytest.skip("needs the three solves above")
+    s0 = F["lev"].star0
+    # both at relative residual 1e-8: solutions agree far below the discretization error
+    assert _s0_rel(s0, xs["mixed_ff"], xs["f64"]) < 1e-7
+    assert _s0_rel(s0, xs["mixed"], xs["f64"]) < 1e-7
+
+
+@pytest.mark.parametrize("solver", ["mg", "mgpcg"])
+@pytest.mark.parametrize("bc", ["gauge", "dirichlet"])
+def test_power_of_two_scaling_is_exact(solver, bc):
+    P = _lib()
+    if bc == "gauge":
+        v, t = W.icosahedron()
+        h = P.Hierarchy(P.Mesh(v, t), 5, 4, bc="gauge", sphere=True)
+    else:
+        v, t = W.unit_square()
+        h = P.Hierarchy(P.Mesh(v, t), 6, 5, bc="dirichlet")
+    b = _dev(W.uniform_field(h.n, 91))
+    x1, s1 = h.solve(b, solver=solver, mode="mixed_ff", tol=1e-10)
+    for k in (-140, -60, 70):
+        # 2^-140 b is below the smallest normal FP32 number: only the scaling keeps it solvable
+        xk, sk = h.solve(b * 2.0 ** k, solver=solver, mode="mixed_ff", tol=1e-10)
+        assert sk.iters == s1.iters
+        assert torch.equal(xk, x1 * 2.0 ** k)
+
+
+@pytest.mark.parametrize("solver", ["mg", "mgpcg"])
+def test_ff_host_and_device_loops_agree(solver):
+    P = _lib()
+    v, t = W.icosahedron()
+    h = P.Hierarchy(P.Mesh(v, t), 5, 4, bc="gauge", sphere=True, smoother="chebyshev")
+    b = _dev(W.uniform_field(h.n, 93))
+    x1, s1 = h.solve(b, solver=solver, mode="mixed_ff", tol=1e-10)
+    x2, s2 = h.solve(b, solver=solver, mode="mixed_ff", tol=1e-10, host_loop=True, check_every=2)
+    assert s1.iters == s2.iters
+    assert torch.equal(x1, x2)
+
+
+def test_ff_warm_start_and_star1_update():
+    # new *1 weights reach the ff operator (w32 + wlo); a warm start from the solution converges at once
+    from oracle import dec
+    P = _lib()
+    v, t = W.unit_square()
+    h = P.Hierarchy(P.Mesh(v, t), 6, 5, bc="dirichlet")
+    m = omesh.refine(v, t, 6)[0][-1]
+    scale = W.lognormal_factors(m.ne, 7)
+    lev = omg.make_level(m, "dirichlet", star1_scale=scale)
+    h.set_star1(_dev(dec.hodge_star1(m, scale)))
+    b = W.uniform_field(h.n, 95)
+    x, st = h.solve(_dev(b), mode="mixed_ff", tol=1e-10, maxit=200)
+    assert omg.rel_residual(lev, lev.free * b, x.cpu().numpy()) <= 4e-10
+    x2, st2 = h.solve(_dev(b), x=x, warm_start=True, mode="mixed_ff", tol=1e-9)
+    assert st2.iters <= 1

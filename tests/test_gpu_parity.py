@@ -122,7 +122,7 @@ def test_one_cycle_matches_oracle(name, smoother, prec, restriction):
 
 @pytest.mark.parametrize("name", ["square5", "ico5", "fan3"])
 @pytest.mark.parametrize("solver", ["mg", "mgpcg", "cg"])
-@pytest.mark.parametrize("mode", ["f64", "mixed"])
+@pytest.mark.parametrize("mode", ["f64", "mixed", "mixed_ff"])
 def test_solve_matches_oracle(name, solver, mode):
     h, oh = _pair(name)
     lev = oh.finest
