@@ -51,6 +51,9 @@ def bytes_per_row(kind, K, mode, cheb):
     f = 4 if mixed else 8  # cycle precision
     if kind == "smooth0":
         return K * f + f + f + (f if cheb else 0)
+    if kind == "smooth01":
+        # operator, diagonal, b, the new x (two steps, nu = 2: no direction is written)
+        return K * 4 + K * f + 3 * f
     if kind == "smooth":
         # with nu = 2 each Chebyshev step reads or writes one direction vector
         return K * 4 + K * f + 3 * f + (f if cheb else 0)
@@ -93,6 +96,13 @@ def kernel_bytes(entry, hier, mode, cheb):
         return restrict_bytes(n, hier.nv[lvl - 1], K, f)
     if kind == "prolong":
         return prolong_bytes(n, hier.nv[lvl - 1], f)
+    nc = hier.nv[lvl - 1] if lvl > 0 else 0
+    if kind == "resrestrict":
+        # fine operator, x and b once; the coarse right-hand side written
+        return n * (K * 4 + K * f + 2 * f) + nc * f
+    if kind == "prolsmooth":
+        # operator, diagonal, b, x in and out, the direction (Chebyshev), the coarse correction and parents
+        return n * (K * 4 + K * f + 4 * f + (f if cheb else 0)) + nc * f + (n - nc) * 8
     per = bytes_per_row(kind, K, mode, cheb)
     return None if per is None else per * n
 

@@ -81,7 +81,8 @@ enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1, DEC_MODE_MIXED_FF = 2 };
 /* Multigrid options.  dec_mg_default_opts() fills the defaults:
  * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
  * [0.3, 1.1] * lambda_max(D^-1 L) with lambda_max from 10 power iterations,
- * gamma = 1 (V-cycle; 2 gives a W-cycle, up to 4), the paper's restriction.
+ * gamma = 1 (V-cycle; 2 gives a W-cycle, up to 4), the paper's restriction,
+ * one kernel per cycle step.
  * With gamma > 1 each coarse correction is repeated gamma times,
  * e <- e + C(b - L e), except on the coarsest level whose solve is exact. */
 typedef struct dec_mg_opts {
@@ -92,7 +93,15 @@ typedef struct dec_mg_opts {
     int power_iters;
     int gamma;
     int restriction;  /* DEC_RESTRICT_* */
+    int fuse;         /* DEC_FUSE_* mask of fused cycle kernels, each bitwise equal to
+                         the two separate kernels it replaces; 0 (default): one
+                         kernel per step, which measured faster on GB300 (the fused
+                         kernels gather two vectors per neighbour) */
 } dec_mg_opts;
+/* Fused cycle kernels: the first two pre-smoothing steps from zero; residual
+ * with restriction (stencils of at most 7 slots); interpolation and
+ * correction with the first post-smoothing step. */
+enum { DEC_FUSE_SMOOTH01 = 1, DEC_FUSE_RESTRICT = 2, DEC_FUSE_PROLONG = 4, DEC_FUSE_ALL = 7 };
 
 /* Solver options.  dec_solve_default_opts(): MG-PCG, mixed precision,
  * tol = 1e-8, maxit = 100, no warm start, device-side iteration loop. */
@@ -396,6 +405,9 @@ enum {
     DEC_PK_MGRES,       /* standalone-MG residual with ||r||                   */
     DEC_PK_ADD,         /* standalone-MG correction                            */
     DEC_PK_AUX,         /* set-up kernels of a solve (gauge mean, initial residual) */
+    DEC_PK_SMOOTH01,    /* fused first two smoothing steps from zero           */
+    DEC_PK_RESRESTRICT, /* fused residual and restriction (launched on the fine level) */
+    DEC_PK_PROLSMOOTH,  /* fused interpolation, correction and first post-smoothing step */
     DEC_PK_COUNT
 };
 typedef struct dec_prof_entry {

@@ -32,7 +32,7 @@ struct Scal {
     double scale;       // power-of-two scale of the ff outer iteration (set by k_outer_init)
     float alpha_hi, alpha_lo;  // alpha as an ff pair
     float beta_f, c_f;         // beta and the gauge shift rounded to FP32
-    int iter, maxit, done, status;  // status: 0 ok, 1 non-finite
+    int iter, maxit, done, status;  // status: 0 ok, 1 non-finite, 2 stalled (alpha = 0)
     int loops, max_loops;           // device-side iteration loop: executions and hard cap
     double hist[kHist];
 };
@@ -144,6 +144,153 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth0(int n, int K, const T *
     }
 }
 
+// Row sums d_i = sum_k w_k (the Jacobi diagonal), summed in slot order as
+// k_smooth0 and row_apply do, so the fused kernels below read the same value.
+template <typename T, int KT>
+__global__ void __launch_bounds__(kThreads, 8) k_diag(int n, int K, const T *__restrict__ w, T *__restrict__ dg) {
+    pdl_prologue();
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(i, n) {
+        T d = T(0);
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            d += ldg(w + (size_t)k * n + i);
+        }
+        dg[i] = d;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused cycle kernels.  Each replaces two consecutive launches of the cycle
+// and recomputes, per neighbour, the value the first would have stored, with
+// the same operations in the same order -- so the results are bitwise those
+// of the separate kernels, with one launch and one vector pass fewer.
+// ---------------------------------------------------------------------------
+
+// The first two smoothing steps from x = 0 (k_smooth0, then k_smooth with
+// DIN = Chebyshev): x1_j = e0 (b_j / d_j) is formed for row i and each
+// neighbour from b and the stored diagonal.  nu >= 2.
+template <typename T, int KT, bool CHEB, bool DOUT>
+__global__ void __launch_bounds__(kThreads, 8) k_smooth01(int n, int K, const int32_t *__restrict__ col,
+                                                      const T *__restrict__ w, const T *__restrict__ dg,
+                                                      const T *__restrict__ b, T *__restrict__ x_out,
+                                                      T *__restrict__ d_out, T e0, T c1, T e1, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(i, n) {
+        const T di = ldg(dg + i);
+        const T bi = ldg(b + i);
+        const T x1i = di != T(0) ? e0 * (bi / di) : T(0);
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + i;
+            const int j = ldg(col + o);
+            const T dj = ldg(dg + j);
+            const T x1j = dj != T(0) ? e0 * (ldg(b + j) / dj) : T(0);
+            s = fma(ldg(w + o), x1i - x1j, s);
+        }
+        const T q = di != T(0) ? (bi - s) / di : T(0);
+        const T delta = CHEB ? fma(c1, x1i, e1 * q) : e1 * q;
+        x_out[i] = x1i + delta;
+        if (DOUT) d_out[i] = delta;
+    }
+}
+
+// What k_prolong adds to fine vertex v.
+template <typename T>
+__device__ __forceinline__ T prolong_add(int v, int nc, const int2 *__restrict__ par, const T *__restrict__ ec) {
+    if (v < nc) return ldg(ec + v);
+    const int2 p = ldg(par + (v - nc));
+    return T(0.5) * (ldg(ec + p.x) + ldg(ec + p.y));
+}
+
+// Interpolation and correction (k_prolong) followed by the first step of the
+// post-smoothing call (k_smooth, DIN = false): x'_j = x_j + (P e)_j is formed
+// for row i and each neighbour; x_in keeps the uncorrected iterate.
+template <typename T, int KT, bool DOUT>
+__global__ void __launch_bounds__(kThreads, 8) k_prolong_smooth(int n, int K, int nc, const int2 *__restrict__ par,
+                                                            const T *__restrict__ ec, const int32_t *__restrict__ col,
+                                                            const T *__restrict__ w, const T *__restrict__ dg,
+                                                            const T *__restrict__ b, const T *__restrict__ x_in,
+                                                            T *__restrict__ x_out, T *__restrict__ d_out, T e0,
+                                                            const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(i, n) {
+        const T xi = ldg(x_in + i) + prolong_add(i, nc, par, ec);
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + i;
+            const int j = ldg(col + o);
+            const T xj = ldg(x_in + j) + prolong_add(j, nc, par, ec);
+            s = fma(ldg(w + o), xi - xj, s);
+        }
+        const T di = ldg(dg + i);
+        const T q = di != T(0) ? (ldg(b + i) - s) / di : T(0);
+        const T delta = e0 * q;
+        x_out[i] = xi + delta;
+        if (DOUT) d_out[i] = delta;
+    }
+}
+
+// Residual (k_residual) followed by restriction (k_restrict): a group of 8
+// lanes per coarse row c; lane 0 forms r_f at fine row c, lane k+1 at the
+// fine neighbour in slot k (a midpoint of a coarse edge at c), and lane 0
+// adds them in slot order.  Requires K <= 7.
+template <typename T, int KT, bool STAR0>
+__global__ void __launch_bounds__(kThreads, 8) k_residual_restrict(int nc, int nf, int K, const int32_t *__restrict__ col,
+                                                               const T *__restrict__ w, const T *__restrict__ b,
+                                                               const T *__restrict__ x, T *__restrict__ bc,
+                                                               const T *__restrict__ s0f, const T *__restrict__ s0c,
+                                                               const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const int Kk = KT > 0 ? KT : K;
+    const int lane8 = threadIdx.x & 7;
+    const int base = threadIdx.x & 31 & ~7;
+    const unsigned gmask = 0xFFu << base;
+    const int groups = (int)((gridDim.x * blockDim.x) >> 3);
+    for (int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3); c < nc; c += groups) {
+        int j = c;
+        bool valid = lane8 == 0;
+        if (lane8 > 0 && lane8 <= Kk) {
+            j = ldg(col + (size_t)(lane8 - 1) * nf + c);
+            valid = j != c;
+        }
+        T r = T(0), sj = T(0);
+        if (valid) {
+            T s, d;
+            row_apply<T, KT>(j, nf, K, col, w, x, s, d);
+            r = d != T(0) ? ldg(b + j) - s : T(0);
+            if (STAR0) sj = ldg(s0f + j);
+        }
+        T acc = T(0);
+        int deg = 0;
+        for (int k = 0; k < Kk; ++k) {
+            const T rk = __shfl_sync(gmask, r, base + k + 1);
+            const T sk = STAR0 ? __shfl_sync(gmask, sj, base + k + 1) : T(0);
+            const int vk = __shfl_sync(gmask, (int)valid, base + k + 1);
+            if (vk) {
+                acc = STAR0 ? fma(sk, rk, acc) : acc + rk;
+                ++deg;
+            }
+        }
+        if (lane8 == 0) {
+            if (STAR0)
+                bc[c] = fma(sj, r, T(0.5) * acc) / ldg(s0c + c);
+            else
+                bc[c] = fma(T(0.5), acc, r) / (T(1) + T(0.5) * T(deg));
+        }
+    }
+}
+
 // y = x (same precision)
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 8) k_copy(int n, const T *__restrict__ x, T *__restrict__ y, const int *skip) {
@@ -183,14 +330,15 @@ __global__ void __launch_bounds__(kThreads, 8) k_restrict(int nc, int nf, int Kf
             if (KT == 0 && k >= Kk) break;
             const int j = ldg(colf + (size_t)k * nf + c);
             if (j != c) {
-                acc += STAR0 ? ldg(s0f + j) * ldg(rf + j) : ldg(rf + j);
+                acc = STAR0 ? fma(ldg(s0f + j), ldg(rf + j), acc) : acc + ldg(rf + j);
                 ++deg;
             }
         }
+        // explicit fma: the fused k_residual_restrict rounds identically
         if (STAR0)
-            bc[c] = (ldg(s0f + c) * ldg(rf + c) + T(0.5) * acc) / ldg(s0c + c);
+            bc[c] = fma(ldg(s0f + c), ldg(rf + c), T(0.5) * acc) / ldg(s0c + c);
         else
-            bc[c] = (ldg(rf + c) + T(0.5) * acc) / (T(1) + T(0.5) * T(deg));
+            bc[c] = fma(T(0.5), acc, ldg(rf + c)) / (T(1) + T(0.5) * T(deg));
     }
 }
 
@@ -485,6 +633,27 @@ __device__ __forceinline__ double ff_scale(double bnorm2, int n) {
     return ldexp(1.0, -(ilogb(ms) >> 1));
 }
 
+// alpha = <r,z> / <p,Lp>.  A zero (or non-finite) quotient means the iteration
+// cannot move in this precision -- exact convergence, or, with FP32 dot
+// products, residuals so small that the products underflow.  Then alpha = 0,
+// the solve stops (status 2) and reports the residual reached so far.
+__device__ __forceinline__ void set_alpha(Scal *S, double pq) {
+    double a = S->rz / pq;
+    if (!isfinite(pq) || !isfinite(S->rz)) {
+        a = 0.0;
+        S->status = 1;
+        S->done = 1;
+    } else if (!(a != 0.0) || !isfinite(a)) {
+        a = 0.0;
+        S->status = 2;
+        S->done = 1;
+    }
+    const float2 af = ff_from(a);
+    S->alpha = a;
+    S->alpha_hi = af.x;
+    S->alpha_lo = af.y;
+}
+
 __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
     S->rnorm2 = rnorm2;
     const bool bad = !isfinite(rnorm2) || !isfinite(S->bnorm2);
@@ -616,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv(int n, int K, const in
         acc[0] += ldg(star0 + i) * ldg(p + i) * qi;
     }
     double tot[1];
-    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) set_alpha(S, tot[0]);
 }
 
 // x += alpha p, r -= alpha q, rv = (TV) r, ||r||^2 -> convergence test
@@ -710,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_d(int n, int K, const 
         acc[0] = fma(ldg(star0 + i) * ldg(p + i), qi, acc[0]);
     }
     double tot[1];
-    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->alpha = S->rz / tot[0];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) set_alpha(S, tot[0]);
 }
 
 // x += alpha p, r -= alpha q (FP64), r32 = (float) r, ||r||^2 from r32
@@ -935,11 +1104,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_ff(int n, int K, const
     }
     double tot[1];
     if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
-        const double a = S->rz / tot[0];
-        const float2 af = ff_from(a);
-        S->alpha = a;
-        S->alpha_hi = af.x;
-        S->alpha_lo = af.y;
+        set_alpha(S, tot[0]);
     }
 }
 

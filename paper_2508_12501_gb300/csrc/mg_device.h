@@ -22,6 +22,8 @@ struct DevLevel {
     double *w64 = nullptr;
     float *w32 = nullptr;
     float *wlo = nullptr;  // finest level: w64 - w32 rounded to FP32 (ff weights w32 + wlo)
+    float *dg32 = nullptr;     // row sums of w32 / w64 (the Jacobi diagonal), read by fused kernels
+    double *dg64 = nullptr;
     double *star0 = nullptr;
     float *star0_32 = nullptr;
     uint8_t *freev = nullptr;
@@ -43,6 +45,7 @@ template <> struct P<float> {
     static float *b(DevLevel &L) { return L.b32; }
     static const float *w(const DevLevel &L) { return L.w32; }
     static const float *s0(const DevLevel &L) { return L.star0_32; }
+    static const float *dg(const DevLevel &L) { return L.dg32; }
     static float *y(DevLevel &L) { return L.y32; }
     static float *c(DevLevel &L) { return L.c32; }
 };
@@ -53,6 +56,7 @@ template <> struct P<double> {
     static double *b(DevLevel &L) { return L.b64; }
     static const double *w(const DevLevel &L) { return L.w64; }
     static const double *s0(const DevLevel &L) { return L.star0; }
+    static const double *dg(const DevLevel &L) { return L.dg64; }
     static double *y(DevLevel &L) { return L.y64; }
     static double *c(DevLevel &L) { return L.c64; }
 };

@@ -124,9 +124,11 @@ void cheb_coeffs(double lmax, double lo, double hi, int nu, std::vector<double> 
 
 // nu smoothing steps on level l; if from_zero the iterate starts at 0.
 // `cur` is the x buffer index holding the iterate on entry/exit.
+// Steps k_start .. nu-1 of one smoothing call on level l.  From zero with
+// fused kernels, steps 0 and 1 run as one k_smooth01 launch.
 template <typename T>
 void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, int &cur, cudaStream_t s,
-            const int *skip) {
+            const int *skip, int k_start = 0) {
     DevLevel &L = mg->lv[l];
     const dec_mg_opts &o = mg->H.opts;
     const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
@@ -136,7 +138,23 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        for (int k = 0; k < nu; ++k) {
+        if (from_zero && nu >= 2 && (o.fuse & DEC_FUSE_SMOOTH01)) {
+            const T e0 = (T)(cheb ? ee[0] : o.omega), e1 = (T)(cheb ? ee[1] : o.omega);
+            const T c1 = (T)(cheb ? cc[1] : 0.0);
+            const bool dout = cheb && 2 < nu;
+            ProfScope ps(mg, DEC_PK_SMOOTH01, l, s);
+            const T *dg = P<T>::dg(L);
+            T *xo = P<T>::x(L, 1), *dn = dout ? P<T>::d(L, 1) : nullptr;
+            if (cheb && dout)
+                launch(mg, k_smooth01<T, KT, true, true>, g, s, L.n, L.K, L.col, w, dg, b, xo, dn, e0, c1, e1, skip);
+            else if (cheb)
+                launch(mg, k_smooth01<T, KT, true, false>, g, s, L.n, L.K, L.col, w, dg, b, xo, dn, e0, c1, e1, skip);
+            else
+                launch(mg, k_smooth01<T, KT, false, false>, g, s, L.n, L.K, L.col, w, dg, b, xo, dn, e0, c1, e1, skip);
+            cur = 1;
+            k_start = 2;
+        }
+        for (int k = k_start; k < nu; ++k) {
             const T e = (T)(cheb ? ee[k] : o.omega);
             const T c = (T)(cheb ? cc[k] : 0.0);
             const bool dout = cheb && k + 1 < nu;
@@ -191,6 +209,17 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
+        if ((o.fuse & DEC_FUSE_RESTRICT) && L.K <= 7) {
+            ProfScope ps(mg, DEC_PK_RESRESTRICT, l, s);
+            const int gr = grid_for(mg, (int64_t)C.n * 8);
+            if (o.restriction == DEC_RESTRICT_STAR0)
+                launch(mg, k_residual_restrict<T, KT, true>, gr, s, C.n, L.n, L.K, L.col, w, b,
+                       (const T *)P<T>::x(L, cur), P<T>::b(C), P<T>::s0(L), P<T>::s0(C), skip);
+            else
+                launch(mg, k_residual_restrict<T, KT, false>, gr, s, C.n, L.n, L.K, L.col, w, b,
+                       (const T *)P<T>::x(L, cur), P<T>::b(C), (const T *)nullptr, (const T *)nullptr, skip);
+            return;
+        }
         {
             ProfScope ps(mg, DEC_PK_RESIDUAL, l, s);
             launch(mg, k_residual<T, KT>, g, s, L.n, L.K, L.col, w, b, P<T>::x(L, cur), P<T>::r(L), skip);
@@ -223,6 +252,27 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
             launch(mg, k_axpy1<T>, gc, s, C.n, (const T *)e2, P<T>::y(C), skip);
             ec = P<T>::y(C);
         }
+    }
+    if ((o.fuse & DEC_FUSE_PROLONG) && o.nu2 > 0) {
+        const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+        const T e0 = (T)(cheb ? L.e_post[0] : o.omega);
+        const bool dout = cheb && 1 < o.nu2;
+        const int nxt = 1 - cur;
+        T *xo = P<T>::x(L, nxt), *dn = dout ? P<T>::d(L, nxt) : nullptr;
+        const T *xi = P<T>::x(L, cur), *dg = P<T>::dg(L);
+        dispatch_k(L.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            ProfScope ps(mg, DEC_PK_PROLSMOOTH, l, s);
+            if (dout)
+                launch(mg, k_prolong_smooth<T, KT, true>, g, s, L.n, L.K, C.n, (const int2 *)L.par, (const T *)ec,
+                       (const int32_t *)L.col, w, dg, b, xi, xo, dn, e0, skip);
+            else
+                launch(mg, k_prolong_smooth<T, KT, false>, g, s, L.n, L.K, C.n, (const int2 *)L.par, (const T *)ec,
+                       (const int32_t *)L.col, w, dg, b, xi, xo, dn, e0, skip);
+        });
+        cur = nxt;
+        smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip, 1);
+        return P<T>::x(L, cur);
     }
     {
         ProfScope ps(mg, DEC_PK_PROLONG, l, s);
@@ -597,7 +647,10 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
                  h->iter, h->bnorm2, h->iter > 0 ? h->hist[std::min(h->iter - 1, kHist - 1)] : 0.0, h->rz);
         return fail(Status::fail(DEC_ERR_NONFINITE, buf));
     }
-    if (!(h->rel <= o.tol)) return fail(Status::fail(DEC_ERR_NOT_CONVERGED, "maxit reached before tol"));
+    if (!(h->rel <= o.tol))
+        return fail(Status::fail(DEC_ERR_NOT_CONVERGED, h->status == 2 ? "iteration stalled (<r,z> or <p,Lp> is zero "
+                                                                         "in working precision) before tol"
+                                                                       : "maxit reached before tol"));
     return rc;
 }
 
@@ -610,6 +663,16 @@ int check_dev(const dec_mg *mg) {
     if (!mg) return fail(Status::fail(DEC_ERR_ARG, "null handle"));
     if (mg->host_only) return fail(Status::fail(DEC_ERR_ARG, "handle was built with DEC_HOST_ONLY"));
     return DEC_OK;
+}
+
+// Row sums of the level weights (FP32 and FP64), on `s` (0: legacy stream).
+void update_diagonals(dec_mg *mg, DevLevel &D, cudaStream_t s) {
+    const int g = grid_for(mg, D.n);
+    dispatch_k(D.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        launch(mg, k_diag<float, KT>, g, s, D.n, D.K, (const float *)D.w32, D.dg32);
+        launch(mg, k_diag<double, KT>, g, s, D.n, D.K, (const double *)D.w64, D.dg64);
+    });
 }
 
 }  // namespace
@@ -630,6 +693,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         return fail(Status::fail(DEC_ERR_ARG, "smoother not available"));
     if (o.restriction != DEC_RESTRICT_ROWNORM && o.restriction != DEC_RESTRICT_STAR0)
         return fail(Status::fail(DEC_ERR_ARG, "unknown restriction"));
+    if (o.fuse < 0 || o.fuse > DEC_FUSE_ALL) return fail(Status::fail(DEC_ERR_ARG, "fuse must be a DEC_FUSE_* mask"));
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma < 1 || o.gamma > 4 || o.power_iters < 1 ||
         !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad multigrid options"));
@@ -696,6 +760,8 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
             return bail(rc);
         cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu1, 1), D.c_pre, D.e_pre);
         cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu2, 1), D.c_post, D.e_post);
+        if ((rc = dalloc(mg, &D.dg32, D.n)) || (rc = dalloc(mg, &D.dg64, D.n))) return bail(rc);
+        update_diagonals(mg, D, nullptr);
     }
     // coarsest dense operator
     {
@@ -804,6 +870,7 @@ int dec_mg_set_star1(dec_mg *mg, const double *star1, dec_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     DevLevel &F = mg->lv.back();
     launch(mg, k_set_weights, grid_for(mg, F.n), s, F.n, F.K, mg->slot_edge, star1, F.star0, F.freev, F.w64, F.w32, F.wlo);
+    update_diagonals(mg, F, s);
     CK(cudaGetLastError());
     return DEC_OK;
 }

@@ -124,3 +124,20 @@ def test_ff_warm_start_and_star1_update():
     assert omg.rel_residual(lev, lev.free * b, x.cpu().numpy()) <= 4e-10
     x2, st2 = h.solve(_dev(b), x=x, warm_start=True, mode="mixed_ff", tol=1e-9)
     assert st2.iters <= 1
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed", "mixed_ff"])
+def test_tol_zero_stops_cleanly(mode):
+    # tol = 0 is never met: the iteration runs until it cannot move in its precision (in the
+    # mixed modes the FP32 dot products underflow near relative residual 1e-20) and then stops
+    # with DEC_ERR_NOT_CONVERGED, a finite x and no NaN
+    P = _lib()
+    v, t = W.unit_square()
+    h = P.Hierarchy(P.Mesh(v, t), 5, 5, bc="dirichlet", smoother="chebyshev")
+    oh = omg.build_hierarchy(v, t, 5, 5, "dirichlet", opts=omg.MGOptions(smoother="chebyshev"))
+    b = W.uniform_field(h.n, 97)
+    x, st = h.solve(_dev(b), mode=mode, tol=0.0, maxit=400, raise_on_fail=False)
+    assert st.status == 5 and torch.isfinite(x).all()
+    assert st.rel_res < 1e-12
+    xs = omg.direct_solve(oh, b)
+    assert _s0_rel(oh.finest.star0, x.cpu().numpy(), xs) < 1e-10
