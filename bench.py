@@ -45,12 +45,15 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # Algorithmic bytes per row of each kernel kind (K = stencil slots per row,
 # FP32 cycle vectors / FP64 outer vectors, int32 columns).  A gathered vector
 # is counted once per row (its entries are reused from cache by neighbours).
-def bytes_per_row(kind, K, mode, cheb):
+def bytes_per_row(kind, K, mode, cheb, outer=False):
     mixed = mode != "f64"
     ff = mode == "mixed_ff"
     f = 4 if mixed else 8  # cycle precision
     if kind == "smooth0":
         return K * f + f + f + (f if cheb else 0)
+    if kind == "smoothdots":
+        # the last smoothing step (operator, b = r32, x, direction, new x) plus *0, free mask, previous z
+        return K * 4 + K * 4 + 3 * 4 + (4 if cheb else 0) + 4 + 1 + 4
     if kind == "smooth01":
         # operator, diagonal, b, the new x (two steps, nu = 2: no direction is written)
         return K * 4 + K * f + 3 * f
@@ -65,7 +68,8 @@ def bytes_per_row(kind, K, mode, cheb):
         return K * 4 + K * 8 + 8 + 8 + 8  # col, w64, p_i, q, *0
     if kind == "update":
         if ff:
-            return 4 + 8 + 16 + 16  # p, q, x and r (hi+lo, read and write)
+            # p, q, x and r (hi+lo, read and write); fused: the diagonal and the first smoothing step's x, d
+            return 4 + 8 + 16 + 16 + (12 if outer else 0)
         return 8 + 8 + 16 + 16 + (4 if mixed else 0)
     if kind == "zdots":
         # mixed: *0 (f32), free, z, r32, z_old (f32); f64: z, zn write, *0, r, z_old, free
@@ -93,7 +97,10 @@ def kernel_bytes(entry, hier, mode, cheb):
     f = 4 if mode != "f64" else 8
     kind = entry["kind"]
     if kind == "restrict":
-        return restrict_bytes(n, hier.nv[lvl - 1], K, f)
+        extra = 0
+        if getattr(hier, "fuse", 0) & 8 and lvl - 1 > 0:
+            extra = hier.nv[lvl - 1] * (3 * f)  # the coarse level's first smoothing step: diagonal in, x and d out
+        return restrict_bytes(n, hier.nv[lvl - 1], K, f) + extra
     if kind == "prolong":
         return prolong_bytes(n, hier.nv[lvl - 1], f)
     nc = hier.nv[lvl - 1] if lvl > 0 else 0
@@ -103,7 +110,7 @@ def kernel_bytes(entry, hier, mode, cheb):
     if kind == "prolsmooth":
         # operator, diagonal, b, x in and out, the direction (Chebyshev), the coarse correction and parents
         return n * (K * 4 + K * f + 4 * f + (f if cheb else 0)) + nc * f + (n - nc) * 8
-    per = bytes_per_row(kind, K, mode, cheb)
+    per = bytes_per_row(kind, K, mode, cheb, outer=bool(getattr(hier, "fuse", 0) & 16))
     return None if per is None else per * n
 
 

@@ -82,7 +82,7 @@ enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1, DEC_MODE_MIXED_FF = 2 };
  * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
  * [0.3, 1.1] * lambda_max(D^-1 L) with lambda_max from 10 power iterations,
  * gamma = 1 (V-cycle; 2 gives a W-cycle, up to 4), the paper's restriction,
- * one kernel per cycle step.
+ * the row-local kernel fusions.
  * With gamma > 1 each coarse correction is repeated gamma times,
  * e <- e + C(b - L e), except on the coarsest level whose solve is exact. */
 typedef struct dec_mg_opts {
@@ -94,14 +94,23 @@ typedef struct dec_mg_opts {
     int gamma;
     int restriction;  /* DEC_RESTRICT_* */
     int fuse;         /* DEC_FUSE_* mask of fused cycle kernels, each bitwise equal to
-                         the two separate kernels it replaces; 0 (default): one
-                         kernel per step, which measured faster on GB300 (the fused
-                         kernels gather two vectors per neighbour) */
+                         the two separate kernels it replaces; default
+                         DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER, the row-local fusions
+                         (those that gather a second vector measured slower on GB300) */
 } dec_mg_opts;
-/* Fused cycle kernels: the first two pre-smoothing steps from zero; residual
- * with restriction (stencils of at most 7 slots); interpolation and
- * correction with the first post-smoothing step. */
-enum { DEC_FUSE_SMOOTH01 = 1, DEC_FUSE_RESTRICT = 2, DEC_FUSE_PROLONG = 4, DEC_FUSE_ALL = 7 };
+/* Fused cycle kernels.  Gathering a second vector per neighbour:
+ *   DEC_FUSE_SMOOTH01  the first two pre-smoothing steps from zero;
+ *   DEC_FUSE_RESTRICT  residual with restriction (stencils of at most 7 slots);
+ *   DEC_FUSE_PROLONG   interpolation and correction with the first post-smoothing step.
+ * Row-local, no extra gathers:
+ *   DEC_FUSE_RESTRICT0 restriction with the first smoothing step of the coarse level;
+ *   DEC_FUSE_OUTER     in MG-PCG with FP32 cycles (mixed modes): the outer update with the
+ *                      first smoothing step of the finest level, and the last post-smoothing
+ *                      step with the dot products of the preconditioned vector. */
+enum {
+    DEC_FUSE_SMOOTH01 = 1, DEC_FUSE_RESTRICT = 2, DEC_FUSE_PROLONG = 4, DEC_FUSE_RESTRICT0 = 8,
+    DEC_FUSE_OUTER = 16, DEC_FUSE_ALL = 31
+};
 
 /* Solver options.  dec_solve_default_opts(): MG-PCG, mixed precision,
  * tol = 1e-8, maxit = 100, no warm start, device-side iteration loop. */
@@ -408,6 +417,7 @@ enum {
     DEC_PK_SMOOTH01,    /* fused first two smoothing steps from zero           */
     DEC_PK_RESRESTRICT, /* fused residual and restriction (launched on the fine level) */
     DEC_PK_PROLSMOOTH,  /* fused interpolation, correction and first post-smoothing step */
+    DEC_PK_SMOOTHDOTS,  /* fused last post-smoothing step and preconditioned-vector dot products */
     DEC_PK_COUNT
 };
 typedef struct dec_prof_entry {

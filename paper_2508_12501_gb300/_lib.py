@@ -28,7 +28,8 @@ DEC_SMOOTH_JACOBI, DEC_SMOOTH_CHEBYSHEV, DEC_SMOOTH_MCGS = 0, 1, 2
 DEC_RESTRICT_ROWNORM, DEC_RESTRICT_STAR0 = 0, 1
 DEC_SOLVER_MG, DEC_SOLVER_MGPCG, DEC_SOLVER_CG = 0, 1, 2
 DEC_MODE_F64, DEC_MODE_MIXED, DEC_MODE_MIXED_FF = 0, 1, 2
-DEC_FUSE_SMOOTH01, DEC_FUSE_RESTRICT, DEC_FUSE_PROLONG, DEC_FUSE_ALL = 1, 2, 4, 7
+DEC_FUSE_SMOOTH01, DEC_FUSE_RESTRICT, DEC_FUSE_PROLONG, DEC_FUSE_RESTRICT0, DEC_FUSE_OUTER = 1, 2, 4, 8, 16
+DEC_FUSE_ALL = 31
 (DEC_TABLE_VERTS, DEC_TABLE_TRIS, DEC_TABLE_EDGES, DEC_TABLE_STAR0, DEC_TABLE_STAR1,
  DEC_TABLE_FREE, DEC_TABLE_PARENTS, DEC_TABLE_COLORS) = range(8)
 
@@ -57,7 +58,8 @@ class dec_prof_entry(C.Structure):
 
 
 PROF_KINDS = ["smooth0", "smooth", "residual", "restrict", "prolong", "coarse", "spmv64", "update", "zdots",
-              "pupd", "mgres", "add", "aux", "smooth01", "resrestrict", "prolsmooth"]
+              "pupd", "mgres", "add", "aux", "smooth01", "resrestrict", "prolsmooth",
+              "smoothdots"]
 
 
 class dec_porous_params(C.Structure):

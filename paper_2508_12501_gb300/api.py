@@ -91,7 +91,7 @@ class Hierarchy:
 
     def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
-                 restriction="rownorm", host_only=False, fuse=0):
+                 restriction="rownorm", host_only=False, fuse=None):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
         o = L.dec_mg_opts()
@@ -101,7 +101,9 @@ class Hierarchy:
         o.cheby_lo, o.cheby_hi = cheby_lo, cheby_hi
         o.power_iters, o.gamma = power_iters, gamma
         o.restriction = RESTRICTIONS[restriction]
-        o.fuse = int(fuse) if not isinstance(fuse, bool) else (L.DEC_FUSE_ALL if fuse else 0)
+        if fuse is not None:  # None keeps the library default (the row-local fusions)
+            o.fuse = int(fuse) if not isinstance(fuse, bool) else (L.DEC_FUSE_ALL if fuse else 0)
+        self.fuse = int(o.fuse)
         flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0)
         scale = None
         if star1_scale is not None:

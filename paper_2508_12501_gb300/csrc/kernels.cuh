@@ -314,11 +314,15 @@ __global__ void __launch_bounds__(kThreads, 8) k_axpy1(int n, const T *__restric
 // coarse edges, so the fine ELL row c lists them (padding: col == c).
 // With STAR0 the *0-adjoint of interpolation is applied instead:
 //   b_c[c] = (s_f[c] r_f[c] + 1/2 sum_m s_f[m] r_f[m]) / s_c[c],  s = *0.
-template <typename T, int KT, bool STAR0>
+// S0 > 0 also runs the first smoothing step of the coarse level from zero
+// on the new row (k_smooth0: xc = e0 bc / dgc, and dc = xc when S0 == 2):
+// row-local, so it costs no gathers.
+template <typename T, int KT, bool STAR0, int S0 = 0>
 __global__ void __launch_bounds__(kThreads, 8) k_restrict(int nc, int nf, int Kf, const int32_t *__restrict__ colf,
                                                       const T *__restrict__ rf, T *__restrict__ bc,
                                                       const T *__restrict__ s0f, const T *__restrict__ s0c,
-                                                      const int *skip) {
+                                                      const int *skip, const T *__restrict__ dgc,
+                                                      T *__restrict__ xc, T *__restrict__ dc, T e0) {
     pdl_prologue();
     if (skipped(skip)) return;
     const int Kk = KT > 0 ? KT : Kf;
@@ -335,10 +339,18 @@ __global__ void __launch_bounds__(kThreads, 8) k_restrict(int nc, int nf, int Kf
             }
         }
         // explicit fma: the fused k_residual_restrict rounds identically
+        T v;
         if (STAR0)
-            bc[c] = fma(ldg(s0f + c), ldg(rf + c), T(0.5) * acc) / ldg(s0c + c);
+            v = fma(ldg(s0f + c), ldg(rf + c), T(0.5) * acc) / ldg(s0c + c);
         else
-            bc[c] = fma(T(0.5), acc, ldg(rf + c)) / (T(1) + T(0.5) * T(deg));
+            v = fma(T(0.5), acc, ldg(rf + c)) / (T(1) + T(0.5) * T(deg));
+        bc[c] = v;
+        if (S0 > 0) {
+            const T d = ldg(dgc + c);
+            const T x1 = d != T(0) ? e0 * (v / d) : T(0);
+            xc[c] = x1;
+            if (S0 == 2) dc[c] = x1;
+        }
     }
 }
 
@@ -907,6 +919,18 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_m(int n, cons
     }
 }
 
+// After the four sums of the preconditioned vector z: gauge shift c, new
+// <r,z> and the Polak-Ribiere beta.
+__device__ __forceinline__ void zdots_epilogue(Scal *S, const double (&tot)[4], int first, int gauge) {
+    double c = gauge ? tot[0] / S->star0_sum : 0.0;
+    double rz_new = tot[1] - c * tot[3];
+    S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
+    S->rz = rz_new;
+    S->c = c;
+    S->beta_f = (float)S->beta;
+    S->c_f = (float)c;
+}
+
 // FP32 dot products of the preconditioned vector z (cycle output) with r32 and the previous z.
 static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_m(int n, const float *__restrict__ s032,
                                                          const uint8_t *__restrict__ freev, const float *__restrict__ z,
@@ -927,15 +951,45 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_m(int n, const
         }
     }
     double tot[4];
-    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) {
-        double c = gauge ? tot[0] / S->star0_sum : 0.0;
-        double rz_new = tot[1] - c * tot[3];
-        S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
-        S->rz = rz_new;
-        S->c = c;
-        S->beta_f = (float)S->beta;
-        S->c_f = (float)c;
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue(S, tot, first, gauge);
+}
+
+// The last post-smoothing step of the finest level (k_smooth with DIN =
+// Chebyshev, no direction out; b is r32) fused with k_pcg_zdots_m: the dot
+// products of z are row-local.  Launch on the reduction grid so that rows
+// map to threads as in k_pcg_zdots_m (bitwise equal sums).
+template <int KT, bool DIN>
+__global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots(int n, int K, const int32_t *__restrict__ col,
+                                                          const float *__restrict__ w, const float *__restrict__ b,
+                                                          const float *__restrict__ x_in,
+                                                          const float *__restrict__ d_in, float *__restrict__ x_out,
+                                                          float c, float e, const float *__restrict__ s032,
+                                                          const uint8_t *__restrict__ freev,
+                                                          const float *__restrict__ zo, int first, int gauge,
+                                                          double *partials, unsigned *counter, Scal *S,
+                                                          const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    GRID_STRIDE(i, n) {
+        float s, d;
+        row_apply<float, KT>(i, n, K, col, w, x_in, s, d);
+        const float ri = ldg(b + i);
+        const float q = d != 0.f ? (ri - s) / d : 0.f;
+        const float delta = DIN ? fmaf(c, ldg(d_in + i), e * q) : e * q;
+        const float zi = ldg(x_in + i) + delta;
+        x_out[i] = zi;
+        if (freev[i]) {
+            const float s0 = ldg(s032 + i);
+            const float sr = s0 * ri;
+            acc[0] = fmaf(s0, zi, acc[0]);
+            acc[1] = fmaf(sr, zi, acc[1]);
+            if (!first) acc[2] = fmaf(sr, ldg(zo + i), acc[2]);
+            acc[3] += sr;
+        }
     }
+    double tot[4];
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue(S, tot, first, gauge);
 }
 
 // z = z - c (free rows, FP32), zo = z, p = z + beta p (FP64)
@@ -1109,12 +1163,17 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_ff(int n, int K, const
 }
 
 // x += alpha p, r -= alpha q (ff), ||r||^2 from r's hi part -> convergence test
+// s0mode > 0 also runs the first smoothing step of the next cycle on the
+// finest level from zero (k_smooth0 on b = r's hi part: x0 = e0 r / dg, and
+// d0 = x0 when s0mode == 2), which is row-local.
 static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_ff(int n, const float *__restrict__ p,
                                                            const float *__restrict__ qh, const float *__restrict__ ql,
                                                            float *__restrict__ xh, float *__restrict__ xl,
                                                            float *__restrict__ rh, float *__restrict__ rl,
                                                            double *partials, unsigned *counter, Scal *S,
-                                                           const int *skip) {
+                                                           const int *skip, int s0mode,
+                                                           const float *__restrict__ dg, float *__restrict__ x0,
+                                                           float *__restrict__ d0, float e0) {
     pdl_prologue();
     if (skipped(skip)) return;
     const float2 a = make_float2(S->alpha_hi, S->alpha_lo);
@@ -1128,6 +1187,12 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_ff(int n, con
         rh[i] = r.x;
         rl[i] = r.y;
         acc[0] = fmaf(r.x, r.x, acc[0]);
+        if (s0mode > 0) {
+            const float di = ldg(dg + i);
+            const float v = di != 0.f ? e0 * (r.x / di) : 0.f;
+            x0[i] = v;
+            if (s0mode == 2) d0[i] = v;
+        }
     }
     double tot[1];
     if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {

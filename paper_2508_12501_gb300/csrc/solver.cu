@@ -124,11 +124,18 @@ void cheb_coeffs(double lmax, double lo, double hi, int nu, std::vector<double> 
 
 // nu smoothing steps on level l; if from_zero the iterate starts at 0.
 // `cur` is the x buffer index holding the iterate on entry/exit.
+// The outer dot products of the preconditioned vector, to be fused into the
+// last post-smoothing step of the finest level (DEC_FUSE_OUTER).
+struct DotsArgs {
+    int first = 0, gauge = 0;
+    bool done = false;  // set once the fused kernel has been enqueued
+};
+
 // Steps k_start .. nu-1 of one smoothing call on level l.  From zero with
 // fused kernels, steps 0 and 1 run as one k_smooth01 launch.
 template <typename T>
 void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, int &cur, cudaStream_t s,
-            const int *skip, int k_start = 0) {
+            const int *skip, int k_start = 0, DotsArgs *da = nullptr) {
     DevLevel &L = mg->lv[l];
     const dec_mg_opts &o = mg->H.opts;
     const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
@@ -138,7 +145,7 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        if (from_zero && nu >= 2 && (o.fuse & DEC_FUSE_SMOOTH01)) {
+        if (from_zero && k_start == 0 && nu >= 2 && (o.fuse & DEC_FUSE_SMOOTH01)) {
             const T e0 = (T)(cheb ? ee[0] : o.omega), e1 = (T)(cheb ? ee[1] : o.omega);
             const T c1 = (T)(cheb ? cc[1] : 0.0);
             const bool dout = cheb && 2 < nu;
@@ -171,6 +178,26 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
             const bool din = cheb && k > 0;
             T *xi = P<T>::x(L, cur), *xo = P<T>::x(L, nxt);
             T *di = P<T>::d(L, cur), *dn = P<T>::d(L, nxt);
+            if constexpr (std::is_same<T, float>::value) {
+                if (da && post && k == nu - 1) {
+                    DevLevel &F = mg->lv.back();
+                    ProfScope ps(mg, DEC_PK_SMOOTHDOTS, l, s);
+                    const int rg = red_grid(mg, L.n);
+                    if (din)
+                        launch(mg, k_smooth_zdots<KT, true>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
+                               (const float *)xi, (const float *)di, xo, c, e, (const float *)F.star0_32,
+                               (const uint8_t *)F.freev, (const float *)mg->zo32, da->first, da->gauge,
+                               mg->partials, mg->counter, mg->scal, skip);
+                    else
+                        launch(mg, k_smooth_zdots<KT, false>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
+                               (const float *)xi, (const float *)nullptr, xo, c, e, (const float *)F.star0_32,
+                               (const uint8_t *)F.freev, (const float *)mg->zo32, da->first, da->gauge,
+                               mg->partials, mg->counter, mg->scal, skip);
+                    da->done = true;
+                    cur = nxt;
+                    continue;
+                }
+            }
             ProfScope ps(mg, DEC_PK_SMOOTH, l, s);
             if (din && dout)
                 launch(mg, k_smooth<T, KT, true, true>, g, s, L.n, L.K, L.col, w, b, xi, di, xo, dn, c, e, skip);
@@ -187,8 +214,13 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
 
 // Enqueue one cycle C_l(b) with zero initial guess; returns the level-l
 // buffer that holds the result.
+// pre0_done: the first pre-smoothing step (from zero) of this level already
+// ran, fused into the kernel that produced b; x[0] (and d[0]) hold it.
+// da: fuse the last post-smoothing step of this (finest) level with the
+// outer dot products.
 template <typename T>
-T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
+T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pre0_done = false,
+         DotsArgs *da = nullptr) {
     DevLevel &L = mg->lv[l];
     if (l == 0) {
         const T *G;
@@ -202,9 +234,12 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
     DevLevel &C = mg->lv[l - 1];
     int cur = 0;
     if (o.nu1 > 0)
-        smooth<T>(mg, l, b, o.nu1, true, false, cur, s, skip);
+        smooth<T>(mg, l, b, o.nu1, true, false, cur, s, skip, pre0_done ? 1 : 0);
     else
         cudaMemsetAsync(P<T>::x(L, 0), 0, sizeof(T) * L.n, s);
+    // the coarse level's first smoothing step rides on the restriction
+    const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0;
+    bool coarse_pre0 = false;
     const int g = grid_for(mg, L.n);
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
@@ -226,15 +261,40 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
         }
         {
             ProfScope ps(mg, DEC_PK_RESTRICT, l, s);
-            if (o.restriction == DEC_RESTRICT_STAR0)
-                launch(mg, k_restrict<T, KT, true>, grid_for(mg, C.n), s, 
-                    C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C), P<T>::s0(L), P<T>::s0(C), skip);
+            const int gc = grid_for(mg, C.n);
+            if (restrict0) {
+                const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+                const T e0 = (T)(cheb ? C.e_pre[0] : o.omega);
+                const bool dout = cheb && 1 < o.nu1;
+                const T *dgc = P<T>::dg(C);
+                T *xc = P<T>::x(C, 0), *dc = P<T>::d(C, 0);
+                const T *s0l = P<T>::s0(L), *s0c = P<T>::s0(C);
+                if (o.restriction == DEC_RESTRICT_STAR0) {
+                    if (dout)
+                        launch(mg, k_restrict<T, KT, true, 2>, gc, s, C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
+                               s0l, s0c, skip, dgc, xc, dc, e0);
+                    else
+                        launch(mg, k_restrict<T, KT, true, 1>, gc, s, C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
+                               s0l, s0c, skip, dgc, xc, dc, e0);
+                } else {
+                    if (dout)
+                        launch(mg, k_restrict<T, KT, false, 2>, gc, s, C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
+                               (const T *)nullptr, (const T *)nullptr, skip, dgc, xc, dc, e0);
+                    else
+                        launch(mg, k_restrict<T, KT, false, 1>, gc, s, C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
+                               (const T *)nullptr, (const T *)nullptr, skip, dgc, xc, dc, e0);
+                }
+                coarse_pre0 = true;
+            } else if (o.restriction == DEC_RESTRICT_STAR0)
+                launch(mg, k_restrict<T, KT, true>, gc, s, C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
+                       P<T>::s0(L), P<T>::s0(C), skip, (const T *)nullptr, (T *)nullptr, (T *)nullptr, T(0));
             else
-                launch(mg, k_restrict<T, KT, false>, grid_for(mg, C.n), s, 
-                    C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C), nullptr, nullptr, skip);
+                launch(mg, k_restrict<T, KT, false>, gc, s, C.n, L.n, L.K, L.col, P<T>::r(L), P<T>::b(C),
+                       (const T *)nullptr, (const T *)nullptr, skip, (const T *)nullptr, (T *)nullptr, (T *)nullptr,
+                       T(0));
         }
     });
-    T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip);
+    T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip, coarse_pre0);
     if (o.gamma > 1 && l - 1 > 0) {
         // W-cycle: repeat the coarse correction gamma times, ec <- ec + C(b_c - L_c ec);
         // (not on the coarsest level, whose dense solve is exact)
@@ -271,14 +331,14 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip) {
                        (const int32_t *)L.col, w, dg, b, xi, xo, dn, e0, skip);
         });
         cur = nxt;
-        smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip, 1);
+        smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip, 1, da);
         return P<T>::x(L, cur);
     }
     {
         ProfScope ps(mg, DEC_PK_PROLONG, l, s);
         launch(mg, k_prolong<T>, g, s, C.n, L.n, L.par, ec, P<T>::x(L, cur), skip);
     }
-    if (o.nu2 > 0) smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip);
+    if (o.nu2 > 0) smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip, 0, da);
     return P<T>::x(L, cur);
 }
 
@@ -318,8 +378,15 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
     } else if (mode == DEC_MODE_MIXED || mode == DEC_MODE_MIXED_FF) {
         // z (FP32 cycle output) and r32 feed FP32 dot products; p is updated in
         // FP64 (mixed) or FP32 (float-float outer iteration)
-        float *z = cycle<float>(mg, top, F.b32, s, skip);
-        {
+        const dec_mg_opts &o = mg->H.opts;
+        const bool outer = (o.fuse & DEC_FUSE_OUTER) != 0;
+        DotsArgs da;
+        da.first = first ? 1 : 0;
+        da.gauge = gauge;
+        // after an ff update with the fused first smoothing step, the cycle starts at step 1
+        const bool pre0 = outer && !first && mode == DEC_MODE_MIXED_FF && o.nu1 > 0;
+        float *z = cycle<float>(mg, top, F.b32, s, skip, pre0, outer ? &da : nullptr);
+        if (!da.done) {
             ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
             launch(mg, k_pcg_zdots_m, rg, s, F.n, (const float *)F.star0_32, (const uint8_t *)F.freev, (const float *)z,
                    (const float *)F.b32, (const float *)mg->zo32, first ? 1 : 0, gauge, mg->partials, mg->counter,
@@ -359,9 +426,17 @@ void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
         });
         {
             ProfScope ps(mg, DEC_PK_UPDATE, top, s);
+            const dec_mg_opts &o = mg->H.opts;
+            int s0mode = 0;
+            float e0 = 0.f;
+            if ((o.fuse & DEC_FUSE_OUTER) && o.nu1 > 0) {
+                const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+                s0mode = cheb && 1 < o.nu1 ? 2 : 1;
+                e0 = (float)(cheb ? F.e_pre[0] : o.omega);
+            }
             launch(mg, k_pcg_update_ff, rg, s, F.n, (const float *)mg->fp, (const float *)mg->fqh,
                    (const float *)mg->fql, mg->fxh, mg->fxl, F.b32, mg->frl, mg->partials, mg->counter, mg->scal,
-                   skip);
+                   skip, s0mode, (const float *)F.dg32, F.x32[0], F.d32[0], e0);
         }
         enqueue_precondition(mg, solver, mode, false, s, skip);
         return;
@@ -1153,10 +1228,11 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
         launch(mg, k_residual<float, KT>, g, s, L.n, L.K, L.col, L.w32, b, B[l].x[cur], B[l].r, nullptr);
         if (o.restriction == DEC_RESTRICT_STAR0)
             launch(mg, k_restrict<float, KT, true>, grid_for(mg, C.n), s, C.n, L.n, L.K, L.col, B[l].r, B[l - 1].b,
-                                                                              L.star0_32, C.star0_32, nullptr);
+                   L.star0_32, C.star0_32, nullptr, (const float *)nullptr, (float *)nullptr, (float *)nullptr, 0.f);
         else
-            launch(mg, k_restrict<float, KT, false>, grid_for(mg, C.n), s, C.n, L.n, L.K, L.col, B[l].r,
-                                                                               B[l - 1].b, nullptr, nullptr, nullptr);
+            launch(mg, k_restrict<float, KT, false>, grid_for(mg, C.n), s, C.n, L.n, L.K, L.col, B[l].r, B[l - 1].b,
+                   (const float *)nullptr, (const float *)nullptr, nullptr, (const float *)nullptr, (float *)nullptr,
+                   (float *)nullptr, 0.f);
     });
     float *ec = noalloc_cycle(mg, B, l - 1, B[l - 1].b, s);
     launch(mg, k_prolong<float>, g, s, C.n, L.n, L.par, ec, B[l].x[cur], nullptr);

@@ -1,10 +1,14 @@
-"""Fused cycle kernels (fuse=True, every DEC_FUSE_* bit) against one kernel per step (fuse=0, the default).
+"""Fused cycle kernels (fuse=True: every DEC_FUSE_* bit) against one kernel per step (fuse=0).
 
 The fused kernels recompute, per neighbour, the value the first kernel of
 the pair would have stored, with the same operations in the same order:
   * the first two pre-smoothing steps from zero (k_smooth0 + k_smooth),
   * residual and restriction (k_residual + k_restrict; stencils of <= 7 slots),
-  * interpolation with the first post-smoothing step (k_prolong + k_smooth).
+  * interpolation with the first post-smoothing step (k_prolong + k_smooth),
+and, without extra gathers,
+  * restriction with the coarse level's first smoothing step (k_restrict + k_smooth0),
+  * in MG-PCG with FP32 cycles, the outer update with the finest level's first
+    smoothing step and the last post-smoothing step with the dot products.
 So cycles and whole solves must agree bit for bit, for every smoother,
 precision, restriction, sweep count and cycle shape; the parity of the
 unfused cycle with the oracle is covered by tests/test_gpu_parity.py.
@@ -92,7 +96,7 @@ def test_fused_solve_is_bitwise_equal(mode, solver):
     assert out[1][1].launches < out[0][1].launches
 
 
-@pytest.mark.parametrize("fuse", [1, 2, 4, 7])
+@pytest.mark.parametrize("fuse", [1, 2, 4, 7, 8, 9, 14])
 def test_fused_masks_match_unfused(fuse):
     import paper_2508_12501_gb300 as P
     base, nsub, nl, bc, sph = CASES["square5"]
@@ -115,3 +119,20 @@ def test_fused_matches_oracle():
     s0 = oh.finest.star0
     d = x.cpu().numpy() - ref
     assert np.sqrt(np.sum(s0 * d * d) / np.sum(s0 * ref * ref)) < 1e-12
+
+
+@pytest.mark.parametrize("fuse", [8, 16, 24, 31])
+@pytest.mark.parametrize("mode", ["mixed", "mixed_ff"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+def test_outer_fusion_solves_match(fuse, mode, smoother):
+    import paper_2508_12501_gb300 as P
+    for name in ("square5", "ico5"):
+        base, nsub, nl, bc, sph = CASES[name]
+        v, t = base()
+        hs = [P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, fuse=f) for f in (0, fuse)]
+        b = torch.as_tensor(W.uniform_field(hs[0].n, 19), device="cuda")
+        out = [h.solve(b, solver="mgpcg", mode=mode, tol=1e-10) for h in hs]
+        assert out[0][1].iters == out[1][1].iters
+        assert torch.equal(out[0][0], out[1][0])
+        out = [h.solve(b, solver="mgpcg", mode=mode, tol=1e-10, host_loop=True) for h in hs]
+        assert torch.equal(out[0][0], out[1][0])
