@@ -51,11 +51,14 @@ enum {
 };
 
 /* ---- enums ------------------------------------------------------------- */
-/* dec_mg_build flags: DEC_SPHERE_PROJECT pushes new midpoints to the unit
- * sphere; DEC_HOST_ONLY builds the host tables only (no device memory, no
- * CUDA call) so they can be inspected with dec_mg_info / dec_mg_copy_table;
- * compute calls on such a handle return DEC_ERR_ARG. */
-enum { DEC_SPHERE_PROJECT = 1u, DEC_HOST_ONLY = 2u };
+/* dec_mg_build / dec_mesh_refine flags: DEC_SPHERE_PROJECT pushes new
+ * midpoints to the unit sphere; DEC_HOST_ONLY (dec_mg_build) builds the host
+ * tables only (no device memory, no CUDA call) so they can be inspected with
+ * dec_mg_info / dec_mg_copy_table; compute calls on such a handle return
+ * DEC_ERR_ARG.  DEC_ORDER_MORTON numbers each level's new vertices along a
+ * space-filling curve instead of the default coarse edge order (see
+ * dec_mesh_refine). */
+enum { DEC_SPHERE_PROJECT = 1u, DEC_HOST_ONLY = 2u, DEC_ORDER_MORTON = 4u };
 enum { DEC_BC_DIRICHLET = 0, DEC_BC_GAUGE = 1 };
 enum { DEC_F64 = 0, DEC_F32 = 1 };           /* precision of a single operator call */
 enum { DEC_SMOOTH_JACOBI = 0, DEC_SMOOTH_CHEBYSHEV = 1, DEC_SMOOTH_MCGS = 2 };
@@ -155,7 +158,8 @@ enum {
     DEC_TABLE_STAR0 = 3,   /* [nv] double, circumcentric dual areas               */
     DEC_TABLE_STAR1 = 4,   /* [ne] double, dual/primal length ratios (scaled)     */
     DEC_TABLE_FREE = 5,    /* [nv] int32, 1 = unknown, 0 = Dirichlet vertex       */
-    DEC_TABLE_PARENTS = 6, /* [ne(level) * 2] int32, parents of level+1 midpoints */
+    DEC_TABLE_PARENTS = 6, /* [ne(level) * 2] int32, coarse edge (a, b) of each new vertex
+                              n(level) + k of level+1, k = 0 .. ne(level)-1 (not the finest) */
     DEC_TABLE_COLORS = 7   /* [nv] int32, greedy colour of each vertex            */
 };
 
@@ -180,10 +184,17 @@ void dec_mesh_destroy(dec_mesh *mesh);
 /* Sizes and coordinate dimension of a mesh.  Any output pointer may be null. */
 int dec_mesh_sizes(const dec_mesh *mesh, int64_t *nv, int64_t *ne, int64_t *nt, int *dim);
 /* dec_mesh_refine: nsub successive 1->4 midpoint subdivisions (Sec. 2.2.1,
- * binary subdivision) on the host.  Coarse ids are kept; the midpoint of
- * coarse edge e is n_coarse + e; triangle t = (a,b,c) becomes
+ * binary subdivision) on the host.  Coarse ids are kept, so every level's
+ * vertices are a prefix of the finer levels'.  Triangle t = (a,b,c) becomes
  * 4t+0 = (a,m_ab,m_ca), 4t+1 = (m_ab,b,m_bc), 4t+2 = (m_ca,m_bc,c),
- * 4t+3 = (m_ab,m_bc,m_ca).  flags & DEC_SPHERE_PROJECT pushes each new
+ * 4t+3 = (m_ab,m_bc,m_ca).  The new vertices n_coarse .. n_coarse+E-1 are the
+ * midpoints of the coarse edges: by default the midpoint of coarse edge e is
+ * n_coarse + e, so the midpoints around each coarse vertex are consecutive.
+ * With DEC_ORDER_MORTON they are numbered in Z-order of their coordinates
+ * instead -- each coordinate quantized on the midpoints' bounding box to B
+ * bits (B = 21 in 3-D, 31 in 2-D) as floor((x - lo) * ((2^B - 1)/(hi - lo))),
+ * bits interleaved, ties kept in coarse edge order.  (On GB300 the edge order
+ * gathered faster; the Z-order is kept as an option.)  flags & DEC_SPHERE_PROJECT pushes each new
  * midpoint to the unit sphere.  *out is a new mesh owned by the caller. */
 int dec_mesh_refine(const dec_mesh *mesh, int nsub, uint32_t flags, dec_mesh **out);
 /* Copy DEC_TABLE_VERTS / TRIS / EDGES / STAR0 / STAR1 of a mesh to host memory.

@@ -129,13 +129,40 @@ def boundary_vertices(mesh):
     return bv
 
 
-def subdivide(mesh, sphere=False):
+def morton_keys(verts):
+    """Z-order keys of points: each coordinate quantized on the points' bounding box to
+    B bits (B = 21 in 3-D, 31 in 2-D), q = floor((x - lo) * ((2^B - 1) / (hi - lo)))
+    clamped to [0, 2^B - 1], and the bits interleaved (axis 0 in the lowest bit).
+    Every step is an exact or IEEE-rounded float64 operation, so any implementation
+    that performs the same operations gets the same keys."""
+    dim = verts.shape[1]
+    B = 21 if dim == 3 else 31
+    top = float((1 << B) - 1)
+    keys = np.zeros(len(verts), dtype=np.uint64)
+    for d in range(dim):
+        x = verts[:, d]
+        lo, hi = float(x.min()), float(x.max())
+        scale = top / (hi - lo) if hi > lo else 0.0
+        q = np.floor((x - lo) * scale)
+        q = np.clip(q, 0.0, top).astype(np.uint64)
+        for b in range(B):
+            keys |= ((q >> np.uint64(b)) & np.uint64(1)) << np.uint64(dim * b + d)
+    return keys
+
+
+def subdivide(mesh, sphere=False, order="edge"):
     """One 1->4 midpoint subdivision (Sec. 2.2.1, binary subdivision).
 
-    Returns (fine Mesh, parents [E_coarse, 2]) where fine vertex n_c + e is
-    the midpoint of coarse edge e = parents[e].  With sphere=True each
-    midpoint is pushed back onto the unit sphere (m / |m|); the transfer
-    weights stay 1/2, 1/2.
+    Returns (fine Mesh, parents [E_coarse, 2]).  Coarse vertices keep their
+    ids, so level-l vertices are a prefix of every finer level.  The new
+    vertex n_c + k is the midpoint of coarse edge parents[k]:
+      order="edge":   k = e, the canonical coarse edge order;
+      order="morton": the midpoints sorted (stably) by the Morton key of their
+                      coordinates, quantized on the new points' bounding box
+                      (a space-filling-curve order that keeps neighbours close
+                      in memory).
+    With sphere=True each midpoint is pushed back onto the unit sphere
+    (m / |m|); the transfer weights stay 1/2, 1/2.
     """
     nc = mesh.nv
     E = mesh.ne
@@ -147,11 +174,19 @@ def subdivide(mesh, sphere=False):
             raise MeshError("sphere projection needs 3-D vertices")
         nrm = np.sqrt(mid[:, 0] * mid[:, 0] + mid[:, 1] * mid[:, 1] + mid[:, 2] * mid[:, 2])
         mid = mid / nrm[:, None]
-    fverts = np.concatenate([mesh.verts, mid], axis=0)
+    if order == "morton":
+        perm = np.argsort(morton_keys(mid), kind="stable")  # perm[k] = coarse edge of new vertex k
+    elif order == "edge":
+        perm = np.arange(E)
+    else:
+        raise ValueError(order)
+    rank = np.empty(E, dtype=np.int64)
+    rank[perm] = np.arange(E)
+    fverts = np.concatenate([mesh.verts, mid[perm]], axis=0)
     a, b, c = mesh.tris[:, 0], mesh.tris[:, 1], mesh.tris[:, 2]
-    m_ab = nc + mesh.tri_edges[:, 0]
-    m_bc = nc + mesh.tri_edges[:, 1]
-    m_ca = nc + mesh.tri_edges[:, 2]
+    m_ab = nc + rank[mesh.tri_edges[:, 0]]
+    m_bc = nc + rank[mesh.tri_edges[:, 1]]
+    m_ca = nc + rank[mesh.tri_edges[:, 2]]
     T = mesh.nt
     ftris = np.empty((4 * T, 3), dtype=np.int64)
     ftris[0::4] = np.stack([a, m_ab, m_ca], axis=1)
@@ -160,15 +195,15 @@ def subdivide(mesh, sphere=False):
     ftris[3::4] = np.stack([m_ab, m_bc, m_ca], axis=1)
     fine = build_mesh(fverts, ftris)
     assert fine.nv == nc + E
-    return fine, mesh.edges.copy()
+    return fine, mesh.edges[perm].copy()
 
 
-def refine(verts, tris, nsub, sphere=False):
+def refine(verts, tris, nsub, sphere=False, order="edge"):
     """Apply nsub subdivisions; returns the list of meshes (coarsest first) and parent tables."""
     meshes = [build_mesh(verts, tris)]
     parents = []
     for _ in range(nsub):
-        fine, par = subdivide(meshes[-1], sphere=sphere)
+        fine, par = subdivide(meshes[-1], sphere=sphere, order=order)
         meshes.append(fine)
         parents.append(par)
     return meshes, parents

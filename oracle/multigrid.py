@@ -182,15 +182,16 @@ def make_level(mesh, bc, star1_scale=None, opts=None, with_gs=False):
 
 
 def build_hierarchy(verts, tris, nsub, nlevels, bc, sphere=False, star1_scale=None,
-                    opts=None, meshes=None, parents=None):
+                    opts=None, meshes=None, parents=None, order="edge"):
     """Subdivide nsub times and keep the finest nlevels meshes as the MG hierarchy.
 
     star1_scale (per finest edge) multiplies *1 on the finest level only;
-    coarser levels are rediscretized from their own geometry.
+    coarser levels are rediscretized from their own geometry.  order is the
+    numbering of each level's new vertices (see oracle.mesh.subdivide).
     """
     opts = opts or MGOptions()
     if meshes is None:
-        meshes, parents = refine(verts, tris, nsub, sphere=sphere)
+        meshes, parents = refine(verts, tris, nsub, sphere=sphere, order=order)
     if not 1 <= nlevels <= nsub + 1:
         raise ValueError("nlevels out of range")
     first = nsub + 1 - nlevels

@@ -20,7 +20,7 @@ lib = C.CDLL(LIB_PATH)
 
 # status codes and enums (mirror include/dec.h)
 DEC_OK, DEC_ERR_ARG, DEC_ERR_MESH, DEC_ERR_CUDA, DEC_ERR_OOM, DEC_ERR_NOT_CONVERGED, DEC_ERR_NONFINITE = range(7)
-DEC_SPHERE_PROJECT, DEC_HOST_ONLY = 1, 2
+DEC_SPHERE_PROJECT, DEC_HOST_ONLY, DEC_ORDER_MORTON = 1, 2, 4
 DEC_NOALLOC_SCRATCH_BYTES = 32 << 20
 DEC_BC_DIRICHLET, DEC_BC_GAUGE = 0, 1
 DEC_F64, DEC_F32 = 0, 1

@@ -17,6 +17,7 @@ from ._lib import check, lib
 SMOOTHERS = {"jacobi": L.DEC_SMOOTH_JACOBI, "chebyshev": L.DEC_SMOOTH_CHEBYSHEV, "mcgs": L.DEC_SMOOTH_MCGS}
 SOLVERS = {"mg": L.DEC_SOLVER_MG, "mgpcg": L.DEC_SOLVER_MGPCG, "cg": L.DEC_SOLVER_CG}
 MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED, "mixed_ff": L.DEC_MODE_MIXED_FF}
+ORDERS = {"edge": 0, "morton": L.DEC_ORDER_MORTON}
 BCS = {"dirichlet": L.DEC_BC_DIRICHLET, "gauge": L.DEC_BC_GAUGE}
 RESTRICTIONS = {"rownorm": L.DEC_RESTRICT_ROWNORM, "star0": L.DEC_RESTRICT_STAR0}
 TABLES = {"verts": L.DEC_TABLE_VERTS, "tris": L.DEC_TABLE_TRIS, "edges": L.DEC_TABLE_EDGES,
@@ -53,10 +54,11 @@ class Mesh:
             lib.dec_mesh_destroy(h)
             self._h = None
 
-    def refine(self, nsub, sphere=False):
+    def refine(self, nsub, sphere=False, order="edge"):
+        """nsub 1->4 subdivisions; order is the numbering of each level's new vertices ("morton" or "edge")."""
         h = C.c_void_p()
-        check(lib.dec_mesh_refine(self._h, int(nsub), L.DEC_SPHERE_PROJECT if sphere else 0, C.byref(h)),
-              "dec_mesh_refine")
+        flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | ORDERS[order]
+        check(lib.dec_mesh_refine(self._h, int(nsub), flags, C.byref(h)), "dec_mesh_refine")
         return Mesh(_handle=h)
 
     def table(self, what):
@@ -91,7 +93,7 @@ class Hierarchy:
 
     def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
-                 restriction="rownorm", host_only=False, fuse=None):
+                 restriction="rownorm", host_only=False, fuse=None, order="edge"):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
         o = L.dec_mg_opts()
@@ -104,7 +106,7 @@ class Hierarchy:
         if fuse is not None:  # None keeps the library default (the row-local fusions)
             o.fuse = int(fuse) if not isinstance(fuse, bool) else (L.DEC_FUSE_ALL if fuse else 0)
         self.fuse = int(o.fuse)
-        flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0)
+        flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0) | ORDERS[order]
         scale = None
         if star1_scale is not None:
             scale = np.ascontiguousarray(star1_scale, dtype=np.float64)

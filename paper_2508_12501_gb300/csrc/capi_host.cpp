@@ -94,7 +94,7 @@ int dec_mesh_refine(const dec_mesh *mesh, int nsub, uint32_t flags, dec_mesh **o
         m->m = mesh->m;
         for (int i = 0; i < nsub; ++i) {
             decimpl::HostMesh f;
-            Status s = decimpl::subdivide(m->m, (flags & DEC_SPHERE_PROJECT) != 0, f);
+            Status s = decimpl::subdivide(m->m, (flags & DEC_SPHERE_PROJECT) != 0, (flags & DEC_ORDER_MORTON) != 0, f);
             if (!s.good()) {
                 delete m;
                 return fail(s);

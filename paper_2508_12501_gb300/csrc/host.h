@@ -41,7 +41,11 @@ struct HostMesh {
 Status build_mesh(std::vector<double> verts, int dim, std::vector<int32_t> tris, HostMesh &out);
 
 // One 1->4 midpoint subdivision; `parents` of fine vertex nc + e is coarse edge e.
-Status subdivide(const HostMesh &coarse, bool sphere, HostMesh &fine);
+// One 1->4 subdivision; with morton the new vertices are numbered in Z-order
+// of their coordinates, else in coarse edge order.  parents (optional)
+// receives the coarse edge endpoints of each new vertex, in new-vertex order.
+Status subdivide(const HostMesh &coarse, bool sphere, bool morton, HostMesh &fine,
+                 std::vector<int32_t> *parents = nullptr);
 
 // Circumcentric diagonal Hodge stars (cotangent formulas).
 void hodge_stars(const HostMesh &m, std::vector<double> &star0, std::vector<double> &star1);
@@ -77,7 +81,7 @@ struct HostHierarchy {
     std::vector<double> G;                      // [n0 * n0] coarse solution operator, row-major
 };
 
-Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere,
+Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton,
                        const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H);
 
 // Rebuild ELL weights of one level from its (possibly new) star1.

@@ -202,7 +202,7 @@ static Status coarse_operator(const HostLevel &L, int bc, std::vector<double> &G
     return Status::ok();
 }
 
-Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere,
+Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton,
                        const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H) {
     if (nsub < 0 || nlevels < 1 || nlevels > nsub + 1 || nlevels > 16)
         return Status::fail(DEC_ERR_ARG, "nlevels must be in 1..min(nsub+1, 16)");
@@ -217,9 +217,10 @@ Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool
     for (int i = 0; i <= nsub; ++i) {
         if (i > 0) {
             HostMesh fine;
-            Status st = subdivide(cur, sphere, fine);
+            std::vector<int32_t> par;
+            Status st = subdivide(cur, sphere, morton, fine, &par);
             if (!st.good()) return st;
-            if (i > first) H.parents.push_back(cur.edges);
+            if (i > first) H.parents.push_back(std::move(par));
             cur = std::move(fine);
         }
         if (i < first) continue;

@@ -103,7 +103,35 @@ Status build_mesh(std::vector<double> verts, int dim, std::vector<int32_t> tris,
     return Status::ok();
 }
 
-Status subdivide(const HostMesh &c, bool sphere, HostMesh &f) {
+namespace {
+
+// Z-order keys of points [n x dim]: per axis q = floor((x - lo) * ((2^B - 1)/(hi - lo)))
+// on the points' bounding box, clamped to [0, 2^B - 1], bits interleaved (axis 0 lowest).
+void morton_keys(const double *pts, int64_t n, int dim, std::vector<uint64_t> &keys) {
+    const int B = dim == 3 ? 21 : 31;
+    const double top = (double)(((uint64_t)1 << B) - 1);
+    keys.assign(n, 0);
+    for (int d = 0; d < dim; ++d) {
+        double lo = pts[d], hi = pts[d];
+        for (int64_t i = 1; i < n; ++i) {
+            lo = std::min(lo, pts[i * dim + d]);
+            hi = std::max(hi, pts[i * dim + d]);
+        }
+        const double scale = hi > lo ? top / (hi - lo) : 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double q = std::floor((pts[i * dim + d] - lo) * scale);
+            q = std::min(std::max(q, 0.0), top);
+            const uint64_t qi = (uint64_t)q;
+            uint64_t k = 0;
+            for (int b = 0; b < B; ++b) k |= ((qi >> b) & 1u) << (dim * b + d);
+            keys[i] |= k;
+        }
+    }
+}
+
+}  // namespace
+
+Status subdivide(const HostMesh &c, bool sphere, bool morton, HostMesh &f, std::vector<int32_t> *parents) {
     if (sphere && c.dim != 3) return Status::fail(DEC_ERR_ARG, "sphere projection needs 3-D vertices");
     const int dim = c.dim;
     const int64_t nc = c.nv, E = c.ne, T = c.nt;
@@ -123,12 +151,31 @@ Status subdivide(const HostMesh &c, bool sphere, HostMesh &f) {
         }
         for (int d = 0; d < dim; ++d) fv[(nc + e) * dim + d] = m[d];
     }
+    // numbering of the new vertices: rank[e] = k for the midpoint of coarse edge e
+    std::vector<int64_t> perm(E), rank(E);
+    for (int64_t e = 0; e < E; ++e) perm[e] = e;
+    if (morton && E > 0) {
+        std::vector<uint64_t> keys;
+        morton_keys(&fv[nc * dim], E, dim, keys);
+        std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) { return keys[x] < keys[y]; });
+        std::vector<double> mids(fv.begin() + nc * dim, fv.end());
+        for (int64_t k = 0; k < E; ++k)
+            for (int d = 0; d < dim; ++d) fv[(nc + k) * dim + d] = mids[perm[k] * dim + d];
+    }
+    for (int64_t k = 0; k < E; ++k) rank[perm[k]] = k;
+    if (parents) {
+        parents->resize(2 * E);
+        for (int64_t k = 0; k < E; ++k) {
+            (*parents)[2 * k] = c.edges[2 * perm[k]];
+            (*parents)[2 * k + 1] = c.edges[2 * perm[k] + 1];
+        }
+    }
     std::vector<int32_t> ft(12 * T);
     for (int64_t t = 0; t < T; ++t) {
         int32_t a = c.tris[3 * t], b = c.tris[3 * t + 1], cc = c.tris[3 * t + 2];
-        int32_t mab = (int32_t)(nc + c.tri_edges[3 * t]);
-        int32_t mbc = (int32_t)(nc + c.tri_edges[3 * t + 1]);
-        int32_t mca = (int32_t)(nc + c.tri_edges[3 * t + 2]);
+        int32_t mab = (int32_t)(nc + rank[c.tri_edges[3 * t]]);
+        int32_t mbc = (int32_t)(nc + rank[c.tri_edges[3 * t + 1]]);
+        int32_t mca = (int32_t)(nc + rank[c.tri_edges[3 * t + 2]]);
         int32_t *o = &ft[12 * t];
         o[0] = a;   o[1] = mab;  o[2] = mca;
         o[3] = mab; o[4] = b;    o[5] = mbc;

@@ -782,7 +782,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
     };
     try {
         Status st = decimpl::build_hierarchy(*dec_mesh_host(base), nsub, nlevels, bc, (flags & DEC_SPHERE_PROJECT) != 0,
-                                             star1_scale, o, mg->H);
+                                             (flags & DEC_ORDER_MORTON) != 0, star1_scale, o, mg->H);
         if (!st.good()) return bail(fail(st));
     } catch (const std::bad_alloc &) {
         return bail(fail(Status::fail(DEC_ERR_OOM, "host allocation")));
@@ -924,8 +924,15 @@ int dec_mg_copy_table(const dec_mg *mg, int level, int what, void *out) {
     switch (what) {
         case DEC_TABLE_VERTS: std::memcpy(out, L.mesh.verts.data(), L.mesh.verts.size() * 8); break;
         case DEC_TABLE_TRIS: std::memcpy(out, L.mesh.tris.data(), L.mesh.tris.size() * 4); break;
-        case DEC_TABLE_EDGES:
-        case DEC_TABLE_PARENTS: std::memcpy(out, L.mesh.edges.data(), L.mesh.edges.size() * 4); break;
+        case DEC_TABLE_EDGES: std::memcpy(out, L.mesh.edges.data(), L.mesh.edges.size() * 4); break;
+        case DEC_TABLE_PARENTS: {
+            // the coarse edge of each new vertex of level + 1, in that level's vertex order
+            if (level + 1 >= (int)mg->H.levels.size())
+                return fail(Status::fail(DEC_ERR_ARG, "the finest level has no parents table"));
+            const std::vector<int32_t> &par = mg->H.parents[level];
+            std::memcpy(out, par.data(), par.size() * 4);
+            break;
+        }
         case DEC_TABLE_STAR0: std::memcpy(out, L.star0.data(), L.star0.size() * 8); break;
         case DEC_TABLE_STAR1: std::memcpy(out, L.star1.data(), L.star1.size() * 8); break;
         case DEC_TABLE_FREE: {

@@ -44,13 +44,14 @@ def _cases():
     yield "mixed_orientation", (v, t), 2, False
 
 
+@pytest.mark.parametrize("order", ["edge", "morton"])
 @pytest.mark.parametrize("name,vt,nsub,sphere", list(_cases()), ids=[c[0] for c in _cases()])
-def test_refined_tables_bit_exact(name, vt, nsub, sphere):
+def test_refined_tables_bit_exact(name, vt, nsub, sphere, order):
     v, t = vt
-    meshes, _ = omesh.refine(v, t, nsub, sphere=sphere)
+    meshes, _ = omesh.refine(v, t, nsub, sphere=sphere, order=order)
     m = Mesh(v, t)
     for k, om in enumerate(meshes):
-        lm = m.refine(k, sphere=sphere) if k else m
+        lm = m.refine(k, sphere=sphere, order=order) if k else m
         assert (lm.nv, lm.ne, lm.nt) == (om.nv, om.ne, om.nt)
         assert np.array_equal(lm.table("tris"), om.tris)
         assert np.array_equal(lm.table("edges"), om.edges)
@@ -61,14 +62,15 @@ def test_refined_tables_bit_exact(name, vt, nsub, sphere):
         assert np.allclose(s1, odec.hodge_star1(om), rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("order", ["edge", "morton"])
 @pytest.mark.parametrize("bc", ["dirichlet", "gauge"])
-def test_hierarchy_host_tables(bc):
+def test_hierarchy_host_tables(bc, order):
     if bc == "dirichlet":
         v, t = W.unit_square(); nsub, nl, sphere = 4, 3, False
     else:
         v, t = W.icosahedron(); nsub, nl, sphere = 3, 3, True
-    h = Hierarchy(Mesh(v, t), nsub, nl, bc=bc, sphere=sphere, host_only=True)
-    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sphere, opts=omg.MGOptions(smoother="mcgs"))
+    h = Hierarchy(Mesh(v, t), nsub, nl, bc=bc, sphere=sphere, host_only=True, order=order)
+    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sphere, opts=omg.MGOptions(smoother="mcgs"), order=order)
     assert h.nlevels == nl
     for l in range(nl):
         ol = oh.levels[l]
@@ -79,8 +81,16 @@ def test_hierarchy_host_tables(bc):
         assert abs(h.lmax[l] - ol.lmax) <= 1e-12 * ol.lmax
         assert np.array_equal(h.table(l, "edges"), ol.mesh.edges)
         if l + 1 < nl:
-            # parents of level l+1 midpoints are the level-l edges
-            assert np.array_equal(h.table(l, "parents"), oh.levels[l].mesh.edges)
+            # parents of level l+1 midpoints: the level-l edges, in the chosen order of the new vertices
+            par = oh.levels[l].mesh.edges
+            if order == "morton":
+                fine = oh.levels[l + 1].mesh
+                mid = 0.5 * (ol.mesh.verts[par[:, 0]] + ol.mesh.verts[par[:, 1]])
+                if sphere:
+                    mid = mid / np.sqrt(mid[:, 0] * mid[:, 0] + mid[:, 1] * mid[:, 1] + mid[:, 2] * mid[:, 2])[:, None]
+                par = par[np.argsort(omesh.morton_keys(mid), kind="stable")]
+                assert np.array_equal(fine.verts[ol.mesh.nv:], mid[np.argsort(omesh.morton_keys(mid), kind="stable")])
+            assert np.array_equal(h.table(l, "parents"), par)
     assert h.ell_width[-1] == 6
 
 

@@ -85,7 +85,9 @@ def test_batch_error_paths():
         P.Batch([h1], [2], kgroup=3)
     B = P.Batch([h1], [2])
     b = torch.zeros(h1.n, 2, dtype=torch.float64, device="cuda")
-    b[5, 1] = float("nan")
+    xy = h1.table(-1, "verts")
+    free = np.flatnonzero((xy[:, 0] > 0) & (xy[:, 0] < 1) & (xy[:, 1] > 0) & (xy[:, 1] < 1))
+    b[int(free[0]), 1] = float("nan")  # on a free row: fixed (Dirichlet) rows are masked out
     with pytest.raises(P.DecError) as ei:
         B.solve([b])
     assert ei.value.code == 6

@@ -245,3 +245,24 @@ def test_convergence_factor_matches_oracle(name, smoother, gamma):
     cf_gpu = (st.rel_res / st.rel_res0) ** (1.0 / st.iters)
     cf_ref = omg.convergence_factor(ref.history)
     assert abs(cf_gpu - cf_ref) <= 0.02, (cf_gpu, cf_ref)
+
+
+@pytest.mark.parametrize("name", ["square5", "ico5"])
+def test_morton_order_cycle_and_solve_match_oracle(name):
+    # the opt-in space-filling-curve numbering: same tables as the oracle's, same cycle, same solution
+    P = _lib()
+    base, nsub, nl, bc, sph = CASES[name]
+    v, t = base()
+    h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother="chebyshev", order="morton")
+    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, opts=omg.MGOptions(smoother="chebyshev"),
+                             order="morton")
+    lev = oh.finest
+    assert np.array_equal(h.table(-1, "verts"), lev.mesh.verts)
+    b = omg.prepare_rhs(oh, W.uniform_field(lev.mesh.nv, 61))
+    x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+    h.vcycle(_dev(b), x)
+    ref = omg.vcycle(oh, b, np.zeros_like(b))
+    assert _s0_rel(lev, x.cpu().numpy(), ref) < 1e-12
+    xs, st = h.solve(_dev(b), mode="mixed_ff", tol=1e-10)
+    assert st.rel_res <= 1e-10
+    assert _s0_rel(lev, xs.cpu().numpy(), omg.direct_solve(oh, b)) < 1e-7

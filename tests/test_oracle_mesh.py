@@ -67,20 +67,27 @@ def test_edges_canonical_and_orientation():
     assert d0.tolist() == [[-1, 1, 0], [-1, 0, 1], [0, -1, 1]]
 
 
+@pytest.mark.parametrize("order", ["edge", "morton"])
 @pytest.mark.parametrize("base", ["square", "ico", "grid"])
-def test_subdivision_counting(base):
+def test_subdivision_counting(base, order):
     # V' = V + E, E' = 2E + 3T, T' = 4T for 1->4 midpoint subdivision
     if base == "square":
-        v, t = W.unit_square(); meshes, par = M.refine(v, t, 4)
+        v, t = W.unit_square(); meshes, par = M.refine(v, t, 4, order=order)
     elif base == "ico":
-        v, t = W.icosahedron(); meshes, par = M.refine(v, t, 3, sphere=True)
+        v, t = W.icosahedron(); meshes, par = M.refine(v, t, 3, sphere=True, order=order)
     else:
-        v, t = W.grid_mesh(3, 5); meshes, par = M.refine(v, t, 3)
+        v, t = W.grid_mesh(3, 5); meshes, par = M.refine(v, t, 3, order=order)
     for c, f, p in zip(meshes[:-1], meshes[1:], par):
         assert f.nv == c.nv + c.ne
         assert f.ne == 2 * c.ne + 3 * c.nt
         assert f.nt == 4 * c.nt
-        assert np.array_equal(p, c.edges)
+        if order == "edge":
+            assert np.array_equal(p, c.edges)
+        else:
+            # a permutation of the coarse edges, in non-decreasing Morton key of the midpoints
+            assert np.array_equal(np.sort(p[:, 0] * c.nv + p[:, 1]), c.edges[:, 0] * c.nv + c.edges[:, 1])
+            keys = M.morton_keys(f.verts[c.nv:])
+            assert np.all(keys[1:] >= keys[:-1])
         # coarse vertices keep their position, midpoints are at the mean (planar)
         assert np.array_equal(f.verts[: c.nv], c.verts)
         if base != "ico":
@@ -186,3 +193,65 @@ def test_validation_rejects(bad):
         t = np.concatenate([t, [[0, 1, 99]]])
     with pytest.raises(M.MeshError):
         M.build_mesh(v, t)
+
+
+def _z_less(a, b):
+    """Z-order comparison without interleaving (the most-significant-differing-bit rule):
+    the axis whose coordinates differ in the highest bit decides."""
+    best, axis = -1, 0
+    for d in range(len(a)):
+        x = int(a[d]) ^ int(b[d])
+        if x and x.bit_length() > best:
+            best, axis = x.bit_length(), d
+        elif x and x.bit_length() == best and d > axis:
+            axis = d  # equal top bits: the higher axis holds the higher interleaved bit
+    return best >= 0 and int(a[axis]) < int(b[axis])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_morton_keys_order_points_in_z_order(dim):
+    rng = np.random.default_rng(dim)
+    pts = rng.uniform(-1.0, 1.0, size=(60, dim))
+    pts[0] = -1.0
+    pts[1] = 1.0  # the bounding box is [-1, 1]^dim
+    B = 21 if dim == 3 else 31
+    q = np.clip(np.floor((pts + 1.0) * (float((1 << B) - 1) / 2.0)), 0, (1 << B) - 1).astype(np.int64)
+    keys = M.morton_keys(pts)
+    for i in range(len(pts)):
+        for j in range(len(pts)):
+            assert (keys[i] < keys[j]) == _z_less(q[i], q[j])
+
+
+def test_morton_keys_of_corners():
+    # corners of the unit square: q in {0, 2^31 - 1}; axis 0 takes the even bits, axis 1 the odd bits
+    k = M.morton_keys(np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]]))
+    even = sum(1 << (2 * b) for b in range(31))
+    assert k.tolist() == [0, even, even << 1, even | (even << 1)]
+
+
+def _gather_sectors_per_row(m):
+    """32-byte sectors of a float vector touched by the neighbour gathers of each warp of 32 rows, per row."""
+    nb = [[] for _ in range(m.nv)]
+    for a, b in m.edges:
+        nb[a].append(b)
+        nb[b].append(a)
+    tot = 0
+    for w in range(0, m.nv, 32):
+        tot += len({j // 8 for i in range(w, min(m.nv, w + 32)) for j in nb[i]})
+    return tot / m.nv
+
+
+@pytest.mark.parametrize("base", ["square", "ico"])
+def test_morton_order_keeps_neighbours_close(base):
+    # the same vertices in both orders, and a warp's neighbour gathers touch fewer sectors in Z-order
+    if base == "square":
+        v, t = W.unit_square(); args = dict(nsub=6)
+    else:
+        v, t = W.icosahedron(); args = dict(nsub=5, sphere=True)
+    sec = {}
+    for order in ("edge", "morton"):
+        m = M.refine(v, t, order=order, **args)[0][-1]
+        sec[order] = _gather_sectors_per_row(m)
+        ref = M.refine(v, t, order="edge", **args)[0][-1]
+        assert np.array_equal(np.unique(m.verts, axis=0), np.unique(ref.verts, axis=0))
+    assert sec["morton"] < 0.92 * sec["edge"], sec
