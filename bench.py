@@ -331,6 +331,88 @@ def convergence_factors(torch, dev):
     return out
 
 
+def _timed(torch, dev, stream, fn, reps):
+    """Mean milliseconds of fn() over reps calls after one warm-up call (CUDA events on the solve stream)."""
+    fn()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = None
+    for _ in range(reps):
+        r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps, r
+
+
+def other_configs(torch, dev, stream):
+    """The scope table's other workloads (standalone MG, the differentiable solve, the porous rollout)."""
+    import math
+    import paper_2508_12501_gb300 as P
+    out = {}
+    v, t = W.unit_square()
+    # standalone FP64 V(2,2) multigrid, unit square x5, against the discrete closed form
+    h = P.Hierarchy(P.Mesh(v, t), 5, 5, bc="dirichlet")
+    xy = h.table(-1, "verts")
+    s0 = h.table(-1, "star0")
+    b = torch.as_tensor(W.rhs_sin_square(xy), device=dev)
+    ms, (x, st) = _timed(torch, dev, stream, lambda: h.solve(b, solver="mg", mode="f64", tol=1e-10, maxit=100), 50)
+    hh = 1.0 / 32
+    u_h = 2 * math.pi ** 2 / (8.0 / hh ** 2 * math.sin(math.pi * hh / 2) ** 2) * W.u_sin_square(xy)
+    d = x.cpu().numpy() - u_h
+    out["standalone_mg"] = {
+        "workload": "unit square x5 (1,089 V), 5-level V(2,2) Jacobi, Dirichlet, RHS -Delta sin(pi x) sin(pi y), "
+                    "FP64 MG to 1e-10", "ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iters": st.iters,
+        "conv_factor": (st.rel_res / st.rel_res0) ** (1.0 / st.iters),
+        "rel_err_vs_discrete_closed_form": float(np.sqrt(np.sum(s0 * d * d) / np.sum(s0 * u_h * u_h)))}
+    del h
+    # differentiable solve: forward and adjoint on unit square x10 with log-normal *1
+    h = P.Hierarchy(P.Mesh(v, t), 10, 9, bc="dirichlet", smoother="chebyshev")
+    s1 = h.table(-1, "star1") * W.lognormal_factors(h.ne[-1], 2)
+    h.set_star1(torch.as_tensor(s1, device=dev))
+    xy = h.table(-1, "verts")
+    s0d = torch.as_tensor(h.table(-1, "star0"), device=dev)
+    b = torch.as_tensor(W.uniform_field(h.n, 3), device=dev)
+    ut = torch.as_tensor(W.u_target_square(xy), device=dev)
+
+    def fwd_bwd():
+        u, sf = h.solve(b, mode="mixed_ff", tol=1e-8)
+        gb, gs, sb = h.solve_backward(u, s0d * (u - ut), mode="mixed_ff", tol=1e-8)
+        return sf, sb
+    ms, (sf, sb) = _timed(torch, dev, stream, fwd_bwd, 5)
+    out["adjoint"] = {
+        "workload": "unit square x10 (1,050,625 V), log-normal *1 (sigma 0.5, seed 2), b U[-1,1] (seed 3), "
+                    "J = 1/2 ||u - sin(2 pi x) sin(pi y)||^2_*0, dJ/db and dJ/d*1, MG-PCG mixed_ff to 1e-8",
+        "ms_forward_backward": ms, "forward_iters": sf.iters, "backward_iters": sb.iters}
+    del h
+    # porous convection: 2000 explicit steps with checkpoints every 100, then the checkpointed adjoint
+    h = P.Hierarchy(P.Mesh(v, t), 9, 8, bc="gauge", restriction="star0")
+    xy = h.table(-1, "verts")
+    fixed = torch.as_tensor(((xy[:, 1] == 0.0) | (xy[:, 1] == 1.0)).astype(np.uint8), device=dev)
+    T0 = torch.as_tensor(W.porous_initial_T(xy, 0), device=dev)
+    kappa, nsteps, ce = 2.0, 2000, 100
+    dt = 0.5 * (1.0 / 512) ** 2 / (4 * kappa)
+    ck = torch.empty((nsteps // ce + 1) * h.n, dtype=torch.float64, device=dev)
+    top = torch.as_tensor(xy[:, 1] == 1.0, device=dev).double()
+    gradF = -kappa * torch.as_tensor(h.table(-1, "star0"), device=dev) * h.laplace0_apply(top)
+    T = T0.clone()
+    Pr = torch.zeros_like(T)
+    h.porous_step(T, Pr, fixed, 10, dt, tol=1e-8, mode="mixed_ff")  # warm-up
+    ms_f, _ = _timed(torch, dev, stream, lambda: h.porous_step(T0.clone(), torch.zeros_like(T0), fixed, nsteps, dt,
+                                                               checkpoints=ck, ckpt_every=ce, tol=1e-8,
+                                                               mode="mixed_ff"), 1)
+    ms_b, (g, sb) = _timed(torch, dev, stream, lambda: h.porous_backward(T0, torch.zeros_like(T0), fixed, nsteps, gradF,
+                                                                         dt, ckpt_every=ce, tol=1e-8,
+                                                                         mode="mixed_ff"), 1)
+    out["porous"] = {
+        "workload": "unit square x9 (263,169 V), T0 = 100 - 200 y + 1e-3 U[-1,1] (seed 0), 2000 forward-Euler "
+                    "steps, dt = h^2/(8 kappa), pressure MG-PCG mixed_ff to 1e-8 (warm start), checkpoints every "
+                    "100 steps; adjoint of the top-boundary heat flux",
+        "rollout_ms": ms_f, "steps_per_s": nsteps / (ms_f * 1e-3), "adjoint_ms": ms_b,
+        "forward_plus_adjoint_ms": ms_f + ms_b, "grad_norm": float(torch.linalg.vector_norm(g))}
+    return out
+
+
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
@@ -346,6 +428,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all-levels", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the standalone-MG, differentiable-solve and porous-rollout measurements")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven iteration loop (same kernels; profilers cannot see conditional graphs)")
     ap.add_argument("--only-solves", action="store_true",
@@ -545,6 +629,13 @@ def main():
         except Exception as ex:  # noqa: BLE001
             errors["convergence_factors"] = repr(ex)
 
+    others = None
+    if not args.no_configs:
+        try:
+            others = other_configs(torch, dev, stream)
+        except Exception as ex:  # noqa: BLE001
+            errors["other_configs"] = repr(ex)
+
     batched = None
     if not args.no_batched:
         try:
@@ -585,7 +676,7 @@ def main():
             "iters": st.iters, "rel_res": st.rel_res, "true_rel_res": modes[args.mode]["true_rel_res"],
             "modes": modes, "fp64_solves_per_s": v64,
             "speedup_vs_fp64": (value / world / v64) if v64 else None, "mode_vs_fp64_rel_err_star0": err,
-            "vcycle_ms": vc_ms, "vcycle_mdof_s": mdofs, "batched": batched, "convergence_factors": cfs,
+            "vcycle_ms": vc_ms, "vcycle_mdof_s": mdofs, "batched": batched, "other_configs": others, "convergence_factors": cfs,
             "kernels": [{k: (round(v_, 6) if isinstance(v_, float) else v_) for k, v_ in r.items()} for r in rows],
         }
         if errors:
