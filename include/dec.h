@@ -96,10 +96,12 @@ typedef struct dec_mg_opts {
     int power_iters;
     int gamma;
     int restriction;  /* DEC_RESTRICT_* */
+    int coarse_max_rows; /* DEC_FUSE_COARSE: largest level (rows) run in the shared-memory
+                            block; 0 (default): the library's choice */
     int fuse;         /* DEC_FUSE_* mask of fused cycle kernels, each bitwise equal to
                          the two separate kernels it replaces; default
-                         DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER, the row-local fusions
-                         (those that gather a second vector measured slower on GB300) */
+                         DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE (those that
+                         gather a second vector measured slower on GB300) */
 } dec_mg_opts;
 /* Fused cycle kernels.  Gathering a second vector per neighbour:
  *   DEC_FUSE_SMOOTH01  the first two pre-smoothing steps from zero;
@@ -110,9 +112,12 @@ typedef struct dec_mg_opts {
  *   DEC_FUSE_OUTER     in MG-PCG with FP32 cycles (mixed modes): the outer update with the
  *                      first smoothing step of the finest level, and the last post-smoothing
  *                      step with the dot products of the preconditioned vector. */
+/*   DEC_FUSE_COARSE    the coarsest levels whose operators fit in one SM's shared memory
+ *                      (FP32 V-cycles) run as one 1024-thread block, __syncthreads between
+ *                      phases instead of kernel boundaries. */
 enum {
     DEC_FUSE_SMOOTH01 = 1, DEC_FUSE_RESTRICT = 2, DEC_FUSE_PROLONG = 4, DEC_FUSE_RESTRICT0 = 8,
-    DEC_FUSE_OUTER = 16, DEC_FUSE_ALL = 31
+    DEC_FUSE_OUTER = 16, DEC_FUSE_COARSE = 32, DEC_FUSE_ALL = 63
 };
 
 /* Solver options.  dec_solve_default_opts(): MG-PCG, mixed precision,
@@ -429,6 +434,7 @@ enum {
     DEC_PK_RESRESTRICT, /* fused residual and restriction (launched on the fine level) */
     DEC_PK_PROLSMOOTH,  /* fused interpolation, correction and first post-smoothing step */
     DEC_PK_SMOOTHDOTS,  /* fused last post-smoothing step and preconditioned-vector dot products */
+    DEC_PK_COARSECYCLE, /* the coarsest levels' whole sub-cycle in one block (launched on its top level) */
     DEC_PK_COUNT
 };
 typedef struct dec_prof_entry {

@@ -29,7 +29,8 @@ DEC_RESTRICT_ROWNORM, DEC_RESTRICT_STAR0 = 0, 1
 DEC_SOLVER_MG, DEC_SOLVER_MGPCG, DEC_SOLVER_CG = 0, 1, 2
 DEC_MODE_F64, DEC_MODE_MIXED, DEC_MODE_MIXED_FF = 0, 1, 2
 DEC_FUSE_SMOOTH01, DEC_FUSE_RESTRICT, DEC_FUSE_PROLONG, DEC_FUSE_RESTRICT0, DEC_FUSE_OUTER = 1, 2, 4, 8, 16
-DEC_FUSE_ALL = 31
+DEC_FUSE_COARSE = 32
+DEC_FUSE_ALL = 63
 (DEC_TABLE_VERTS, DEC_TABLE_TRIS, DEC_TABLE_EDGES, DEC_TABLE_STAR0, DEC_TABLE_STAR1,
  DEC_TABLE_FREE, DEC_TABLE_PARENTS, DEC_TABLE_COLORS) = range(8)
 
@@ -40,7 +41,7 @@ STATUS_NAMES = {0: "DEC_OK", 1: "DEC_ERR_ARG", 2: "DEC_ERR_MESH", 3: "DEC_ERR_CU
 class dec_mg_opts(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("cheby_lo", C.c_double), ("cheby_hi", C.c_double), ("power_iters", C.c_int), ("gamma", C.c_int),
-                ("restriction", C.c_int), ("fuse", C.c_int)]
+                ("restriction", C.c_int), ("coarse_max_rows", C.c_int), ("fuse", C.c_int)]
 
 
 class dec_solve_opts(C.Structure):
@@ -59,7 +60,7 @@ class dec_prof_entry(C.Structure):
 
 PROF_KINDS = ["smooth0", "smooth", "residual", "restrict", "prolong", "coarse", "spmv64", "update", "zdots",
               "pupd", "mgres", "add", "aux", "smooth01", "resrestrict", "prolsmooth",
-              "smoothdots"]
+              "smoothdots", "coarsecycle"]
 
 
 class dec_porous_params(C.Structure):

@@ -35,7 +35,8 @@ void dec_mg_default_opts(dec_mg_opts *o) {
     o->power_iters = 10;
     o->gamma = 1;
     o->restriction = DEC_RESTRICT_ROWNORM;
-    o->fuse = DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER;
+    o->fuse = DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE;
+    o->coarse_max_rows = 0;
 }
 
 void dec_solve_default_opts(dec_solve_opts *o) {

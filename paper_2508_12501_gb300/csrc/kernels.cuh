@@ -50,6 +50,20 @@ __device__ __forceinline__ bool skipped(const int *skip) { return skip != nullpt
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
+// Round-to-nearest add and multiply that the compiler may not contract into
+// an FMA: every kernel that forms the same smoothing update or interpolated
+// value rounds it identically, so fused and unfused cycles agree bit for bit.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// One smoothing update: delta = c d_in + e q (DIN) or e q; x_out = x_in + delta.
+template <typename T>
+__device__ __forceinline__ T smooth_delta(bool din, T c, T d_in, T e, T q) {
+    return din ? fma(c, d_in, mul_rn(e, q)) : mul_rn(e, q);
+}
+
 // (L x)_i and L_ii for one row.
 template <typename T, int KT>
 __device__ __forceinline__ void row_apply(int i, int n, int K, const int32_t *__restrict__ col,
@@ -117,8 +131,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth(int n, int K, const int3
         T s, d;
         row_apply<T, KT>(i, n, K, col, w, x_in, s, d);
         T q = d != T(0) ? (ldg(b + i) - s) / d : T(0);
-        T delta = DIN ? fma(c, ldg(d_in + i), e * q) : e * q;
-        x_out[i] = ldg(x_in + i) + delta;
+        const T delta = smooth_delta<T>(DIN, c, DIN ? ldg(d_in + i) : T(0), e, q);
+        x_out[i] = add_rn(ldg(x_in + i), delta);
         if (DOUT) d_out[i] = delta;
     }
 }
@@ -194,8 +208,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth01(int n, int K, const in
             s = fma(ldg(w + o), x1i - x1j, s);
         }
         const T q = di != T(0) ? (bi - s) / di : T(0);
-        const T delta = CHEB ? fma(c1, x1i, e1 * q) : e1 * q;
-        x_out[i] = x1i + delta;
+        const T delta = smooth_delta<T>(CHEB, c1, x1i, e1, q);
+        x_out[i] = add_rn(x1i, delta);
         if (DOUT) d_out[i] = delta;
     }
 }
@@ -205,7 +219,7 @@ template <typename T>
 __device__ __forceinline__ T prolong_add(int v, int nc, const int2 *__restrict__ par, const T *__restrict__ ec) {
     if (v < nc) return ldg(ec + v);
     const int2 p = ldg(par + (v - nc));
-    return T(0.5) * (ldg(ec + p.x) + ldg(ec + p.y));
+    return mul_rn(T(0.5), add_rn(ldg(ec + p.x), ldg(ec + p.y)));
 }
 
 // Interpolation and correction (k_prolong) followed by the first step of the
@@ -222,20 +236,20 @@ __global__ void __launch_bounds__(kThreads, 8) k_prolong_smooth(int n, int K, in
     if (skipped(skip)) return;
     const int Kk = KT > 0 ? KT : K;
     GRID_STRIDE(i, n) {
-        const T xi = ldg(x_in + i) + prolong_add(i, nc, par, ec);
+        const T xi = add_rn(ldg(x_in + i), prolong_add(i, nc, par, ec));
         T s = T(0);
 #pragma unroll
         for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
             if (KT == 0 && k >= Kk) break;
             const size_t o = (size_t)k * n + i;
             const int j = ldg(col + o);
-            const T xj = ldg(x_in + j) + prolong_add(j, nc, par, ec);
+            const T xj = add_rn(ldg(x_in + j), prolong_add(j, nc, par, ec));
             s = fma(ldg(w + o), xi - xj, s);
         }
         const T di = ldg(dg + i);
         const T q = di != T(0) ? (ldg(b + i) - s) / di : T(0);
-        const T delta = e0 * q;
-        x_out[i] = xi + delta;
+        const T delta = smooth_delta<T>(false, T(0), T(0), e0, q);
+        x_out[i] = add_rn(xi, delta);
         if (DOUT) d_out[i] = delta;
     }
 }
@@ -286,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_residual_restrict(int nc, int n
             if (STAR0)
                 bc[c] = fma(sj, r, T(0.5) * acc) / ldg(s0c + c);
             else
-                bc[c] = fma(T(0.5), acc, r) / (T(1) + T(0.5) * T(deg));
+                bc[c] = fma(T(0.5), acc, r) / add_rn(T(1), mul_rn(T(0.5), T(deg)));
         }
     }
 }
@@ -343,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_restrict(int nc, int nf, int Kf
         if (STAR0)
             v = fma(ldg(s0f + c), ldg(rf + c), T(0.5) * acc) / ldg(s0c + c);
         else
-            v = fma(T(0.5), acc, ldg(rf + c)) / (T(1) + T(0.5) * T(deg));
+            v = fma(T(0.5), acc, ldg(rf + c)) / add_rn(T(1), mul_rn(T(0.5), T(deg)));
         bc[c] = v;
         if (S0 > 0) {
             const T d = ldg(dgc + c);
@@ -362,16 +376,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_prolong(int nc, int nf, const i
                                                      const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
-    GRID_STRIDE(v, nf) {
-        T add;
-        if (v < nc) {
-            add = ldg(ec + v);
-        } else {
-            const int2 p = ldg(par + (v - nc));
-            add = T(0.5) * (ldg(ec + p.x) + ldg(ec + p.y));
-        }
-        xf[v] += add;
-    }
+    GRID_STRIDE(v, nf) xf[v] = add_rn(xf[v], prolong_add(v, nc, par, ec));
 }
 
 // Coarsest level: x = G b with the dense precomputed solution operator, one warp per row.
@@ -976,8 +981,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots(int n, int K, cons
         row_apply<float, KT>(i, n, K, col, w, x_in, s, d);
         const float ri = ldg(b + i);
         const float q = d != 0.f ? (ri - s) / d : 0.f;
-        const float delta = DIN ? fmaf(c, ldg(d_in + i), e * q) : e * q;
-        const float zi = ldg(x_in + i) + delta;
+        const float delta = smooth_delta<float>(DIN, c, DIN ? ldg(d_in + i) : 0.f, e, q);
+        const float zi = add_rn(ldg(x_in + i), delta);
         x_out[i] = zi;
         if (freev[i]) {
             const float s0 = ldg(s032 + i);

@@ -10,6 +10,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "coarse_cycle.cuh"
 #include "host.h"
 #include "kernels.cuh"
 
@@ -23,6 +24,8 @@ struct DevLevel {
     float *w32 = nullptr;
     float *wlo = nullptr;  // finest level: w64 - w32 rounded to FP32 (ff weights w32 + wlo)
     float *dg32 = nullptr;     // row sums of w32 / w64 (the Jacobi diagonal), read by fused kernels
+    int16_t *col16 = nullptr;  // levels of the shared-memory coarse cycle: col and parents as int16
+    int16_t *par16 = nullptr;
     double *dg64 = nullptr;
     double *star0 = nullptr;
     float *star0_32 = nullptr;
@@ -79,6 +82,10 @@ struct dec_mg {
     int n0 = 0;
     double *G64 = nullptr;
     float *G32 = nullptr;
+    // shared-memory coarse cycle (DEC_FUSE_COARSE): levels 0..coarse_top, -1 if none fits
+    int coarse_top = -1;
+    int coarse_smem = 0;
+    decdev::CoarseArgs coarse_args{};
     // finest-level extras
     int32_t *slot_edge = nullptr;
     int2 *edges = nullptr;
@@ -175,6 +182,23 @@ inline void launch(const dec_mg *mg, void (*kernel)(KArgs...), int grid, cudaStr
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = mg->pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// A launch with an explicit block size and dynamic shared memory (PDL as above).
+template <typename... KArgs, typename... Args>
+inline void launch_block(const dec_mg *mg, void (*kernel)(KArgs...), int grid, int block, int smem, cudaStream_t s,
+                         Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

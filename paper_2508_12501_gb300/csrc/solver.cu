@@ -231,6 +231,16 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
         return P<T>::x(L, 0);
     }
     const dec_mg_opts &o = mg->H.opts;
+    if constexpr (std::is_same<T, float>::value) {
+        if ((o.fuse & DEC_FUSE_COARSE) && l == mg->coarse_top) {
+            decdev::CoarseArgs A = mg->coarse_args;
+            A.b = b;
+            A.x = L.x32[0];
+            ProfScope ps(mg, DEC_PK_COARSECYCLE, l, s);
+            launch_block(mg, decdev::k_coarse_cycle, 1, decdev::kCoarseThreads, mg->coarse_smem, s, A, skip);
+            return L.x32[0];
+        }
+    }
     DevLevel &C = mg->lv[l - 1];
     int cur = 0;
     if (o.nu1 > 0)
@@ -238,7 +248,9 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     else
         cudaMemsetAsync(P<T>::x(L, 0), 0, sizeof(T) * L.n, s);
     // the coarse level's first smoothing step rides on the restriction
-    const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0;
+    // (not into the shared-memory coarse cycle, which starts from b itself)
+    const bool coarse_next = std::is_same<T, float>::value && (o.fuse & DEC_FUSE_COARSE) && l - 1 == mg->coarse_top;
+    const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0 && !coarse_next;
     bool coarse_pre0 = false;
     const int g = grid_for(mg, L.n);
     const T *w = P<T>::w(L);
@@ -750,6 +762,100 @@ void update_diagonals(dec_mg *mg, DevLevel &D, cudaStream_t s) {
     });
 }
 
+// Choose the levels 0..top of the shared-memory coarse cycle (the most that
+// fit in one block's shared memory, at least levels 0 and 1), lay out their
+// arrays and upload int16 copies of their column and parent tables.
+int setup_coarse_cycle(dec_mg *mg) {
+    using namespace decdev;
+    mg->coarse_top = -1;
+    const dec_mg_opts &o = mg->H.opts;
+    const int nl = (int)mg->lv.size();
+    if (nl < 2 || o.gamma != 1 || o.nu1 > kCoarseMaxNu || o.nu2 > kCoarseMaxNu) return DEC_OK;
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, mg->device);
+    const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV, star0 = o.restriction == DEC_RESTRICT_STAR0;
+    auto al = [](int64_t b) { return (b + 15) & ~(int64_t)15; };
+    CoarseArgs A{};
+    int64_t off = 0;
+    int top = -1;
+    int64_t top_bytes = 0;
+    for (int l = 0; l < std::min(nl, kCoarseMaxLevels); ++l) {
+        const DevLevel &D = mg->lv[l];
+        const int max_rows = o.coarse_max_rows > 0 ? std::min(o.coarse_max_rows, kCoarseMaxN) : kCoarseMaxN;
+        if (D.n > max_rows || D.K > kCoarseMaxK) break;
+        CoarseLevel &L = A.lv[l];
+        L = CoarseLevel{};
+        L.n = D.n;
+        L.K = D.K;
+        L.o_col = L.o_w = L.o_dg = L.o_dir = L.o_r = L.o_s0 = L.o_par = -1;
+        int64_t b = off;
+        auto take = [&](int &o_, int64_t bytes) {
+            o_ = (int)b;
+            b += al(bytes);
+        };
+        take(L.o_x, 4 * (int64_t)D.n);
+        take(L.o_b, 4 * (int64_t)D.n);
+        if (star0) take(L.o_s0, 4 * (int64_t)D.n);
+        if (l > 0) {
+            take(L.o_col, 2 * (int64_t)D.K * D.n);
+            take(L.o_w, 4 * (int64_t)D.K * D.n);
+            take(L.o_dg, 4 * (int64_t)D.n);
+            take(L.o_r, 4 * (int64_t)D.n);
+            take(L.o_par, 4 * (int64_t)(D.n - mg->lv[l - 1].n));
+            if (cheb) take(L.o_dir, 4 * (int64_t)D.n);
+        }
+        if (b > smem_max) break;
+        off = b;
+        if (l > 0) {
+            top = l;
+            top_bytes = off;
+        }
+    }
+    if (top < 1) return DEC_OK;
+    for (int l = 0; l <= top; ++l) {
+        DevLevel &D = mg->lv[l];
+        CoarseLevel &L = A.lv[l];
+        L.s0 = D.star0_32;
+        if (l > 0) {
+            const decimpl::HostLevel &HL = mg->H.levels[l];
+            std::vector<int16_t> c16(((size_t)D.K * D.n + 1) & ~(size_t)1, 0);  // even count: 4-byte loads
+            for (size_t i = 0; i < (size_t)D.K * D.n; ++i) c16[i] = (int16_t)HL.col[i];
+            const std::vector<int32_t> &par = mg->H.parents[l - 1];
+            std::vector<int16_t> p16(par.begin(), par.end());
+            int rc;
+            if ((rc = upload(mg, &D.col16, c16.data(), c16.size())) || (rc = upload(mg, &D.par16, p16.data(), p16.size())))
+                return rc;
+            L.col = D.col16;
+            L.par = D.par16;
+            L.w = D.w32;
+            L.dg = D.dg32;
+        }
+        for (int k = 0; k < kCoarseMaxNu; ++k) {
+            L.e_pre[k] = (float)(cheb ? (k < (int)D.e_pre.size() ? D.e_pre[k] : 0.0) : o.omega);
+            L.c_pre[k] = (float)(cheb ? (k < (int)D.c_pre.size() ? D.c_pre[k] : 0.0) : 0.0);
+            L.e_post[k] = (float)(cheb ? (k < (int)D.e_post.size() ? D.e_post[k] : 0.0) : o.omega);
+            L.c_post[k] = (float)(cheb ? (k < (int)D.c_post.size() ? D.c_post[k] : 0.0) : 0.0);
+        }
+    }
+    A.top = top;
+    A.nu1 = o.nu1;
+    A.nu2 = o.nu2;
+    A.cheb = cheb ? 1 : 0;
+    A.star0 = star0 ? 1 : 0;
+    A.G = mg->G32;
+    // The dynamic shared-memory limit is a property of the kernel, shared by
+    // every hierarchy on the device: raise it once to the device maximum
+    // (each layout is at most that), never to one hierarchy's size.
+    if (cudaFuncSetAttribute(k_coarse_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DEC_OK;  // leave the shared-memory cycle off for this hierarchy
+    }
+    mg->coarse_args = A;
+    mg->coarse_smem = (int)top_bytes;
+    mg->coarse_top = top;
+    return DEC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -769,6 +875,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
     if (o.restriction != DEC_RESTRICT_ROWNORM && o.restriction != DEC_RESTRICT_STAR0)
         return fail(Status::fail(DEC_ERR_ARG, "unknown restriction"));
     if (o.fuse < 0 || o.fuse > DEC_FUSE_ALL) return fail(Status::fail(DEC_ERR_ARG, "fuse must be a DEC_FUSE_* mask"));
+    if (o.coarse_max_rows < 0) return fail(Status::fail(DEC_ERR_ARG, "coarse_max_rows must be >= 0"));
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma < 1 || o.gamma > 4 || o.power_iters < 1 ||
         !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad multigrid options"));
@@ -885,6 +992,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
             if (HF.free_[v]) s += HF.star0[v];
         mg->star0_sum = s;
     }
+    if ((rc = setup_coarse_cycle(mg))) return bail(rc);
     ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceSynchronize"));
     *out = mg;

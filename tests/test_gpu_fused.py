@@ -136,3 +136,57 @@ def test_outer_fusion_solves_match(fuse, mode, smoother):
         assert torch.equal(out[0][0], out[1][0])
         out = [h.solve(b, solver="mgpcg", mode=mode, tol=1e-10, host_loop=True) for h in hs]
         assert torch.equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("name", ["square5", "ico5", "fan7"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("restriction", ["rownorm", "star0"])
+def test_shared_memory_coarse_cycle_is_bitwise_equal(name, smoother, restriction):
+    # DEC_FUSE_COARSE: the coarsest levels in one 1024-thread block out of shared memory
+    import paper_2508_12501_gb300 as P
+    base, nsub, nl, bc, sph = CASES[name]
+    v, t = base()
+    hs = [P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, restriction=restriction,
+                      fuse=f) for f in (0, 32, 56)]
+    _cycles_equal(hs[:2], torch.float32, 23)
+    _cycles_equal([hs[0], hs[2]], torch.float32, 23)
+    b = torch.as_tensor(W.uniform_field(hs[0].n, 29), device="cuda")
+    out = [h.solve(b, solver="mgpcg", mode="mixed_ff", tol=1e-10) for h in hs]
+    assert out[0][1].iters == out[1][1].iters == out[2][1].iters
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][0], out[2][0])
+    assert out[1][1].launches < out[0][1].launches
+
+
+@pytest.mark.parametrize("nu", [(0, 1), (1, 0), (1, 1), (3, 2), (4, 4)])
+def test_shared_memory_coarse_cycle_sweep_counts(nu):
+    import paper_2508_12501_gb300 as P
+    v, t = W.icosahedron()
+    hs = [P.Hierarchy(P.Mesh(v, t), 5, 5, bc="gauge", sphere=True, smoother="chebyshev", nu1=nu[0], nu2=nu[1],
+                      fuse=f) for f in (0, 32)]
+    _cycles_equal(hs, torch.float32, 31)
+
+
+def test_whole_small_hierarchy_in_one_block():
+    # unit square x5 with 5 levels (1,089 vertices at most): every level fits, the whole cycle is one launch
+    import paper_2508_12501_gb300 as P
+    v, t = W.unit_square()
+    hs = [P.Hierarchy(P.Mesh(v, t), 5, 5, bc="dirichlet", fuse=f) for f in (0, 32)]
+    _cycles_equal(hs, torch.float32, 37)
+    b = torch.as_tensor(W.rhs_sin_square(hs[0].table(-1, "verts")), device="cuda")
+    out = [h.solve(b, solver="mg", mode="mixed_ff", tol=1e-10) for h in hs]
+    assert torch.equal(out[0][0], out[1][0]) and out[0][1].iters == out[1][1].iters
+
+
+def test_coarse_cycle_after_smaller_hierarchies():
+    # the shared-memory limit of the block kernel belongs to the kernel, not to a hierarchy:
+    # a large layout built first still launches after smaller hierarchies were built
+    import paper_2508_12501_gb300 as P
+    v, t = W.icosahedron()
+    hs = [P.Hierarchy(P.Mesh(v, t), 7, 6, bc="gauge", sphere=True, smoother="chebyshev", fuse=f) for f in (0, 32)]
+    vs, ts = W.unit_square()
+    small = [P.Hierarchy(P.Mesh(vs, ts), n, n - 1, bc="dirichlet", fuse=32) for n in (5, 4)]
+    b = torch.as_tensor(W.uniform_field(hs[0].n, 41), device="cuda")
+    out = [h.solve(b, mode="mixed_ff", tol=1e-8) for h in hs]
+    assert out[1][1].rel_res <= 1e-8 and torch.equal(out[0][0], out[1][0])
+    bs = torch.as_tensor(W.uniform_field(small[0].n, 43), device="cuda")
+    assert small[0].solve(bs, mode="mixed_ff", tol=1e-8)[1].rel_res <= 1e-8
