@@ -316,7 +316,7 @@ def convergence_factors(torch, dev):
              ("unit square x7 (16,641 V), Dirichlet", W.unit_square, 7, 6, "dirichlet", False)]
     for label, base, nsub, nl, bc, sph in cases:
         v, t = base()
-        for smoother in ("jacobi", "chebyshev"):
+        for smoother in ("jacobi", "chebyshev", "mcgs"):
             for gamma in (1, 2):
                 h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, gamma=gamma)
                 oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph,

@@ -61,6 +61,10 @@ enum {
 enum { DEC_SPHERE_PROJECT = 1u, DEC_HOST_ONLY = 2u, DEC_ORDER_MORTON = 4u };
 enum { DEC_BC_DIRICHLET = 0, DEC_BC_GAUGE = 1 };
 enum { DEC_F64 = 0, DEC_F32 = 1 };           /* precision of a single operator call */
+/* Smoothers: damped Jacobi (omega); Chebyshev on [cheby_lo, cheby_hi] * lambda_max(D^-1 L);
+ * multicolour Gauss-Seidel -- the paper's Gauss-Seidel (Sec. 3.1.2) over the colour classes
+ * of a greedy vertex colouring (smallest colour not taken by a lower-numbered neighbour),
+ * in increasing colour order, one kernel per class. */
 enum { DEC_SMOOTH_JACOBI = 0, DEC_SMOOTH_CHEBYSHEV = 1, DEC_SMOOTH_MCGS = 2 };
 /* Restriction: DEC_RESTRICT_ROWNORM is the paper's transpose of the
  * row-normalized subdivision matrix (Sec. 2.2.1); DEC_RESTRICT_STAR0 is the

@@ -158,6 +158,24 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth0(int n, int K, const T *
     }
 }
 
+// One multicolour Gauss-Seidel step over the rows of one colour class (rows
+// listed in `rows`): x_i += (b_i - (L x)_i) / L_ii in place.  Rows of one
+// colour are never neighbours, so every row reads the current values of the
+// other colours and no row of the class is read while it is written.
+template <typename T, int KT>
+__global__ void __launch_bounds__(kThreads, 8) k_mcgs(int n, int K, const int32_t *__restrict__ col,
+                                                  const T *__restrict__ w, const T *__restrict__ b, T *x,
+                                                  const int32_t *__restrict__ rows, int cnt, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    GRID_STRIDE(t, cnt) {
+        const int i = ldg(rows + t);
+        T s, d;
+        row_apply<T, KT>(i, n, K, col, w, x, s, d);
+        if (d != T(0)) x[i] = add_rn(x[i], (ldg(b + i) - s) / d);
+    }
+}
+
 // Row sums d_i = sum_k w_k (the Jacobi diagonal), summed in slot order as
 // k_smooth0 and row_apply do, so the fused kernels below read the same value.
 template <typename T, int KT>

@@ -24,6 +24,8 @@ struct DevLevel {
     float *w32 = nullptr;
     float *wlo = nullptr;  // finest level: w64 - w32 rounded to FP32 (ff weights w32 + wlo)
     float *dg32 = nullptr;     // row sums of w32 / w64 (the Jacobi diagonal), read by fused kernels
+    int32_t *crow = nullptr;   // rows sorted by greedy colour (multicolour Gauss-Seidel)
+    std::vector<int> coff;     // colour c owns crow[coff[c] .. coff[c+1])
     int16_t *col16 = nullptr;  // levels of the shared-memory coarse cycle: col and parents as int16
     int16_t *par16 = nullptr;
     double *dg64 = nullptr;

@@ -138,6 +138,26 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
             const int *skip, int k_start = 0, DotsArgs *da = nullptr) {
     DevLevel &L = mg->lv[l];
     const dec_mg_opts &o = mg->H.opts;
+    if (o.smoother == DEC_SMOOTH_MCGS) {
+        // multicolour Gauss-Seidel: nu sweeps over the colour classes in increasing
+        // colour order, in place on the current iterate (zero when from_zero)
+        if (from_zero) {
+            cur = 0;
+            cudaMemsetAsync(P<T>::x(L, 0), 0, sizeof(T) * L.n, s);
+        }
+        T *x = P<T>::x(L, cur);
+        dispatch_k(L.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            for (int k = k_start; k < nu; ++k)
+                for (size_t c = 0; c + 1 < L.coff.size(); ++c) {
+                    const int cnt = L.coff[c + 1] - L.coff[c];
+                    ProfScope ps(mg, DEC_PK_SMOOTH, l, s);
+                    launch(mg, k_mcgs<T, KT>, grid_for(mg, cnt), s, L.n, L.K, (const int32_t *)L.col, P<T>::w(L), b, x,
+                           (const int32_t *)(L.crow + L.coff[c]), cnt, skip);
+                }
+        });
+        return;
+    }
     const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
     const std::vector<double> &cc = post ? L.c_post : L.c_pre;
     const std::vector<double> &ee = post ? L.e_post : L.e_pre;
@@ -250,7 +270,8 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     // the coarse level's first smoothing step rides on the restriction
     // (not into the shared-memory coarse cycle, which starts from b itself)
     const bool coarse_next = std::is_same<T, float>::value && (o.fuse & DEC_FUSE_COARSE) && l - 1 == mg->coarse_top;
-    const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0 && !coarse_next;
+    const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0 && !coarse_next &&
+                           o.smoother != DEC_SMOOTH_MCGS;
     bool coarse_pre0 = false;
     const int g = grid_for(mg, L.n);
     const T *w = P<T>::w(L);
@@ -325,7 +346,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
             ec = P<T>::y(C);
         }
     }
-    if ((o.fuse & DEC_FUSE_PROLONG) && o.nu2 > 0) {
+    if ((o.fuse & DEC_FUSE_PROLONG) && o.nu2 > 0 && o.smoother != DEC_SMOOTH_MCGS) {
         const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
         const T e0 = (T)(cheb ? L.e_post[0] : o.omega);
         const bool dout = cheb && 1 < o.nu2;
@@ -396,7 +417,7 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
         da.first = first ? 1 : 0;
         da.gauge = gauge;
         // after an ff update with the fused first smoothing step, the cycle starts at step 1
-        const bool pre0 = outer && !first && mode == DEC_MODE_MIXED_FF && o.nu1 > 0;
+        const bool pre0 = outer && !first && mode == DEC_MODE_MIXED_FF && o.nu1 > 0 && o.smoother != DEC_SMOOTH_MCGS;
         float *z = cycle<float>(mg, top, F.b32, s, skip, pre0, outer ? &da : nullptr);
         if (!da.done) {
             ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
@@ -441,7 +462,7 @@ void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
             const dec_mg_opts &o = mg->H.opts;
             int s0mode = 0;
             float e0 = 0.f;
-            if ((o.fuse & DEC_FUSE_OUTER) && o.nu1 > 0) {
+            if ((o.fuse & DEC_FUSE_OUTER) && o.nu1 > 0 && o.smoother != DEC_SMOOTH_MCGS) {
                 const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
                 s0mode = cheb && 1 < o.nu1 ? 2 : 1;
                 e0 = (float)(cheb ? F.e_pre[0] : o.omega);
@@ -770,7 +791,8 @@ int setup_coarse_cycle(dec_mg *mg) {
     mg->coarse_top = -1;
     const dec_mg_opts &o = mg->H.opts;
     const int nl = (int)mg->lv.size();
-    if (nl < 2 || o.gamma != 1 || o.nu1 > kCoarseMaxNu || o.nu2 > kCoarseMaxNu) return DEC_OK;
+    if (nl < 2 || o.gamma != 1 || o.nu1 > kCoarseMaxNu || o.nu2 > kCoarseMaxNu || o.smoother == DEC_SMOOTH_MCGS)
+        return DEC_OK;
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, mg->device);
     const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV, star0 = o.restriction == DEC_RESTRICT_STAR0;
@@ -870,8 +892,8 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         o = *opts;
     else
         dec_mg_default_opts(&o);
-    if (o.smoother != DEC_SMOOTH_JACOBI && o.smoother != DEC_SMOOTH_CHEBYSHEV)
-        return fail(Status::fail(DEC_ERR_ARG, "smoother not available"));
+    if (o.smoother != DEC_SMOOTH_JACOBI && o.smoother != DEC_SMOOTH_CHEBYSHEV && o.smoother != DEC_SMOOTH_MCGS)
+        return fail(Status::fail(DEC_ERR_ARG, "unknown smoother"));
     if (o.restriction != DEC_RESTRICT_ROWNORM && o.restriction != DEC_RESTRICT_STAR0)
         return fail(Status::fail(DEC_ERR_ARG, "unknown restriction"));
     if (o.fuse < 0 || o.fuse > DEC_FUSE_ALL) return fail(Status::fail(DEC_ERR_ARG, "fuse must be a DEC_FUSE_* mask"));
@@ -944,6 +966,16 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu2, 1), D.c_post, D.e_post);
         if ((rc = dalloc(mg, &D.dg32, D.n)) || (rc = dalloc(mg, &D.dg64, D.n))) return bail(rc);
         update_diagonals(mg, D, nullptr);
+        if (o.smoother == DEC_SMOOTH_MCGS) {
+            // rows by colour, ascending row id within a colour (counting sort)
+            D.coff.assign(HL.ncolors + 1, 0);
+            for (int v = 0; v < D.n; ++v) D.coff[HL.colors[v] + 1] += 1;
+            for (int c = 0; c < HL.ncolors; ++c) D.coff[c + 1] += D.coff[c];
+            std::vector<int32_t> rows(D.n);
+            std::vector<int> fill(D.coff.begin(), D.coff.end() - 1);
+            for (int v = 0; v < D.n; ++v) rows[fill[HL.colors[v]]++] = v;
+            if ((rc = upload(mg, &D.crow, rows.data(), rows.size()))) return bail(rc);
+        }
     }
     // coarsest dense operator
     {
@@ -1161,6 +1193,8 @@ int dec_mg_time_smooth(dec_mg *mg, int level, int reps, double *avg_ms, double *
     if (level < 0) level += nl;
     if (reps < 1 || !avg_ms || !bytes || level < 1 || level >= nl)
         return fail(Status::fail(DEC_ERR_ARG, "bad argument (level must lie above the coarsest)"));
+    if (mg->H.opts.smoother == DEC_SMOOTH_MCGS)
+        return fail(Status::fail(DEC_ERR_ARG, "dec_mg_time_smooth times the Jacobi / Chebyshev sweep"));
     DevLevel &L = mg->lv[level];
     const bool cheb = mg->H.opts.smoother == DEC_SMOOTH_CHEBYSHEV;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1361,6 +1395,8 @@ extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_s
     if (int rc = check_dev(mg)) return rc;
     if (!b || !x) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
     if (mg->H.opts.gamma != 1) return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle is a V-cycle (gamma = 1)"));
+    if (mg->H.opts.smoother == DEC_SMOOTH_MCGS)
+        return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle smooths with Jacobi or Chebyshev"));
     const size_t need = noalloc_floats(mg) * sizeof(float);
     if (need > DEC_NOALLOC_SCRATCH_BYTES)
         return fail(Status::fail(DEC_ERR_ARG, "hierarchy needs " + std::to_string(need) +

@@ -103,7 +103,7 @@ def _s0_rel(lev, a, b):
 
 
 @pytest.mark.parametrize("name", ["square5", "ico5", "fan3", "grid_ragged"])
-@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "mcgs"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("restriction", ["rownorm", "star0"])
 def test_one_cycle_matches_oracle(name, smoother, prec, restriction):
@@ -230,7 +230,7 @@ def test_w_cycle_matches_oracle(name, prec):
 
 
 @pytest.mark.parametrize("name", ["square5", "ico5"])
-@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev", "mcgs"])
 @pytest.mark.parametrize("gamma", [1, 2])
 def test_convergence_factor_matches_oracle(name, smoother, gamma):
     # standalone MG in FP64: geometric-mean residual reduction per cycle, GPU vs oracle
@@ -266,3 +266,21 @@ def test_morton_order_cycle_and_solve_match_oracle(name):
     xs, st = h.solve(_dev(b), mode="mixed_ff", tol=1e-10)
     assert st.rel_res <= 1e-10
     assert _s0_rel(lev, xs.cpu().numpy(), omg.direct_solve(oh, b)) < 1e-7
+
+
+@pytest.mark.parametrize("name", ["square5", "ico5", "fan3"])
+@pytest.mark.parametrize("mode", ["f64", "mixed_ff"])
+def test_mcgs_solves_match_oracle(name, mode):
+    # the paper's Gauss-Seidel, multicoloured: standalone MG and MG-PCG reach the direct solution
+    h, oh = _pair(name, smoother="mcgs")
+    lev = oh.finest
+    b = W.uniform_field(lev.mesh.nv, 67)
+    xs = omg.direct_solve(oh, b)
+    for solver in ("mg", "mgpcg"):
+        x, st = h.solve(_dev(b), solver=solver, mode=mode, tol=1e-10, maxit=100)
+        assert st.rel_res <= 1e-10
+        assert _s0_rel(lev, x.cpu().numpy(), xs) < 1e-7
+    if mode == "f64":
+        ref = omg.mg_solve(oh, b, 1e-10, 100)
+        _, st = h.solve(_dev(b), solver="mg", mode="f64", tol=1e-10, maxit=100)
+        assert abs(st.iters - ref.iters) <= 1
