@@ -317,14 +317,16 @@ def convergence_factors(torch, dev):
     for label, base, nsub, nl, bc, sph in cases:
         v, t = base()
         for smoother in ("jacobi", "chebyshev", "mcgs"):
-            for gamma in (1, 2):
-                h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, gamma=gamma)
+            for gamma in (1, 2, "F"):
+                fc = gamma == "F"
+                g = 1 if fc else gamma
+                h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, gamma=g, fcycle=fc)
                 oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph,
-                                         opts=omg.MGOptions(smoother=smoother, gamma=gamma))
+                                         opts=omg.MGOptions(smoother=smoother, gamma=g, fcycle=fc))
                 b = W.uniform_field(h.n, 71)
                 _, st = h.solve(torch.as_tensor(b, device=dev), solver="mg", mode="f64", tol=1e-10, maxit=100)
                 ref = omg.mg_solve(oh, b, 1e-10, 100)
-                out.append({"mesh": label, "smoother": smoother, "cycle": "V(2,2)" if gamma == 1 else "W(2,2)",
+                out.append({"mesh": label, "smoother": smoother, "cycle": {1: "V(2,2)", 2: "W(2,2)", "F": "F(2,2)"}[gamma],
                             "gpu": round((st.rel_res / st.rel_res0) ** (1.0 / st.iters), 4),
                             "oracle": round(omg.convergence_factor(ref.history), 4),
                             "gpu_cycles": st.iters, "oracle_cycles": ref.iters})

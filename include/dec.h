@@ -88,7 +88,7 @@ enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1, DEC_MODE_MIXED_FF = 2 };
 /* Multigrid options.  dec_mg_default_opts() fills the defaults:
  * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
  * [0.3, 1.1] * lambda_max(D^-1 L) with lambda_max from 10 power iterations,
- * gamma = 1 (V-cycle; 2 gives a W-cycle, up to 4), the paper's restriction,
+ * gamma = 1 (V-cycle; 2 gives a W-cycle, up to 4), no F-cycle, the paper's restriction,
  * the row-local kernel fusions.
  * With gamma > 1 each coarse correction is repeated gamma times,
  * e <- e + C(b - L e), except on the coarsest level whose solve is exact. */
@@ -100,6 +100,8 @@ typedef struct dec_mg_opts {
     int power_iters;
     int gamma;
     int restriction;  /* DEC_RESTRICT_* */
+    int fcycle;       /* 1: F-cycles -- the coarse correction is an F-cycle followed by a
+                         V-cycle (gamma ignored); 0: gamma-cycles */
     int coarse_max_rows; /* DEC_FUSE_COARSE: largest level (rows) run in the shared-memory
                             block; 0 (default): the library's choice */
     int fuse;         /* DEC_FUSE_* mask of fused cycle kernels, each bitwise equal to

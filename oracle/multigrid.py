@@ -51,6 +51,7 @@ class MGOptions:
     cheby_hi: float = 1.1
     power_iters: int = 10
     gamma: int = 1                # 1: V-cycle, 2: W-cycle
+    fcycle: bool = False          # F-cycle: coarse correction = an F-cycle then a V-cycle
     restriction: str = "rownorm"  # rownorm: the paper's; star0: *0-adjoint of interpolation
 
 
@@ -323,10 +324,18 @@ def coarse_solve(h, lev, b):
 # cycles and solvers
 # ----------------------------------------------------------------------------
 
-def vcycle(h, b, x, l=None):
-    """One cycle (V for gamma=1, W for gamma=2) on level l (default: finest)."""
+def vcycle(h, b, x, l=None, kind=None):
+    """One cycle x <- x + C(b - L x) on level l (default: finest).
+
+    kind "gamma": the coarse correction is gamma cycles of the same kind
+    (gamma = 1: V-cycle, 2: W-cycle); "V": one V-cycle below; "F": the coarse
+    correction is an F-cycle followed by a V-cycle.  Default: "F" if
+    opts.fcycle else "gamma".  On the coarsest level the solve is exact.
+    """
     if l is None:
         l = len(h.levels) - 1
+    if kind is None:
+        kind = "F" if h.opts.fcycle else "gamma"
     lev = h.levels[l]
     if l == 0:
         return x + coarse_solve(h, lev, residual(lev, b, x))
@@ -335,8 +344,12 @@ def vcycle(h, b, x, l=None):
     clev = h.levels[l - 1]
     rc = clev.free * (h.R[l - 1] @ r)
     ec = np.zeros(clev.mesh.nv)
-    for _ in range(h.opts.gamma):
-        ec = vcycle(h, rc, ec, l - 1)
+    if kind == "F":
+        ec = vcycle(h, rc, ec, l - 1, "F")
+        ec = vcycle(h, rc, ec, l - 1, "V")
+    else:
+        for _ in range(h.opts.gamma if kind == "gamma" else 1):
+            ec = vcycle(h, rc, ec, l - 1, kind)
     x = x + lev.free * (h.P[l - 1] @ ec)
     x = smooth(h, lev, b, x, h.opts.nu2)
     return x

@@ -93,7 +93,8 @@ class Hierarchy:
 
     def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
-                 restriction="rownorm", host_only=False, fuse=None, order="edge", coarse_max_rows=0):
+                 restriction="rownorm", host_only=False, fuse=None, order="edge", coarse_max_rows=0,
+                 fcycle=False):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
         o = L.dec_mg_opts()
@@ -107,6 +108,7 @@ class Hierarchy:
             o.fuse = int(fuse) if not isinstance(fuse, bool) else (L.DEC_FUSE_ALL if fuse else 0)
         self.fuse = int(o.fuse)
         o.coarse_max_rows = int(coarse_max_rows)
+        o.fcycle = 1 if fcycle else 0
         flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0) | ORDERS[order]
         scale = None
         if star1_scale is not None:

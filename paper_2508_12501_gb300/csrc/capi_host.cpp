@@ -35,6 +35,7 @@ void dec_mg_default_opts(dec_mg_opts *o) {
     o->power_iters = 10;
     o->gamma = 1;
     o->restriction = DEC_RESTRICT_ROWNORM;
+    o->fcycle = 0;
     o->fuse = DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE;
     o->coarse_max_rows = 0;
 }

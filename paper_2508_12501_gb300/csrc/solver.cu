@@ -238,9 +238,14 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
 // ran, fused into the kernel that produced b; x[0] (and d[0]) hold it.
 // da: fuse the last post-smoothing step of this (finest) level with the
 // outer dot products.
+// kind: the cycle below this level -- gamma repetitions of the same kind (V
+// for gamma = 1, W), a single V, or F (an F-cycle, then a V-cycle); -1 takes
+// the hierarchy's option.
+enum { kCycGamma = 0, kCycV = 1, kCycF = 2 };
 template <typename T>
 T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pre0_done = false,
-         DotsArgs *da = nullptr) {
+         DotsArgs *da = nullptr, int kind = -1) {
+    if (kind < 0) kind = mg->H.opts.fcycle ? kCycF : kCycGamma;
     DevLevel &L = mg->lv[l];
     if (l == 0) {
         const T *G;
@@ -327,13 +332,15 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
                        T(0));
         }
     });
-    T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip, coarse_pre0);
-    if (o.gamma > 1 && l - 1 > 0) {
-        // W-cycle: repeat the coarse correction gamma times, ec <- ec + C(b_c - L_c ec);
-        // (not on the coarsest level, whose dense solve is exact)
+    T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip, coarse_pre0, nullptr, kind);
+    const int reps = kind == kCycF ? 2 : (kind == kCycGamma ? o.gamma : 1);
+    if (reps > 1 && l - 1 > 0) {
+        // W- or F-cycle: repeat the coarse correction, ec <- ec + C(b_c - L_c ec), gamma
+        // times with the same cycle (W) or once with a V-cycle (F); not on the
+        // coarsest level, whose dense solve is exact
         const int gc = grid_for(mg, C.n);
         const T *wc = P<T>::w(C);
-        for (int rep = 1; rep < o.gamma; ++rep) {
+        for (int rep = 1; rep < reps; ++rep) {
             launch(mg, k_copy<T>, gc, s, C.n, (const T *)ec, P<T>::y(C), skip);
             dispatch_k(C.K, [&](auto kt) {
                 constexpr int KT = decltype(kt)::value;
@@ -341,7 +348,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
                 launch(mg, k_residual<T, KT>, gc, s, C.n, C.K, (const int32_t *)C.col, wc, (const T *)P<T>::b(C),
                        (const T *)P<T>::y(C), P<T>::c(C), skip);
             });
-            T *e2 = cycle<T>(mg, l - 1, P<T>::c(C), s, skip);
+            T *e2 = cycle<T>(mg, l - 1, P<T>::c(C), s, skip, false, nullptr, kind == kCycF ? kCycV : kind);
             launch(mg, k_axpy1<T>, gc, s, C.n, (const T *)e2, P<T>::y(C), skip);
             ec = P<T>::y(C);
         }
@@ -791,7 +798,8 @@ int setup_coarse_cycle(dec_mg *mg) {
     mg->coarse_top = -1;
     const dec_mg_opts &o = mg->H.opts;
     const int nl = (int)mg->lv.size();
-    if (nl < 2 || o.gamma != 1 || o.nu1 > kCoarseMaxNu || o.nu2 > kCoarseMaxNu || o.smoother == DEC_SMOOTH_MCGS)
+    if (nl < 2 || o.gamma != 1 || o.fcycle || o.nu1 > kCoarseMaxNu || o.nu2 > kCoarseMaxNu ||
+        o.smoother == DEC_SMOOTH_MCGS)
         return DEC_OK;
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, mg->device);
@@ -898,6 +906,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         return fail(Status::fail(DEC_ERR_ARG, "unknown restriction"));
     if (o.fuse < 0 || o.fuse > DEC_FUSE_ALL) return fail(Status::fail(DEC_ERR_ARG, "fuse must be a DEC_FUSE_* mask"));
     if (o.coarse_max_rows < 0) return fail(Status::fail(DEC_ERR_ARG, "coarse_max_rows must be >= 0"));
+    if (o.fcycle != 0 && o.fcycle != 1) return fail(Status::fail(DEC_ERR_ARG, "fcycle must be 0 or 1"));
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma < 1 || o.gamma > 4 || o.power_iters < 1 ||
         !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad multigrid options"));
@@ -959,7 +968,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         if ((rc = dalloc(mg, &D.r32, D.n)) || (rc = dalloc(mg, &D.b32, D.n)) || (rc = dalloc(mg, &D.r64, D.n)) ||
             (rc = dalloc(mg, &D.b64, D.n)))
             return bail(rc);
-        if (o.gamma > 1 && (((rc = dalloc(mg, &D.y32, D.n))) || (rc = dalloc(mg, &D.c32, D.n)) ||
+        if ((o.gamma > 1 || o.fcycle) && (((rc = dalloc(mg, &D.y32, D.n))) || (rc = dalloc(mg, &D.c32, D.n)) ||
                             (rc = dalloc(mg, &D.y64, D.n)) || (rc = dalloc(mg, &D.c64, D.n))))
             return bail(rc);
         cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu1, 1), D.c_pre, D.e_pre);
@@ -1394,7 +1403,8 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
 extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_stream_t stream) {
     if (int rc = check_dev(mg)) return rc;
     if (!b || !x) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
-    if (mg->H.opts.gamma != 1) return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle is a V-cycle (gamma = 1)"));
+    if (mg->H.opts.gamma != 1 || mg->H.opts.fcycle)
+        return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle is a V-cycle (gamma = 1)"));
     if (mg->H.opts.smoother == DEC_SMOOTH_MCGS)
         return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle smooths with Jacobi or Chebyshev"));
     const size_t need = noalloc_floats(mg) * sizeof(float);

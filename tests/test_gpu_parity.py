@@ -284,3 +284,30 @@ def test_mcgs_solves_match_oracle(name, mode):
         ref = omg.mg_solve(oh, b, 1e-10, 100)
         _, st = h.solve(_dev(b), solver="mg", mode="f64", tol=1e-10, maxit=100)
         assert abs(st.iters - ref.iters) <= 1
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["square5", "ico5"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+def test_f_cycle_matches_oracle(name, prec, smoother):
+    # F-cycles: the coarse correction is an F-cycle then a V-cycle (4 levels: differs from V and W)
+    P = _lib()
+    base, nsub, nl, bc, sph = CASES[name]
+    v, t = base()
+    h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, fcycle=True)
+    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, opts=omg.MGOptions(smoother=smoother, fcycle=True))
+    lev = oh.finest
+    b = omg.prepare_rhs(oh, W.uniform_field(lev.mesh.nv, 63))
+    ref = omg.vcycle(oh, b, np.zeros_like(b))
+    dt = torch.float64 if prec == "f64" else torch.float32
+    x = torch.zeros(lev.mesh.nv, dtype=dt, device="cuda")
+    h.vcycle(_dev(b, dt), x)
+    assert _s0_rel(lev, x.double().cpu().numpy(), ref) < (1e-12 if prec == "f64" else 2e-5)
+    b2 = W.uniform_field(lev.mesh.nv, 64)
+    _, st = h.solve(_dev(b2), solver="mg", mode="f64", tol=1e-10)
+    ref2 = omg.mg_solve(oh, b2, 1e-10, 100)
+    assert abs(st.iters - ref2.iters) <= 1
+    cf = (st.rel_res / st.rel_res0) ** (1.0 / st.iters)
+    assert abs(cf - omg.convergence_factor(ref2.history)) <= 0.02
+    xs, st = h.solve(_dev(b2), solver="mgpcg", mode="mixed_ff", tol=1e-10)
+    assert st.rel_res <= 1e-10 and _s0_rel(lev, xs.cpu().numpy(), omg.direct_solve(oh, b2)) < 1e-7

@@ -227,3 +227,31 @@ def test_star0_restriction_keeps_pcg_stable_on_boundary_data():
     b = np.where(np.abs(y - (1 - 1.0 / 64)) < 1e-12, W.uniform_field(lev.mesh.nv, 9) * 1e5, 0.0)
     r = mg.pcg_solve(h, b, 1e-10, 60)
     assert r.rel_res <= 1e-10 and r.iters < 20
+
+
+def test_f_cycle_on_three_levels_is_the_w_cycle():
+    # F(2) = pre, [F(1) then V(1)], post and F(1) = V(1) (its coarse correction is exact): the W-cycle,
+    # up to the rounding of the W-cycle's repeated exact coarse solve
+    v, t = W.unit_square()
+    hf = mg.build_hierarchy(v, t, 4, 3, "dirichlet", opts=mg.MGOptions(fcycle=True))
+    hw = mg.build_hierarchy(v, t, 4, 3, "dirichlet", opts=mg.MGOptions(gamma=2))
+    hv = mg.build_hierarchy(v, t, 4, 3, "dirichlet")
+    b = W.uniform_field(hf.finest.mesh.nv, 13)
+    x0 = np.zeros_like(b)
+    xf, xw, xv = mg.vcycle(hf, b, x0), mg.vcycle(hw, b, x0), mg.vcycle(hv, b, x0)
+    assert np.max(np.abs(xf - xw)) <= 1e-12 * np.max(np.abs(xw))
+    assert np.max(np.abs(xf - xv)) > 1e-6 * np.max(np.abs(xv))
+
+
+def test_f_cycle_between_v_and_w():
+    # 5 levels: F differs from V and W; its convergence lies between theirs (and it reaches the solution)
+    v, t = W.unit_square()
+    b = W.uniform_field(mg.build_hierarchy(v, t, 6, 1, "dirichlet").finest.mesh.nv, 14)
+    res = {}
+    for name, o in (("V", mg.MGOptions()), ("F", mg.MGOptions(fcycle=True)), ("W", mg.MGOptions(gamma=2))):
+        h = mg.build_hierarchy(v, t, 6, 5, "dirichlet", opts=o)
+        r = mg.mg_solve(h, b, 1e-10, 60)
+        assert r.rel_res <= 1e-10
+        res[name] = mg.convergence_factor(r.history)
+    assert res["W"] <= res["F"] * 1.05 and res["F"] <= res["V"] * 1.05, res
+    assert res["F"] < res["V"], res
