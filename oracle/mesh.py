@@ -198,11 +198,77 @@ def subdivide(mesh, sphere=False, order="edge"):
     return fine, mesh.edges[perm].copy()
 
 
-def refine(verts, tris, nsub, sphere=False, order="edge"):
-    """Apply nsub subdivisions; returns the list of meshes (coarsest first) and parent tables."""
+def subdivide_cubic(mesh, sphere=False):
+    """One 1->9 subdivision (Sec. 2.2.1, cubic subdivision).
+
+    Coarse vertices keep their ids.  Coarse edge e = (lo, hi) gets two new
+    vertices, n_c + 2e at (2 x_lo + x_hi)/3 and n_c + 2e + 1 at (x_lo + 2 x_hi)/3;
+    coarse triangle t = (a, b, c) gets its centroid n_c + 2E + t at
+    ((x_a + x_b) + x_c)/3.  With lattice points (i, j, k)/3 of weights on
+    (a, b, c), the triangle becomes the nine lattice triangles
+      9t+0 (a, ab1, ca2)   9t+1 (ab1, ab2, m)   9t+2 (ab2, b, bc1)
+      9t+3 (ca2, m, ca1)   9t+4 (m, bc1, bc2)   9t+5 (ca1, bc2, c)
+      9t+6 (ab1, m, ca2)   9t+7 (ab2, bc1, m)   9t+8 (m, bc2, ca1)
+    where xy1 is the point on edge xy next to x and xy2 the one next to y, and
+    m the centroid; all keep the coarse orientation.  With sphere=True the new
+    points are pushed to the unit sphere and the weights stay combinatorial.
+
+    Returns (fine Mesh, M) with M = M(f), the n_c x n_f matrix whose column j
+    holds the global barycentric coordinates of fine vertex j (Sec. 2.2.1):
+    1 for a kept vertex, 2/3 and 1/3 for an edge point, 1/3 three times for a
+    centroid.
+    """
+    nc, E, T = mesh.nv, mesh.ne, mesh.nt
+    lo, hi = mesh.edges[:, 0], mesh.edges[:, 1]
+    xl, xh = mesh.verts[lo], mesh.verts[hi]
+    pts = np.empty((2 * E + T, mesh.verts.shape[1]))
+    pts[0:2 * E:2] = (2.0 * xl + xh) / 3.0
+    pts[1:2 * E:2] = (xl + 2.0 * xh) / 3.0
+    a, b, c = mesh.tris[:, 0], mesh.tris[:, 1], mesh.tris[:, 2]
+    pts[2 * E:] = ((mesh.verts[a] + mesh.verts[b]) + mesh.verts[c]) / 3.0
+    if sphere:
+        if mesh.verts.shape[1] != 3:
+            raise MeshError("sphere projection needs 3-D vertices")
+        nrm = np.sqrt(pts[:, 0] * pts[:, 0] + pts[:, 1] * pts[:, 1] + pts[:, 2] * pts[:, 2])
+        pts = pts / nrm[:, None]
+    fverts = np.concatenate([mesh.verts, pts], axis=0)
+
+    def near(k, corner):
+        e = mesh.tri_edges[:, k]
+        return nc + 2 * e + (corner != lo[e])
+
+    ab1, ab2 = near(0, a), near(0, b)
+    bc1, bc2 = near(1, b), near(1, c)
+    ca1, ca2 = near(2, c), near(2, a)
+    m = nc + 2 * E + np.arange(T)
+    ftris = np.empty((9 * T, 3), dtype=np.int64)
+    for q, tri in enumerate(((a, ab1, ca2), (ab1, ab2, m), (ab2, b, bc1), (ca2, m, ca1), (m, bc1, bc2),
+                             (ca1, bc2, c), (ab1, m, ca2), (ab2, bc1, m), (m, bc2, ca1))):
+        ftris[q::9] = np.stack(tri, axis=1)
+    fine = build_mesh(fverts, ftris)
+    assert fine.nv == nc + 2 * E + T
+    third, two_thirds = 1.0 / 3.0, 2.0 / 3.0
+    ids = np.arange(E)
+    rows = np.concatenate([np.arange(nc), lo, hi, lo, hi, a, b, c])
+    cols = np.concatenate([np.arange(nc), nc + 2 * ids, nc + 2 * ids, nc + 2 * ids + 1, nc + 2 * ids + 1, m, m, m])
+    vals = np.concatenate([np.ones(nc), np.full(E, two_thirds), np.full(E, third), np.full(E, third),
+                           np.full(E, two_thirds), np.full(3 * T, third)])
+    M = sp.csr_matrix((vals, (rows, cols)), shape=(nc, fine.nv))
+    return fine, M
+
+
+def refine(verts, tris, nsub, sphere=False, order="edge", scheme="binary"):
+    """Apply nsub subdivisions; returns the list of meshes (coarsest first) and, per step,
+    the parent table (binary: the coarse edge of each new vertex) or, for
+    scheme="cubic", the geometric-map matrix M(f) of subdivide_cubic."""
     meshes = [build_mesh(verts, tris)]
     parents = []
     for _ in range(nsub):
+        if scheme == "cubic":
+            fine, par = subdivide_cubic(meshes[-1], sphere=sphere)
+            meshes.append(fine)
+            parents.append(par)
+            continue
         fine, par = subdivide(meshes[-1], sphere=sphere, order=order)
         meshes.append(fine)
         parents.append(par)

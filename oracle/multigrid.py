@@ -97,14 +97,19 @@ def barycentric_matrix(nc, parents):
     return sp.csr_matrix((vals, (rows, cols)), shape=(nc, nf))
 
 
+def _map_matrix(nc, parents):
+    """M(f) from a binary parent table or an explicit map matrix (cubic subdivision)."""
+    return parents if sp.issparse(parents) else barycentric_matrix(nc, parents)
+
+
 def interpolation(nc, parents):
     """Interpolation acting on column vectors: x_f = M(f)^T x_c."""
-    return barycentric_matrix(nc, parents).T.tocsr()
+    return _map_matrix(nc, parents).T.tocsr()
 
 
 def restriction(nc, parents):
     """Row-normalized M(f): r_c = rownorm(M(f)) r_f (the transpose of what acts on row vectors)."""
-    M = barycentric_matrix(nc, parents)
+    M = _map_matrix(nc, parents)
     rs = np.asarray(M.sum(axis=1)).ravel()
     return (sp.diags(1.0 / rs) @ M).tocsr()
 
@@ -115,7 +120,7 @@ def restriction_star0(nc, parents, star0_c, star0_f):
     Not the paper's operator (an option): with it the cycle is self-adjoint in
     the *0 inner product, as CG's preconditioner needs.
     """
-    M = barycentric_matrix(nc, parents)
+    M = _map_matrix(nc, parents)
     return (sp.diags(1.0 / star0_c) @ M @ sp.diags(star0_f)).tocsr()
 
 
@@ -183,16 +188,17 @@ def make_level(mesh, bc, star1_scale=None, opts=None, with_gs=False):
 
 
 def build_hierarchy(verts, tris, nsub, nlevels, bc, sphere=False, star1_scale=None,
-                    opts=None, meshes=None, parents=None, order="edge"):
+                    opts=None, meshes=None, parents=None, order="edge", scheme="binary"):
     """Subdivide nsub times and keep the finest nlevels meshes as the MG hierarchy.
 
     star1_scale (per finest edge) multiplies *1 on the finest level only;
     coarser levels are rediscretized from their own geometry.  order is the
-    numbering of each level's new vertices (see oracle.mesh.subdivide).
+    numbering of each level's new vertices (see oracle.mesh.subdivide);
+    scheme is "binary" (1->4) or "cubic" (1->9, oracle.mesh.subdivide_cubic).
     """
     opts = opts or MGOptions()
     if meshes is None:
-        meshes, parents = refine(verts, tris, nsub, sphere=sphere, order=order)
+        meshes, parents = refine(verts, tris, nsub, sphere=sphere, order=order, scheme=scheme)
     if not 1 <= nlevels <= nsub + 1:
         raise ValueError("nlevels out of range")
     first = nsub + 1 - nlevels
