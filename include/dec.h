@@ -58,7 +58,7 @@ enum {
  * DEC_ERR_ARG.  DEC_ORDER_MORTON numbers each level's new vertices along a
  * space-filling curve instead of the default coarse edge order (see
  * dec_mesh_refine). */
-enum { DEC_SPHERE_PROJECT = 1u, DEC_HOST_ONLY = 2u, DEC_ORDER_MORTON = 4u };
+enum { DEC_SPHERE_PROJECT = 1u, DEC_HOST_ONLY = 2u, DEC_ORDER_MORTON = 4u, DEC_SUBDIV_CUBIC = 8u };
 enum { DEC_BC_DIRICHLET = 0, DEC_BC_GAUGE = 1 };
 enum { DEC_F64 = 0, DEC_F32 = 1 };           /* precision of a single operator call */
 /* Smoothers: damped Jacobi (omega); Chebyshev on [cheby_lo, cheby_hi] * lambda_max(D^-1 L);
@@ -171,7 +171,10 @@ enum {
     DEC_TABLE_FREE = 5,    /* [nv] int32, 1 = unknown, 0 = Dirichlet vertex       */
     DEC_TABLE_PARENTS = 6, /* [ne(level) * 2] int32, coarse edge (a, b) of each new vertex
                               n(level) + k of level+1, k = 0 .. ne(level)-1 (not the finest) */
-    DEC_TABLE_COLORS = 7   /* [nv] int32, greedy colour of each vertex            */
+    DEC_TABLE_COLORS = 7,  /* [nv] int32, greedy colour of each vertex            */
+    DEC_TABLE_MAP_IDX = 8, /* [nv(level+1) * 3] int32: the geometric map from level to level+1,
+                              three coarse vertices per fine vertex (not the finest)        */
+    DEC_TABLE_MAP_W = 9    /* [nv(level+1) * 3] double: their barycentric weights (0 = unused) */
 };
 
 /* ---- errors, defaults --------------------------------------------------- */
@@ -206,7 +209,14 @@ int dec_mesh_sizes(const dec_mesh *mesh, int64_t *nv, int64_t *ne, int64_t *nt, 
  * bits (B = 21 in 3-D, 31 in 2-D) as floor((x - lo) * ((2^B - 1)/(hi - lo))),
  * bits interleaved, ties kept in coarse edge order.  (On GB300 the edge order
  * gathered faster; the Z-order is kept as an option.)  flags & DEC_SPHERE_PROJECT pushes each new
- * midpoint to the unit sphere.  *out is a new mesh owned by the caller. */
+ * midpoint to the unit sphere.  With DEC_SUBDIV_CUBIC each step is the
+ * cubic 1->9 subdivision instead (Sec. 2.2.1): coarse edge e = (lo, hi) gets
+ * n_coarse + 2e at (2 x_lo + x_hi)/3 and n_coarse + 2e + 1 at (x_lo + 2 x_hi)/3,
+ * triangle t = (a,b,c) its centroid n_coarse + 2E + t at ((x_a + x_b) + x_c)/3
+ * and becomes the nine lattice triangles (a,ab1,ca2), (ab1,ab2,m), (ab2,b,bc1),
+ * (ca2,m,ca1), (m,bc1,bc2), (ca1,bc2,c), (ab1,m,ca2), (ab2,bc1,m), (m,bc2,ca1)
+ * (xy1 next to x, xy2 next to y, m the centroid), numbered 9t .. 9t+8; not
+ * with DEC_ORDER_MORTON.  *out is a new mesh owned by the caller. */
 int dec_mesh_refine(const dec_mesh *mesh, int nsub, uint32_t flags, dec_mesh **out);
 /* Copy DEC_TABLE_VERTS / TRIS / EDGES / STAR0 / STAR1 of a mesh to host memory.
  * STAR0 and STAR1 are the circumcentric Hodge stars (Sec. 3.1.1). */

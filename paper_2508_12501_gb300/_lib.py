@@ -20,7 +20,7 @@ lib = C.CDLL(LIB_PATH)
 
 # status codes and enums (mirror include/dec.h)
 DEC_OK, DEC_ERR_ARG, DEC_ERR_MESH, DEC_ERR_CUDA, DEC_ERR_OOM, DEC_ERR_NOT_CONVERGED, DEC_ERR_NONFINITE = range(7)
-DEC_SPHERE_PROJECT, DEC_HOST_ONLY, DEC_ORDER_MORTON = 1, 2, 4
+DEC_SPHERE_PROJECT, DEC_HOST_ONLY, DEC_ORDER_MORTON, DEC_SUBDIV_CUBIC = 1, 2, 4, 8
 DEC_NOALLOC_SCRATCH_BYTES = 32 << 20
 DEC_BC_DIRICHLET, DEC_BC_GAUGE = 0, 1
 DEC_F64, DEC_F32 = 0, 1
@@ -32,7 +32,7 @@ DEC_FUSE_SMOOTH01, DEC_FUSE_RESTRICT, DEC_FUSE_PROLONG, DEC_FUSE_RESTRICT0, DEC_
 DEC_FUSE_COARSE = 32
 DEC_FUSE_ALL = 63
 (DEC_TABLE_VERTS, DEC_TABLE_TRIS, DEC_TABLE_EDGES, DEC_TABLE_STAR0, DEC_TABLE_STAR1,
- DEC_TABLE_FREE, DEC_TABLE_PARENTS, DEC_TABLE_COLORS) = range(8)
+ DEC_TABLE_FREE, DEC_TABLE_PARENTS, DEC_TABLE_COLORS, DEC_TABLE_MAP_IDX, DEC_TABLE_MAP_W) = range(10)
 
 STATUS_NAMES = {0: "DEC_OK", 1: "DEC_ERR_ARG", 2: "DEC_ERR_MESH", 3: "DEC_ERR_CUDA", 4: "DEC_ERR_OOM",
                 5: "DEC_ERR_NOT_CONVERGED", 6: "DEC_ERR_NONFINITE"}

@@ -18,11 +18,13 @@ SMOOTHERS = {"jacobi": L.DEC_SMOOTH_JACOBI, "chebyshev": L.DEC_SMOOTH_CHEBYSHEV,
 SOLVERS = {"mg": L.DEC_SOLVER_MG, "mgpcg": L.DEC_SOLVER_MGPCG, "cg": L.DEC_SOLVER_CG}
 MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED, "mixed_ff": L.DEC_MODE_MIXED_FF}
 ORDERS = {"edge": 0, "morton": L.DEC_ORDER_MORTON}
+SCHEMES = {"binary": 0, "cubic": L.DEC_SUBDIV_CUBIC}
 BCS = {"dirichlet": L.DEC_BC_DIRICHLET, "gauge": L.DEC_BC_GAUGE}
 RESTRICTIONS = {"rownorm": L.DEC_RESTRICT_ROWNORM, "star0": L.DEC_RESTRICT_STAR0}
 TABLES = {"verts": L.DEC_TABLE_VERTS, "tris": L.DEC_TABLE_TRIS, "edges": L.DEC_TABLE_EDGES,
           "star0": L.DEC_TABLE_STAR0, "star1": L.DEC_TABLE_STAR1, "free": L.DEC_TABLE_FREE,
-          "parents": L.DEC_TABLE_PARENTS, "colors": L.DEC_TABLE_COLORS}
+          "parents": L.DEC_TABLE_PARENTS, "colors": L.DEC_TABLE_COLORS, "map_idx": L.DEC_TABLE_MAP_IDX,
+          "map_w": L.DEC_TABLE_MAP_W}
 
 
 def _np_ptr(a):
@@ -54,10 +56,11 @@ class Mesh:
             lib.dec_mesh_destroy(h)
             self._h = None
 
-    def refine(self, nsub, sphere=False, order="edge"):
-        """nsub 1->4 subdivisions; order is the numbering of each level's new vertices ("morton" or "edge")."""
+    def refine(self, nsub, sphere=False, order="edge", scheme="binary"):
+        """nsub subdivisions (scheme "binary": 1->4, "cubic": 1->9); order numbers each binary level's
+        new vertices ("edge" or "morton")."""
         h = C.c_void_p()
-        flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | ORDERS[order]
+        flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | ORDERS[order] | SCHEMES[scheme]
         check(lib.dec_mesh_refine(self._h, int(nsub), flags, C.byref(h)), "dec_mesh_refine")
         return Mesh(_handle=h)
 
@@ -94,7 +97,7 @@ class Hierarchy:
     def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
                  restriction="rownorm", host_only=False, fuse=None, order="edge", coarse_max_rows=0,
-                 fcycle=False):
+                 fcycle=False, scheme="binary"):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
         o = L.dec_mg_opts()
@@ -109,7 +112,8 @@ class Hierarchy:
         self.fuse = int(o.fuse)
         o.coarse_max_rows = int(coarse_max_rows)
         o.fcycle = 1 if fcycle else 0
-        flags = (L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0) | ORDERS[order]
+        flags = ((L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0) | ORDERS[order]
+                 | SCHEMES[scheme])
         scale = None
         if star1_scale is not None:
             scale = np.ascontiguousarray(star1_scale, dtype=np.float64)
@@ -149,9 +153,10 @@ class Hierarchy:
     def table(self, level, what):
         level = level % self.nlevels
         nv, ne, nt = self.nv[level], self.ne[level], self.nt[level]
+        nf = self.nv[level + 1] if level + 1 < self.nlevels else 0
         n = {"verts": nv * self.dim, "tris": nt * 3, "edges": ne * 2, "parents": ne * 2, "star0": nv,
-             "star1": ne, "free": nv, "colors": nv}[what]
-        dt = np.float64 if what in ("verts", "star0", "star1") else np.int32
+             "star1": ne, "free": nv, "colors": nv, "map_idx": nf * 3, "map_w": nf * 3}[what]
+        dt = np.float64 if what in ("verts", "star0", "star1", "map_w") else np.int32
         out = np.empty(n, dtype=dt)
         check(lib.dec_mg_copy_table(self._h, level, TABLES[what], _np_ptr(out)), "dec_mg_copy_table")
         if what == "verts":
@@ -160,6 +165,8 @@ class Hierarchy:
             return out.reshape(nt, 3)
         if what in ("edges", "parents"):
             return out.reshape(ne, 2)
+        if what in ("map_idx", "map_w"):
+            return out.reshape(nf, 3)
         return out
 
     # ---- device calls ----------------------------------------------------

@@ -96,7 +96,15 @@ int dec_mesh_refine(const dec_mesh *mesh, int nsub, uint32_t flags, dec_mesh **o
         m->m = mesh->m;
         for (int i = 0; i < nsub; ++i) {
             decimpl::HostMesh f;
-            Status s = decimpl::subdivide(m->m, (flags & DEC_SPHERE_PROJECT) != 0, (flags & DEC_ORDER_MORTON) != 0, f);
+            Status s;
+            if (flags & DEC_SUBDIV_CUBIC) {
+                if (flags & DEC_ORDER_MORTON) return fail(Status::fail(DEC_ERR_ARG, "cubic subdivision keeps the edge order"));
+                std::vector<int32_t> mi;
+                std::vector<double> mw;
+                s = decimpl::subdivide_cubic(m->m, (flags & DEC_SPHERE_PROJECT) != 0, f, mi, mw);
+            } else {
+                s = decimpl::subdivide(m->m, (flags & DEC_SPHERE_PROJECT) != 0, (flags & DEC_ORDER_MORTON) != 0, f);
+            }
             if (!s.good()) {
                 delete m;
                 return fail(s);

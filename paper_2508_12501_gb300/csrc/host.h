@@ -41,6 +41,14 @@ struct HostMesh {
 Status build_mesh(std::vector<double> verts, int dim, std::vector<int32_t> tris, HostMesh &out);
 
 // One 1->4 midpoint subdivision; `parents` of fine vertex nc + e is coarse edge e.
+// One 1->9 (cubic) subdivision: coarse edge e gets n_c + 2e at (2 x_lo + x_hi)/3
+// and n_c + 2e + 1 at (x_lo + 2 x_hi)/3, triangle t its centroid n_c + 2E + t.
+// map_idx / map_w (3 per fine vertex, row-major) receive the geometric map:
+// the coarse vertices and barycentric weights of each fine vertex (padding:
+// weight 0 on the first entry's vertex).
+Status subdivide_cubic(const HostMesh &coarse, bool sphere, HostMesh &fine, std::vector<int32_t> &map_idx,
+                       std::vector<double> &map_w);
+
 // One 1->4 subdivision; with morton the new vertices are numbered in Z-order
 // of their coordinates, else in coarse edge order.  parents (optional)
 // receives the coarse edge endpoints of each new vertex, in new-vertex order.
@@ -78,10 +86,13 @@ struct HostHierarchy {
     dec_mg_opts opts{};
     std::vector<HostLevel> levels;
     std::vector<std::vector<int32_t>> parents;  // parents[l]: level-l edges = parents of level l+1 midpoints
+    bool cubic = false;                         // 1->9 subdivision: general maps below instead of parents
+    std::vector<std::vector<int32_t>> map_idx;  // map_idx[l], map_w[l]: the map from level l to l+1,
+    std::vector<std::vector<double>> map_w;     // 3 (coarse vertex, weight) pairs per level-(l+1) vertex
     std::vector<double> G;                      // [n0 * n0] coarse solution operator, row-major
 };
 
-Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton,
+Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton, bool cubic,
                        const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H);
 
 // Rebuild ELL weights of one level from its (possibly new) star1.

@@ -202,7 +202,7 @@ static Status coarse_operator(const HostLevel &L, int bc, std::vector<double> &G
     return Status::ok();
 }
 
-Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton,
+Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton, bool cubic,
                        const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H) {
     if (nsub < 0 || nlevels < 1 || nlevels > nsub + 1 || nlevels > 16)
         return Status::fail(DEC_ERR_ARG, "nlevels must be in 1..min(nsub+1, 16)");
@@ -212,15 +212,29 @@ Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool
     H.opts = opts;
     H.levels.clear();
     H.parents.clear();
+    H.cubic = cubic;
+    H.map_idx.clear();
+    H.map_w.clear();
     const int first = nsub + 1 - nlevels;
     HostMesh cur = base;
     for (int i = 0; i <= nsub; ++i) {
         if (i > 0) {
             HostMesh fine;
-            std::vector<int32_t> par;
-            Status st = subdivide(cur, sphere, morton, fine, &par);
-            if (!st.good()) return st;
-            if (i > first) H.parents.push_back(std::move(par));
+            if (cubic) {
+                std::vector<int32_t> mi;
+                std::vector<double> mw;
+                Status st = subdivide_cubic(cur, sphere, fine, mi, mw);
+                if (!st.good()) return st;
+                if (i > first) {
+                    H.map_idx.push_back(std::move(mi));
+                    H.map_w.push_back(std::move(mw));
+                }
+            } else {
+                std::vector<int32_t> par;
+                Status st = subdivide(cur, sphere, morton, fine, &par);
+                if (!st.good()) return st;
+                if (i > first) H.parents.push_back(std::move(par));
+            }
             cur = std::move(fine);
         }
         if (i < first) continue;

@@ -185,6 +185,86 @@ Status subdivide(const HostMesh &c, bool sphere, bool morton, HostMesh &f, std::
     return build_mesh(std::move(fv), dim, std::move(ft), f);
 }
 
+Status subdivide_cubic(const HostMesh &c, bool sphere, HostMesh &f, std::vector<int32_t> &map_idx,
+                       std::vector<double> &map_w) {
+    if (sphere && c.dim != 3) return Status::fail(DEC_ERR_ARG, "sphere projection needs 3-D vertices");
+    const int dim = c.dim;
+    const int64_t nc = c.nv, E = c.ne, T = c.nt;
+    const int64_t nf = nc + 2 * E + T;
+    if (nf >= (int64_t)1 << 31 || 27 * T >= (int64_t)1 << 31) return Status::fail(DEC_ERR_ARG, "refined mesh too large");
+    std::vector<double> fv(nf * dim);
+    std::copy(c.verts.begin(), c.verts.end(), fv.begin());
+    auto put = [&](int64_t v, double *m) {
+        if (sphere) {
+            double s = m[0] * m[0] + m[1] * m[1];
+            s = s + m[2] * m[2];
+            const double nrm = std::sqrt(s);
+            for (int d = 0; d < 3; ++d) m[d] = m[d] / nrm;
+        }
+        for (int d = 0; d < dim; ++d) fv[v * dim + d] = m[d];
+    };
+    for (int64_t e = 0; e < E; ++e) {
+        const double *pl = &c.verts[(int64_t)c.edges[2 * e] * dim];
+        const double *ph = &c.verts[(int64_t)c.edges[2 * e + 1] * dim];
+        double m1[3] = {0, 0, 0}, m2[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            m1[d] = (2.0 * pl[d] + ph[d]) / 3.0;
+            m2[d] = (pl[d] + 2.0 * ph[d]) / 3.0;
+        }
+        put(nc + 2 * e, m1);
+        put(nc + 2 * e + 1, m2);
+    }
+    for (int64_t t = 0; t < T; ++t) {
+        const double *pa = &c.verts[(int64_t)c.tris[3 * t] * dim];
+        const double *pb = &c.verts[(int64_t)c.tris[3 * t + 1] * dim];
+        const double *pc = &c.verts[(int64_t)c.tris[3 * t + 2] * dim];
+        double m[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) m[d] = ((pa[d] + pb[d]) + pc[d]) / 3.0;
+        put(nc + 2 * E + t, m);
+    }
+    // the point of triangle t's edge k next to its corner `corner`
+    auto near = [&](int64_t t, int k, int32_t corner) {
+        const int64_t e = c.tri_edges[3 * t + k];
+        return (int32_t)(nc + 2 * e + (corner != c.edges[2 * e] ? 1 : 0));
+    };
+    std::vector<int32_t> ft(27 * T);
+    for (int64_t t = 0; t < T; ++t) {
+        const int32_t a = c.tris[3 * t], b = c.tris[3 * t + 1], cc = c.tris[3 * t + 2];
+        const int32_t ab1 = near(t, 0, a), ab2 = near(t, 0, b), bc1 = near(t, 1, b), bc2 = near(t, 1, cc);
+        const int32_t ca1 = near(t, 2, cc), ca2 = near(t, 2, a), m = (int32_t)(nc + 2 * E + t);
+        const int32_t sub[9][3] = {{a, ab1, ca2},  {ab1, ab2, m},  {ab2, b, bc1},  {ca2, m, ca1},  {m, bc1, bc2},
+                                   {ca1, bc2, cc}, {ab1, m, ca2},  {ab2, bc1, m},  {m, bc2, ca1}};
+        for (int q = 0; q < 9; ++q)
+            for (int k = 0; k < 3; ++k) ft[27 * t + 3 * q + k] = sub[q][k];
+    }
+    map_idx.assign(3 * nf, 0);
+    map_w.assign(3 * nf, 0.0);
+    const double third = 1.0 / 3.0, two_thirds = 2.0 / 3.0;
+    for (int64_t v = 0; v < nc; ++v) {
+        map_idx[3 * v] = map_idx[3 * v + 1] = map_idx[3 * v + 2] = (int32_t)v;
+        map_w[3 * v] = 1.0;
+    }
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t lo = c.edges[2 * e], hi = c.edges[2 * e + 1];
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int64_t v = nc + 2 * e + s2;
+            map_idx[3 * v] = lo;
+            map_idx[3 * v + 1] = hi;
+            map_idx[3 * v + 2] = lo;
+            map_w[3 * v] = s2 == 0 ? two_thirds : third;
+            map_w[3 * v + 1] = s2 == 0 ? third : two_thirds;
+        }
+    }
+    for (int64_t t = 0; t < T; ++t) {
+        const int64_t v = nc + 2 * E + t;
+        for (int k = 0; k < 3; ++k) {
+            map_idx[3 * v + k] = c.tris[3 * t + k];
+            map_w[3 * v + k] = third;
+        }
+    }
+    return build_mesh(std::move(fv), dim, std::move(ft), f);
+}
+
 void hodge_stars(const HostMesh &m, std::vector<double> &star0, std::vector<double> &star1) {
     star0.assign(m.nv, 0.0);
     star1.assign(m.ne, 0.0);

@@ -397,6 +397,37 @@ __global__ void __launch_bounds__(kThreads, 8) k_prolong(int nc, int nf, const i
     GRID_STRIDE(v, nf) xf[v] = add_rn(xf[v], prolong_add(v, nc, par, ec));
 }
 
+// Interpolation along a general geometric map (Sec. 2.2.1; cubic subdivision):
+// x_f[v] += sum_q w_q e_c[idx_q], three slots per fine vertex (unused: w = 0).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8) k_prolong_map(int nf, const int32_t *__restrict__ idx,
+                                                         const T *__restrict__ w, const T *__restrict__ ec,
+                                                         T *__restrict__ xf, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    GRID_STRIDE(v, nf) {
+        T a = T(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a = fma(ldg(w + (size_t)q * nf + v), ldg(ec + ldg(idx + (size_t)q * nf + v)), a);
+        xf[v] = add_rn(xf[v], a);
+    }
+}
+
+// Restriction along a general geometric map: b_c[c] = sum_q rw_q r_f[ridx_q], the
+// rows of the transpose of the row-normalized map (or of the *0-adjoint).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8) k_restrict_map(int nc, int Kr, const int32_t *__restrict__ ridx,
+                                                          const T *__restrict__ rw, const T *__restrict__ rf,
+                                                          T *__restrict__ bc, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    GRID_STRIDE(c, nc) {
+        T a = T(0);
+        for (int q = 0; q < Kr; ++q) a = fma(ldg(rw + (size_t)q * nc + c), ldg(rf + ldg(ridx + (size_t)q * nc + c)), a);
+        bc[c] = a;
+    }
+}
+
 // Coarsest level: x = G b with the dense precomputed solution operator, one warp per row.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 8) k_coarse(int n0, const T *__restrict__ G, const T *__restrict__ b,

@@ -24,6 +24,15 @@ struct DevLevel {
     float *w32 = nullptr;
     float *wlo = nullptr;  // finest level: w64 - w32 rounded to FP32 (ff weights w32 + wlo)
     float *dg32 = nullptr;     // row sums of w32 / w64 (the Jacobi diagonal), read by fused kernels
+    // general geometric map to the next coarser level (cubic subdivision): 3 (coarse vertex,
+    // weight) slots per row, slot-major; restriction rows of the coarser level, Kr slots
+    int32_t *gidx = nullptr;
+    float *gw32 = nullptr;
+    double *gw64 = nullptr;
+    int gKr = 0;
+    int32_t *ridx = nullptr;
+    float *rw32 = nullptr;
+    double *rw64 = nullptr;
     int32_t *crow = nullptr;   // rows sorted by greedy colour (multicolour Gauss-Seidel)
     std::vector<int> coff;     // colour c owns crow[coff[c] .. coff[c+1])
     int16_t *col16 = nullptr;  // levels of the shared-memory coarse cycle: col and parents as int16
@@ -51,6 +60,8 @@ template <> struct P<float> {
     static const float *w(const DevLevel &L) { return L.w32; }
     static const float *s0(const DevLevel &L) { return L.star0_32; }
     static const float *dg(const DevLevel &L) { return L.dg32; }
+    static const float *gw(const DevLevel &L) { return L.gw32; }
+    static const float *rw(const DevLevel &L) { return L.rw32; }
     static float *y(DevLevel &L) { return L.y32; }
     static float *c(DevLevel &L) { return L.c32; }
 };
@@ -62,6 +73,8 @@ template <> struct P<double> {
     static const double *w(const DevLevel &L) { return L.w64; }
     static const double *s0(const DevLevel &L) { return L.star0; }
     static const double *dg(const DevLevel &L) { return L.dg64; }
+    static const double *gw(const DevLevel &L) { return L.gw64; }
+    static const double *rw(const DevLevel &L) { return L.rw64; }
     static double *y(DevLevel &L) { return L.y64; }
     static double *c(DevLevel &L) { return L.c64; }
 };

@@ -275,14 +275,15 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     // the coarse level's first smoothing step rides on the restriction
     // (not into the shared-memory coarse cycle, which starts from b itself)
     const bool coarse_next = std::is_same<T, float>::value && (o.fuse & DEC_FUSE_COARSE) && l - 1 == mg->coarse_top;
+    const bool cubic = mg->H.cubic;  // general map transfers (k_restrict_map, k_prolong_map), unfused
     const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0 && !coarse_next &&
-                           o.smoother != DEC_SMOOTH_MCGS;
+                           o.smoother != DEC_SMOOTH_MCGS && !cubic;
     bool coarse_pre0 = false;
     const int g = grid_for(mg, L.n);
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        if ((o.fuse & DEC_FUSE_RESTRICT) && L.K <= 7) {
+        if ((o.fuse & DEC_FUSE_RESTRICT) && L.K <= 7 && !cubic) {
             ProfScope ps(mg, DEC_PK_RESRESTRICT, l, s);
             const int gr = grid_for(mg, (int64_t)C.n * 8);
             if (o.restriction == DEC_RESTRICT_STAR0)
@@ -300,7 +301,10 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
         {
             ProfScope ps(mg, DEC_PK_RESTRICT, l, s);
             const int gc = grid_for(mg, C.n);
-            if (restrict0) {
+            if (cubic) {
+                launch(mg, k_restrict_map<T>, gc, s, C.n, L.gKr, (const int32_t *)L.ridx, P<T>::rw(L),
+                       (const T *)P<T>::r(L), P<T>::b(C), skip);
+            } else if (restrict0) {
                 const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
                 const T e0 = (T)(cheb ? C.e_pre[0] : o.omega);
                 const bool dout = cheb && 1 < o.nu1;
@@ -353,7 +357,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
             ec = P<T>::y(C);
         }
     }
-    if ((o.fuse & DEC_FUSE_PROLONG) && o.nu2 > 0 && o.smoother != DEC_SMOOTH_MCGS) {
+    if ((o.fuse & DEC_FUSE_PROLONG) && o.nu2 > 0 && o.smoother != DEC_SMOOTH_MCGS && !cubic) {
         const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
         const T e0 = (T)(cheb ? L.e_post[0] : o.omega);
         const bool dout = cheb && 1 < o.nu2;
@@ -376,7 +380,11 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     }
     {
         ProfScope ps(mg, DEC_PK_PROLONG, l, s);
-        launch(mg, k_prolong<T>, g, s, C.n, L.n, L.par, ec, P<T>::x(L, cur), skip);
+        if (cubic)
+            launch(mg, k_prolong_map<T>, g, s, L.n, (const int32_t *)L.gidx, P<T>::gw(L), (const T *)ec,
+                   P<T>::x(L, cur), skip);
+        else
+            launch(mg, k_prolong<T>, g, s, C.n, L.n, L.par, ec, P<T>::x(L, cur), skip);
     }
     if (o.nu2 > 0) smooth<T>(mg, l, b, o.nu2, false, true, cur, s, skip, 0, da);
     return P<T>::x(L, cur);
@@ -790,6 +798,63 @@ void update_diagonals(dec_mg *mg, DevLevel &D, cudaStream_t s) {
     });
 }
 
+// Device tables of the general map from level l-1 to level l: the 3 slots per
+// fine vertex (slot-major) and the restriction rows of level l-1 -- the
+// transpose of the row-normalized map, or its *0-adjoint -- in FP64 and FP32.
+int upload_map(dec_mg *mg, int l, DevLevel &D) {
+    const decimpl::HostHierarchy &H = mg->H;
+    const std::vector<int32_t> &mi = H.map_idx[l - 1];
+    const std::vector<double> &mw = H.map_w[l - 1];
+    const int nf = D.n, nc = (int)H.levels[l - 1].mesh.nv;
+    std::vector<int32_t> gi(3 * (size_t)nf);
+    std::vector<double> gw(3 * (size_t)nf);
+    for (int v = 0; v < nf; ++v)
+        for (int q = 0; q < 3; ++q) {
+            gi[(size_t)q * nf + v] = mi[3 * (size_t)v + q];
+            gw[(size_t)q * nf + v] = mw[3 * (size_t)v + q];
+        }
+    // restriction rows: every (fine v, weight) whose map slot points at coarse c, in increasing v
+    std::vector<int> cnt(nc + 1, 0);
+    for (int v = 0; v < nf; ++v)
+        for (int q = 0; q < 3; ++q)
+            if (mw[3 * (size_t)v + q] != 0.0) cnt[mi[3 * (size_t)v + q] + 1] += 1;
+    int Kr = 1;
+    for (int c = 0; c < nc; ++c) Kr = std::max(Kr, cnt[c + 1]);
+    for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    std::vector<int32_t> ent_v(cnt[nc]);
+    std::vector<double> ent_w(cnt[nc]);
+    for (int v = 0; v < nf; ++v)
+        for (int q = 0; q < 3; ++q) {
+            const double w = mw[3 * (size_t)v + q];
+            if (w == 0.0) continue;
+            const int c = mi[3 * (size_t)v + q];
+            ent_v[fill[c]] = v;
+            ent_w[fill[c]++] = w;
+        }
+    const bool star0 = H.opts.restriction == DEC_RESTRICT_STAR0;
+    const std::vector<double> &s0f = H.levels[l].star0, &s0c = H.levels[l - 1].star0;
+    std::vector<int32_t> ri((size_t)Kr * nc, 0);
+    std::vector<double> rw((size_t)Kr * nc, 0.0);
+    for (int c = 0; c < nc; ++c) {
+        double rs = 0.0;
+        for (int k = cnt[c]; k < cnt[c + 1]; ++k) rs += ent_w[k];
+        for (int k = cnt[c], q = 0; k < cnt[c + 1]; ++k, ++q) {
+            ri[(size_t)q * nc + c] = ent_v[k];
+            rw[(size_t)q * nc + c] = star0 ? s0f[ent_v[k]] * ent_w[k] / s0c[c] : ent_w[k] / rs;
+        }
+        for (int q = cnt[c + 1] - cnt[c]; q < Kr; ++q) ri[(size_t)q * nc + c] = cnt[c + 1] > cnt[c] ? ent_v[cnt[c]] : 0;
+    }
+    std::vector<float> gw32(gw.begin(), gw.end()), rw32(rw.begin(), rw.end());
+    int rc;
+    if ((rc = upload(mg, &D.gidx, gi.data(), gi.size())) || (rc = upload(mg, &D.gw64, gw.data(), gw.size())) ||
+        (rc = upload(mg, &D.gw32, gw32.data(), gw32.size())) || (rc = upload(mg, &D.ridx, ri.data(), ri.size())) ||
+        (rc = upload(mg, &D.rw64, rw.data(), rw.size())) || (rc = upload(mg, &D.rw32, rw32.data(), rw32.size())))
+        return rc;
+    D.gKr = Kr;
+    return DEC_OK;
+}
+
 // Choose the levels 0..top of the shared-memory coarse cycle (the most that
 // fit in one block's shared memory, at least levels 0 and 1), lay out their
 // arrays and upload int16 copies of their column and parent tables.
@@ -799,7 +864,7 @@ int setup_coarse_cycle(dec_mg *mg) {
     const dec_mg_opts &o = mg->H.opts;
     const int nl = (int)mg->lv.size();
     if (nl < 2 || o.gamma != 1 || o.fcycle || o.nu1 > kCoarseMaxNu || o.nu2 > kCoarseMaxNu ||
-        o.smoother == DEC_SMOOTH_MCGS)
+        o.smoother == DEC_SMOOTH_MCGS || mg->H.cubic)
         return DEC_OK;
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, mg->device);
@@ -919,8 +984,11 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         return code;
     };
     try {
+        if ((flags & DEC_SUBDIV_CUBIC) && (flags & DEC_ORDER_MORTON))
+            return bail(fail(Status::fail(DEC_ERR_ARG, "cubic subdivision keeps the edge order")));
         Status st = decimpl::build_hierarchy(*dec_mesh_host(base), nsub, nlevels, bc, (flags & DEC_SPHERE_PROJECT) != 0,
-                                             (flags & DEC_ORDER_MORTON) != 0, star1_scale, o, mg->H);
+                                             (flags & DEC_ORDER_MORTON) != 0, (flags & DEC_SUBDIV_CUBIC) != 0,
+                                             star1_scale, o, mg->H);
         if (!st.good()) return bail(fail(st));
     } catch (const std::bad_alloc &) {
         return bail(fail(Status::fail(DEC_ERR_OOM, "host allocation")));
@@ -956,9 +1024,12 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
             if ((rc = upload(mg, &D.star0_32, s32.data(), D.n))) return bail(rc);
         }
         if ((rc = upload(mg, &D.freev, HL.free_.data(), D.n))) return bail(rc);
-        if (l > 0) {
+        if (l > 0 && !mg->H.cubic) {
             const std::vector<int32_t> &par = mg->H.parents[l - 1];
             if ((rc = upload(mg, &D.par, reinterpret_cast<const int2 *>(par.data()), par.size() / 2))) return bail(rc);
+        }
+        if (l > 0 && mg->H.cubic) {
+            if ((rc = upload_map(mg, l, D))) return bail(rc);
         }
         for (int i = 0; i < 2; ++i) {
             if ((rc = dalloc(mg, &D.x32[i], D.n)) || (rc = dalloc(mg, &D.d32[i], D.n)) ||
@@ -1074,10 +1145,42 @@ int dec_mg_copy_table(const dec_mg *mg, int level, int what, void *out) {
         case DEC_TABLE_VERTS: std::memcpy(out, L.mesh.verts.data(), L.mesh.verts.size() * 8); break;
         case DEC_TABLE_TRIS: std::memcpy(out, L.mesh.tris.data(), L.mesh.tris.size() * 4); break;
         case DEC_TABLE_EDGES: std::memcpy(out, L.mesh.edges.data(), L.mesh.edges.size() * 4); break;
+        case DEC_TABLE_MAP_IDX:
+        case DEC_TABLE_MAP_W: {
+            // the map from level to level + 1: three (coarse vertex, weight) slots per fine vertex
+            if (level + 1 >= (int)mg->H.levels.size())
+                return fail(Status::fail(DEC_ERR_ARG, "the finest level has no map to a finer level"));
+            const int nf = (int)mg->H.levels[level + 1].mesh.nv, nc = (int)L.mesh.nv;
+            std::vector<int32_t> mi;
+            std::vector<double> mw;
+            if (mg->H.cubic) {
+                mi = mg->H.map_idx[level];
+                mw = mg->H.map_w[level];
+            } else {
+                const std::vector<int32_t> &par = mg->H.parents[level];
+                mi.assign(3 * (size_t)nf, 0);
+                mw.assign(3 * (size_t)nf, 0.0);
+                for (int v = 0; v < nf; ++v) {
+                    const bool kept = v < nc;
+                    const int32_t a = kept ? v : par[2 * (size_t)(v - nc)], b = kept ? v : par[2 * (size_t)(v - nc) + 1];
+                    mi[3 * (size_t)v] = a;
+                    mi[3 * (size_t)v + 1] = b;
+                    mi[3 * (size_t)v + 2] = a;
+                    mw[3 * (size_t)v] = kept ? 1.0 : 0.5;
+                    mw[3 * (size_t)v + 1] = kept ? 0.0 : 0.5;
+                }
+            }
+            if (what == DEC_TABLE_MAP_IDX)
+                std::memcpy(out, mi.data(), mi.size() * 4);
+            else
+                std::memcpy(out, mw.data(), mw.size() * 8);
+            break;
+        }
         case DEC_TABLE_PARENTS: {
             // the coarse edge of each new vertex of level + 1, in that level's vertex order
             if (level + 1 >= (int)mg->H.levels.size())
                 return fail(Status::fail(DEC_ERR_ARG, "the finest level has no parents table"));
+            if (mg->H.cubic) return fail(Status::fail(DEC_ERR_ARG, "cubic hierarchies store DEC_TABLE_MAP_*"));
             const std::vector<int32_t> &par = mg->H.parents[level];
             std::memcpy(out, par.data(), par.size() * 4);
             break;
@@ -1407,6 +1510,7 @@ extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_s
         return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle is a V-cycle (gamma = 1)"));
     if (mg->H.opts.smoother == DEC_SMOOTH_MCGS)
         return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle smooths with Jacobi or Chebyshev"));
+    if (mg->H.cubic) return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle transfers along binary subdivision"));
     const size_t need = noalloc_floats(mg) * sizeof(float);
     if (need > DEC_NOALLOC_SCRATCH_BYTES)
         return fail(Status::fail(DEC_ERR_ARG, "hierarchy needs " + std::to_string(need) +

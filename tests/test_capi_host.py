@@ -143,3 +143,50 @@ def test_coarse_limit_and_nan_free_setup():
     with pytest.raises(DecError) as ei:
         Hierarchy(Mesh(v, t), 5, 1, bc="gauge", sphere=True, host_only=True)  # 10,242-vertex coarsest level
     assert ei.value.code == lib_mod.DEC_ERR_MESH
+
+
+@pytest.mark.parametrize("name,vt,nsub,sphere", [c for c in _cases() if c[0] != "grid"], ids=lambda c: str(c)[:12])
+def test_cubic_refined_tables_bit_exact(name, vt, nsub, sphere):
+    v, t = vt
+    meshes, _ = omesh.refine(v, t, min(nsub, 2), sphere=sphere, scheme="cubic")
+    m = Mesh(v, t)
+    for k, om in enumerate(meshes):
+        lm = m.refine(k, sphere=sphere, scheme="cubic") if k else m
+        assert (lm.nv, lm.ne, lm.nt) == (om.nv, om.ne, om.nt)
+        assert np.array_equal(lm.table("tris"), om.tris)
+        assert np.array_equal(lm.table("edges"), om.edges)
+        assert np.array_equal(lm.table("verts"), om.verts)
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "gauge"])
+def test_cubic_hierarchy_map_tables(bc):
+    # the library's map from level l to l+1, as three (coarse vertex, weight) slots per fine vertex,
+    # is the oracle's M(f) exactly
+    if bc == "dirichlet":
+        v, t = W.unit_square(); nsub, nl, sphere = 3, 3, False
+    else:
+        v, t = W.icosahedron(); nsub, nl, sphere = 2, 3, True
+    h = Hierarchy(Mesh(v, t), nsub, nl, bc=bc, sphere=sphere, host_only=True, scheme="cubic")
+    meshes, maps = omesh.refine(v, t, nsub, sphere=sphere, scheme="cubic")
+    first = nsub + 1 - nl
+    for l in range(nl - 1):
+        idx, w = h.table(l, "map_idx"), h.table(l, "map_w")
+        Mo = maps[first + l].toarray()
+        Ml = np.zeros_like(Mo)
+        for q in range(3):
+            np.add.at(Ml, (idx[:, q], np.arange(len(idx))), w[:, q])
+        assert np.array_equal(Ml, Mo)
+    with pytest.raises(Exception):
+        h.table(0, "parents")
+
+
+def test_binary_map_tables_are_the_parents():
+    v, t = W.unit_square()
+    h = Hierarchy(Mesh(v, t), 3, 3, bc="dirichlet", host_only=True)
+    oh = omg.build_hierarchy(v, t, 3, 3, "dirichlet")
+    idx, w = h.table(0, "map_idx"), h.table(0, "map_w")
+    Mo = omg.barycentric_matrix(oh.levels[0].mesh.nv, h.table(0, "parents")).toarray()
+    Ml = np.zeros_like(Mo)
+    for q in range(3):
+        np.add.at(Ml, (idx[:, q], np.arange(len(idx))), w[:, q])
+    assert np.array_equal(Ml, Mo)

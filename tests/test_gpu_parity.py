@@ -311,3 +311,69 @@ def test_f_cycle_matches_oracle(name, prec, smoother):
     assert abs(cf - omg.convergence_factor(ref2.history)) <= 0.02
     xs, st = h.solve(_dev(b2), solver="mgpcg", mode="mixed_ff", tol=1e-10)
     assert st.rel_res <= 1e-10 and _s0_rel(lev, xs.cpu().numpy(), omg.direct_solve(oh, b2)) < 1e-7
+
+
+CUBIC = {
+    # name: (base, nsub, nlevels, bc, sphere)
+    "square_cubic": (W.unit_square, 3, 3, "dirichlet", False),
+    "ico_cubic": (W.icosahedron, 3, 3, "gauge", True),
+}
+
+
+@pytest.mark.parametrize("name", list(CUBIC))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("restriction", ["rownorm", "star0"])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+def test_cubic_cycle_matches_oracle(name, prec, restriction, smoother):
+    # cubic (1->9) subdivision: interpolation by the geometric map, restriction by the transpose of its
+    # row normalization (or the *0-adjoint), both as general gather kernels
+    P = _lib()
+    base, nsub, nl, bc, sph = CUBIC[name]
+    v, t = base()
+    h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother=smoother, restriction=restriction,
+                    scheme="cubic")
+    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, scheme="cubic",
+                             opts=omg.MGOptions(smoother=smoother, restriction=restriction))
+    lev = oh.finest
+    assert h.nv == [l.mesh.nv for l in oh.levels]
+    b = omg.prepare_rhs(oh, W.uniform_field(lev.mesh.nv, 71))
+    ref = omg.vcycle(oh, b, np.zeros_like(b))
+    dt = torch.float64 if prec == "f64" else torch.float32
+    x = torch.zeros(lev.mesh.nv, dtype=dt, device="cuda")
+    h.vcycle(_dev(b, dt), x)
+    assert _s0_rel(lev, x.double().cpu().numpy(), ref) < (1e-12 if prec == "f64" else 2e-5)
+
+
+@pytest.mark.parametrize("name", list(CUBIC))
+def test_cubic_solves_match_oracle(name):
+    P = _lib()
+    base, nsub, nl, bc, sph = CUBIC[name]
+    v, t = base()
+    h = P.Hierarchy(P.Mesh(v, t), nsub, nl, bc=bc, sphere=sph, smoother="chebyshev", scheme="cubic")
+    oh = omg.build_hierarchy(v, t, nsub, nl, bc, sphere=sph, scheme="cubic", opts=omg.MGOptions(smoother="chebyshev"))
+    lev = oh.finest
+    b = W.uniform_field(lev.mesh.nv, 72)
+    xs = omg.direct_solve(oh, b)
+    for solver, mode in (("mg", "f64"), ("mgpcg", "mixed_ff"), ("mgpcg", "mixed")):
+        x, st = h.solve(_dev(b), solver=solver, mode=mode, tol=1e-10, maxit=200)
+        assert st.rel_res <= 1e-10
+        assert _s0_rel(lev, x.cpu().numpy(), xs) < 1e-7
+    _, st = h.solve(_dev(b), solver="mg", mode="f64", tol=1e-10, maxit=200)
+    ref = omg.mg_solve(oh, b, 1e-10, 200)
+    assert abs(st.iters - ref.iters) <= 1
+    cf = (st.rel_res / st.rel_res0) ** (1.0 / st.iters)
+    assert abs(cf - omg.convergence_factor(ref.history)) <= 0.02
+
+
+def test_cubic_square_closed_form():
+    # unit square cubed three times (28 x 28 grid): MG reaches the discrete solution of -Delta sin sin
+    P = _lib()
+    v, t = W.unit_square()
+    h = P.Hierarchy(P.Mesh(v, t), 3, 3, bc="dirichlet", scheme="cubic")
+    xy = h.table(-1, "verts")
+    x, st = h.solve(_dev(W.rhs_sin_square(xy)), solver="mg", mode="f64", tol=1e-12, maxit=200)
+    hh = 1.0 / 27
+    u_h = 2 * math.pi ** 2 / (8.0 / hh ** 2 * math.sin(math.pi * hh / 2) ** 2) * W.u_sin_square(xy)
+    s0 = h.table(-1, "star0")
+    d = x.cpu().numpy() - u_h
+    assert np.sqrt(np.sum(s0 * d * d) / np.sum(s0 * u_h * u_h)) < 1e-10
