@@ -78,13 +78,18 @@ __device__ __forceinline__ void sm_load(unsigned char *sm, int off, const void *
     for (int i = 4 * n16 + threadIdx.x; i < bytes / 4; i += kCoarseThreads) d4[i] = __ldg(s4 + i);
 }
 
-// s = sum_k w_k (x_i - x_col(k)) and d = sum_k w_k for one row, in slot order (row_apply).
+// s = sum_k w_k (x_i - x_col(k)) and d = sum_k w_k for one row, in slot order
+// (row_apply); KT > 0 fixes the slot count at compile time, 0 reads K.
+template <int KT>
 __device__ __forceinline__ void sm_row(int i, int n, int K, const int16_t *col, const float *w, const float *x,
                                        float &s, float &d) {
+    const int Kk = KT > 0 ? KT : K;
     const float xi = x[i];
     s = 0.f;
     d = 0.f;
-    for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int k = 0; k < (KT > 0 ? KT : kCoarseMaxK); ++k) {
+        if (KT == 0 && k >= Kk) break;
         const int o = k * n + i;
         const float wk = w[o];
         s = fmaf(wk, xi - x[col[o]], s);
@@ -93,6 +98,7 @@ __device__ __forceinline__ void sm_row(int i, int n, int K, const int16_t *col, 
 }
 
 // One smoothing call of nu steps on level L.
+template <int KT>
 static __device__ void sm_smooth(unsigned char *sm, const CoarseLevel &L, int nu, bool post, bool cheb) {
     const int n = L.n, K = L.K;
     const int16_t *col = sm_at<int16_t>(sm, L.o_col);
@@ -123,7 +129,7 @@ static __device__ void sm_smooth(unsigned char *sm, const CoarseLevel &L, int nu
             const int i = threadIdx.x + r * kCoarseThreads;
             if (i < n) {
                 float s, d;
-                sm_row(i, n, K, col, w, x, s, d);
+                sm_row<KT>(i, n, K, col, w, x, s, d);
                 const float q = d != 0.f ? (b[i] - s) / d : 0.f;
                 nd[r] = smooth_delta<float>(din, c, din ? dir[i] : 0.f, e, q);
                 nx[r] = add_rn(x[i], nd[r]);
@@ -142,7 +148,8 @@ static __device__ void sm_smooth(unsigned char *sm, const CoarseLevel &L, int nu
     }
 }
 
-static __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid_constant__ CoarseArgs A,
+template <int KT>
+__global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid_constant__ CoarseArgs A,
                                                                     const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
@@ -167,7 +174,7 @@ static __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const
     for (int l = top; l >= 1; --l) {
         const CoarseLevel &L = A.lv[l], &C = A.lv[l - 1];
         if (A.nu1 > 0) {
-            sm_smooth(sm, L, A.nu1, false, cheb);
+            sm_smooth<KT>(sm, L, A.nu1, false, cheb);
         } else {
             float *x = sm_at<float>(sm, L.o_x);
             for (int i = threadIdx.x; i < L.n; i += kCoarseThreads) x[i] = 0.f;
@@ -178,7 +185,7 @@ static __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const
         float *r = sm_at<float>(sm, L.o_r);
         for (int i = threadIdx.x; i < L.n; i += kCoarseThreads) {
             float s, d;
-            sm_row(i, L.n, L.K, col, w, x, s, d);
+            sm_row<KT>(i, L.n, L.K, col, w, x, s, d);
             r[i] = d != 0.f ? b[i] - s : 0.f;
         }
         __syncthreads();
@@ -188,7 +195,10 @@ static __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const
         for (int c = threadIdx.x; c < C.n; c += kCoarseThreads) {
             float acc = 0.f;
             int deg = 0;
-            for (int k = 0; k < L.K; ++k) {
+            const int Kk = KT > 0 ? KT : L.K;
+#pragma unroll
+            for (int k = 0; k < (KT > 0 ? KT : kCoarseMaxK); ++k) {
+                if (KT == 0 && k >= Kk) break;
                 const int j = col[k * L.n + c];
                 if (j != c) {
                     acc = star0 ? fmaf(s0f[j], r[j], acc) : acc + r[j];
@@ -246,7 +256,7 @@ static __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const
             x[v] = add_rn(x[v], add);
         }
         __syncthreads();
-        if (A.nu2 > 0) sm_smooth(sm, L, A.nu2, true, cheb);
+        if (A.nu2 > 0) sm_smooth<KT>(sm, L, A.nu2, true, cheb);
     }
 
     const float *xt = sm_at<float>(sm, A.lv[top].o_x);

@@ -100,6 +100,7 @@ struct dec_mg {
     // shared-memory coarse cycle (DEC_FUSE_COARSE): levels 0..coarse_top, -1 if none fits
     int coarse_top = -1;
     int coarse_smem = 0;
+    bool coarse_k6 = false;  // every fused level above the coarsest has 6 stencil slots
     decdev::CoarseArgs coarse_args{};
     // finest-level extras
     int32_t *slot_edge = nullptr;

@@ -262,7 +262,10 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
             A.b = b;
             A.x = L.x32[0];
             ProfScope ps(mg, DEC_PK_COARSECYCLE, l, s);
-            launch_block(mg, decdev::k_coarse_cycle, 1, decdev::kCoarseThreads, mg->coarse_smem, s, A, skip);
+            if (mg->coarse_k6)
+                launch_block(mg, decdev::k_coarse_cycle<6>, 1, decdev::kCoarseThreads, mg->coarse_smem, s, A, skip);
+            else
+                launch_block(mg, decdev::k_coarse_cycle<0>, 1, decdev::kCoarseThreads, mg->coarse_smem, s, A, skip);
             return L.x32[0];
         }
     }
@@ -941,10 +944,14 @@ int setup_coarse_cycle(dec_mg *mg) {
     // The dynamic shared-memory limit is a property of the kernel, shared by
     // every hierarchy on the device: raise it once to the device maximum
     // (each layout is at most that), never to one hierarchy's size.
-    if (cudaFuncSetAttribute(k_coarse_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_coarse_cycle<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
+        cudaFuncSetAttribute(k_coarse_cycle<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess) {
         (void)cudaGetLastError();
         return DEC_OK;  // leave the shared-memory cycle off for this hierarchy
     }
+    bool k6 = true;
+    for (int l = 1; l <= top; ++l) k6 = k6 && mg->lv[l].K == 6;
+    mg->coarse_k6 = k6;
     mg->coarse_args = A;
     mg->coarse_smem = (int)top_bytes;
     mg->coarse_top = top;
