@@ -125,7 +125,7 @@ def peaks():
 
 def kernels_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "solver.cu"):
+    for f in ("kernels.cuh", "coarse_cycle.cuh"):  # the device code the counters were taken on
         with open(os.path.join(ROOT, "paper_2508_12501_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -569,9 +569,9 @@ def main():
         if top and top["bytes"]:
             tr = ncu_traffic(top["kind"])
             avg_ms, by, how = top["avg_ms"], top["bytes"], "event pair around each launch inside the solve graph"
-            if top["kind"] == "smooth":
+            if top["kind"] in ("smooth", "smoothdots", "spmv64", "update") and args.mode == "mixed_ff":
                 # the same kernel and launch shape, back to back on the solve stream: no event between launches
-                avg_ms, by = h.time_smooth(level=top["level"], reps=200)
+                avg_ms, by = h.time_kernel(top["kind"], level=top["level"], reps=200)
                 how = "200 back-to-back launches between two CUDA events on the solve stream"
             gbs = by / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": f"{top['kind']} (level {top['level']}, {top['rows']} rows)",

@@ -471,6 +471,14 @@ int dec_mg_profile_read(const dec_mg *mg, dec_prof_entry *out, int max, int *cou
  * direction).  Overwrites that level's FP32 cycle work vectors with zeros
  * first (a timing call, not a computation). */
 int dec_mg_time_smooth(dec_mg *mg, int level, int reps, double *avg_ms, double *bytes, dec_stream_t stream);
+/* dec_mg_time_kernel: the same for other finest-level kernels of the mixed_ff
+ * MG-PCG loop -- kind DEC_PK_SMOOTH (as dec_mg_time_smooth, any level),
+ * DEC_PK_SMOOTHDOTS (last smoothing step fused with the dot products),
+ * DEC_PK_SPMV64 (float-float q = L p) or DEC_PK_UPDATE (float-float x, r
+ * update) -- on zeroed FP32 work vectors, with their algorithmic bytes per
+ * launch; overwrites the finest level's work vectors and the solver's
+ * scalar block (a timing call, not a computation). */
+int dec_mg_time_kernel(dec_mg *mg, int kind, int level, int reps, double *avg_ms, double *bytes, dec_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -124,6 +124,7 @@ _SIGS = {
                                  C.POINTER(dec_stats), _p]),
     "dec_mg_profile_read": (_i, [_p, C.POINTER(dec_prof_entry), _i, C.POINTER(_i)]),
     "dec_mg_time_smooth": (_i, [_p, _i, _i, C.POINTER(C.c_double), C.POINTER(C.c_double), _p]),
+    "dec_mg_time_kernel": (_i, [_p, _i, _i, _i, C.POINTER(C.c_double), C.POINTER(C.c_double), _p]),
 }
 
 for _name, (_res, _args) in _SIGS.items():

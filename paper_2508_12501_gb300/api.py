@@ -292,6 +292,14 @@ class Hierarchy:
               "dec_mg_time_smooth")
         return ms.value, by.value
 
+    def time_kernel(self, kind, level=-1, reps=50):
+        """(mean ms, algorithmic bytes) of back-to-back launches of one kernel kind ("smooth", "smoothdots",
+        "spmv64", "update"; all but "smooth" on the finest level)."""
+        ms, by = C.c_double(), C.c_double()
+        check(lib.dec_mg_time_kernel(self._h, L.PROF_KINDS.index(kind), int(level), int(reps), C.byref(ms),
+                                     C.byref(by), self._stream()), "dec_mg_time_kernel")
+        return ms.value, by.value
+
     # ---- porous convection (Sec. 3.2) ------------------------------------
     def _porous_params(self, dt, g=(0.0, -9.81, 0.0), alpha_rho0=0.0, phi=0.1, k_eta=1.0, kappa=2.0, tol=1e-8,
                        mode="mixed", maxit=100):

@@ -45,56 +45,86 @@ struct CoarseArgs {
     const float *G;  // coarsest dense solution operator [n0][n0]
     const float *b;  // right-hand side of level `top` (global)
     float *x;        // result on level `top` (global)
+    Scal *S;         // solver scalars: status 3 if the load wait gave up
+    int top_mutable; // level `top` is the finest level (its w and dg change with dec_mg_set_star1)
     CoarseLevel lv[kCoarseMaxLevels];
 };
+
+// Shared-memory bytes the kernel keeps before the level arrays (its mbarrier).
+constexpr int kCoarseHeader = 16;
+// try_wait rounds before the load wait gives up (each round suspends the
+// thread for at most a hardware time slice, so this bounds the wait to well
+// under a second).
+constexpr int kCoarseWaitRounds = 1 << 20;
+
+__device__ __forceinline__ unsigned sm_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase 0 of the load barrier.
+__device__ __forceinline__ bool mbar_wait0(unsigned bar) {
+    for (int it = 0; it < kCoarseWaitRounds; ++it)
+        if (mbar_try_wait(bar, 0)) return true;
+    return false;
+}
+
+// Thread 0: queue one global -> shared bulk copy of `bytes` (a multiple of 16;
+// both addresses 16-byte aligned) completing on the barrier.
+__device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :
+                 : "r"(dst), "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Bytes of an array that go by bulk copy: a 16-byte aligned source up to its
+// last 16-byte boundary, nothing from any other source.
+__device__ __forceinline__ int bulk_bytes(const void *src, int bytes) {
+    return ((uintptr_t)src & 15) == 0 ? bytes & ~15 : 0;
+}
+
+// One array of the load phase (`bytes` a multiple of 4): thread 0 queues
+// the bulk part (issue == true), the threads copy the rest by plain 4-byte
+// loads (issue == false).
+__device__ __forceinline__ void stage(unsigned char *sm, int off, const void *src, int bytes, unsigned bar,
+                                      bool issue) {
+    const int bulk = bulk_bytes(src, bytes);
+    if (issue && threadIdx.x == 0 && bulk > 0) bulk_load(sm_addr(sm + off), src, (unsigned)bulk, bar);
+    if (issue) return;
+    const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d4 = reinterpret_cast<uint32_t *>(sm + off);
+    for (int i = bulk / 4 + threadIdx.x; i < bytes / 4; i += kCoarseThreads) d4[i] = __ldg(s4 + i);
+}
 
 template <typename T>
 __device__ __forceinline__ T *sm_at(unsigned char *sm, int off) {
     return reinterpret_cast<T *>(sm + off);
 }
 
-// Copy `bytes` (a multiple of 4) from global to shared memory: 16-byte loads,
-// two per thread in flight, then the 4-byte tail.  src and the shared
-// offset are 16-byte aligned (cudaMalloc'ed arrays, 16-byte aligned layout).
-__device__ __forceinline__ void sm_load(unsigned char *sm, int off, const void *src, int bytes) {
-    const int n16 = bytes / 16;
-    const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
-    uint4 *d16 = reinterpret_cast<uint4 *>(sm + off);
-    for (int i0 = threadIdx.x; i0 < n16; i0 += 2 * kCoarseThreads) {
-        uint4 v[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int i = i0 + u * kCoarseThreads;
-            if (i < n16) v[u] = __ldg(s16 + i);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int i = i0 + u * kCoarseThreads;
-            if (i < n16) d16[i] = v[u];
-        }
-    }
-    const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src);
-    uint32_t *d4 = reinterpret_cast<uint32_t *>(sm + off);
-    for (int i = 4 * n16 + threadIdx.x; i < bytes / 4; i += kCoarseThreads) d4[i] = __ldg(s4 + i);
-}
-
-// s = sum_k w_k (x_i - x_col(k)) and d = sum_k w_k for one row, in slot order
-// (row_apply); KT > 0 fixes the slot count at compile time, 0 reads K.
+// s = sum_k w_k (x_i - x_col(k)) for one row, in slot order (row_apply);
+// KT > 0 fixes the slot count at compile time, 0 reads K.  The row's
+// d = sum_k w_k is the stored diagonal: k_diag adds the same weights in the
+// same order, so it is the same float.
 template <int KT>
-__device__ __forceinline__ void sm_row(int i, int n, int K, const int16_t *col, const float *w, const float *x,
-                                       float &s, float &d) {
+__device__ __forceinline__ float sm_row(int i, int n, int K, const int16_t *col, const float *w, const float *x) {
     const int Kk = KT > 0 ? KT : K;
     const float xi = x[i];
-    s = 0.f;
-    d = 0.f;
+    float s = 0.f;
 #pragma unroll
     for (int k = 0; k < (KT > 0 ? KT : kCoarseMaxK); ++k) {
         if (KT == 0 && k >= Kk) break;
         const int o = k * n + i;
-        const float wk = w[o];
-        s = fmaf(wk, xi - x[col[o]], s);
-        d += wk;
+        s = fmaf(w[o], xi - x[col[o]], s);
     }
+    return s;
 }
 
 // One smoothing call of nu steps on level L.
@@ -128,8 +158,7 @@ static __device__ void sm_smooth(unsigned char *sm, const CoarseLevel &L, int nu
         for (int r = 0; r < kCoarseRows; ++r) {
             const int i = threadIdx.x + r * kCoarseThreads;
             if (i < n) {
-                float s, d;
-                sm_row<KT>(i, n, K, col, w, x, s, d);
+                const float s = sm_row<KT>(i, n, K, col, w, x), d = dg[i];
                 const float q = d != 0.f ? (b[i] - s) / d : 0.f;
                 nd[r] = smooth_delta<float>(din, c, din ? dir[i] : 0.f, e, q);
                 nx[r] = add_rn(x[i], nd[r]);
@@ -151,24 +180,87 @@ static __device__ void sm_smooth(unsigned char *sm, const CoarseLevel &L, int nu
 template <int KT>
 __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid_constant__ CoarseArgs A,
                                                                     const int *skip) {
-    pdl_prologue();
-    if (skipped(skip)) return;
+    // Programmatic dependent launch, split: the operators of the coarse
+    // levels and G never change after set-up, so their loads are queued
+    // before waiting for the previous kernel and overlap its tail.  Only the
+    // right-hand side (and the finest level's w and dg, which
+    // dec_mg_set_star1 rewrites in stream order) wait.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned char sm[];
     const int top = A.top;
     const bool cheb = A.cheb != 0, star0 = A.star0 != 0;
-    // operators of every level, then the right-hand side of the top level
-    for (int l = 0; l <= top; ++l) {
-        const CoarseLevel &L = A.lv[l];
-        if (l > 0) {
-            sm_load(sm, L.o_col, L.col, ((L.K * L.n * 2) + 3) & ~3);
-            sm_load(sm, L.o_w, L.w, L.K * L.n * 4);
-            sm_load(sm, L.o_dg, L.dg, L.n * 4);
-            sm_load(sm, L.o_par, L.par, (L.n - A.lv[l - 1].n) * 4);
+    // Thread 0 queues one bulk copy per array (all in flight together) on an
+    // mbarrier in the shared-memory header, armed with their byte count; the
+    // threads copy the unaligned remainders meanwhile, then wait on the
+    // barrier.  f(offset, source, bytes, before_wait).
+    const unsigned bar = sm_addr(sm);
+    auto each_array = [&](auto &&f) {
+        for (int l = 0; l <= top; ++l) {
+            const CoarseLevel &L = A.lv[l];
+            const bool fixed = !(A.top_mutable && l == top);
+            if (l > 0) {
+                f(L.o_col, L.col, ((L.K * L.n * 2) + 3) & ~3, true);
+                f(L.o_w, L.w, L.K * L.n * 4, fixed);
+                f(L.o_dg, L.dg, L.n * 4, fixed);
+                f(L.o_par, L.par, (L.n - A.lv[l - 1].n) * 4, true);
+            }
+            if (star0) f(L.o_s0, L.s0, L.n * 4, true);
         }
-        if (star0) sm_load(sm, L.o_s0, L.s0, L.n * 4);
+        f(A.lv[top].o_b, A.b, A.lv[top].n * 4, false);
+    };
+    if (threadIdx.x == 0) {
+        unsigned tx = 0;
+        each_array([&](int, const void *src, int bytes, bool pre) {
+            if (pre) tx += (unsigned)bulk_bytes(src, bytes);
+        });
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+        each_array([&](int off, const void *src, int bytes, bool pre) {
+            if (pre) stage(sm, off, src, bytes, bar, true);
+        });
+        // G is read on the way back up: start it towards L2 now
+        const int gbytes = (A.lv[0].n * A.lv[0].n * 4) & ~15;
+        if (gbytes > 0 && ((uintptr_t)A.G & 15) == 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                             (unsigned long long)__cvta_generic_to_global(A.G)),
+                         "r"(gbytes)
+                         : "memory");
     }
-    sm_load(sm, A.lv[top].o_b, A.b, A.lv[top].n * 4);
-    __syncthreads();
+    each_array([&](int off, const void *src, int bytes, bool pre) {
+        if (pre) stage(sm, off, src, bytes, bar, false);
+    });
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const bool skip_now = skipped(skip);
+    if (threadIdx.x == 0) {
+        unsigned tx = 0;
+        if (!skip_now)
+            each_array([&](int, const void *src, int bytes, bool pre) {
+                if (!pre) tx += (unsigned)bulk_bytes(src, bytes);
+            });
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+        if (!skip_now)
+            each_array([&](int off, const void *src, int bytes, bool pre) {
+                if (!pre) stage(sm, off, src, bytes, bar, true);
+            });
+    }
+    if (!skip_now)
+        each_array([&](int off, const void *src, int bytes, bool pre) {
+            if (!pre) stage(sm, off, src, bytes, bar, false);
+        });
+    __syncthreads();  // the barrier is initialized before anyone waits on it
+    const bool loaded = mbar_wait0(bar);
+    if (!__syncthreads_and(loaded)) {
+        // copies still in flight after the bound: report, wait once more (bounded) so that no copy
+        // lands in shared memory after the block has left, and leave x untouched
+        if (threadIdx.x == 0) {
+            A.S->status = 3;
+            A.S->done = 1;
+        }
+        mbar_wait0(bar);
+        return;
+    }
+    if (skip_now) return;  // the queued copies have landed
 
     // down: smooth from zero, residual, restriction
     for (int l = top; l >= 1; --l) {
@@ -183,10 +275,10 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid
         const int16_t *col = sm_at<int16_t>(sm, L.o_col);
         const float *w = sm_at<float>(sm, L.o_w), *b = sm_at<float>(sm, L.o_b), *x = sm_at<float>(sm, L.o_x);
         float *r = sm_at<float>(sm, L.o_r);
+        const float *dg = sm_at<float>(sm, L.o_dg);
         for (int i = threadIdx.x; i < L.n; i += kCoarseThreads) {
-            float s, d;
-            sm_row<KT>(i, L.n, L.K, col, w, x, s, d);
-            r[i] = d != 0.f ? b[i] - s : 0.f;
+            const float s = sm_row<KT>(i, L.n, L.K, col, w, x);
+            r[i] = dg[i] != 0.f ? b[i] - s : 0.f;
         }
         __syncthreads();
         float *bc = sm_at<float>(sm, C.o_b);
@@ -213,7 +305,9 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid
 
     // coarsest: x0 = G b0.  Each row is summed as in k_coarse (lane l adds
     // columns l, l+32, ... with fma, then a butterfly); a warp takes rows
-    // warp, warp+32, ... and keeps up to 6 of them in flight.
+    // warp, warp+32, ... and keeps up to 6 of them in flight.  G is read from
+    // L2 in batches of 32 kCj columns: every load of a batch is issued before
+    // its first fma, so a batch costs one round trip (n0 <= 192: one batch).
     {
         const CoarseLevel &L0 = A.lv[0];
         const int n0 = L0.n;
@@ -221,16 +315,31 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid
         float *x0 = sm_at<float>(sm, L0.o_x);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         constexpr int kW = kCoarseThreads / 32;
+        constexpr int kCj = 6;
         for (int row0 = warp; row0 < n0; row0 += 6 * kW) {
             float acc[6];
 #pragma unroll
             for (int m = 0; m < 6; ++m) acc[m] = 0.f;
-            for (int j = lane; j < n0; j += 32) {
-                const float bj = b0[j];
+            for (int j0 = 0; j0 < n0; j0 += 32 * kCj) {
+                float g[kCj][6];
 #pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    const int row = row0 + m * kW;
-                    if (row < n0) acc[m] = fmaf(__ldg(A.G + (size_t)row * n0 + j), bj, acc[m]);
+                for (int c = 0; c < kCj; ++c) {
+                    const int j = j0 + c * 32 + lane;
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) {
+                        const int row = row0 + m * kW;
+                        g[c][m] = (row < n0 && j < n0) ? __ldg(A.G + (size_t)row * n0 + j) : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < kCj; ++c) {
+                    const int j = j0 + c * 32 + lane;
+                    if (j < n0) {
+                        const float bj = b0[j];
+#pragma unroll
+                        for (int m = 0; m < 6; ++m)
+                            if (row0 + m * kW < n0) acc[m] = fmaf(g[c][m], bj, acc[m]);
+                    }
                 }
             }
 #pragma unroll

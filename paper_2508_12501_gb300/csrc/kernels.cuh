@@ -17,7 +17,10 @@
 namespace decdev {
 
 constexpr int kThreads = 256;
-constexpr int kMaxRedBlocks = 2048;  // partial-sum slots per reduction
+// Partial-sum slots per reduction: at least the one-wave reduction grid of
+// GB300 (8 blocks on each of 152 SMs = 1216), a multiple of 4 (float4 reads
+// of the FP32 partials) and of kThreads (the FP64 tail's rounds).
+constexpr int kMaxRedBlocks = 1280;
 constexpr int kHist = 1024;          // residual history entries
 
 // Scalars of the outer iteration, resident in device memory.
@@ -30,9 +33,13 @@ struct Scal {
     double star0_sum;   // sum of *0 over free vertices
     double mean;        // result of the last k_mean
     double scale;       // power-of-two scale of the ff outer iteration (set by k_outer_init)
+    double iscale2;     // 1 / scale^2 (exact)
+    double thr2;        // stopping threshold on ||r||^2: tol^2 ||b||^2 (+inf for b = 0)
+    double rnorm2_0;    // ||r||^2 of the initial iterate
+    double inv_star0_sum;  // 1 / star0_sum
     float alpha_hi, alpha_lo;  // alpha as an ff pair
     float beta_f, c_f;         // beta and the gauge shift rounded to FP32
-    int iter, maxit, done, status;  // status: 0 ok, 1 non-finite, 2 stalled (alpha = 0)
+    int iter, maxit, done, status;  // status: 0 ok, 1 non-finite, 2 stalled (alpha = 0), 3 a device wait gave up
     int loops, max_loops;           // device-side iteration loop: executions and hard cap
     double hist[kHist];
 };
@@ -83,7 +90,14 @@ __device__ __forceinline__ void row_apply(int i, int n, int K, const int32_t *__
     }
 }
 
-#define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+// Grid-stride loop over rows, unrolled by two: a thread's next row issues its
+// loads while the previous row's gathers are in flight (measured 9-19 % on
+// the finest smoothing sweep).  Rows keep their order, so per-thread sums
+// and results are unchanged.
+#define GRID_STRIDE(i, n) \
+    _Pragma("unroll 2") for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+// The same loop not unrolled, for kernels whose two rows do not fit in 32 registers.
+#define GRID_STRIDE_1(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
 // y = L x
 template <typename T, int KT>
@@ -641,50 +655,73 @@ __device__ bool grid_reduce(double (&v)[NS], double *partials, unsigned *counter
     return true;
 }
 
-// FP32 per-thread values: warp, block and grid sums as compensated (ff)
-// sums on the FP32 pipe, so rounding beyond the per-thread FP32 sums is
-// about 2^-47 relative; only thread 0's final hi + lo touches FP64.  The
-// partials buffer holds one ff pair (8 bytes) per block and sum.
+__device__ __forceinline__ float warps_sum(float v) {
+#pragma unroll
+    for (int o = kWarps / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP32 per-thread values: FP32 sums throughout, in a fixed order -- a warp
+// butterfly, the block's warps, then the blocks' partials in the last block
+// -- so about 21 roundings of the sum of magnitudes (the dot products and
+// norms it forms steer alpha, beta, the gauge shift and the stopping test,
+// which need FP32 accuracy).  In the last block sum s belongs to the
+// kThreads / NS threads [s kT, (s+1) kT): thread u adds the partials of
+// blocks 4u..4u+3, 4(u + kT)..., read as float4 with every load issued
+// before the first add, so the tail costs one L2 round trip for any NS.
+// Only thread 0 touches FP64 (tot).  partials holds one float per block and sum.
 template <int NS>
 __device__ bool grid_reduce(float (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
-    __shared__ float2 sh[NS][kWarps];
-    float2 *part2 = reinterpret_cast<float2 *>(partials);
+    static_assert(kWarps % NS == 0 && kMaxRedBlocks % 4 == 0, "reduction layout");
+    __shared__ float sh[NS][kWarps];
+    float *part = reinterpret_cast<float *>(partials);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const float2 x = warp_sum(make_float2(v[s], 0.f));
+        const float x = warp_sum(v[s]);
         if (lane == 0) sh[s][warp] = x;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const float2 x = warps_sum(lane < kWarps ? sh[s][lane] : make_float2(0.f, 0.f));
-            if (lane == 0) part2[s * kMaxRedBlocks + blockIdx.x] = x;
+            const float x = warps_sum(lane < kWarps ? sh[s][lane] : 0.f);
+            if (lane == 0) part[s * kMaxRedBlocks + blockIdx.x] = x;
         }
     }
     if (!last_block(counter)) return false;
-    constexpr int kPer = kMaxRedBlocks / kThreads;
-    const int nj = ((int)gridDim.x - warp * 32 + kThreads - 1) / kThreads;
+    constexpr int kT = kThreads / NS;                  // threads per sum
+    constexpr int kPer = (kMaxRedBlocks + 4 * kT - 1) / (4 * kT);  // float4 rounds per thread
+    const int s = threadIdx.x / kT, u = threadIdx.x % kT;
+    const float4 *p4 = reinterpret_cast<const float4 *>(part + s * kMaxRedBlocks);
+    const int nb = (int)gridDim.x;
+    float4 q[kPer];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        float2 pt[kPer];
+    for (int j = 0; j < kPer; ++j) {
+        const int b = 4 * (u + j * kT);
+        q[j] = b < nb ? __ldcg(p4 + u + j * kT) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float acc = 0.f;
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int b = threadIdx.x + j * kThreads;
-            pt[j] = b < (int)gridDim.x ? __ldcg(part2 + s * kMaxRedBlocks + b) : make_float2(0.f, 0.f);
-        }
-        float2 acc = pt[0];
+    for (int j = 0; j < kPer; ++j) {
+        const int b = 4 * (u + j * kT);  // slots at or past the grid hold stale sums
+        acc += b < nb ? q[j].x : 0.f;
+        acc += b + 1 < nb ? q[j].y : 0.f;
+        acc += b + 2 < nb ? q[j].z : 0.f;
+        acc += b + 3 < nb ? q[j].w : 0.f;
+    }
+    acc = warp_sum(acc);
+    float *shw = &sh[0][0];  // free: warp 0 read sh before last_block's first barrier
+    if (lane == 0) shw[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        constexpr int kWs = kWarps / NS;  // warps per sum
 #pragma unroll
-        for (int j = 1; j < kPer; ++j)
-            if (j < nj) acc = ff_add(acc, pt[j]);
-        acc = warp_sum(acc);
-        __syncthreads();
-        if (lane == 0) sh[s][warp] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            const float2 t = warps_sum(lane < kWarps ? sh[s][lane] : make_float2(0.f, 0.f));
-            if (lane == 0) tot[s] = (double)t.x + (double)t.y;
+        for (int t = 0; t < NS; ++t) {
+            float a = shw[t * kWs];
+#pragma unroll
+            for (int w = 1; w < kWs; ++w) a += shw[t * kWs + w];
+            tot[t] = a;
         }
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -720,16 +757,38 @@ __device__ __forceinline__ void set_alpha(Scal *S, double pq) {
     S->alpha_lo = af.y;
 }
 
-__device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
-    S->rnorm2 = rnorm2;
-    const bool bad = !isfinite(rnorm2) || !isfinite(S->bnorm2);
-    double rel = bad ? (double)NAN : (S->bnorm2 > 0.0 ? sqrt(rnorm2 / S->bnorm2) : 0.0);
-    S->rel = rel;
-    if (S->iter < kHist) S->hist[S->iter] = rel;
-    if (bad) {
+// Records ||r||^2 and runs the stopping test ||r|| <= tol ||b|| as ||r||^2 <=
+// thr2, with no FP64 divide or square root on the device (GB300 runs FP64
+// at a small fraction of its FP32 rate, and this sits in a single thread at
+// the tail of a kernel).  The host forms the relative residuals.
+// alpha for the float-float iteration from FP32 dot products: an FP32
+// quotient (the sums carry FP32 accuracy, and x and r take the same alpha,
+// so r keeps tracking b - L x); same stop rules as set_alpha.
+__device__ __forceinline__ void set_alpha_f(Scal *S, double pq) {
+    const double rz = S->rz;
+    float a = (float)rz / (float)pq;
+    if (!isfinite(pq) || !isfinite(rz)) {
+        a = 0.f;
         S->status = 1;
         S->done = 1;
-    } else if (rel <= S->tol || S->iter >= S->maxit) {
+    } else if (!(a != 0.f) || !isfinite(a)) {
+        a = 0.f;
+        S->status = 2;
+        S->done = 1;
+    }
+    S->alpha = a;
+    S->alpha_hi = a;
+    S->alpha_lo = 0.f;
+}
+
+__device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
+    S->rnorm2 = rnorm2;
+    const int it = S->iter;
+    if (it < kHist) S->hist[it] = rnorm2;
+    if (!isfinite(rnorm2) || !isfinite(S->bnorm2)) {
+        S->status = 1;
+        S->done = 1;
+    } else if (rnorm2 <= S->thr2 || it >= S->maxit) {
         S->done = 1;
     }
 }
@@ -778,12 +837,16 @@ __global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const 
     double tot[2];
     if (grid_reduce<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
         S->bnorm2 = tot[1];
-        S->scale = ff_scale(tot[1], n);
+        const double sc = ff_scale(tot[1], n);
+        S->scale = sc;
+        S->iscale2 = 1.0 / (sc * sc);
+        S->thr2 = tot[1] > 0.0 ? S->tol * S->tol * tot[1] : (double)INFINITY;
+        S->inv_star0_sum = S->star0_sum > 0.0 ? 1.0 / S->star0_sum : 0.0;
         S->iter = 0;
         S->done = 0;
         S->status = 0;
+        S->rnorm2_0 = tot[0];
         record_residual(S, tot[0]);
-        S->rel0 = S->rel;
     }
 }
 
@@ -985,6 +1048,20 @@ __device__ __forceinline__ void zdots_epilogue(Scal *S, const double (&tot)[4], 
     S->c_f = (float)c;
 }
 
+// The same from FP32 dot products (whose sums carry FP32 accuracy): the
+// gauge shift by a precomputed 1/sum(*0) and beta as an FP32 quotient, so the
+// single-thread tail has no FP64 divide.
+__device__ __forceinline__ void zdots_epilogue_f(Scal *S, const double (&tot)[4], int first, int gauge) {
+    const double c = gauge ? tot[0] * S->inv_star0_sum : 0.0;
+    const double rz_new = tot[1] - c * tot[3];
+    const float beta = first ? 0.f : (float)(rz_new - tot[2]) / (float)S->rz;
+    S->beta = beta;
+    S->rz = rz_new;
+    S->c = c;
+    S->beta_f = beta;
+    S->c_f = (float)c;
+}
+
 // FP32 dot products of the preconditioned vector z (cycle output) with r32 and the previous z.
 static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_m(int n, const float *__restrict__ s032,
                                                          const uint8_t *__restrict__ freev, const float *__restrict__ z,
@@ -1005,7 +1082,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_m(int n, const
         }
     }
     double tot[4];
-    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue(S, tot, first, gauge);
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue_f(S, tot, first, gauge);
 }
 
 // The last post-smoothing step of the finest level (k_smooth with DIN =
@@ -1025,7 +1102,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots(int n, int K, cons
     pdl_prologue();
     if (skipped(skip)) return;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_1(i, n) {
         float s, d;
         row_apply<float, KT>(i, n, K, col, w, x_in, s, d);
         const float ri = ldg(b + i);
@@ -1043,7 +1120,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots(int n, int K, cons
         }
     }
     double tot[4];
-    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue(S, tot, first, gauge);
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue_f(S, tot, first, gauge);
 }
 
 // z = z - c (free rows, FP32), zo = z, p = z + beta p (FP64)
@@ -1203,7 +1280,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_ff(int n, int K, const
     pdl_prologue();
     if (skipped(skip)) return;
     float acc[1] = {0.f};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_1(i, n) {
         const float pi = ldg(p + i);
         const float2 q = row_apply_ff<KT>(i, n, K, col, wh, wl, p, pi);
         qh[i] = q.x;
@@ -1211,9 +1288,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_ff(int n, int K, const
         acc[0] = fmaf(ldg(s032 + i) * pi, q.x, acc[0]);
     }
     double tot[1];
-    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
-        set_alpha(S, tot[0]);
-    }
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) set_alpha_f(S, tot[0]);
 }
 
 // x += alpha p, r -= alpha q (ff), ||r||^2 from r's hi part -> convergence test
@@ -1250,9 +1325,8 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_ff(int n, con
     }
     double tot[1];
     if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
-        const double is = 1.0 / S->scale;
         S->iter += 1;
-        record_residual(S, tot[0] * is * is);
+        record_residual(S, tot[0] * S->iscale2);
     }
 }
 
@@ -1294,9 +1368,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_mg_residual_ff(int n, int K, co
     }
     double tot[1];
     if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
-        const double is = 1.0 / S->scale;
         S->iter += 1;
-        record_residual(S, tot[0] * is * is);
+        record_residual(S, tot[0] * S->iscale2);
     }
 }
 

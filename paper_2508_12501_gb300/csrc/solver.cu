@@ -760,20 +760,29 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
+    // relative residuals from the squared norms the device recorded; converged
+    // means the device's own test ||r||^2 <= tol^2 ||b||^2 held
+    auto rel_of = [&](double rn2) {
+        if (!std::isfinite(rn2) || !std::isfinite(h->bnorm2)) return (double)NAN;
+        return h->bnorm2 > 0.0 ? std::sqrt(rn2 / h->bnorm2) : 0.0;
+    };
+    const bool converged = std::isfinite(h->bnorm2) && h->rnorm2 <= h->thr2;
     if (stats) {
         stats->iters = h->iter;
-        stats->rel_res = h->rel;
-        stats->rel_res0 = h->rel0;
+        stats->rel_res = rel_of(h->rnorm2);
+        stats->rel_res0 = rel_of(h->rnorm2_0);
         stats->launches = (mg->launches - launches0) + graph_launches * mg->graph_kernels[o.solver][o.mode] +
                           (loop_runs ? (int64_t)h->loops * mg->loop_kernels[o.solver][o.mode] : 0);
     }
+    if (h->status == 3)
+        return fail(Status::fail(DEC_ERR_CUDA, "a device-side wait gave up (shared-memory coarse cycle load)"));
     if (h->status == 1) {
         char buf[160];
         snprintf(buf, sizeof(buf), "non-finite residual at iteration %d (||b||^2 = %.3e, last rel = %.3e, rz = %.3e)",
-                 h->iter, h->bnorm2, h->iter > 0 ? h->hist[std::min(h->iter - 1, kHist - 1)] : 0.0, h->rz);
+                 h->iter, h->bnorm2, rel_of(h->rnorm2), h->rz);
         return fail(Status::fail(DEC_ERR_NONFINITE, buf));
     }
-    if (!(h->rel <= o.tol))
+    if (!converged)
         return fail(Status::fail(DEC_ERR_NOT_CONVERGED, h->status == 2 ? "iteration stalled (<r,z> or <p,Lp> is zero "
                                                                          "in working precision) before tol"
                                                                        : "maxit reached before tol"));
@@ -874,7 +883,7 @@ int setup_coarse_cycle(dec_mg *mg) {
     const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV, star0 = o.restriction == DEC_RESTRICT_STAR0;
     auto al = [](int64_t b) { return (b + 15) & ~(int64_t)15; };
     CoarseArgs A{};
-    int64_t off = 0;
+    int64_t off = kCoarseHeader;
     int top = -1;
     int64_t top_bytes = 0;
     for (int l = 0; l < std::min(nl, kCoarseMaxLevels); ++l) {
@@ -941,6 +950,8 @@ int setup_coarse_cycle(dec_mg *mg) {
     A.cheb = cheb ? 1 : 0;
     A.star0 = star0 ? 1 : 0;
     A.G = mg->G32;
+    A.S = mg->scal;
+    A.top_mutable = top == nl - 1 ? 1 : 0;
     // The dynamic shared-memory limit is a property of the kernel, shared by
     // every hierarchy on the device: raise it once to the device maximum
     // (each layout is at most that), never to one hierarchy's size.
@@ -1356,6 +1367,82 @@ int dec_mg_time_smooth(dec_mg *mg, int level, int reps, double *avg_ms, double *
     *avg_ms = ms / reps;
     // per row: K column indices and K weights, x_i, b_i, the new x_i (+ the direction)
     *bytes = (double)L.n * (8.0 * L.K + 4.0 * (3 + (cheb ? 1 : 0)));
+    return DEC_OK;
+}
+
+int dec_mg_time_kernel(dec_mg *mg, int kind, int level, int reps, double *avg_ms, double *bytes, dec_stream_t stream) {
+    if (kind == DEC_PK_SMOOTH) return dec_mg_time_smooth(mg, level, reps, avg_ms, bytes, stream);
+    if (int rc = check_dev(mg)) return rc;
+    const int nl = (int)mg->lv.size();
+    if (level < 0) level += nl;
+    const dec_mg_opts &o = mg->H.opts;
+    if (reps < 1 || !avg_ms || !bytes || level != nl - 1 || o.smoother == DEC_SMOOTH_MCGS ||
+        (kind != DEC_PK_SMOOTHDOTS && kind != DEC_PK_SPMV64 && kind != DEC_PK_UPDATE))
+        return fail(Status::fail(DEC_ERR_ARG, "bad argument (finest level; DEC_PK_SMOOTH, SMOOTHDOTS, SPMV64 or UPDATE)"));
+    DevLevel &F = mg->lv.back();
+    const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = sizeof(float) * F.n;
+    // zeroed FP32 work vectors: the same kernels and launch shapes as in the mixed_ff loop
+    float *zero[] = {F.x32[0], F.x32[1], F.d32[0], F.b32, mg->zo32, mg->fp, mg->fqh, mg->fql, mg->fxh, mg->fxl, mg->frl};
+    for (float *z : zero) CK(cudaMemsetAsync(z, 0, vb, s));
+    const int rg = red_grid(mg, F.n);
+    const int *noskip = nullptr;
+    const int gauge = mg->H.bc == DEC_BC_GAUGE;
+    int s0mode = 0;  // the outer update carries the first smoothing step as in the solve
+    float e0s = 0.f;
+    if ((o.fuse & DEC_FUSE_OUTER) && o.nu1 > 0) {
+        s0mode = cheb && 1 < o.nu1 ? 2 : 1;
+        e0s = (float)(cheb ? F.e_pre[0] : o.omega);
+    }
+    auto one = [&]() {
+        dispatch_k(F.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            if (kind == DEC_PK_SMOOTHDOTS) {
+                const float e = (float)(cheb ? F.e_post.back() : o.omega), c = (float)(cheb ? F.c_post.back() : 0.0);
+                if (cheb)
+                    launch(mg, k_smooth_zdots<KT, true>, rg, s, F.n, F.K, (const int32_t *)F.col, (const float *)F.w32,
+                           (const float *)F.b32, (const float *)F.x32[0], (const float *)F.d32[0], F.x32[1], c, e,
+                           (const float *)F.star0_32, (const uint8_t *)F.freev, (const float *)mg->zo32, 0, gauge,
+                           mg->partials, mg->counter, mg->scal, noskip);
+                else
+                    launch(mg, k_smooth_zdots<KT, false>, rg, s, F.n, F.K, (const int32_t *)F.col,
+                           (const float *)F.w32, (const float *)F.b32, (const float *)F.x32[0], (const float *)nullptr,
+                           F.x32[1], c, e, (const float *)F.star0_32, (const uint8_t *)F.freev,
+                           (const float *)mg->zo32, 0, gauge, mg->partials, mg->counter, mg->scal, noskip);
+            } else if (kind == DEC_PK_SPMV64) {
+                launch(mg, k_pcg_spmv_ff<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const float *)F.w32,
+                       (const float *)F.wlo, (const float *)F.star0_32, (const float *)mg->fp, mg->fqh, mg->fql,
+                       mg->partials, mg->counter, mg->scal, noskip);
+            } else {
+                launch(mg, k_pcg_update_ff, rg, s, F.n, (const float *)mg->fp, (const float *)mg->fqh,
+                       (const float *)mg->fql, mg->fxh, mg->fxl, F.b32, mg->frl, mg->partials, mg->counter, mg->scal,
+                       noskip, s0mode, (const float *)F.dg32, F.x32[0], F.d32[0], e0s);
+            }
+        });
+    };
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int r = 0; r < 3; ++r) one();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) one();
+    cudaEventRecord(e1, s);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return cuda_fail(ce, "dec_mg_time_kernel");
+    CK(cudaGetLastError());
+    *avg_ms = ms / reps;
+    const double K = F.K, n = F.n;
+    if (kind == DEC_PK_SMOOTHDOTS)  // operator, b = r32, x, direction, new x; *0, free mask, previous z
+        *bytes = n * (8.0 * K + 4.0 * (3 + (cheb ? 1 : 0)) + 4.0 + 1.0 + 4.0);
+    else if (kind == DEC_PK_SPMV64)  // col, w32 + wlo, p_i, q hi+lo, *0
+        *bytes = n * (12.0 * K + 4.0 + 8.0 + 4.0);
+    else  // p, q hi+lo, x and r hi+lo read and written; fused: the diagonal, the first step's x (and direction)
+        *bytes = n * (4.0 + 8.0 + 16.0 + 16.0 + (s0mode ? 8.0 : 0.0) + (s0mode == 2 ? 4.0 : 0.0));
     return DEC_OK;
 }
 

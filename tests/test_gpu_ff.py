@@ -141,3 +141,26 @@ def test_tol_zero_stops_cleanly(mode):
     assert st.rel_res < 1e-12
     xs = omg.direct_solve(oh, b)
     assert _s0_rel(oh.finest.star0, x.cpu().numpy(), xs) < 1e-10
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+def test_kernel_timer(smoother):
+    # back-to-back timing of the finest-level kernels of the float-float loop: positive times, the byte model,
+    # argument checks, and a solve afterwards still converges (the timer only overwrote work vectors)
+    import paper_2508_12501_gb300 as P
+    v, t = W.icosahedron()
+    h = P.Hierarchy(P.Mesh(v, t), 5, 4, bc="gauge", sphere=True, smoother=smoother)
+    n, K = h.n, 6
+    cheb = smoother == "chebyshev"
+    want = {"smoothdots": n * (8 * K + 12 + (4 if cheb else 0) + 9), "spmv64": n * (12 * K + 16),
+            "update": n * (44 + 8 + (4 if cheb else 0))}
+    for kind, by in want.items():
+        ms, b = h.time_kernel(kind, reps=5)
+        assert ms > 0 and b == by
+    ms, b = h.time_kernel("smooth", level=1, reps=5)
+    assert ms > 0 and b > 0
+    for bad in (dict(kind="spmv64", level=1), dict(kind="residual"), dict(kind="update", reps=0)):
+        with pytest.raises(P.DecError):
+            h.time_kernel(**bad)
+    b = torch.as_tensor(W.uniform_field(n, 3), device="cuda")
+    assert h.solve(b, mode="mixed_ff", tol=1e-10)[1].rel_res <= 1e-10
