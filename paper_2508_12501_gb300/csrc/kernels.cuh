@@ -52,6 +52,37 @@ __device__ __forceinline__ void pdl_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// The same for the kernels that rewrite operator tables (weights, diagonals):
+// they let dependents start only when they finish, so a kernel that reads a
+// table before its own wait (pdl_prologue_ell) never overlaps a writer of it.
+__device__ __forceinline__ void pdl_wait_only() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// Programmatic dependent launch for a kernel over the rows of a level: before
+// waiting for the previous kernel, pull this thread's first row's slots of
+// the level's ELL tables (columns, weights) into L1.  The tables do not
+// depend on the previous kernel, so the row loop's first table loads after
+// the wait need not go to L2.  w2 (may be null) is a second weight table.
+template <int KT, typename TW>
+__device__ __forceinline__ void pdl_prologue_ell(int n, int K, const int32_t *col, const TW *w,
+                                                 const TW *w2 = nullptr) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int Kk = KT > 0 ? KT : K;
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + i;
+            prefetch_l1(col + o);
+            prefetch_l1(w + o);
+            if (w2) prefetch_l1(w2 + o);
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ bool skipped(const int *skip) { return skip != nullptr && *skip != 0; }
 
 template <typename T>
@@ -119,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_residual(int n, int K, const in
                                                       const T *__restrict__ w, const T *__restrict__ b,
                                                       const T *__restrict__ x, T *__restrict__ r,
                                                       const int *skip) {
-    pdl_prologue();
+    pdl_prologue_ell<KT>(n, K, col, w);
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) {
         T s, d;
@@ -139,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth(int n, int K, const int3
                                                     const T *__restrict__ x_in, const T *__restrict__ d_in,
                                                     T *__restrict__ x_out, T *__restrict__ d_out, T c, T e,
                                                     const int *skip) {
-    pdl_prologue();
+    pdl_prologue_ell<KT>(n, K, col, w);
     if (skipped(skip)) return;
     GRID_STRIDE(i, n) {
         T s, d;
@@ -194,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_mcgs(int n, int K, const int32_
 // k_smooth0 and row_apply do, so the fused kernels below read the same value.
 template <typename T, int KT>
 __global__ void __launch_bounds__(kThreads, 8) k_diag(int n, int K, const T *__restrict__ w, T *__restrict__ dg) {
-    pdl_prologue();
+    pdl_wait_only();
     const int Kk = KT > 0 ? KT : K;
     GRID_STRIDE(i, n) {
         T d = T(0);
@@ -369,7 +400,19 @@ __global__ void __launch_bounds__(kThreads, 8) k_restrict(int nc, int nf, int Kf
                                                       const T *__restrict__ s0f, const T *__restrict__ s0c,
                                                       const int *skip, const T *__restrict__ dgc,
                                                       T *__restrict__ xc, T *__restrict__ dc, T e0) {
-    pdl_prologue();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    {
+        // this thread's first coarse row: its fine column slots, before the wait (see pdl_prologue_ell)
+        const int c = blockIdx.x * blockDim.x + threadIdx.x;
+        if (c < nc) {
+#pragma unroll
+            for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+                if (KT == 0 && k >= Kf) break;
+                prefetch_l1(colf + (size_t)k * nf + c);
+            }
+        }
+    }
+    pdl_wait_only();
     if (skipped(skip)) return;
     const int Kk = KT > 0 ? KT : Kf;
     GRID_STRIDE(c, nc) {
@@ -406,7 +449,13 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 8) k_prolong(int nc, int nf, const int2 *__restrict__ par,
                                                      const T *__restrict__ ec, T *__restrict__ xf,
                                                      const int *skip) {
-    pdl_prologue();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    {
+        // this thread's first midpoint's parents, before the wait (see pdl_prologue_ell)
+        const int v = blockIdx.x * blockDim.x + threadIdx.x;
+        if (v >= nc && v < nf) prefetch_l1(par + (v - nc));
+    }
+    pdl_wait_only();
     if (skipped(skip)) return;
     GRID_STRIDE(v, nf) xf[v] = add_rn(xf[v], prolong_add(v, nc, par, ec));
 }
@@ -1099,7 +1148,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots(int n, int K, cons
                                                           const float *__restrict__ zo, int first, int gauge,
                                                           double *partials, unsigned *counter, Scal *S,
                                                           const int *skip) {
-    pdl_prologue();
+    pdl_prologue_ell<KT>(n, K, col, w);
     if (skipped(skip)) return;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     GRID_STRIDE_1(i, n) {
@@ -1277,7 +1326,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_ff(int n, int K, const
                                                          float *__restrict__ qh, float *__restrict__ ql,
                                                          double *partials, unsigned *counter, Scal *S,
                                                          const int *skip) {
-    pdl_prologue();
+    pdl_prologue_ell<KT>(n, K, col, wh, wl);
     if (skipped(skip)) return;
     float acc[1] = {0.f};
     GRID_STRIDE_1(i, n) {
@@ -1407,7 +1456,7 @@ static __global__ void __launch_bounds__(kThreads) k_set_weights(int n, int K, c
                                                          const double *__restrict__ star1, const double *__restrict__ star0,
                                                          const uint8_t *__restrict__ freev, double *__restrict__ w64,
                                                          float *__restrict__ w32, float *__restrict__ wlo) {
-    pdl_prologue();
+    pdl_wait_only();
     GRID_STRIDE(i, n) {
         const double s0 = ldg(star0 + i);
         for (int k = 0; k < K; ++k) {
