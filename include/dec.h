@@ -108,6 +108,9 @@ typedef struct dec_mg_opts {
                          the two separate kernels it replaces; default
                          DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE (those that
                          gather a second vector measured slower on GB300) */
+    int fuse_max_rows; /* the gathering fusions (DEC_FUSE_SMOOTH01, _RESTRICT, _PROLONG) run
+                          on levels of at most this many rows, the separate kernels on larger
+                          ones; 0 (default): every level */
 } dec_mg_opts;
 /* Fused cycle kernels.  Gathering a second vector per neighbour:
  *   DEC_FUSE_SMOOTH01  the first two pre-smoothing steps from zero;

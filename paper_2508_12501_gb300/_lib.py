@@ -41,7 +41,8 @@ STATUS_NAMES = {0: "DEC_OK", 1: "DEC_ERR_ARG", 2: "DEC_ERR_MESH", 3: "DEC_ERR_CU
 class dec_mg_opts(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("cheby_lo", C.c_double), ("cheby_hi", C.c_double), ("power_iters", C.c_int), ("gamma", C.c_int),
-                ("restriction", C.c_int), ("fcycle", C.c_int), ("coarse_max_rows", C.c_int), ("fuse", C.c_int)]
+                ("restriction", C.c_int), ("fcycle", C.c_int), ("coarse_max_rows", C.c_int), ("fuse", C.c_int),
+                ("fuse_max_rows", C.c_int)]
 
 
 class dec_solve_opts(C.Structure):

@@ -97,7 +97,7 @@ class Hierarchy:
     def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
                  restriction="rownorm", host_only=False, fuse=None, order="edge", coarse_max_rows=0,
-                 fcycle=False, scheme="binary"):
+                 fcycle=False, scheme="binary", fuse_max_rows=None):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
         o = L.dec_mg_opts()
@@ -110,6 +110,8 @@ class Hierarchy:
         if fuse is not None:  # None keeps the library default (the row-local fusions)
             o.fuse = int(fuse) if not isinstance(fuse, bool) else (L.DEC_FUSE_ALL if fuse else 0)
         self.fuse = int(o.fuse)
+        if fuse_max_rows is not None:  # None keeps the library default
+            o.fuse_max_rows = int(fuse_max_rows)
         o.coarse_max_rows = int(coarse_max_rows)
         o.fcycle = 1 if fcycle else 0
         flags = ((L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0) | ORDERS[order]

@@ -38,6 +38,7 @@ void dec_mg_default_opts(dec_mg_opts *o) {
     o->fcycle = 0;
     o->fuse = DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE;
     o->coarse_max_rows = 0;
+    o->fuse_max_rows = 0;
 }
 
 void dec_solve_default_opts(dec_solve_opts *o) {

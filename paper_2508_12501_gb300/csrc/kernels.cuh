@@ -320,13 +320,15 @@ __global__ void __launch_bounds__(kThreads, 8) k_prolong_smooth(int n, int K, in
 // Residual (k_residual) followed by restriction (k_restrict): a group of 8
 // lanes per coarse row c; lane 0 forms r_f at fine row c, lane k+1 at the
 // fine neighbour in slot k (a midpoint of a coarse edge at c), and lane 0
-// adds them in slot order.  Requires K <= 7.
-template <typename T, int KT, bool STAR0>
+// adds them in slot order.  Requires K <= 7.  S0 > 0 also runs the coarse
+// level's first smoothing step from zero on the new row, as k_restrict does.
+template <typename T, int KT, bool STAR0, int S0 = 0>
 __global__ void __launch_bounds__(kThreads, 8) k_residual_restrict(int nc, int nf, int K, const int32_t *__restrict__ col,
                                                                const T *__restrict__ w, const T *__restrict__ b,
                                                                const T *__restrict__ x, T *__restrict__ bc,
                                                                const T *__restrict__ s0f, const T *__restrict__ s0c,
-                                                               const int *skip) {
+                                                               const int *skip, const T *__restrict__ dgc,
+                                                               T *__restrict__ xc, T *__restrict__ dc, T e0) {
     pdl_prologue();
     if (skipped(skip)) return;
     const int Kk = KT > 0 ? KT : K;
@@ -360,10 +362,18 @@ __global__ void __launch_bounds__(kThreads, 8) k_residual_restrict(int nc, int n
             }
         }
         if (lane8 == 0) {
+            T v;
             if (STAR0)
-                bc[c] = fma(sj, r, T(0.5) * acc) / ldg(s0c + c);
+                v = fma(sj, r, T(0.5) * acc) / ldg(s0c + c);
             else
-                bc[c] = fma(T(0.5), acc, r) / add_rn(T(1), mul_rn(T(0.5), T(deg)));
+                v = fma(T(0.5), acc, r) / add_rn(T(1), mul_rn(T(0.5), T(deg)));
+            bc[c] = v;
+            if (S0 > 0) {
+                const T d = ldg(dgc + c);
+                const T x1 = d != T(0) ? e0 * (v / d) : T(0);
+                xc[c] = x1;
+                if (S0 == 2) dc[c] = x1;
+            }
         }
     }
 }

@@ -133,6 +133,15 @@ struct DotsArgs {
 
 // Steps k_start .. nu-1 of one smoothing call on level l.  From zero with
 // fused kernels, steps 0 and 1 run as one k_smooth01 launch.
+// A DEC_FUSE_* bit on a level of n rows: the row-local fusions apply on
+// every level, the gathering ones (SMOOTH01, RESTRICT, PROLONG) on levels of
+// at most fuse_max_rows rows (0: every level).
+inline bool fuse_here(const dec_mg_opts &o, int bit, int64_t n) {
+    if (!(o.fuse & bit)) return false;
+    const bool gathering = (bit & (DEC_FUSE_SMOOTH01 | DEC_FUSE_RESTRICT | DEC_FUSE_PROLONG)) != 0;
+    return !gathering || o.fuse_max_rows <= 0 || n <= o.fuse_max_rows;
+}
+
 template <typename T>
 void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, int &cur, cudaStream_t s,
             const int *skip, int k_start = 0, DotsArgs *da = nullptr) {
@@ -165,7 +174,7 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        if (from_zero && k_start == 0 && nu >= 2 && (o.fuse & DEC_FUSE_SMOOTH01)) {
+        if (from_zero && k_start == 0 && nu >= 2 && fuse_here(o, DEC_FUSE_SMOOTH01, L.n)) {
             const T e0 = (T)(cheb ? ee[0] : o.omega), e1 = (T)(cheb ? ee[1] : o.omega);
             const T c1 = (T)(cheb ? cc[1] : 0.0);
             const bool dout = cheb && 2 < nu;
@@ -286,15 +295,34 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        if ((o.fuse & DEC_FUSE_RESTRICT) && L.K <= 7 && !cubic) {
+        if (fuse_here(o, DEC_FUSE_RESTRICT, L.n) && L.K <= 7 && !cubic) {
             ProfScope ps(mg, DEC_PK_RESRESTRICT, l, s);
             const int gr = grid_for(mg, (int64_t)C.n * 8);
-            if (o.restriction == DEC_RESTRICT_STAR0)
-                launch(mg, k_residual_restrict<T, KT, true>, gr, s, C.n, L.n, L.K, L.col, w, b,
-                       (const T *)P<T>::x(L, cur), P<T>::b(C), P<T>::s0(L), P<T>::s0(C), skip);
-            else
-                launch(mg, k_residual_restrict<T, KT, false>, gr, s, C.n, L.n, L.K, L.col, w, b,
-                       (const T *)P<T>::x(L, cur), P<T>::b(C), (const T *)nullptr, (const T *)nullptr, skip);
+            const T *s0l = P<T>::s0(L), *s0c = P<T>::s0(C);
+            const bool st0 = o.restriction == DEC_RESTRICT_STAR0;
+            // with DEC_FUSE_RESTRICT0 the coarse level's first smoothing step rides along (S0)
+            const int s0 = restrict0 ? (o.smoother == DEC_SMOOTH_CHEBYSHEV && 1 < o.nu1 ? 2 : 1) : 0;
+            const T e0 = restrict0 ? (T)(o.smoother == DEC_SMOOTH_CHEBYSHEV ? C.e_pre[0] : o.omega) : T(0);
+            const T *dgc = P<T>::dg(C);
+            T *xc = P<T>::x(C, 0), *dc = P<T>::d(C, 0), *bcv = P<T>::b(C);
+            const T *xl = P<T>::x(L, cur);
+            auto go = [&](auto st0c, auto s0c_) {
+                constexpr bool ST0 = decltype(st0c)::value;
+                constexpr int S0 = decltype(s0c_)::value;
+                launch(mg, k_residual_restrict<T, KT, ST0, S0>, gr, s, C.n, L.n, L.K, L.col, w, b, xl, bcv,
+                       ST0 ? s0l : (const T *)nullptr, ST0 ? s0c : (const T *)nullptr, skip, dgc, xc, dc, e0);
+            };
+            using F = std::false_type;
+            using Tr = std::true_type;
+            using I0 = std::integral_constant<int, 0>;
+            using I1 = std::integral_constant<int, 1>;
+            using I2 = std::integral_constant<int, 2>;
+            if (st0) {
+                if (s0 == 2) go(Tr{}, I2{}); else if (s0 == 1) go(Tr{}, I1{}); else go(Tr{}, I0{});
+            } else {
+                if (s0 == 2) go(F{}, I2{}); else if (s0 == 1) go(F{}, I1{}); else go(F{}, I0{});
+            }
+            coarse_pre0 = s0 > 0;
             return;
         }
         {
@@ -360,7 +388,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
             ec = P<T>::y(C);
         }
     }
-    if ((o.fuse & DEC_FUSE_PROLONG) && o.nu2 > 0 && o.smoother != DEC_SMOOTH_MCGS && !cubic) {
+    if (fuse_here(o, DEC_FUSE_PROLONG, L.n) && o.nu2 > 0 && o.smoother != DEC_SMOOTH_MCGS && !cubic) {
         const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
         const T e0 = (T)(cheb ? L.e_post[0] : o.omega);
         const bool dout = cheb && 1 < o.nu2;
@@ -988,6 +1016,7 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
     if (o.restriction != DEC_RESTRICT_ROWNORM && o.restriction != DEC_RESTRICT_STAR0)
         return fail(Status::fail(DEC_ERR_ARG, "unknown restriction"));
     if (o.fuse < 0 || o.fuse > DEC_FUSE_ALL) return fail(Status::fail(DEC_ERR_ARG, "fuse must be a DEC_FUSE_* mask"));
+    if (o.fuse_max_rows < 0) return fail(Status::fail(DEC_ERR_ARG, "fuse_max_rows must be >= 0"));
     if (o.coarse_max_rows < 0) return fail(Status::fail(DEC_ERR_ARG, "coarse_max_rows must be >= 0"));
     if (o.fcycle != 0 && o.fcycle != 1) return fail(Status::fail(DEC_ERR_ARG, "fcycle must be 0 or 1"));
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma < 1 || o.gamma > 4 || o.power_iters < 1 ||

@@ -96,7 +96,7 @@ def test_fused_solve_is_bitwise_equal(mode, solver):
     assert out[1][1].launches < out[0][1].launches
 
 
-@pytest.mark.parametrize("fuse", [1, 2, 4, 7, 8, 9, 14])
+@pytest.mark.parametrize("fuse", [1, 2, 4, 7, 8, 9, 10, 14])
 def test_fused_masks_match_unfused(fuse):
     import paper_2508_12501_gb300 as P
     base, nsub, nl, bc, sph = CASES["square5"]
@@ -190,3 +190,33 @@ def test_coarse_cycle_after_smaller_hierarchies():
     assert out[1][1].rel_res <= 1e-8 and torch.equal(out[0][0], out[1][0])
     bs = torch.as_tensor(W.uniform_field(small[0].n, 43), device="cuda")
     assert small[0].solve(bs, mode="mixed_ff", tol=1e-8)[1].rel_res <= 1e-8
+
+
+@pytest.mark.parametrize("max_rows", [100, 300, 1000])
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("restriction", ["rownorm", "star0"])
+def test_gathering_fusions_on_small_levels(max_rows, smoother, restriction):
+    # fuse_max_rows: the gathering fusions only on levels of at most max_rows rows
+    # (unit square x5: 9, 25, 81, 289, 1089 rows), the separate kernels above; still bitwise
+    import paper_2508_12501_gb300 as P
+    v, t = W.unit_square()
+    hs = [P.Hierarchy(P.Mesh(v, t), 5, 5, bc="dirichlet", smoother=smoother, restriction=restriction, fuse=f,
+                      fuse_max_rows=m) for f, m in ((0, 0), (31, max_rows), (63, max_rows))]
+    _cycles_equal(hs[:2], torch.float32, 47)
+    _cycles_equal([hs[0], hs[2]], torch.float32, 47)
+    _cycles_equal(hs[:2], torch.float64, 47)
+    b = torch.as_tensor(W.uniform_field(hs[0].n, 53), device="cuda")
+    out = [h.solve(b, solver="mgpcg", mode="mixed_ff", tol=1e-10) for h in hs]
+    assert out[0][1].iters == out[1][1].iters == out[2][1].iters
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][0], out[2][0])
+    # fewer launches than the row-local fusions alone only when some level takes the gathering ones
+    hr = P.Hierarchy(P.Mesh(v, t), 5, 5, bc="dirichlet", smoother=smoother, restriction=restriction, fuse=24)
+    nr = hr.solve(b, solver="mgpcg", mode="mixed_ff", tol=1e-10)[1].launches
+    assert out[1][1].launches < nr
+
+
+def test_fuse_max_rows_is_validated():
+    import paper_2508_12501_gb300 as P
+    v, t = W.unit_square()
+    with pytest.raises(P.DecError):
+        P.Hierarchy(P.Mesh(v, t), 3, 3, bc="dirichlet", fuse_max_rows=-1)
