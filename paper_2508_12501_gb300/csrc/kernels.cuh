@@ -33,7 +33,7 @@ struct Scal {
     double star0_sum;   // sum of *0 over free vertices
     double mean;        // result of the last k_mean
     double scale;       // power-of-two scale of the ff outer iteration (set by k_outer_init)
-    double iscale2;     // 1 / scale^2 (exact)
+    double iscale, iscale2;  // 1 / scale and 1 / scale^2 (exact)
     double thr2;        // stopping threshold on ||r||^2: tol^2 ||b||^2 (+inf for b = 0)
     double rnorm2_0;    // ||r||^2 of the initial iterate
     double inv_star0_sum;  // 1 / star0_sum
@@ -898,9 +898,9 @@ __global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const 
         S->bnorm2 = tot[1];
         const double sc = ff_scale(tot[1], n);
         S->scale = sc;
+        S->iscale = 1.0 / sc;
         S->iscale2 = 1.0 / (sc * sc);
         S->thr2 = tot[1] > 0.0 ? S->tol * S->tol * tot[1] : (double)INFINITY;
-        S->inv_star0_sum = S->star0_sum > 0.0 ? 1.0 / S->star0_sum : 0.0;
         S->iter = 0;
         S->done = 0;
         S->status = 0;
@@ -1304,13 +1304,124 @@ static __global__ void __launch_bounds__(kThreads, 8) k_ff_split(int n, const do
     }
 }
 
-// End of an ff solve: x = (hi + lo) / scale.
+// End of an ff solve: x = (hi + lo) / scale (also into x2 when given).
 static __global__ void __launch_bounds__(kThreads, 8) k_ff_join(int n, const float *__restrict__ xh,
                                                      const float *__restrict__ xl, double *__restrict__ x,
-                                                     const Scal *S) {
+                                                     double *__restrict__ x2, const Scal *S) {
     pdl_prologue();
-    const double is = 1.0 / S->scale;
-    GRID_STRIDE(i, n) x[i] = ((double)ldg(xh + i) + (double)ldg(xl + i)) * is;
+    const double is = S->iscale;
+    GRID_STRIDE(i, n) {
+        const double v = ((double)ldg(xh + i) + (double)ldg(xl + i)) * is;
+        x[i] = v;
+        if (x2) x2[i] = v;
+    }
+}
+
+// The same with the gauge: x = (hi + lo) / scale and the *0-weighted mean of x
+// over free rows, for k_shift_out.
+static __global__ void __launch_bounds__(kThreads, 8) k_ff_join_mean(int n, const float *__restrict__ xh,
+                                                          const float *__restrict__ xl, double *__restrict__ x,
+                                                          const double *__restrict__ star0,
+                                                          const uint8_t *__restrict__ freev, double *partials,
+                                                          unsigned *counter, Scal *S) {
+    pdl_prologue();
+    const double is = S->iscale;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) {
+        const double v = ((double)ldg(xh + i) + (double)ldg(xl + i)) * is;
+        x[i] = v;
+        if (freev[i]) acc[0] = fma(ldg(star0 + i), v, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] * S->inv_star0_sum;
+}
+
+// v <- v - mean on free rows, 0 on fixed rows, also into out.
+static __global__ void __launch_bounds__(kThreads, 8) k_shift_out(int n, const uint8_t *__restrict__ freev,
+                                                       double *__restrict__ v, double *__restrict__ out,
+                                                       const Scal *S) {
+    pdl_prologue();
+    const double m = S->mean;
+    GRID_STRIDE(i, n) {
+        const double y = freev[i] ? v[i] - m : 0.0;
+        v[i] = y;
+        out[i] = y;
+    }
+}
+
+// Start of a cold-start (x = 0) float-float solve, pass 1: the *0-weighted
+// mean of b over free rows (gauge) and ||b||^2 over free rows, whose size
+// fixes the power-of-two scale of the ff iteration (ff_scale).
+static __global__ void __launch_bounds__(kThreads, 8) k_b_stats(int n, const double *__restrict__ star0,
+                                                     const uint8_t *__restrict__ freev,
+                                                     const double *__restrict__ b, int gauge, double *partials,
+                                                     unsigned *counter, Scal *S) {
+    pdl_prologue();
+    double acc[2] = {0.0, 0.0};
+    GRID_STRIDE(i, n) {
+        if (freev[i]) {
+            const double bi = ldg(b + i);
+            if (gauge) acc[0] = fma(ldg(star0 + i), bi, acc[0]);
+            acc[1] = fma(bi, bi, acc[1]);
+        }
+    }
+    double tot[2];
+    if (grid_reduce<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->mean = gauge ? tot[0] * S->inv_star0_sum : 0.0;
+        const double sc = ff_scale(tot[1], n);
+        S->scale = sc;
+        S->iscale = 1.0 / sc;
+        S->iscale2 = 1.0 / (sc * sc);
+    }
+}
+
+// Pass 2, row-local: b <- b - mean on free rows, 0 on fixed rows (written
+// back); with x = 0, r = b, stored as scaled ff pairs (rh is the cycle's
+// right-hand side; bh, bl, when given, get the same pair for standalone MG);
+// x = 0 in ff; ||r||^2 from rh in FP32 starts the stopping test.  s0mode > 0
+// also runs the first cycle's first smoothing step on the finest level from
+// zero, as k_smooth0 does (x0 = e0 r / dg, and d0 = x0 when s0mode == 2).
+static __global__ void __launch_bounds__(kThreads, 8) k_init_ff(int n, const uint8_t *__restrict__ freev,
+                                                     double *b, float *__restrict__ xh, float *__restrict__ xl,
+                                                     float *__restrict__ rh, float *__restrict__ rl,
+                                                     float *__restrict__ bh, float *__restrict__ bl, int s0mode,
+                                                     const float *__restrict__ dg, float *__restrict__ x0,
+                                                     float *__restrict__ d0, float e0, double *partials,
+                                                     unsigned *counter, Scal *S) {
+    pdl_prologue();
+    const double m = S->mean, sc = S->scale;
+    float acc[1] = {0.f};
+    GRID_STRIDE(i, n) {
+        const double v = freev[i] ? b[i] - m : 0.0;
+        b[i] = v;
+        const float2 r = ff_from(v * sc);
+        rh[i] = r.x;
+        rl[i] = r.y;
+        xh[i] = 0.f;
+        xl[i] = 0.f;
+        if (bh) {
+            bh[i] = r.x;
+            bl[i] = r.y;
+        }
+        acc[0] = fmaf(r.x, r.x, acc[0]);
+        if (s0mode > 0) {
+            const float di = ldg(dg + i);
+            const float x1 = di != 0.f ? e0 * (r.x / di) : 0.f;
+            x0[i] = x1;
+            if (s0mode == 2) d0[i] = x1;
+        }
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        const double bn2 = tot[0] * S->iscale2;
+        S->bnorm2 = bn2;
+        S->thr2 = bn2 > 0.0 ? S->tol * S->tol * bn2 : (double)INFINITY;
+        S->iter = 0;
+        S->done = 0;
+        S->status = 0;
+        S->rnorm2_0 = bn2;
+        record_residual(S, bn2);
+    }
 }
 
 // z = z - c (free rows), zo = z, p = z + beta p, all FP32.

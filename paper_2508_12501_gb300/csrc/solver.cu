@@ -445,7 +445,10 @@ void enqueue_mean_shift(dec_mg *mg, double *v, cudaStream_t s, const int *skip) 
 }
 
 // z <- M r, then the dot products and the new search direction.
-void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStream_t s, const int *skip) {
+// first_pre0: the first iteration's finest first smoothing step already ran
+// (k_init_ff), as the fused ff update provides it on later iterations.
+void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStream_t s, const int *skip,
+                          bool first_pre0 = false) {
     DevLevel &F = mg->lv.back();
     const int gauge = mg->H.bc == DEC_BC_GAUGE;
     const int rg = red_grid(mg, F.n);
@@ -463,7 +466,8 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
         da.first = first ? 1 : 0;
         da.gauge = gauge;
         // after an ff update with the fused first smoothing step, the cycle starts at step 1
-        const bool pre0 = outer && !first && mode == DEC_MODE_MIXED_FF && o.nu1 > 0 && o.smoother != DEC_SMOOTH_MCGS;
+        const bool pre0 = (outer && !first && mode == DEC_MODE_MIXED_FF && o.nu1 > 0 && o.smoother != DEC_SMOOTH_MCGS) ||
+                          (first && first_pre0);
         float *z = cycle<float>(mg, top, F.b32, s, skip, pre0, outer ? &da : nullptr);
         if (!da.done) {
             ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
@@ -713,10 +717,23 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     const bool ff = o.mode == DEC_MODE_MIXED_FF;
     const int64_t launches0 = mg->launches;
     int64_t graph_launches = 0;
+    // A cold float-float solve (x = 0, so r = b) starts in two kernels: the
+    // gauge mean and the ff scale from one pass over b, then the shifted b as
+    // ff pairs with x = 0 and the first cycle's first smoothing step.
+    const bool cold_ff = ff && !o.warm_start;
+    const dec_mg_opts &mo = mg->H.opts;
+    int s0mode = 0;
+    float e0 = 0.f;
+    if (cold_ff && o.solver == DEC_SOLVER_MGPCG && (mo.fuse & DEC_FUSE_OUTER) && mo.nu1 > 0 &&
+        mo.smoother != DEC_SMOOTH_MCGS) {
+        const bool cheb = mo.smoother == DEC_SMOOTH_CHEBYSHEV;
+        s0mode = cheb && 1 < mo.nu1 ? 2 : 1;
+        e0 = (float)(cheb ? F.e_pre[0] : mo.omega);
+    }
     CK(cudaMemcpyAsync(mg->ob, b, vb, cudaMemcpyDeviceToDevice, s));
     if (o.warm_start)
         CK(cudaMemcpyAsync(mg->ox, x, vb, cudaMemcpyDeviceToDevice, s));
-    else
+    else if (!cold_ff)
         CK(cudaMemsetAsync(mg->ox, 0, vb, s));
     // scalar header (everything before the history)
     Scal *h = mg->scal_h;
@@ -725,7 +742,18 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     h->maxit = o.maxit;
     h->max_loops = o.maxit + 1;
     h->star0_sum = mg->star0_sum;
+    h->inv_star0_sum = mg->star0_sum > 0.0 ? 1.0 / mg->star0_sum : 0.0;
     CK(cudaMemcpyAsync(mg->scal, h, offsetof(Scal, hist), cudaMemcpyHostToDevice, s));
+    if (cold_ff) {
+        ProfScope p1(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s), p2(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
+        const bool mg_solver = o.solver == DEC_SOLVER_MG;
+        const int rg = red_grid(mg, F.n);
+        launch(mg, k_b_stats, rg, s, F.n, (const double *)F.star0, (const uint8_t *)F.freev, (const double *)mg->ob,
+               gauge ? 1 : 0, mg->partials, mg->counter, mg->scal);
+        launch(mg, k_init_ff, rg, s, F.n, (const uint8_t *)F.freev, mg->ob, mg->fxh, mg->fxl, F.b32, mg->frl,
+               mg_solver ? mg->fbh : nullptr, mg_solver ? mg->fbl : nullptr, s0mode, (const float *)F.dg32,
+               F.x32[0], F.d32[0], e0, mg->partials, mg->counter, mg->scal);
+    } else {
     if (gauge) {
         enqueue_mean_shift(mg, mg->ob, s, nullptr);
         if (o.warm_start) enqueue_mean_shift(mg, mg->ox, s, nullptr);
@@ -734,7 +762,8 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         enqueue_outer_init<float>(mg, F.b32, s);
     else
         enqueue_outer_init<double>(mg, (double *)nullptr, s);
-    if (ff) {
+    }
+    if (ff && !cold_ff) {
         ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
         const bool mg_solver = o.solver == DEC_SOLVER_MG;
         launch(mg, k_ff_split, grid_for(mg, F.n), s, F.n, o.warm_start ? (const double *)mg->ox : nullptr,
@@ -753,14 +782,15 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     }
     int64_t loop_runs = 0;
     if (lg) {
-        if (o.solver != DEC_SOLVER_MG) enqueue_precondition(mg, o.solver, o.mode, true, s, &mg->scal->done);
+        if (o.solver != DEC_SOLVER_MG)
+            enqueue_precondition(mg, o.solver, o.mode, true, s, &mg->scal->done, s0mode > 0);
         CK(cudaGraphLaunch(lg, s));
         loop_runs = 1;
     } else {
     CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (!h->done && o.maxit > 0) {
-        if (o.solver != DEC_SOLVER_MG) enqueue_precondition(mg, o.solver, o.mode, true, s, nullptr);
+        if (o.solver != DEC_SOLVER_MG) enqueue_precondition(mg, o.solver, o.mode, true, s, nullptr, s0mode > 0);
         cudaGraphExec_t ge;
         rc = iteration_graph(mg, o.solver, o.mode, &ge);
         if (rc) return rc;
@@ -779,12 +809,24 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     }
     }
     if (ff) {
-        ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
-        launch(mg, k_ff_join, grid_for(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl, mg->ox,
-               (const Scal *)mg->scal);
+        // x = (hi + lo) / scale straight into the caller's x (and ox); with the
+        // gauge, the mean of x comes out of the same pass
+        const int top = (int)mg->lv.size() - 1;
+        if (gauge) {
+            ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
+            launch(mg, k_ff_join_mean, red_grid(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl,
+                   mg->ox, (const double *)F.star0, (const uint8_t *)F.freev, mg->partials, mg->counter, mg->scal);
+            launch(mg, k_shift_out, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, mg->ox, x,
+                   (const Scal *)mg->scal);
+        } else {
+            ProfScope p1(mg, DEC_PK_AUX, top, s);
+            launch(mg, k_ff_join, grid_for(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl, mg->ox,
+                   x, (const Scal *)mg->scal);
+        }
+    } else {
+        if (gauge) enqueue_mean_shift(mg, mg->ox, s, nullptr);
+        CK(cudaMemcpyAsync(x, mg->ox, vb, cudaMemcpyDeviceToDevice, s));
     }
-    if (gauge) enqueue_mean_shift(mg, mg->ox, s, nullptr);
-    CK(cudaMemcpyAsync(x, mg->ox, vb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
