@@ -311,6 +311,14 @@ int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_stream_t str
  * or DEC_ERR_NONFINITE; stats may be null. */
 int dec_solve(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts,
               dec_stats *stats, dec_stream_t stream);
+/* dec_solve_host: dec_solve with b and x in HOST memory (nv(finest) doubles
+ * each, pinned or pageable; pinned memory lets the copies run as DMA).  b is
+ * copied straight into the solver's own right-hand side and the result out
+ * of its own iterate (x is read first when opts->warm_start), so the call
+ * makes no device copy of either; it returns once x holds the result.  Same
+ * options, status codes and gauge handling as dec_solve. */
+int dec_solve_host(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts, dec_stats *stats,
+                   dec_stream_t stream);
 
 /* dec_solve_backward: adjoint of x = L^-1 b.  Given u = L^-1 b and
  * grad_u = dJ/du (device, [nv]), solve L mu = *0^-1 grad_u with the same

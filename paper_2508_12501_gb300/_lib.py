@@ -107,6 +107,7 @@ _SIGS = {
     "dec_residual": (_i, [_p, _i, _p, _p, _p, _i, _i, _p]),
     "dec_mg_vcycle": (_i, [_p, _p, _p, _i, _i, _p]),
     "dec_solve": (_i, [_p, _p, _p, _i, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
+    "dec_solve_host": (_i, [_p, _p, _p, _i, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_solve_backward": (_i, [_p, _p, _p, _p, _p, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_mg_profile": (_i, [_p, _i]),
     "dec_mg_vcycle_noalloc": (_i, [_p, _p, _p, _p]),

@@ -172,12 +172,13 @@ class Hierarchy:
         return out
 
     # ---- device calls ----------------------------------------------------
-    def _vec(self, t, n, dtypes, name):
+    def _vec(self, t, n, dtypes, name, device=None):
         torch = _torch()
         if not isinstance(t, torch.Tensor):
             raise TypeError(f"{name} must be a torch tensor")
-        if t.device != self.device:
-            raise ValueError(f"{name} must live on {self.device}")
+        dev = self.device if device is None else device
+        if t.device != dev:
+            raise ValueError(f"{name} must live on {dev}")
         if t.dtype not in dtypes:
             raise TypeError(f"{name} has dtype {t.dtype}")
         if t.numel() != n or not t.is_contiguous():
@@ -235,28 +236,26 @@ class Hierarchy:
               check_every=1, raise_on_fail=True, host_loop=False):
         """Solve L x = b on the finest level; returns (x, SolveStats).
 
-        b may be a CUDA or a CPU float64 tensor; a CPU input is copied to the
-        device and the result copied back (the host-buffer entry point).
+        b may be a CUDA or a CPU float64 tensor.  A CPU b goes through
+        dec_solve_host: b is copied into the solver and the result into x, a
+        CPU tensor (the one given, else a new one); pinned b and x make the
+        copies DMA transfers.
         """
         torch = _torch()
         host = b.device.type == "cpu"
-        if host:
-            b = b.to(self.device, non_blocking=True)
-            if x is not None:
-                x = x.to(self.device, non_blocking=True)
+        cpu = torch.device("cpu")
         if x is None:
-            x = torch.empty_like(b)
+            x = torch.empty(self.n, dtype=torch.float64, device=cpu if host else self.device)
             warm_start = False
-        pb = self._vec(b, self.n, (torch.float64,), "b")
-        px = self._vec(x, self.n, (torch.float64,), "x")
+        pb = self._vec(b, self.n, (torch.float64,), "b", cpu if host else None)
+        px = self._vec(x, self.n, (torch.float64,), "x", cpu if host else None)
         o = self._solve_opts(solver, mode, tol, maxit, warm_start, check_every, host_loop)
         st = L.dec_stats()
-        rc = lib.dec_solve(self._h, pb, px, 1, C.byref(o), C.byref(st), self._stream())
+        fn = lib.dec_solve_host if host else lib.dec_solve
+        rc = fn(self._h, pb, px, 1, C.byref(o), C.byref(st), self._stream())
         if rc not in (L.DEC_OK, L.DEC_ERR_NOT_CONVERGED) or (raise_on_fail and rc != L.DEC_OK):
-            check(rc, "dec_solve")
+            check(rc, "dec_solve_host" if host else "dec_solve")
         stats = SolveStats(st.iters, st.rel_res, st.rel_res0, rc, st.launches)
-        if host:
-            x = x.cpu()
         return x, stats
 
     def solve_backward(self, u, grad_u, want_star1=True, solver="mgpcg", mode="mixed", tol=1e-8, maxit=100,

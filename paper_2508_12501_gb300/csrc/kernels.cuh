@@ -874,8 +874,9 @@ static __global__ void __launch_bounds__(kThreads, 8) k_shift(int n, const uint8
 }
 
 // Initial residual of the outer iteration: r = b - L x, ||r||^2, ||b||^2 (free rows);
-// also writes the cycle's input rv (cast) when rv != nullptr.
-template <int KT, typename TV>
+// also writes the cycle's input rv (cast) when rv != nullptr.  X0: x = 0, so
+// r = b without the operator apply.
+template <int KT, typename TV, bool X0 = false>
 __global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w, const uint8_t *__restrict__ freev,
                                                         const double *__restrict__ b, const double *__restrict__ x,
@@ -884,8 +885,11 @@ __global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const 
     pdl_prologue();
     double acc[2] = {0.0, 0.0};
     GRID_STRIDE(i, n) {
-        double s, d;
-        row_apply<double, KT>(i, n, K, col, w, x, s, d);
+        double s = 0.0;
+        if (!X0) {
+            double d;
+            row_apply<double, KT>(i, n, K, col, w, x, s, d);
+        }
         double bi = freev[i] ? ldg(b + i) : 0.0;
         double ri = freev[i] ? bi - s : 0.0;
         r[i] = ri;
@@ -1336,7 +1340,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_ff_join_mean(int n, cons
     if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] * S->inv_star0_sum;
 }
 
-// v <- v - mean on free rows, 0 on fixed rows, also into out.
+// v <- v - mean on free rows, 0 on fixed rows, also into out when given.
 static __global__ void __launch_bounds__(kThreads, 8) k_shift_out(int n, const uint8_t *__restrict__ freev,
                                                        double *__restrict__ v, double *__restrict__ out,
                                                        const Scal *S) {
@@ -1345,7 +1349,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_shift_out(int n, const u
     GRID_STRIDE(i, n) {
         const double y = freev[i] ? v[i] - m : 0.0;
         v[i] = y;
-        out[i] = y;
+        if (out) out[i] = y;
     }
 }
 

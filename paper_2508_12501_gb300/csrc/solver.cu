@@ -425,14 +425,19 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
 // outer iterations
 // ---------------------------------------------------------------------------
 
+// x0: the iterate is zero (a cold start), so r = b without the operator apply.
 template <typename TV>
-void enqueue_outer_init(dec_mg *mg, TV *rv, cudaStream_t s) {
+void enqueue_outer_init(dec_mg *mg, TV *rv, cudaStream_t s, bool x0) {
     DevLevel &F = mg->lv.back();
     ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        launch(mg, k_outer_init<KT, TV>, red_grid(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox,
-                                                                    mg->orr, rv, mg->partials, mg->counter, mg->scal);
+        if (x0)
+            launch(mg, k_outer_init<KT, TV, true>, red_grid(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob,
+                   mg->ox, mg->orr, rv, mg->partials, mg->counter, mg->scal);
+        else
+            launch(mg, k_outer_init<KT, TV, false>, red_grid(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob,
+                   mg->ox, mg->orr, rv, mg->partials, mg->counter, mg->scal);
     });
 }
 
@@ -697,8 +702,11 @@ int loop_graph(dec_mg *mg, int solver, int mode, cudaGraphExec_t *out) {
     return DEC_OK;
 }
 
+// b_host / x_host: b and x are host arrays (pinned or pageable): b is copied
+// straight into the solver's right-hand side and the result out of its
+// iterate, so no device copy of either is made.
 int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po, dec_stats *stats,
-               cudaStream_t s) {
+               cudaStream_t s, bool b_host = false, bool x_host = false) {
     dec_solve_opts o;
     if (po)
         o = *po;
@@ -730,9 +738,9 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         s0mode = cheb && 1 < mo.nu1 ? 2 : 1;
         e0 = (float)(cheb ? F.e_pre[0] : mo.omega);
     }
-    CK(cudaMemcpyAsync(mg->ob, b, vb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(mg->ob, b, vb, b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     if (o.warm_start)
-        CK(cudaMemcpyAsync(mg->ox, x, vb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(mg->ox, x, vb, x_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     else if (!cold_ff)
         CK(cudaMemsetAsync(mg->ox, 0, vb, s));
     // scalar header (everything before the history)
@@ -759,9 +767,9 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         if (o.warm_start) enqueue_mean_shift(mg, mg->ox, s, nullptr);
     }
     if (mixed)
-        enqueue_outer_init<float>(mg, F.b32, s);
+        enqueue_outer_init<float>(mg, F.b32, s, !o.warm_start);
     else
-        enqueue_outer_init<double>(mg, (double *)nullptr, s);
+        enqueue_outer_init<double>(mg, (double *)nullptr, s, !o.warm_start);
     }
     if (ff && !cold_ff) {
         ProfScope ps(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
@@ -816,17 +824,25 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
             ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
             launch(mg, k_ff_join_mean, red_grid(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl,
                    mg->ox, (const double *)F.star0, (const uint8_t *)F.freev, mg->partials, mg->counter, mg->scal);
-            launch(mg, k_shift_out, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, mg->ox, x,
-                   (const Scal *)mg->scal);
+            launch(mg, k_shift_out, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, mg->ox,
+                   x_host ? nullptr : x, (const Scal *)mg->scal);
         } else {
             ProfScope p1(mg, DEC_PK_AUX, top, s);
             launch(mg, k_ff_join, grid_for(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl, mg->ox,
-                   x, (const Scal *)mg->scal);
+                   x_host ? nullptr : x, (const Scal *)mg->scal);
         }
-    } else {
-        if (gauge) enqueue_mean_shift(mg, mg->ox, s, nullptr);
+    } else if (gauge) {
+        // the mean shift writes the caller's x as it goes
+        const int top = (int)mg->lv.size() - 1;
+        ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
+        launch(mg, k_mean, red_grid(mg, F.n), s, F.n, F.star0, F.freev, (const double *)mg->ox, mg->partials,
+               mg->counter, mg->scal, (const int *)nullptr);
+        launch(mg, k_shift_out, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, mg->ox,
+               x_host ? nullptr : x, (const Scal *)mg->scal);
+    } else if (!x_host) {
         CK(cudaMemcpyAsync(x, mg->ox, vb, cudaMemcpyDeviceToDevice, s));
     }
+    if (x_host) CK(cudaMemcpyAsync(x, mg->ox, vb, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h, mg->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
@@ -1522,6 +1538,13 @@ int dec_solve(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opt
     if (int rc = check_dev(mg)) return rc;
     if (!b || !x || k != 1) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
     return solve_impl(mg, b, x, opts, stats, (cudaStream_t)stream);
+}
+
+int dec_solve_host(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts, dec_stats *stats,
+                   dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    if (!b || !x || k != 1) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    return solve_impl(mg, b, x, opts, stats, (cudaStream_t)stream, true, true);
 }
 
 int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double *grad_b, double *grad_star1,

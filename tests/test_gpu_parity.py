@@ -170,6 +170,24 @@ def test_host_buffers_and_warm_start():
     assert st2.iters <= 1 and st2.rel_res0 <= 1e-8
 
 
+@pytest.mark.parametrize("name", ["ico5", "square5"])
+@pytest.mark.parametrize("mode", ["f64", "mixed", "mixed_ff"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_matches_device(name, mode, pinned):
+    # dec_solve_host runs the same kernels on copies of b and x: bitwise the device solve
+    h, oh = _pair(name)
+    b = W.uniform_field(oh.finest.mesh.nv, 43)
+    bh = torch.as_tensor(b)
+    if pinned:
+        bh = bh.pin_memory()
+    xd, sd = h.solve(_dev(b), mode=mode, tol=1e-10)
+    xh, sh = h.solve(bh, mode=mode, tol=1e-10)
+    assert xh.device.type == "cpu" and sh.iters == sd.iters and torch.equal(xh, xd.cpu())
+    x0 = xh.clone().pin_memory() if pinned else xh.clone()
+    x2, s2 = h.solve(bh, x0, warm_start=True, mode=mode, tol=1e-10)
+    assert x2 is x0 and s2.iters <= 1 and s2.rel_res <= 1e-10
+
+
 def test_error_paths():
     P = _lib()
     h, oh = _pair("ico5")
