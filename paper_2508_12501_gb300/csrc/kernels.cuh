@@ -647,16 +647,20 @@ __device__ __forceinline__ float2 warps_sum(float2 v) {
 }
 
 // Block arrival: true in every thread of the block that arrives last.
+// Thread 0 wrote the block's partials; its acquire-release add on the
+// counter publishes them (release) and, in the last block, makes every
+// other block's partials visible to it (acquire, through the release
+// sequence of the counter's read-modify-writes).  The block barrier then
+// orders the other threads' reads of the partials (at L2, ld.cg) after it.
 __device__ __forceinline__ bool last_block(unsigned *counter) {
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(counter, 1u);
+        unsigned t;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(t) : "l"(counter) : "memory");
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (last) __threadfence();
     return last;
 }
 
