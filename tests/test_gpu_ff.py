@@ -164,3 +164,35 @@ def test_kernel_timer(smoother):
             h.time_kernel(**bad)
     b = torch.as_tensor(W.uniform_field(n, 3), device="cuda")
     assert h.solve(b, mode="mixed_ff", tol=1e-10)[1].rel_res <= 1e-10
+
+
+@pytest.mark.parametrize("bc", ["gauge", "dirichlet"])
+@pytest.mark.parametrize("solver", ["mg", "mgpcg"])
+def test_ff_cold_start_edges(bc, solver):
+    # the two-kernel cold start (x = 0): b = 0, maxit = 0, a NaN on a free row, and agreement with a
+    # warm start from x = 0, which forms r = b - L x and splits it the general way
+    P = _lib()
+    if bc == "gauge":
+        v, t = W.icosahedron()
+        h = P.Hierarchy(P.Mesh(v, t), 5, 4, bc="gauge", sphere=True, smoother="chebyshev")
+    else:
+        v, t = W.unit_square()
+        h = P.Hierarchy(P.Mesh(v, t), 6, 5, bc="dirichlet", smoother="chebyshev")
+    n = h.n
+    z, st = h.solve(torch.zeros(n, dtype=torch.float64, device="cuda"), solver=solver, mode="mixed_ff")
+    assert st.status == 0 and st.iters == 0 and torch.count_nonzero(z) == 0
+    b = _dev(W.uniform_field(n, 99))
+    x0, st0 = h.solve(b, solver=solver, mode="mixed_ff", maxit=0, raise_on_fail=False)
+    assert st0.status == 5 and st0.iters == 0 and torch.count_nonzero(x0) == 0 and st0.rel_res == st0.rel_res0 == 1.0
+    free = np.flatnonzero(h.table(-1, "free"))
+    bn = b.clone()
+    bn[int(free[len(free) // 2])] = float("nan")
+    with pytest.raises(P.DecError) as ei:
+        h.solve(bn, solver=solver, mode="mixed_ff")
+    assert ei.value.code == 6
+    xc, sc = h.solve(b, solver=solver, mode="mixed_ff", tol=1e-10)
+    xw, sw = h.solve(b, torch.zeros(n, dtype=torch.float64, device="cuda"), solver=solver, mode="mixed_ff", tol=1e-10,
+                     warm_start=True)
+    assert sc.status == sw.status == 0 and sc.iters == sw.iters
+    s0 = h.table(-1, "star0")
+    assert _s0_rel(s0, xc.cpu().numpy(), xw.cpu().numpy()) < 1e-8
