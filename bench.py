@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -156,7 +157,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples; the JSON line carries their summary
+        self.path = os.path.join(os.environ.get("DEC_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"dec_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
