@@ -17,7 +17,8 @@ Readings (the paper leaves the discrete operators implicit):
   * heat equation dT/dt = -(1/phi) L_q T + kappa Delta T = -(1/phi) L_q T - kappa L T,
     with the bc mask setting dT/dt = 0 on the top and bottom rows;
   * kappa = (1/Ra) g alpha rho0 k_eta dT y_max / phi (Sec. 3.2.2);
-  * time stepping: forward Euler with a fixed dt (the paper uses adaptive Tsit5).
+  * time stepping: forward Euler with a fixed dt here; the paper's adaptive
+    Tsit5 integration of the same right-hand side (tdot_fn) is oracle/rk.py.
 The adjoint restates reverse-mode differentiation of that step; its
 derivation is in the docstring of `step_adjoint`.  Parity beyond the pins in
 tests/test_oracle_porous.py (conductive equilibrium, linear-field Lie
@@ -108,6 +109,15 @@ class _One:
 def solve_pressure(lev, rhs):
     """*0-mean-zero solution of the pure-Neumann pressure problem (direct solve)."""
     return direct_solve(_One(lev), rhs)
+
+
+def tdot_fn(lev, pot, fixed, prm):
+    """f(T) = dT/dt of the method of lines (Sec. 3.2.1), the pressure solved directly:
+    the right-hand side the adaptive integrator (oracle/rk.py) advances."""
+    def f(T):
+        P = solve_pressure(lev, pressure_rhs(lev, T, pot))
+        return tdot(lev, T, P, pot, fixed, prm)
+    return f
 
 
 def step(lev, T, pot, fixed, prm):
