@@ -423,7 +423,33 @@ void dec_porous_default_params(dec_porous_params *prm);
 int dec_porous_step(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const dec_porous_params *prm,
                     int nsteps, double *checkpoints, int ckpt_every, dec_stats *stats, dec_stream_t stream);
 
-/* dec_porous_backward: reverse-mode derivative of T_N = step^N(T_0):
+/* dec_porous_rk: adaptive explicit integration of the same model from t = 0
+ * to t_end, in place: Tsitouras' 5(4) Runge-Kutta pair, the "Tsit5" method
+ * of Sec. 3.2.2.  Seven stages, the last evaluated at the new state and
+ * reused as the next step's first, so a step costs six right-hand sides,
+ * each an MG-PCG pressure solve warm-started from P.  Error norm: the root
+ * mean square over all vertices of err_v / (atol + rtol max(|T_v|, |T_new_v|));
+ * a step is accepted when it is <= 1; the next step is dt * min(10, max(0.2,
+ * 0.9 norm^(-1/5))), at most dt right after a rejection; the last step ends
+ * exactly at t_end.  dt0: first step (fixed_step != 0: every step, no error
+ * control).  P: warm start on entry, the pressure of the final T on exit.
+ * prm as for dec_porous_step, prm->dt ignored.  stats (nullable): accepted
+ * and rejected steps, right-hand-side evaluations, the time reached, the next
+ * step, pressure iterations summed and the worst final pressure residual.
+ * Errors: DEC_ERR_ARG; DEC_ERR_NOT_CONVERGED when max_steps attempts end
+ * before t_end (T is the state at stats->t); DEC_ERR_NONFINITE; the errors of
+ * dec_solve.  Synchronizes `stream` once per step. */
+typedef struct dec_rk_stats {
+    int64_t naccept, nreject, nfev;
+    double t, dt;
+    int64_t pressure_iters;
+    double pressure_rel_res;
+} dec_rk_stats;
+int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const dec_porous_params *prm,
+                  double t_end, double dt0, double rtol, double atol, int64_t max_steps, int fixed_step,
+                  dec_rk_stats *stats, dec_stream_t stream);
+
+/* dec_porous_backward: reverse-mode derivative of T_N = step^N(T_0):/* dec_porous_backward: reverse-mode derivative of T_N = step^N(T_0):
  * given grad_TN = dF/dT_N, writes grad_T0 = dF/dT_0.  Checkpoints every
  * ckpt_every steps are kept on the device and each segment is recomputed
  * forward before it is differentiated (memory: (nsteps/ckpt_every + 2 *

@@ -64,6 +64,11 @@ PROF_KINDS = ["smooth0", "smooth", "residual", "restrict", "prolong", "coarse", 
               "smoothdots", "coarsecycle"]
 
 
+class dec_rk_stats(C.Structure):
+    _fields_ = [("naccept", C.c_int64), ("nreject", C.c_int64), ("nfev", C.c_int64), ("t", C.c_double),
+                ("dt", C.c_double), ("pressure_iters", C.c_int64), ("pressure_rel_res", C.c_double)]
+
+
 class dec_porous_params(C.Structure):
     _fields_ = [("g", C.c_double * 3), ("alpha_rho0", C.c_double), ("phi", C.c_double), ("k_eta", C.c_double),
                 ("kappa", C.c_double), ("dt", C.c_double), ("tol", C.c_double), ("mode", C.c_int),
@@ -121,6 +126,8 @@ _SIGS = {
                             C.POINTER(C.c_double), _p]),
     "dec_batch_time_smooth": (_i, [_p, _i, C.POINTER(C.c_double), C.POINTER(C.c_double), _p]),
     "dec_porous_default_params": (None, [C.POINTER(dec_porous_params)]),
+    "dec_porous_rk": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), C.c_double, C.c_double, C.c_double,
+                           C.c_double, C.c_int64, _i, C.POINTER(dec_rk_stats), _p]),
     "dec_porous_step": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _p, _i, C.POINTER(dec_stats), _p]),
     "dec_porous_backward": (_i, [_p, _p, _p, _p, C.POINTER(dec_porous_params), _i, _i, _p, _p,
                                  C.POINTER(dec_stats), _p]),

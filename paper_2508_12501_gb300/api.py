@@ -329,6 +329,22 @@ class Hierarchy:
                                   C.byref(st), self._stream()), "dec_porous_step")
         return SolveStats(st.iters, st.rel_res, st.rel_res0, 0, st.launches)
 
+    def porous_rk(self, T, P, fixed, t_end, dt0, rtol=1e-9, atol=1e-6, max_steps=10 ** 7, fixed_step=False,
+                  **params):
+        """Integrate the porous model adaptively (Tsit5, dec_porous_rk) from 0 to t_end, T and P in place.
+
+        Returns a dict: naccept, nreject, nfev, t, dt, pressure_iters, pressure_rel_res."""
+        torch = _torch()
+        pT = self._vec(T, self.n, (torch.float64,), "T")
+        pP = self._vec(P, self.n, (torch.float64,), "P")
+        pf = self._vec(fixed, self.n, (torch.uint8,), "fixed")
+        prm = self._porous_params(dt0, **params)
+        st = L.dec_rk_stats()
+        check(lib.dec_porous_rk(self._h, pT, pP, pf, C.byref(prm), float(t_end), float(dt0), float(rtol),
+                                float(atol), int(max_steps), 1 if fixed_step else 0, C.byref(st), self._stream()),
+              "dec_porous_rk")
+        return {k: getattr(st, k) for k, _ in L.dec_rk_stats._fields_}
+
     def porous_backward(self, T0, P0, fixed, nsteps, grad_TN, dt, ckpt_every=100, **params):
         """dF/dT0 of T_N = step^N(T0) given dF/dT_N (checkpointed recomputation)."""
         torch = _torch()

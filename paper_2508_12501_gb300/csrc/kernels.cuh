@@ -1675,6 +1675,78 @@ __global__ void __launch_bounds__(kThreads) k_porous_update(int n, int K, const 
     }
 }
 
+// dT/dt = mask * ( -(1/phi) L_q T - kappa L T ): the bracket of k_porous_update,
+// the right-hand side an explicit Runge-Kutta stage evaluates.
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_porous_tdot(int n, int K, const int32_t *__restrict__ col,
+                                                         const double *__restrict__ w, const double *__restrict__ T,
+                                                         const double *__restrict__ P, const double *__restrict__ pot,
+                                                         const uint8_t *__restrict__ fixed, double inv_phi,
+                                                         double k_eta, double kappa, double *__restrict__ out) {
+    pdl_prologue();
+    const int Kk = KT > 0 ? KT : K;
+    GRID_STRIDE(v, n) {
+        if (fixed[v]) {
+            out[v] = 0.0;
+            continue;
+        }
+        const double Tv = ldg(T + v), Pv = ldg(P + v), pv = ldg(pot + v);
+        double adv = 0.0, dif = 0.0;
+#pragma unroll
+        for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+            if (KT == 0 && k >= Kk) break;
+            const size_t o = (size_t)k * n + v;
+            const int u = ldg(col + o);
+            const double wk = ldg(w + o);
+            const double Tu = ldg(T + u);
+            const double q = -k_eta * ((ldg(P + u) - Pv) - (ldg(pot + u) - pv) * 0.5 * (Tu + Tv));
+            adv += wk * 0.5 * (Tu - Tv) * q;
+            dif += wk * (Tv - Tu);
+        }
+        out[v] = -inv_phi * adv - kappa * dif;
+    }
+}
+
+// Up to seven stage vectors with their coefficients (explicit Runge-Kutta).
+struct RkStages {
+    const double *k[7];
+    double a[7];
+    int nk;
+};
+
+// y = T + dt * sum_j a_j k_j (a stage state, or the new state).
+static __global__ void __launch_bounds__(kThreads) k_rk_combine(int n, const double *__restrict__ T,
+                                                        const __grid_constant__ RkStages c, double dt,
+                                                        double *__restrict__ y) {
+    pdl_prologue();
+    GRID_STRIDE(v, n) {
+        double s = 0.0;
+        for (int j = 0; j < c.nk; ++j) s = fma(c.a[j], ldg(c.k[j] + v), s);
+        y[v] = ldg(T + v) + dt * s;
+    }
+}
+
+// Embedded error estimate err = dt * sum_j e_j k_j, scaled componentwise by
+// atol + rtol max(|T|, |T_new|); *out = the sum of the squares (FP64).
+static __global__ void __launch_bounds__(kThreads, 8) k_rk_error(int n, const double *__restrict__ T,
+                                                          const double *__restrict__ Tn,
+                                                          const __grid_constant__ RkStages e, double dt,
+                                                          double rtol, double atol, double *partials,
+                                                          unsigned *counter, double *out) {
+    pdl_prologue();
+    double acc[1] = {0.0};
+    GRID_STRIDE(v, n) {
+        double s = 0.0;
+        for (int j = 0; j < e.nk; ++j) s = fma(e.a[j], ldg(e.k[j] + v), s);
+        const double err = dt * s;
+        const double sc = atol + rtol * fmax(fabs(ldg(T + v)), fabs(ldg(Tn + v)));
+        const double r = err / sc;
+        acc[0] = fma(r, r, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
 // Adjoint step, part 1: ms = mu / *0 with mu = dt * mask * lam.
 static __global__ void __launch_bounds__(kThreads) k_porous_adj1(int n, const double *__restrict__ lam,
                                                          const uint8_t *__restrict__ fixed,

@@ -1886,6 +1886,151 @@ int dec_porous_step(dec_mg *mg, double *T, double *P, const uint8_t *fixed, cons
     return DEC_OK;
 }
 
+// Tsitouras' 5(4) pair (Ch. Tsitouras, Comput. Math. Appl. 62 (2011) 770-775),
+// the "Tsit5" integrator of Sec. 3.2.2: nodes, strictly lower coupling
+// coefficients (row 6 doubles as the 5th-order weights: first same as last)
+// and the error weights of the embedded 4th-order solution.
+constexpr double kTsC[7] = {0.0, 0.161, 0.327, 0.9, 0.9800255409045097, 1.0, 1.0};
+constexpr double kTsA[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {0.161, 0, 0, 0, 0, 0},
+    {-0.008480655492356989, 0.335480655492357, 0, 0, 0, 0},
+    {2.897153057105493, -6.359448489975075, 4.3622954328695815, 0, 0, 0},
+    {5.325864828439257, -11.748883564062828, 7.4955393428898365, -0.09249506636175525, 0, 0},
+    {5.86145544294642, -12.92096931784711, 8.159367898576159, -0.071584973281401, -0.028269050394068383, 0},
+    {0.09646076681806523, 0.01, 0.4798896504144996, 1.379008574103742, -3.290069515436081, 2.324710524099774}};
+constexpr double kTsE[7] = {-0.00178001105222577714, -0.0008164344596567469, 0.007880878010261995,
+                            -0.1447110071732629,     0.5823571654525552,     -0.45808210592918697,
+                            1.0 / 66.0};
+
+// k = f(Y): the pressure of Y (MG-PCG, warm-started from P), then dT/dt.
+int porous_rate(PorousRun &R, const double *Y, double *P, double *k) {
+    dec_mg *mg = R.mg;
+    DevLevel &F = mg->lv.back();
+    const int g = grid_for(mg, F.n);
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        launch(mg, k_porous_rhs<KT>, g, R.s, F.n, F.K, F.col, F.w64, Y, mg->pot, mg->prhs);
+    });
+    dec_stats st{};
+    int rc = solve_impl(mg, mg->prhs, P, &R.so, &st, R.s);
+    if (rc != DEC_OK) decimpl::set_error("pressure solve: " + std::string(dec_last_error()));
+    R.iters += st.iters;
+    R.worst = std::max(R.worst, st.rel_res);
+    R.launches += st.launches + 2;
+    if (rc != DEC_OK) return rc;
+    dispatch_k(F.K, [&](auto kt) {
+        constexpr int KT = decltype(kt)::value;
+        launch(mg, k_porous_tdot<KT>, g, R.s, F.n, F.K, F.col, F.w64, Y, (const double *)P, mg->pot, R.fixed,
+               1.0 / R.prm.phi, R.prm.k_eta, R.prm.kappa, k);
+    });
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
+
+int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const dec_porous_params *prm,
+                  double t_end, double dt0, double rtol, double atol, int64_t max_steps, int fixed_step,
+                  dec_rk_stats *stats, dec_stream_t stream) {
+    if (int rc = check_dev(mg)) return rc;
+    dec_porous_params p;
+    if (prm)
+        p = *prm;
+    else
+        dec_porous_default_params(&p);
+    p.dt = dt0;
+    PorousRun R{mg, (cudaStream_t)stream, {}, fixed, {}};
+    if (int rc = porous_check(mg, &p, R.prm)) return rc;
+    if (!T || !P || !fixed || !(t_end >= 0.0) || !std::isfinite(t_end) || !(rtol >= 0.0) || !(atol >= 0.0) ||
+        (!fixed_step && !(rtol > 0.0 || atol > 0.0)) || max_steps < 1)
+        return fail(Status::fail(DEC_ERR_ARG, "bad argument (T, P, fixed, t_end, dt0, rtol, atol, max_steps)"));
+    dec_solve_default_opts(&R.so);
+    R.so.mode = R.prm.mode;
+    R.so.tol = R.prm.tol;
+    R.so.maxit = R.prm.maxit;
+    R.so.warm_start = 1;
+    DevLevel &F = mg->lv.back();
+    const int n = F.n;
+    const size_t vb = sizeof(double) * n;
+    // device work: the seven stage rates, the next state and one scalar
+    double *work = nullptr;
+    cudaError_t ce = cudaMalloc(&work, 8 * vb + sizeof(double));
+    if (ce != cudaSuccess)
+        return ce == cudaErrorMemoryAllocation ? fail(Status::fail(DEC_ERR_OOM, "cudaMalloc")) : cuda_fail(ce, "cudaMalloc");
+    double *k[7];
+    for (int j = 0; j < 7; ++j) k[j] = work + (size_t)j * n;
+    double *nxt = work + (size_t)7 * n, *esum = work + (size_t)8 * n;
+    double *cur = T;
+    dec_rk_stats out{};
+    const int g = grid_for(mg, n), rg = red_grid(mg, n);
+    auto finish = [&](int code) {
+        if ((code == DEC_OK || code == DEC_ERR_NOT_CONVERGED) && cur != T) {
+            cudaError_t e = cudaMemcpyAsync(T, cur, vb, cudaMemcpyDeviceToDevice, R.s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(R.s);
+            if (e != cudaSuccess) code = cuda_fail(e, "dec_porous_rk");
+        }
+        cudaFree(work);
+        out.pressure_iters = R.iters;
+        out.pressure_rel_res = R.worst;
+        if (stats) *stats = out;
+        return code;
+    };
+    porous_potential(R);
+    if (int rc = porous_rate(R, cur, P, k[0])) return finish(rc);
+    out.nfev = 1;
+    double t = 0.0, dt = dt0;
+    const double slack = 1e-12 * t_end;
+    bool rejected_last = false;
+    while (t < t_end && out.naccept + out.nreject < max_steps) {
+        const bool last = dt >= t_end - t - slack;
+        const double h = last ? t_end - t : dt;
+        // stages 2..7; stage 7's state is the new state (first same as last)
+        for (int i = 1; i < 7; ++i) {
+            RkStages c{};
+            for (int j = 0; j < i; ++j) {
+                c.k[j] = k[j];
+                c.a[j] = kTsA[i][j];
+            }
+            c.nk = i;
+            double *y = i < 6 ? mg->ptmp : nxt;
+            launch(mg, k_rk_combine, g, R.s, n, (const double *)cur, c, h, y);
+            if (int rc = porous_rate(R, y, P, k[i])) return finish(rc);
+        }
+        out.nfev += 6;
+        RkStages e{};
+        for (int j = 0; j < 7; ++j) {
+            e.k[j] = k[j];
+            e.a[j] = kTsE[j];
+        }
+        e.nk = 7;
+        launch(mg, k_rk_error, rg, R.s, n, (const double *)cur, (const double *)nxt, e, h, rtol, atol,
+               mg->partials, mg->counter, esum);
+        double ssum = 0.0;
+        CK(cudaMemcpyAsync(&ssum, esum, sizeof(double), cudaMemcpyDeviceToHost, R.s));
+        CK(cudaStreamSynchronize(R.s));
+        const double en = std::sqrt(ssum / (double)n);
+        if (!std::isfinite(en) && !fixed_step) return finish(fail(Status::fail(DEC_ERR_NONFINITE, "non-finite step error")));
+        if (fixed_step || en <= 1.0) {
+            t = last ? t_end : t + h;
+            std::swap(cur, nxt);
+            std::swap(k[0], k[6]);
+            out.naccept += 1;
+            if (!fixed_step) {
+                const double grow = rejected_last ? 1.0 : 10.0;
+                dt = h * (en == 0.0 ? grow : std::min(grow, std::max(0.2, 0.9 * std::pow(en, -0.2))));
+            }
+            rejected_last = false;
+        } else {
+            out.nreject += 1;
+            dt = h * std::max(0.2, 0.9 * std::pow(en, -0.2));
+            rejected_last = true;
+        }
+    }
+    out.t = t;
+    out.dt = dt;
+    if (t < t_end) return finish(fail(Status::fail(DEC_ERR_NOT_CONVERGED, "max_steps reached before t_end")));
+    return finish(DEC_OK);
+}
+
 int dec_porous_backward(dec_mg *mg, const double *T0, const double *P0, const uint8_t *fixed,
                         const dec_porous_params *prm, int nsteps, int ckpt_every, const double *grad_TN,
                         double *grad_T0, dec_stats *stats, dec_stream_t stream) {

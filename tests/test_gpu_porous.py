@@ -123,3 +123,107 @@ def test_full_size_rollout_and_flux_gradient():
         fd = (F(T0 + eps * d) - F(T0 - eps * d)) / (2 * eps)
         an = float((g0 * d).sum())
         assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def _paper_T0(xy):
+    # the paper's initial state (Sec. 3.2.2): 400 x the Gaussian of mean the centre and covariance I/2,
+    # top wall at -100 and bottom wall at +100
+    T0 = W.gaussian_initial_T(xy, (0.5, 0.5))
+    return np.where(xy[:, 1] == 1.0, -100.0, np.where(xy[:, 1] == 0.0, 100.0, T0))
+
+
+def _rk_pair(nsub, nlevels):
+    from oracle import rk  # noqa: F401  (imported for the callers)
+    h, xy, fixed = _setup(nsub, nlevels)
+    lev = _oracle_level(nsub)
+    prm = por.PorousParams()
+    pot = por.potential(xy, prm)
+    return h, xy, fixed, lev, prm, pot
+
+
+@pytest.mark.parametrize("nsub", [3, 4])
+def test_rk_fixed_steps_match_oracle(nsub):
+    from oracle import rk
+    h, xy, fixed, lev, prm, pot = _rk_pair(nsub, 3)
+    T0 = _paper_T0(xy)
+    dt = 2e-4 if nsub == 3 else 5e-5
+    ref, rst = rk.integrate(por.tdot_fn(lev, pot, fixed, prm), T0, 5 * dt, dt, 1.0, 1.0, fixed_step=True)
+    T = torch.as_tensor(T0, device="cuda")
+    P = torch.zeros_like(T)
+    fx = torch.as_tensor(fixed.astype(np.uint8), device="cuda")
+    st = h.porous_rk(T, P, fx, 5 * dt, dt, fixed_step=True, tol=1e-12, mode="f64", maxit=200)
+    assert st["naccept"] == rst.naccept == 5 and st["nfev"] == rst.nfev == 31 and st["t"] == 5 * dt
+    got = T.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+    assert np.array_equal(got[fixed], T0[fixed]) and np.max(np.abs(got - T0)) > 1e-3
+
+
+@pytest.mark.parametrize("rtol", [1e-6, 1e-8])
+def test_rk_adaptive_matches_oracle(rtol):
+    # the same accepted and rejected steps as the oracle (pressure solved to 1e-12 against its direct
+    # solve), from a first step far too large, so that the controller has to reject
+    from oracle import rk
+    h, xy, fixed, lev, prm, pot = _rk_pair(3, 3)
+    T0 = _paper_T0(xy)
+    t_end, dt0 = 2e-3, 1e-3
+    ref, rst = rk.integrate(por.tdot_fn(lev, pot, fixed, prm), T0, t_end, dt0, rtol, rtol)
+    T = torch.as_tensor(T0, device="cuda")
+    P = torch.zeros_like(T)
+    fx = torch.as_tensor(fixed.astype(np.uint8), device="cuda")
+    st = h.porous_rk(T, P, fx, t_end, dt0, rtol=rtol, atol=rtol, tol=1e-12, mode="f64", maxit=200)
+    assert rst.nreject > 0 and rst.naccept > 3
+    assert (st["naccept"], st["nreject"], st["nfev"]) == (rst.naccept, rst.nreject, rst.nfev)
+    # the error estimate is a difference of stage rates whose weights sum to zero: it amplifies the
+    # pressure solves' 1e-12 relative error to ~1e-6 in the error norm, and the next step follows its
+    # -1/5 power
+    assert st["t"] == t_end and st["dt"] == pytest.approx(rst.dt, rel=1e-4)
+    assert np.max(np.abs(T.cpu().numpy() - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_rk_conductive_state_stays_put():
+    h, xy, fixed = _setup(5, 4)
+    T0 = 100.0 - 200.0 * xy[:, 1]
+    T = torch.as_tensor(T0, device="cuda")
+    P = torch.zeros_like(T)
+    fx = torch.as_tensor(fixed.astype(np.uint8), device="cuda")
+    # an equilibrium only to the pressure solves' accuracy: the step grows until the explicit method's
+    # diffusion stability bound limits it (with rejections there), and the state stays put
+    st = h.porous_rk(T, P, fx, 0.01, 1e-5, rtol=1e-9, atol=1e-6, tol=1e-11, mode="mixed")
+    assert st["t"] == 0.01 and st["naccept"] >= 5
+    assert np.max(np.abs(T.cpu().numpy() - T0)) < 1e-7 * 100.0
+
+
+def test_rk_paper_setup_mg_against_fp64_pressure():
+    # the paper's porous setup on its 16,641-vertex mesh (unit square x7), Tsit5 at rtol 1e-9:
+    # float-float MG-PCG pressure solves to 1e-8 against FP64 ones to 1e-12 over the same interval
+    h, xy, fixed = _setup(7, 6)
+    assert h.n == 16641
+    T0 = torch.as_tensor(_paper_T0(xy), device="cuda")
+    fx = torch.as_tensor(fixed.astype(np.uint8), device="cuda")
+    out = {}
+    for key, kw in (("ref", dict(tol=1e-12, mode="f64", maxit=300)), ("mg", dict(tol=1e-8, mode="mixed_ff"))):
+        T = T0.clone()
+        P = torch.zeros_like(T)
+        st = h.porous_rk(T, P, fx, 2e-4, 1e-6, rtol=1e-9, atol=1e-6, **kw)
+        assert st["t"] == 2e-4 and st["naccept"] > 5 and st["pressure_rel_res"] <= kw["tol"] * 1.01
+        out[key] = (T.cpu().numpy(), st)
+    rmse = float(np.sqrt(np.mean((out["mg"][0] - out["ref"][0]) ** 2)))
+    assert rmse < 1e-5, rmse
+    assert abs(out["mg"][1]["naccept"] - out["ref"][1]["naccept"]) <= 1
+
+
+def test_rk_argument_and_step_limit_errors():
+    import paper_2508_12501_gb300 as P_
+    h, xy, fixed = _setup(3, 3)
+    T0 = _paper_T0(xy)
+    T = torch.as_tensor(T0, device="cuda")
+    P = torch.zeros_like(T)
+    fx = torch.as_tensor(fixed.astype(np.uint8), device="cuda")
+    with pytest.raises(P_.DecError):
+        h.porous_rk(T, P, fx, 1e-3, 0.0)
+    with pytest.raises(P_.DecError):
+        h.porous_rk(T, P, fx, 1e-3, 1e-5, rtol=0.0, atol=0.0)
+    with pytest.raises(P_.DecError) as ei:
+        h.porous_rk(T, P, fx, 1.0, 1e-6, max_steps=3, mode="f64", tol=1e-12)
+    assert ei.value.code == 5  # DEC_ERR_NOT_CONVERGED: T holds the state reached
+    assert np.max(np.abs(T.cpu().numpy() - T0)) > 0.0
