@@ -807,6 +807,7 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
         return bail(rc);
     ce = cudaMemcpy(B->dtiles, tiles.data(), tiles.size() * sizeof(BTile), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(B->dlv, B->hlv.data(), B->hlv.size() * sizeof(BLevel), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(B->scal, 0, sizeof(Scal));
     if (ce == cudaSuccess) ce = cudaMallocHost((void **)&B->scal_h, sizeof(Scal));
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "batch upload"));
     *out = B;

@@ -847,7 +847,7 @@ __device__ __forceinline__ void set_alpha_f(Scal *S, double pq) {
 __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
     S->rnorm2 = rnorm2;
     const int it = S->iter;
-    if (it < kHist) S->hist[it] = rnorm2;
+    if (it >= 0 && it < kHist) S->hist[it] = rnorm2;
     if (!isfinite(rnorm2) || !isfinite(S->bnorm2)) {
         S->status = 1;
         S->done = 1;

@@ -1200,6 +1200,8 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         if ((rc = dalloc(mg, &mg->partials, 8 * kMaxRedBlocks))) return bail(rc);
         if ((rc = dalloc(mg, &mg->counter, 1))) return bail(rc);
         if ((rc = dalloc(mg, &mg->scal, 1))) return bail(rc);
+        ce = cudaMemset(mg->scal, 0, sizeof(Scal));
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
         ce = cudaMemset(mg->counter, 0, sizeof(unsigned));
         if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
         ce = cudaMallocHost((void **)&mg->scal_h, sizeof(Scal));
@@ -1473,6 +1475,8 @@ int dec_mg_time_kernel(dec_mg *mg, int kind, int level, int reps, double *avg_ms
     // zeroed FP32 work vectors: the same kernels and launch shapes as in the mixed_ff loop
     float *zero[] = {F.x32[0], F.x32[1], F.d32[0], F.b32, mg->zo32, mg->fp, mg->fqh, mg->fql, mg->fxh, mg->fxl, mg->frl};
     for (float *z : zero) CK(cudaMemsetAsync(z, 0, vb, s));
+    // the reduction epilogues update the solver's scalars (iteration count, history slot): start them at zero
+    CK(cudaMemsetAsync(mg->scal, 0, sizeof(Scal), s));
     const int rg = red_grid(mg, F.n);
     const int *noskip = nullptr;
     const int gauge = mg->H.bc == DEC_BC_GAUGE;
