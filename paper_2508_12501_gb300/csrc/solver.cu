@@ -1965,8 +1965,11 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
     double *nxt = work + (size_t)7 * n, *esum = work + (size_t)8 * n;
     double *cur = T;
     dec_rk_stats out{};
+    double t = 0.0, dt = dt0;  // time reached and next step (reported on every return)
     const int g = grid_for(mg, n), rg = red_grid(mg, n);
     auto finish = [&](int code) {
+        out.t = t;
+        out.dt = dt;
         if ((code == DEC_OK || code == DEC_ERR_NOT_CONVERGED) && cur != T) {
             cudaError_t e = cudaMemcpyAsync(T, cur, vb, cudaMemcpyDeviceToDevice, R.s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(R.s);
@@ -1981,7 +1984,6 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
     porous_potential(R);
     if (int rc = porous_rate(R, cur, P, k[0])) return finish(rc);
     out.nfev = 1;
-    double t = 0.0, dt = dt0;
     const double slack = 1e-12 * t_end;
     bool rejected_last = false;
     while (t < t_end && out.naccept + out.nreject < max_steps) {
@@ -2029,8 +2031,6 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
             rejected_last = true;
         }
     }
-    out.t = t;
-    out.dt = dt;
     if (t < t_end) return finish(fail(Status::fail(DEC_ERR_NOT_CONVERGED, "max_steps reached before t_end")));
     return finish(DEC_OK);
 }
