@@ -30,7 +30,12 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# The CPU oracle (cpu_baseline, --impl reference) is timed on one core: BLAS and OpenMP pools default to one
+# thread unless the caller sets them (before numpy loads its BLAS).  The GPU path does no host arithmetic.
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -214,23 +219,28 @@ def oracle_setup(smoother="chebyshev"):
     return oh, b
 
 
+_ORACLE_CPU = {"cpu_s": 0.0, "wall_s": 0.0}
+
+
 def oracle_time(oh, b, nsolve):
     from oracle import multigrid as omg
     ts = []
     res = None
+    c0, w0 = time.process_time(), time.perf_counter()
     for _ in range(nsolve):
         t0 = time.perf_counter()
         res = omg.pcg_solve(oh, b, TOL, 100)
         ts.append(time.perf_counter() - t0)
+    _ORACLE_CPU["cpu_s"] = time.process_time() - c0
+    _ORACLE_CPU["wall_s"] = time.perf_counter() - w0
     return ts, res
 
 
 def cpu_cores_used():
-    # the oracle is numpy/scipy on one process; sparse products are single-threaded
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        if os.environ.get(var):
-            return int(os.environ[var])
-    return 1
+    """Cores the last timed oracle solves kept busy: the process's CPU time (all its threads, e.g. a
+    multithreaded BLAS) over the wall time, at least 1."""
+    w = _ORACLE_CPU["wall_s"]
+    return max(1.0, round(_ORACLE_CPU["cpu_s"] / w, 1)) if w > 0 else 1.0
 
 
 def run_reference(args, rank):
