@@ -190,3 +190,30 @@ def test_binary_map_tables_are_the_parents():
     for q in range(3):
         np.add.at(Ml, (idx[:, q], np.arange(len(idx))), w[:, q])
     assert np.array_equal(Ml, Mo)
+
+
+def test_option_defaults_and_fuse_max_rows_validation():
+    o = lib_mod.dec_mg_opts()
+    lib_mod.lib.dec_mg_default_opts(C.byref(o))
+    assert o.fuse == lib_mod.DEC_FUSE_RESTRICT0 | lib_mod.DEC_FUSE_OUTER | lib_mod.DEC_FUSE_COARSE
+    assert o.fuse_max_rows == 0 and o.coarse_max_rows == 0 and o.fcycle == 0
+    v, t = W.unit_square()
+    Hierarchy(Mesh(v, t), 3, 2, bc="dirichlet", host_only=True, fuse=63, fuse_max_rows=100)
+    with pytest.raises(DecError) as ei:
+        Hierarchy(Mesh(v, t), 3, 2, bc="dirichlet", host_only=True, fuse_max_rows=-1)
+    assert ei.value.code == lib_mod.DEC_ERR_ARG
+
+
+def test_host_only_handles_refuse_device_entry_points():
+    # dec_solve_host, dec_porous_rk and the kernel timer check the handle before anything else
+    v, t = W.icosahedron()
+    h = Hierarchy(Mesh(v, t), 2, 2, bc="gauge", sphere=True, host_only=True)
+    L = lib_mod
+    st = L.dec_stats()
+    assert L.lib.dec_solve_host(h._h, None, None, 1, None, C.byref(st), None) == L.DEC_ERR_ARG
+    rk = L.dec_rk_stats()
+    assert L.lib.dec_porous_rk(h._h, None, None, None, None, 1e-3, 1e-5, 1e-9, 1e-6, 10, 0, C.byref(rk),
+                               None) == L.DEC_ERR_ARG
+    ms, by = C.c_double(), C.c_double()
+    assert L.lib.dec_mg_time_kernel(h._h, L.PROF_KINDS.index("spmv64"), -1, 5, C.byref(ms), C.byref(by),
+                                    None) == L.DEC_ERR_ARG
