@@ -22,7 +22,8 @@ Readings (the paper names the method and its relative tolerance only):
     end exactly at t_end, so rounding in the accumulated time adds no step.
 Pins: tests/test_oracle_rk.py (the Butcher order conditions of both weight
 vectors, fifth-order convergence, fourth-order local error estimate,
-tolerance proportionality, an exact fixed point).
+tolerance proportionality, an exact fixed point, and the porous model
+integrated by an independent library integrator at a far tighter tolerance).
 """
 from __future__ import annotations
 

@@ -146,3 +146,23 @@ def test_porous_adaptive_matches_fine_fixed_steps():
     assert sta.t == t_end and sta.naccept > 3
     assert np.max(np.abs(Ta - Tr)) < 1e-5 * np.max(np.abs(T0))
     assert np.array_equal(Ta[fixed], T0[fixed])
+
+
+def test_porous_adaptive_matches_an_independent_integrator():
+    # the same porous right-hand side integrated by SciPy's DOP853 (Dormand-Prince 8(5,3)) at a
+    # tolerance far below ours: the oracle's Tsit5 result agrees to its own tolerance
+    integrate = pytest.importorskip("scipy.integrate")
+    lev, fixed = _square(3)
+    prm = por.PorousParams()
+    xy = lev.mesh.verts
+    pot = por.potential(xy, prm)
+    T0 = W.gaussian_initial_T(xy, (0.5, 0.5))
+    T0 = np.where(xy[:, 1] == 1.0, -100.0, np.where(xy[:, 1] == 0.0, 100.0, T0))
+    f = por.tdot_fn(lev, pot, fixed, prm)
+    t_end = 2e-3
+    ref = integrate.solve_ivp(lambda t, y: f(y), (0.0, t_end), T0, method="DOP853", rtol=1e-12, atol=1e-10)
+    assert ref.success
+    for tol, bound in ((1e-6, 1e-4), (1e-9, 1e-7)):
+        T, st = rk.integrate(f, T0, t_end, 1e-5, tol, tol)
+        err = np.max(np.abs(T - ref.y[:, -1]))
+        assert err < bound * np.max(np.abs(T0)), (tol, err)
