@@ -13,6 +13,7 @@ Modules
              V-cycle, coarse dense solve, standalone MG, flexible MG-PCG
   adjoint    adjoint solve and gradients with respect to b and *1
   porous     one explicit porous-convection step and its adjoint
+  rk         adaptive Tsitouras 5(4) integration (the Tsit5 method of Sec. 3.2.2)
 
 Parity pins live in tests/test_oracle_*.py.  Functions without an external
 pin say "parity unpinned" in their docstring.

@@ -65,6 +65,24 @@ def test_chebyshev_is_scaled_chebyshev_polynomial():
         assert np.allclose(x, expect, rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("kl", [(1, 1), (3, 2), (7, 11), (15, 15)])
+def test_jacobi_damps_each_sine_mode_by_its_symbol(kl):
+    # On the unit square L is the 5-point stencil (/h^2), whose Dirichlet eigenvectors are the sine modes
+    # sin(k pi x) sin(l pi y) with D^-1 L eigenvalue sin^2(k pi h/2) + sin^2(l pi h/2): one damped-Jacobi
+    # sweep with b = 0 multiplies the mode by exactly 1 - omega (that sum), on the DEC operator itself.
+    k, l = kl
+    v, t = W.unit_square()
+    h = mg.build_hierarchy(v, t, 4, 1, "dirichlet")
+    lev = h.finest
+    xy = lev.mesh.verts
+    e = np.sin(k * np.pi * xy[:, 0]) * np.sin(l * np.pi * xy[:, 1]) * lev.free
+    hh = 1.0 / 16
+    sym = np.sin(k * np.pi * hh / 2) ** 2 + np.sin(l * np.pi * hh / 2) ** 2
+    for omega in (2.0 / 3.0, 0.8, 1.0):
+        x = mg.jacobi(lev, np.zeros(lev.mesh.nv), e.copy(), omega, 1)
+        assert np.max(np.abs(x - (1.0 - omega * sym) * e)) < 1e-13
+
+
 def test_gauss_seidel_matches_sequential_sweep():
     h = _square(2, 2, smoother="gs")
     lev = h.finest
