@@ -23,7 +23,9 @@
  *     and the midpoint of coarse edge e gets id n_coarse + e.  With k > 1
  *     right-hand sides a vector is interleaved: value j of vertex v at
  *     [v * k + j].
- *   - A handle may be used by one thread / one stream at a time.
+ *   - A handle may be used by one thread / one stream at a time, with its
+ *     device current: a compute call made while another device is current
+ *     returns DEC_ERR_ARG.
  */
 #ifndef DEC_H
 #define DEC_H
@@ -74,16 +76,26 @@ enum { DEC_RESTRICT_ROWNORM = 0, DEC_RESTRICT_STAR0 = 1 };
 enum { DEC_SOLVER_MG = 0, DEC_SOLVER_MGPCG = 1, DEC_SOLVER_CG = 2 };
 /* Precision of a solve (Sec. 3.1.2 with the mixed-precision pattern):
  *   DEC_MODE_F64       cycles and outer iteration in FP64;
- *   DEC_MODE_MIXED     FP32 cycles inside an FP64 outer iteration;
+ *   DEC_MODE_MIXED     FP32 cycles (smoothing, transfers, coarse solve)
+ *                      inside an FP64 outer iteration: the residual b - L x
+ *                      and its updates, every dot product (FP64 products and
+ *                      FP64 sums), the search directions, the iterate and the
+ *                      gauge projection are FP64; the cycle reads the residual
+ *                      rounded to FP32 and returns its correction in FP32;
  *   DEC_MODE_MIXED_FF  FP32 cycles inside a float-float outer iteration
  *                      (not in the paper): x, r and L p as unevaluated sums
  *                      of two floats (~48 bits), search directions in FP32,
  *                      all on the FP32 pipe.  The updated residual tracks
  *                      b - L x to about 1e-12 of ||b|| on 10^6-vertex meshes,
  *                      so tolerances down to ~1e-10 are met by the true
- *                      residual; use DEC_MODE_MIXED or DEC_MODE_F64 below that.
+ *                      residual; use DEC_MODE_MIXED or DEC_MODE_F64 below that;
+ *   DEC_MODE_MIXED_F32DOT  as DEC_MODE_MIXED (FP64 residual, iterate and
+ *                      updates), but the dot products that steer alpha, beta,
+ *                      the gauge shift and the stopping test are formed from
+ *                      FP32 copies with FP32 products and sums (not in the
+ *                      paper; fewer FP64 instructions per row).
  * Plain CG (DEC_SOLVER_CG) always runs in FP64. */
-enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1, DEC_MODE_MIXED_FF = 2 };
+enum { DEC_MODE_F64 = 0, DEC_MODE_MIXED = 1, DEC_MODE_MIXED_FF = 2, DEC_MODE_MIXED_F32DOT = 3 };
 
 /* Multigrid options.  dec_mg_default_opts() fills the defaults:
  * Jacobi, nu1 = nu2 = 2, omega = 2/3, Chebyshev interval
@@ -380,8 +392,9 @@ int dec_batch_tune(dec_mg *const *mgs, const int *nrhs, int nmesh, const double 
 /* dec_batch_time_smooth: mean duration of one launch of the batched
  * finest-level smoothing sweep (every group), over `reps` back-to-back
  * launches timed with CUDA events on `stream`, and its algorithmic bytes
- * (per row K column indices and K weights once, per right-hand side x, b,
- * the new x and, for Chebyshev, a direction vector). */
+ * (each mesh's finest operator once -- K column indices and K weights per
+ * row, shared by all its groups -- and per right-hand side x, b, the new x
+ * and, for Chebyshev, a direction vector; padding columns not counted). */
 int dec_batch_time_smooth(dec_batch *batch, int reps, double *avg_ms, double *bytes, dec_stream_t stream);
 
 /* ---- porous convection (Sec. 3.2) -------------------------------------------
@@ -432,13 +445,16 @@ int dec_porous_step(dec_mg *mg, double *T, double *P, const uint8_t *fixed, cons
  * a step is accepted when it is <= 1; the next step is dt * min(10, max(0.2,
  * 0.9 norm^(-1/5))), at most dt right after a rejection; the last step ends
  * exactly at t_end.  dt0: first step (fixed_step != 0: every step, no error
- * control).  P: warm start on entry, the pressure of the final T on exit.
- * prm as for dec_porous_step, prm->dt ignored.  stats (nullable): accepted
- * and rejected steps, right-hand-side evaluations, the time reached, the next
- * step, pressure iterations summed and the worst final pressure residual.
- * Errors: DEC_ERR_ARG; DEC_ERR_NOT_CONVERGED when max_steps attempts end
- * before t_end (T is the state at stats->t); DEC_ERR_NONFINITE; the errors of
- * dec_solve.  Synchronizes `stream` once per step. */
+ * control).  P: warm start on entry.  On every return, also an error
+ * return, T is the last accepted state (the state at stats->t) and P its
+ * pressure (P is unchanged when the first pressure solve fails); a
+ * rejected or failed step leaves neither.  prm as for dec_porous_step,
+ * prm->dt ignored.  stats (nullable): accepted and rejected steps,
+ * right-hand-side evaluations, the time reached, the next step, pressure
+ * iterations summed and the worst final pressure residual.  Errors:
+ * DEC_ERR_ARG; DEC_ERR_NOT_CONVERGED when max_steps attempts end before
+ * t_end; DEC_ERR_NONFINITE; the errors of dec_solve.  Allocates 10 work
+ * vectors for the call.  Synchronizes `stream` once per step. */
 typedef struct dec_rk_stats {
     int64_t naccept, nreject, nfev;
     double t, dt;
@@ -449,7 +465,7 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
                   double t_end, double dt0, double rtol, double atol, int64_t max_steps, int fixed_step,
                   dec_rk_stats *stats, dec_stream_t stream);
 
-/* dec_porous_backward: reverse-mode derivative of T_N = step^N(T_0):/* dec_porous_backward: reverse-mode derivative of T_N = step^N(T_0):
+/* dec_porous_backward: reverse-mode derivative of T_N = step^N(T_0):
  * given grad_TN = dF/dT_N, writes grad_T0 = dF/dT_0.  Checkpoints every
  * ckpt_every steps are kept on the device and each segment is recomputed
  * forward before it is differentiated (memory: (nsteps/ckpt_every + 2 *
@@ -459,6 +475,20 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
 int dec_porous_backward(dec_mg *mg, const double *T0, const double *P0, const uint8_t *fixed,
                         const dec_porous_params *prm, int nsteps, int ckpt_every, const double *grad_TN,
                         double *grad_T0, dec_stats *stats, dec_stream_t stream);
+
+/* dec_mg_set_wait_limit: the bound on the one device-side wait of the
+ * cycle -- the shared-memory coarse cycle (DEC_FUSE_COARSE) waits on an
+ * mbarrier for the bulk copies of its tables.  After `rounds` try_wait rounds
+ * without completion the block records the failure, waits for the copies
+ * in flight with the default bound so that none lands after it exits, and
+ * returns without touching its output; every later kernel of the solve is
+ * skipped and dec_solve returns DEC_ERR_CUDA ("a device-side wait gave
+ * up"), x holding the iterate from before the failed cycle.  rounds < 0
+ * restores the default (2^20 rounds, well under a second); larger values are
+ * clamped to it; 0 makes the wait give up at once, which exercises the
+ * failure path without a fault.  Applies to later calls (captured solve
+ * graphs are rebuilt).  Not in the paper. */
+int dec_mg_set_wait_limit(dec_mg *mg, int rounds);
 
 /* ---- live kernel timing ------------------------------------------------------
  * dec_mg_profile: enable = 1 records a CUDA event pair around every launch of

@@ -27,7 +27,7 @@ DEC_F64, DEC_F32 = 0, 1
 DEC_SMOOTH_JACOBI, DEC_SMOOTH_CHEBYSHEV, DEC_SMOOTH_MCGS = 0, 1, 2
 DEC_RESTRICT_ROWNORM, DEC_RESTRICT_STAR0 = 0, 1
 DEC_SOLVER_MG, DEC_SOLVER_MGPCG, DEC_SOLVER_CG = 0, 1, 2
-DEC_MODE_F64, DEC_MODE_MIXED, DEC_MODE_MIXED_FF = 0, 1, 2
+DEC_MODE_F64, DEC_MODE_MIXED, DEC_MODE_MIXED_FF, DEC_MODE_MIXED_F32DOT = 0, 1, 2, 3
 DEC_FUSE_SMOOTH01, DEC_FUSE_RESTRICT, DEC_FUSE_PROLONG, DEC_FUSE_RESTRICT0, DEC_FUSE_OUTER = 1, 2, 4, 8, 16
 DEC_FUSE_COARSE = 32
 DEC_FUSE_ALL = 63
@@ -115,6 +115,7 @@ _SIGS = {
     "dec_solve_host": (_i, [_p, _p, _p, _i, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_solve_backward": (_i, [_p, _p, _p, _p, _p, C.POINTER(dec_solve_opts), C.POINTER(dec_stats), _p]),
     "dec_mg_profile": (_i, [_p, _i]),
+    "dec_mg_set_wait_limit": (_i, [_p, _i]),
     "dec_mg_vcycle_noalloc": (_i, [_p, _p, _p, _p]),
     "dec_batch_default_opts": (None, [C.POINTER(dec_batch_opts)]),
     "dec_batch_create": (_i, [C.POINTER(_p), C.POINTER(_i), _i, C.POINTER(dec_batch_opts), C.POINTER(_p)]),

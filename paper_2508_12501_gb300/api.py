@@ -16,7 +16,8 @@ from ._lib import check, lib
 
 SMOOTHERS = {"jacobi": L.DEC_SMOOTH_JACOBI, "chebyshev": L.DEC_SMOOTH_CHEBYSHEV, "mcgs": L.DEC_SMOOTH_MCGS}
 SOLVERS = {"mg": L.DEC_SOLVER_MG, "mgpcg": L.DEC_SOLVER_MGPCG, "cg": L.DEC_SOLVER_CG}
-MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED, "mixed_ff": L.DEC_MODE_MIXED_FF}
+MODES = {"f64": L.DEC_MODE_F64, "mixed": L.DEC_MODE_MIXED, "mixed_ff": L.DEC_MODE_MIXED_FF,
+         "mixed_f32dot": L.DEC_MODE_MIXED_F32DOT}
 ORDERS = {"edge": 0, "morton": L.DEC_ORDER_MORTON}
 SCHEMES = {"binary": 0, "cubic": L.DEC_SUBDIV_CUBIC}
 BCS = {"dirichlet": L.DEC_BC_DIRICHLET, "gauge": L.DEC_BC_GAUGE}
@@ -273,6 +274,11 @@ class Hierarchy:
                                     C.byref(o), C.byref(st), self._stream())
         check(rc, "dec_solve_backward")
         return gb, gs, SolveStats(st.iters, st.rel_res, st.rel_res0, rc, st.launches)
+
+    def set_wait_limit(self, rounds=-1):
+        """Bound (try_wait rounds) of the coarse cycle's device-side table-load wait; -1 restores the default,
+        0 makes it give up at once (the solve then fails with DEC_ERR_CUDA and leaves x as it was)."""
+        check(lib.dec_mg_set_wait_limit(self._h, int(rounds)), "dec_mg_set_wait_limit")
 
     def profile(self, enable=1):
         """Live CUDA-event timing of the solver's kernels (1: finest level, 2: all levels, 0: off)."""

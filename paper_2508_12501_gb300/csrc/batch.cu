@@ -824,6 +824,13 @@ int dec_batch_solve(dec_batch *B, const double *const *b, double *const *x, doub
                     dec_batch_stats *stats, dec_stream_t stream) {
     if (!B || !b || !x) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
     if (!(tol >= 0.0) || maxit < 0 || maxit >= decdev::kHist) return fail(Status::fail(DEC_ERR_ARG, "bad tol or maxit"));
+    {
+        int cur = -1;
+        CK(cudaGetDevice(&cur));
+        if (cur != B->device)
+            return fail(Status::fail(DEC_ERR_ARG, "the batch lives on device " + std::to_string(B->device) +
+                                                      " but device " + std::to_string(cur) + " is current"));
+    }
     for (size_t m = 0; m < B->mgs.size(); ++m)
         if (!b[m] || !x[m]) return fail(Status::fail(DEC_ERR_ARG, "null vector"));
     cudaStream_t s = (cudaStream_t)stream;
@@ -976,11 +983,20 @@ extern "C" int dec_batch_time_smooth(dec_batch *B, int reps, double *avg_ms, dou
     if (!op) return fail(Status::fail(DEC_ERR_ARG, "batch has no smoothing sweep"));
     cudaStream_t s = (cudaStream_t)stream;
     const int cheb = B->opts.smoother == DEC_SMOOTH_CHEBYSHEV;
+    // Algorithmic bytes: the finest operator of each mesh once (K columns + K
+    // weights per row, whatever the number of its groups: the groups of a mesh
+    // share one table), then per item x, b, x_out (+ direction) for the
+    // right-hand sides the mesh actually has (padding columns excluded).
     double by = 0.0;
+    std::vector<const int32_t *> seen;
     for (auto &G : B->groups) {
         const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
-        // per row: K columns + K weights (shared by the k right-hand sides), then per item x, b, x_out (+ direction)
-        by += (double)L.n * (8.0 * L.K) + (double)L.n * G.k * 4.0 * (3 + (cheb ? 1 : 0));
+        if (std::find(seen.begin(), seen.end(), L.col) == seen.end()) {
+            seen.push_back(L.col);
+            by += (double)L.n * (8.0 * L.K);
+        }
+        const int kk = std::min(G.k, B->nrhs[G.mesh] - G.col0);
+        by += (double)L.n * kk * 4.0 * (3 + (cheb ? 1 : 0));
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

@@ -47,14 +47,17 @@ struct CoarseArgs {
     float *x;        // result on level `top` (global)
     Scal *S;         // solver scalars: status 3 if the load wait gave up
     int top_mutable; // level `top` is the finest level (its w and dg change with dec_mg_set_star1)
+    int wait_rounds; // try_wait rounds the load wait allows before it gives up (status 3)
     CoarseLevel lv[kCoarseMaxLevels];
 };
 
 // Shared-memory bytes the kernel keeps before the level arrays (its mbarrier).
 constexpr int kCoarseHeader = 16;
-// try_wait rounds before the load wait gives up (each round suspends the
-// thread for at most a hardware time slice, so this bounds the wait to well
-// under a second).
+// Default try_wait rounds before the load wait gives up (each round suspends
+// the thread for at most a hardware time slice, so this bounds the wait to
+// well under a second).  The first wait takes CoarseArgs::wait_rounds (this
+// value unless the caller set another); the drain wait after a give-up always
+// takes this one.
 constexpr int kCoarseWaitRounds = 1 << 20;
 
 __device__ __forceinline__ unsigned sm_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -69,9 +72,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait for phase 0 of the load barrier.
-__device__ __forceinline__ bool mbar_wait0(unsigned bar) {
-    for (int it = 0; it < kCoarseWaitRounds; ++it)
+// Bounded wait for phase 0 of the load barrier: at most `rounds` try_wait rounds.
+__device__ __forceinline__ bool mbar_wait0(unsigned bar, int rounds) {
+    for (int it = 0; it < rounds; ++it)
         if (mbar_try_wait(bar, 0)) return true;
     return false;
 }
@@ -249,15 +252,16 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) k_coarse_cycle(const __grid
             if (!pre) stage(sm, off, src, bytes, bar, false);
         });
     __syncthreads();  // the barrier is initialized before anyone waits on it
-    const bool loaded = mbar_wait0(bar);
+    const bool loaded = mbar_wait0(bar, A.wait_rounds);
     if (!__syncthreads_and(loaded)) {
-        // copies still in flight after the bound: report, wait once more (bounded) so that no copy
-        // lands in shared memory after the block has left, and leave x untouched
+        // copies still in flight after the bound: report, wait once more with the full
+        // (bounded) limit so that no copy lands in shared memory after the block has left,
+        // and leave x untouched
         if (threadIdx.x == 0) {
             A.S->status = 3;
             A.S->done = 1;
         }
-        mbar_wait0(bar);
+        mbar_wait0(bar, kCoarseWaitRounds);
         return;
     }
     if (skip_now) return;  // the queued copies have landed

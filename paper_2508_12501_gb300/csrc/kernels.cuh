@@ -1038,10 +1038,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_mg_residual(int n, int K, const
 // difference form sum_k w_k (x_i - x_k) -- for smooth x the differences are
 // exact, whereas the diagonal form L_ii x_i - sum_k w_k x_k cancels and
 // limits the attainable residual -- but drops the FP64 diagonal sum: fixed
-// rows have all weights 0 and come out 0 without a mask.  In mixed
-// precision the dot products that steer alpha, beta, the gauge shift and the
-// stopping test use FP32 copies, FP32 products and FP32 warp sums (combined
-// in FP64 across warps and blocks).  The x and r updates stay FP64.
+// rows have all weights 0 and come out 0 without a mask.  In
+// DEC_MODE_MIXED_F32DOT the dot products that steer alpha, beta, the gauge
+// shift and the stopping test use FP32 copies, FP32 products and FP32 sums;
+// the x and r updates stay FP64.
 // ---------------------------------------------------------------------------
 
 template <int KT>
@@ -1225,6 +1225,172 @@ __global__ void __launch_bounds__(kThreads, 8) k_mg_residual_m(int n, int K, con
         const float rf = (float)ri;
         r32[i] = rf;
         acc[0] = fmaf(rf, rf, acc[0]);
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->iter += 1;
+        record_residual(S, tot[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 outer iteration around FP32 cycles (DEC_MODE_MIXED): the residual
+// update r -= alpha L p, every dot product -- FP64 products and FP64 sums --
+// the gauge shift and the search-direction update are FP64; the cycle reads
+// r rounded to FP32 (r32) and returns the preconditioned vector z in FP32.
+// Scalars (alpha, beta, the gauge shift) are FP64 quotients of FP64 sums.
+// ---------------------------------------------------------------------------
+
+// x += alpha p, r -= alpha q, r32 = (float) r, ||r||^2 -> convergence test.
+// s0mode > 0 also runs the next cycle's first smoothing step on the finest
+// level from zero, as k_smooth0 does on b = r32 (x0 = e0 r32 / dg, and d0 =
+// x0 when s0mode == 2); it is row-local.
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_d(int n, const double *__restrict__ p,
+                                                          const double *__restrict__ q, double *__restrict__ x,
+                                                          double *__restrict__ r, float *__restrict__ r32,
+                                                          double *partials, unsigned *counter, Scal *S,
+                                                          const int *skip, int s0mode, const float *__restrict__ dg,
+                                                          float *__restrict__ x0, float *__restrict__ d0, float e0) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const double a = S->alpha;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) {
+        x[i] = fma(a, ldg(p + i), x[i]);
+        const double ri = fma(-a, ldg(q + i), r[i]);
+        r[i] = ri;
+        const float rf = (float)ri;
+        r32[i] = rf;
+        acc[0] = fma(ri, ri, acc[0]);
+        if (s0mode > 0) {
+            const float di = ldg(dg + i);
+            const float v = di != 0.f ? e0 * (rf / di) : 0.f;
+            x0[i] = v;
+            if (s0mode == 2) d0[i] = v;
+        }
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->iter += 1;
+        record_residual(S, tot[0]);
+    }
+}
+
+// After the four FP64 sums of the preconditioned vector z: sum *0 z, sum *0 r z,
+// sum *0 r z_prev and sum *0 r over free rows, z and z_prev being the cycle
+// outputs before their gauge shifts c and c_prev (S->c until it is replaced
+// here).  Shift c = sum *0 z / sum *0, <r, z - c> = tot1 - c tot3,
+// <r, z_prev - c_prev> = tot2 - c_prev tot3, and the Polak-Ribiere
+// beta = (<r, z> - <r, z_prev>) / <r_prev, z_prev>.
+__device__ __forceinline__ void zdots_epilogue_d(Scal *S, const double (&tot)[4], int first, int gauge) {
+    const double c = gauge ? tot[0] / S->star0_sum : 0.0;
+    const double rz_new = tot[1] - c * tot[3];
+    const double rzo = tot[2] - S->c * tot[3];
+    S->beta = first ? 0.0 : (rz_new - rzo) / S->rz;
+    S->rz = rz_new;
+    S->c = c;
+}
+
+// The four FP64 dot products of z (FP32 cycle output, unshifted) with *0 and
+// the FP64 residual r; zo is the previous unshifted z (FP32).
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_d(int n, const double *__restrict__ star0,
+                                                         const uint8_t *__restrict__ freev,
+                                                         const float *__restrict__ z, const double *__restrict__ r,
+                                                         const float *__restrict__ zo, int first, int gauge,
+                                                         double *partials, unsigned *counter, Scal *S,
+                                                         const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    GRID_STRIDE(i, n) {
+        if (freev[i]) {
+            const double s0 = ldg(star0 + i), zi = (double)ldg(z + i);
+            const double sr = s0 * ldg(r + i);
+            acc[0] = fma(s0, zi, acc[0]);
+            acc[1] = fma(sr, zi, acc[1]);
+            if (!first) acc[2] = fma(sr, (double)ldg(zo + i), acc[2]);
+            acc[3] += sr;
+        }
+    }
+    double tot[4];
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue_d(S, tot, first, gauge);
+}
+
+// The last post-smoothing step of the finest level (k_smooth with DIN =
+// Chebyshev, no direction out; b = r32) fused with k_pcg_zdots_d, whose sums
+// are row-local.  Launched on the reduction grid so that rows map to threads
+// as in k_pcg_zdots_d (bitwise equal sums).
+template <int KT, bool DIN>
+__global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots_d(int n, int K, const int32_t *__restrict__ col,
+                                                            const float *__restrict__ w, const float *__restrict__ b,
+                                                            const float *__restrict__ x_in,
+                                                            const float *__restrict__ d_in, float *__restrict__ x_out,
+                                                            float c, float e, const double *__restrict__ star0,
+                                                            const uint8_t *__restrict__ freev,
+                                                            const double *__restrict__ r64,
+                                                            const float *__restrict__ zo, int first, int gauge,
+                                                            double *partials, unsigned *counter, Scal *S,
+                                                            const int *skip) {
+    pdl_prologue_ell<KT>(n, K, col, w);
+    if (skipped(skip)) return;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    GRID_STRIDE_1(i, n) {
+        float s, d;
+        row_apply<float, KT>(i, n, K, col, w, x_in, s, d);
+        const float q = d != 0.f ? (ldg(b + i) - s) / d : 0.f;
+        const float delta = smooth_delta<float>(DIN, c, DIN ? ldg(d_in + i) : 0.f, e, q);
+        const float zf = add_rn(ldg(x_in + i), delta);
+        x_out[i] = zf;
+        if (freev[i]) {
+            const double s0 = ldg(star0 + i), zi = (double)zf;
+            const double sr = s0 * ldg(r64 + i);
+            acc[0] = fma(s0, zi, acc[0]);
+            acc[1] = fma(sr, zi, acc[1]);
+            if (!first) acc[2] = fma(sr, (double)ldg(zo + i), acc[2]);
+            acc[3] += sr;
+        }
+    }
+    double tot[4];
+    if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue_d(S, tot, first, gauge);
+}
+
+// zo = z (unshifted, FP32; 0 on fixed rows), p = (z - c) + beta p in FP64
+// (p = z - c on the first pass).
+static __global__ void __launch_bounds__(kThreads, 8) k_pcg_pupd_d(int n, const uint8_t *__restrict__ freev,
+                                                        const float *__restrict__ z, float *__restrict__ zo,
+                                                        double *__restrict__ p, int first, const Scal *S,
+                                                        const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const double c = S->c, beta = S->beta;
+    GRID_STRIDE(i, n) {
+        const bool f = freev[i] != 0;
+        const float zr = f ? ldg(z + i) : 0.f;
+        zo[i] = zr;
+        const double zi = f ? (double)zr - c : 0.0;
+        p[i] = first ? zi : fma(beta, p[i], zi);
+    }
+}
+
+// Standalone MG / iterative refinement with the FP64 outer loop: r = b - L x
+// (FP64), r32 = (float) r, ||r||^2 in FP64 -> convergence test.
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 8) k_mg_residual_d(int n, int K, const int32_t *__restrict__ col,
+                                                           const double *__restrict__ w,
+                                                           const uint8_t *__restrict__ freev,
+                                                           const double *__restrict__ b, const double *__restrict__ x,
+                                                           double *__restrict__ r, float *__restrict__ r32,
+                                                           double *partials, unsigned *counter, Scal *S,
+                                                           const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) {
+        const double s = row_apply_nod<KT>(i, n, K, col, w, x);
+        const double ri = freev[i] ? ldg(b + i) - s : 0.0;
+        r[i] = ri;
+        r32[i] = (float)ri;
+        acc[0] = fma(ri, ri, acc[0]);
     }
     double tot[1];
     if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {

@@ -122,18 +122,18 @@ struct dec_mg {
     double star0_sum = 0.0;
     cudaStream_t cap = nullptr;
     // [solver][mode]
-    cudaGraphExec_t graphs[3][3] = {};
+    cudaGraphExec_t graphs[3][4] = {};
     // whole iteration loop on the device: a while node around one iteration
-    cudaGraphExec_t loops[3][3] = {};
+    cudaGraphExec_t loops[3][4] = {};
     bool no_device_loop = false;  // set if the driver refuses conditional nodes
-    int64_t loop_kernels[3][3] = {};  // kernel nodes in one pass of a loop body
+    int64_t loop_kernels[3][4] = {};  // kernel nodes in one pass of a loop body
     std::vector<void *> allocs;
     size_t bytes = 0;
     bool host_only = false;
     bool pdl = true;  // programmatic dependent launch between consecutive kernels
     // live kernel timing (dec_mg_profile)
     int64_t launches = 0;       // kernels enqueued outside graph capture
-    int64_t graph_kernels[3][3] = {};  // kernel nodes per captured iteration graph
+    int64_t graph_kernels[3][4] = {};  // kernel nodes per captured iteration graph
     int prof = 0;               // 0 off, 1 finest level, 2 all levels
     bool prof_capture = false;  // true while a profiled iteration graph is being captured
     bool capturing = false;     // true while any iteration graph is being captured

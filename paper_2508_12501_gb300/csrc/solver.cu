@@ -128,6 +128,7 @@ void cheb_coeffs(double lmax, double lo, double hi, int nu, std::vector<double> 
 // last post-smoothing step of the finest level (DEC_FUSE_OUTER).
 struct DotsArgs {
     int first = 0, gauge = 0;
+    bool d64 = false;   // FP64 dot products with the FP64 residual (DEC_MODE_MIXED)
     bool done = false;  // set once the fused kernel has been enqueued
 };
 
@@ -212,7 +213,18 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
                     DevLevel &F = mg->lv.back();
                     ProfScope ps(mg, DEC_PK_SMOOTHDOTS, l, s);
                     const int rg = red_grid(mg, L.n);
-                    if (din)
+                    if (da->d64) {
+                        if (din)
+                            launch(mg, k_smooth_zdots_d<KT, true>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
+                                   (const float *)xi, (const float *)di, xo, c, e, (const double *)F.star0,
+                                   (const uint8_t *)F.freev, (const double *)mg->orr, (const float *)mg->zo32,
+                                   da->first, da->gauge, mg->partials, mg->counter, mg->scal, skip);
+                        else
+                            launch(mg, k_smooth_zdots_d<KT, false>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
+                                   (const float *)xi, (const float *)nullptr, xo, c, e, (const double *)F.star0,
+                                   (const uint8_t *)F.freev, (const double *)mg->orr, (const float *)mg->zo32,
+                                   da->first, da->gauge, mg->partials, mg->counter, mg->scal, skip);
+                    } else if (din)
                         launch(mg, k_smooth_zdots<KT, true>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
                                (const float *)xi, (const float *)di, xo, c, e, (const float *)F.star0_32,
                                (const uint8_t *)F.freev, (const float *)mg->zo32, da->first, da->gauge,
@@ -462,28 +474,41 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
         ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
         launch(mg, k_pcg_zdots<double>, rg, s, F.n, F.star0, F.freev, mg->orr, mg->ozn, mg->orr, mg->ozo, first,
                                                     gauge, mg->partials, mg->counter, mg->scal, skip);
-    } else if (mode == DEC_MODE_MIXED || mode == DEC_MODE_MIXED_FF) {
-        // z (FP32 cycle output) and r32 feed FP32 dot products; p is updated in
-        // FP64 (mixed) or FP32 (float-float outer iteration)
+    } else if (mode != DEC_MODE_F64) {
+        // z is the FP32 cycle output.  DEC_MODE_MIXED: FP64 dot products with
+        // the FP64 residual and FP64 search directions; DEC_MODE_MIXED_F32DOT:
+        // FP32 dot products with r32, FP64 directions; DEC_MODE_MIXED_FF: FP32
+        // dot products and FP32 directions (float-float outer iteration)
         const dec_mg_opts &o = mg->H.opts;
         const bool outer = (o.fuse & DEC_FUSE_OUTER) != 0;
+        const bool d64 = mode == DEC_MODE_MIXED;
         DotsArgs da;
         da.first = first ? 1 : 0;
         da.gauge = gauge;
-        // after an ff update with the fused first smoothing step, the cycle starts at step 1
-        const bool pre0 = (outer && !first && mode == DEC_MODE_MIXED_FF && o.nu1 > 0 && o.smoother != DEC_SMOOTH_MCGS) ||
+        da.d64 = d64;
+        // after an outer update with the fused first smoothing step, the cycle starts at step 1
+        const bool pre0 = (outer && !first && (mode == DEC_MODE_MIXED_FF || mode == DEC_MODE_MIXED) && o.nu1 > 0 &&
+                           o.smoother != DEC_SMOOTH_MCGS) ||
                           (first && first_pre0);
         float *z = cycle<float>(mg, top, F.b32, s, skip, pre0, outer ? &da : nullptr);
         if (!da.done) {
             ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
-            launch(mg, k_pcg_zdots_m, rg, s, F.n, (const float *)F.star0_32, (const uint8_t *)F.freev, (const float *)z,
-                   (const float *)F.b32, (const float *)mg->zo32, first ? 1 : 0, gauge, mg->partials, mg->counter,
-                   mg->scal, skip);
+            if (d64)
+                launch(mg, k_pcg_zdots_d, rg, s, F.n, (const double *)F.star0, (const uint8_t *)F.freev,
+                       (const float *)z, (const double *)mg->orr, (const float *)mg->zo32, first ? 1 : 0, gauge,
+                       mg->partials, mg->counter, mg->scal, skip);
+            else
+                launch(mg, k_pcg_zdots_m, rg, s, F.n, (const float *)F.star0_32, (const uint8_t *)F.freev,
+                       (const float *)z, (const float *)F.b32, (const float *)mg->zo32, first ? 1 : 0, gauge,
+                       mg->partials, mg->counter, mg->scal, skip);
         }
         ProfScope ps(mg, DEC_PK_PUPD, top, s);
         if (mode == DEC_MODE_MIXED_FF)
             launch(mg, k_pcg_pupd_f, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
                    mg->fp, first ? 1 : 0, (const Scal *)mg->scal, skip);
+        else if (d64)
+            launch(mg, k_pcg_pupd_d, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
+                   mg->op, first ? 1 : 0, (const Scal *)mg->scal, skip);
         else
             launch(mg, k_pcg_pupd_m, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
                    mg->op, first ? 1 : 0, (const Scal *)mg->scal, skip);
@@ -537,7 +562,18 @@ void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
     });
     {
     ProfScope ps(mg, DEC_PK_UPDATE, top, s);
-    if (mode == DEC_MODE_MIXED && solver != DEC_SOLVER_CG)
+    if (mode == DEC_MODE_MIXED && solver != DEC_SOLVER_CG) {
+        const dec_mg_opts &o = mg->H.opts;
+        int s0mode = 0;
+        float e0 = 0.f;
+        if ((o.fuse & DEC_FUSE_OUTER) && o.nu1 > 0 && o.smoother != DEC_SMOOTH_MCGS) {
+            const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+            s0mode = cheb && 1 < o.nu1 ? 2 : 1;
+            e0 = (float)(cheb ? F.e_pre[0] : o.omega);
+        }
+        launch(mg, k_pcg_update_d, rg, s, F.n, (const double *)mg->op, (const double *)mg->oq, mg->ox, mg->orr, F.b32,
+               mg->partials, mg->counter, mg->scal, skip, s0mode, (const float *)F.dg32, F.x32[0], F.d32[0], e0);
+    } else if (mode == DEC_MODE_MIXED_F32DOT && solver != DEC_SOLVER_CG)
         launch(mg, k_pcg_update_m, rg, s, F.n, (const double *)mg->op, (const double *)mg->oq, mg->ox, mg->orr, F.b32,
                mg->partials, mg->counter, mg->scal, skip);
     else
@@ -566,7 +602,7 @@ void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
                    (const float *)mg->fxh, (const float *)mg->fxl, F.b32, mg->frl, mg->partials, mg->counter,
                    mg->scal, skip);
         });
-    } else if (mode == DEC_MODE_MIXED) {
+    } else if (mode == DEC_MODE_MIXED || mode == DEC_MODE_MIXED_F32DOT) {
         float *e = cycle<float>(mg, top, F.b32, s, skip);
         {
             ProfScope ps(mg, DEC_PK_ADD, top, s);
@@ -575,9 +611,14 @@ void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
         dispatch_k(F.K, [&](auto kt) {
             constexpr int KT = decltype(kt)::value;
             ProfScope ps(mg, DEC_PK_MGRES, top, s);
-            launch(mg, k_mg_residual_m<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
-                   (const uint8_t *)F.freev, (const double *)mg->ob,
-                   (const double *)mg->ox, mg->orr, F.b32, mg->partials, mg->counter, mg->scal, skip);
+            if (mode == DEC_MODE_MIXED)
+                launch(mg, k_mg_residual_d<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
+                       (const uint8_t *)F.freev, (const double *)mg->ob, (const double *)mg->ox, mg->orr, F.b32,
+                       mg->partials, mg->counter, mg->scal, skip);
+            else
+                launch(mg, k_mg_residual_m<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
+                       (const uint8_t *)F.freev, (const double *)mg->ob,
+                       (const double *)mg->ox, mg->orr, F.b32, mg->partials, mg->counter, mg->scal, skip);
         });
     } else {
         double *e = cycle<double>(mg, top, mg->orr, s, skip);
@@ -712,7 +753,7 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         o = *po;
     else
         dec_solve_default_opts(&o);
-    if (o.solver < 0 || o.solver > 2 || o.mode < DEC_MODE_F64 || o.mode > DEC_MODE_MIXED_FF || o.maxit < 0 ||
+    if (o.solver < 0 || o.solver > 2 || o.mode < DEC_MODE_F64 || o.mode > DEC_MODE_MIXED_F32DOT || o.maxit < 0 ||
         o.maxit >= kHist || !(o.tol >= 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad solve options"));
     if (o.check_every < 1) o.check_every = 1;
@@ -880,9 +921,16 @@ int check_mg(const dec_mg *mg) {
     return DEC_OK;
 }
 
+// A compute call needs a device handle whose device is the current one: its
+// tables, its work vectors and the caller's vectors all live there.
 int check_dev(const dec_mg *mg) {
     if (!mg) return fail(Status::fail(DEC_ERR_ARG, "null handle"));
     if (mg->host_only) return fail(Status::fail(DEC_ERR_ARG, "handle was built with DEC_HOST_ONLY"));
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != mg->device)
+        return fail(Status::fail(DEC_ERR_ARG, "the hierarchy lives on device " + std::to_string(mg->device) +
+                                                  " but device " + std::to_string(cur) + " is current"));
     return DEC_OK;
 }
 
@@ -1038,6 +1086,7 @@ int setup_coarse_cycle(dec_mg *mg) {
     A.G = mg->G32;
     A.S = mg->scal;
     A.top_mutable = top == nl - 1 ? 1 : 0;
+    A.wait_rounds = kCoarseWaitRounds;
     // The dynamic shared-memory limit is a property of the kernel, shared by
     // every hierarchy on the device: raise it once to the device maximum
     // (each layout is at most that), never to one hierarchy's size.
@@ -1382,6 +1431,17 @@ int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_strea
     return DEC_OK;
 }
 
+int dec_mg_set_wait_limit(dec_mg *mg, int rounds) {
+    if (int rc = check_dev(mg)) return rc;
+    if (mg->coarse_top < 0) return DEC_OK;  // no device-side wait in this hierarchy's cycles
+    const int r = rounds < 0 ? decdev::kCoarseWaitRounds : std::min(rounds, decdev::kCoarseWaitRounds);
+    if (r != mg->coarse_args.wait_rounds) {
+        mg->coarse_args.wait_rounds = r;
+        drop_graphs(mg);  // captured graphs hold the old argument block
+    }
+    return DEC_OK;
+}
+
 int dec_mg_profile(dec_mg *mg, int enable) {
     if (int rc = check_dev(mg)) return rc;
     if (enable < 0 || enable > 2) return fail(Status::fail(DEC_ERR_ARG, "enable must be 0, 1 or 2"));
@@ -1661,7 +1721,10 @@ void noalloc_smooth(dec_mg *mg, int l, NoallocLevel &B, const float *b, int nu, 
     });
 }
 
-float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const float *b, cudaStream_t s) {
+// err keeps the first failed enqueue that is not a kernel launch (launch
+// errors surface through cudaGetLastError).
+float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const float *b, cudaStream_t s,
+                     cudaError_t &err) {
     DevLevel &L = mg->lv[l];
     if (l == 0) {
         int g = (int)std::min<int64_t>(mg->nsm * 4, (L.n * 32 + kThreads - 1) / kThreads);
@@ -1671,10 +1734,12 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
     const dec_mg_opts &o = mg->H.opts;
     DevLevel &C = mg->lv[l - 1];
     int cur = 0;
-    if (o.nu1 > 0)
+    if (o.nu1 > 0) {
         noalloc_smooth(mg, l, B[l], b, o.nu1, true, false, cur, s);
-    else
-        cudaMemsetAsync(B[l].x[0], 0, sizeof(float) * L.n, s);  // the iterate starts at zero
+    } else {
+        const cudaError_t e = cudaMemsetAsync(B[l].x[0], 0, sizeof(float) * L.n, s);  // the iterate starts at zero
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    }
     const int g = grid_for(mg, L.n);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
@@ -1687,7 +1752,7 @@ float *noalloc_cycle(dec_mg *mg, std::vector<NoallocLevel> &B, int l, const floa
                    (const float *)nullptr, (const float *)nullptr, nullptr, (const float *)nullptr, (float *)nullptr,
                    (float *)nullptr, 0.f);
     });
-    float *ec = noalloc_cycle(mg, B, l - 1, B[l - 1].b, s);
+    float *ec = noalloc_cycle(mg, B, l - 1, B[l - 1].b, s, err);
     launch(mg, k_prolong<float>, g, s, C.n, L.n, L.par, ec, B[l].x[cur], nullptr);
     if (o.nu2 > 0) noalloc_smooth(mg, l, B[l], b, o.nu2, false, true, cur, s);
     return B[l].x[cur];
@@ -1728,8 +1793,13 @@ extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_s
         constexpr int KT = decltype(kt)::value;
         launch(mg, k_residual<float, KT>, g, s, F.n, F.K, F.col, F.w32, b, x, B[top].b, nullptr);
     });
-    float *e = noalloc_cycle(mg, B, top, B[top].b, s);
+    cudaError_t err = cudaSuccess;
+    float *e = noalloc_cycle(mg, B, top, B[top].b, s, err);
     launch(mg, k_axpy1<float>, g, s, F.n, e, x, nullptr);
+    if (err != cudaSuccess) {
+        (void)cudaGetLastError();
+        return cuda_fail(err, "cudaMemsetAsync (allocation-free cycle)");
+    }
     CK(cudaGetLastError());
     return DEC_OK;
 }
@@ -1891,10 +1961,10 @@ int dec_porous_step(dec_mg *mg, double *T, double *P, const uint8_t *fixed, cons
 }
 
 // Tsitouras' 5(4) pair (Ch. Tsitouras, Comput. Math. Appl. 62 (2011) 770-775),
-// the "Tsit5" integrator of Sec. 3.2.2: nodes, strictly lower coupling
-// coefficients (row 6 doubles as the 5th-order weights: first same as last)
-// and the error weights of the embedded 4th-order solution.
-constexpr double kTsC[7] = {0.0, 0.161, 0.327, 0.9, 0.9800255409045097, 1.0, 1.0};
+// the "Tsit5" integrator of Sec. 3.2.2: the strictly lower coupling
+// coefficients (row 6 doubles as the 5th-order weights: first same as last;
+// the model is autonomous, so the nodes are not needed) and the error
+// weights of the embedded 4th-order solution.
 constexpr double kTsA[7][6] = {
     {0, 0, 0, 0, 0, 0},
     {0.161, 0, 0, 0, 0, 0},
@@ -1955,34 +2025,43 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
     DevLevel &F = mg->lv.back();
     const int n = F.n;
     const size_t vb = sizeof(double) * n;
-    // device work: the seven stage rates, the next state and one scalar
+    // device work: the seven stage rates, the current and the next state, the
+    // pressure of the current state and one scalar.  T and P are written only
+    // by finish(), so on every return T is the state at out.t and P its pressure.
     double *work = nullptr;
-    cudaError_t ce = cudaMalloc(&work, 8 * vb + sizeof(double));
+    cudaError_t ce = cudaMalloc(&work, 10 * vb + sizeof(double));
     if (ce != cudaSuccess)
         return ce == cudaErrorMemoryAllocation ? fail(Status::fail(DEC_ERR_OOM, "cudaMalloc")) : cuda_fail(ce, "cudaMalloc");
     double *k[7];
     for (int j = 0; j < 7; ++j) k[j] = work + (size_t)j * n;
-    double *nxt = work + (size_t)7 * n, *esum = work + (size_t)8 * n;
-    double *cur = T;
+    double *cur = work + (size_t)7 * n, *nxt = work + (size_t)8 * n, *pacc = work + (size_t)9 * n;
+    double *esum = work + (size_t)10 * n;
     dec_rk_stats out{};
     double t = 0.0, dt = dt0;  // time reached and next step (reported on every return)
     const int g = grid_for(mg, n), rg = red_grid(mg, n);
     auto finish = [&](int code) {
         out.t = t;
         out.dt = dt;
-        if ((code == DEC_OK || code == DEC_ERR_NOT_CONVERGED) && cur != T) {
-            cudaError_t e = cudaMemcpyAsync(T, cur, vb, cudaMemcpyDeviceToDevice, R.s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(R.s);
-            if (e != cudaSuccess) code = cuda_fail(e, "dec_porous_rk");
-        }
+        cudaError_t e = cudaMemcpyAsync(T, cur, vb, cudaMemcpyDeviceToDevice, R.s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(P, pacc, vb, cudaMemcpyDeviceToDevice, R.s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(R.s);
+        if (e != cudaSuccess && code == DEC_OK) code = cuda_fail(e, "dec_porous_rk");
         cudaFree(work);
         out.pressure_iters = R.iters;
         out.pressure_rel_res = R.worst;
         if (stats) *stats = out;
         return code;
     };
+    ce = cudaMemcpyAsync(cur, T, vb, cudaMemcpyDeviceToDevice, R.s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(pacc, P, vb, cudaMemcpyDeviceToDevice, R.s);
+    if (ce != cudaSuccess) {
+        cudaFree(work);
+        return cuda_fail(ce, "dec_porous_rk");
+    }
     porous_potential(R);
     if (int rc = porous_rate(R, cur, P, k[0])) return finish(rc);
+    if ((ce = cudaMemcpyAsync(pacc, P, vb, cudaMemcpyDeviceToDevice, R.s)) != cudaSuccess)
+        return finish(cuda_fail(ce, "dec_porous_rk"));
     out.nfev = 1;
     const double slack = 1e-12 * t_end;
     bool rejected_last = false;
@@ -2011,14 +2090,18 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
         launch(mg, k_rk_error, rg, R.s, n, (const double *)cur, (const double *)nxt, e, h, rtol, atol,
                mg->partials, mg->counter, esum);
         double ssum = 0.0;
-        CK(cudaMemcpyAsync(&ssum, esum, sizeof(double), cudaMemcpyDeviceToHost, R.s));
-        CK(cudaStreamSynchronize(R.s));
+        ce = cudaMemcpyAsync(&ssum, esum, sizeof(double), cudaMemcpyDeviceToHost, R.s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(R.s);
+        if (ce != cudaSuccess) return finish(cuda_fail(ce, "dec_porous_rk step error"));
         const double en = std::sqrt(ssum / (double)n);
         if (!std::isfinite(en) && !fixed_step) return finish(fail(Status::fail(DEC_ERR_NONFINITE, "non-finite step error")));
         if (fixed_step || en <= 1.0) {
             t = last ? t_end : t + h;
             std::swap(cur, nxt);
             std::swap(k[0], k[6]);
+            // P holds the pressure of the accepted stage-7 state
+            if ((ce = cudaMemcpyAsync(pacc, P, vb, cudaMemcpyDeviceToDevice, R.s)) != cudaSuccess)
+                return finish(cuda_fail(ce, "dec_porous_rk"));
             out.naccept += 1;
             if (!fixed_step) {
                 const double grow = rejected_last ? 1.0 : 10.0;

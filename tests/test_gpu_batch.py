@@ -133,6 +133,22 @@ def test_full_batched_workload():
         a = xs[0][:, j].cpu().numpy()
         r = xj.cpu().numpy()
         assert omg.star0_norm(oh.finest, a - r) / omg.star0_norm(oh.finest, r) < 1e-6
+    # sampled right-hand sides against the oracle's u*: its FP64 MG-PCG to 1e-13 on the full hierarchy,
+    # *0-norm error <= 1e-6 (four of the 64 on the icosphere x7, one square per subdivision level)
+    ohi = omg.build_hierarchy(v, t, 7, 6, "gauge", sphere=True)
+    for j in (0, 21, 42, 63):
+        ref = omg.pcg_solve(ohi, b_ico[:, j], 1e-13, 200)
+        a = xs[0].reshape(hi.n, -1)[:, j].cpu().numpy()
+        err = omg.star0_norm(ohi.finest, a - ref.x) / omg.star0_norm(ohi.finest, ref.x)
+        print(f"batched icosphere x7 rhs {j}: *0 error vs oracle u* {err:.3e}")
+        assert err <= 1e-6, (j, err)
+    for m, nsub in zip((1, 9, 17, 25), (6, 7, 8, 9)):
+        ohq = omg.build_hierarchy(vs, ts, nsub, nsub - 1, "dirichlet")
+        ref = omg.pcg_solve(ohq, bs[m][:, 0], 1e-13, 200)
+        a = xs[m].reshape(-1).cpu().numpy()
+        err = omg.star0_norm(ohq.finest, a - ref.x) / omg.star0_norm(ohq.finest, ref.x)
+        print(f"batched square x{nsub} (mesh {m}): *0 error vs oracle u* {err:.3e}")
+        assert err <= 1e-6, (m, err)
 
 
 def test_autotuner_picks_a_converging_setting():

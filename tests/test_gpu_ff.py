@@ -10,7 +10,10 @@ results are compared bitwise, including a b far below the FP32 range.
 
 The full-size case is the benchmark workload: icosphere x8 (655,362
 vertices), levels 8..2, Chebyshev V(2,2), gauge, a sum of real spherical
-harmonics l = 1..16 (seed 1), MG-PCG to 1e-8, in every precision mode.
+harmonics l = 1..16 (seed 1), MG-PCG to 1e-8, in every precision mode.  Each
+mode's solution is compared with the oracle's u*: the oracle's own flexible
+MG-PCG (FP64, the same hierarchy and smoother) run to a relative residual of
+1e-13, in the *0 norm, to the stated 1e-6.
 """
 import numpy as np
 import pytest
@@ -44,14 +47,26 @@ def _full_size():
         P = _lib()
         v, t = W.icosahedron()
         h = P.Hierarchy(P.Mesh(v, t), 8, 7, bc="gauge", sphere=True, smoother="chebyshev")
-        meshes, _ = omesh.refine(v, t, 8, sphere=True)
-        lev = omg.make_level(meshes[-1], "gauge")
+        oh = omg.build_hierarchy(v, t, 8, 7, "gauge", sphere=True, opts=omg.MGOptions(smoother="chebyshev"))
+        lev = oh.finest
         b = W.sh_sum(lev.mesh.verts, W.sh_coefficients(1))
-        _full.update(h=h, lev=lev, b=b, bp=omg.project_mean_zero(lev, b))
+        _full.update(h=h, oh=oh, lev=lev, b=b, bp=omg.project_mean_zero(lev, b))
     return _full
 
 
-@pytest.mark.parametrize("mode", ["f64", "mixed", "mixed_ff"])
+def _u_star():
+    F = _full_size()
+    if "ustar" not in F:
+        ref = omg.pcg_solve(F["oh"], F["b"], 1e-13, 200)
+        assert ref.rel_res <= 1e-13
+        F["ustar"] = ref.x
+    return F["ustar"]
+
+
+MODES = ["f64", "mixed", "mixed_ff", "mixed_f32dot"]
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_benchmark_workload_true_residual(mode):
     F = _full_size()
     h, lev = F["h"], F["lev"]
@@ -70,12 +85,24 @@ def test_benchmark_workload_true_residual(mode):
 def test_benchmark_workload_modes_agree():
     F = _full_size()
     xs = F.get("x", {})
-    if len(xs) < 3:
-        pytest.skip("needs the three solves above")
+    if len(xs) < len(MODES):
+        pytest.skip("needs the solves above")
     s0 = F["lev"].star0
-    # both at relative residual 1e-8: solutions agree far below the discretization error
-    assert _s0_rel(s0, xs["mixed_ff"], xs["f64"]) < 1e-7
-    assert _s0_rel(s0, xs["mixed"], xs["f64"]) < 1e-7
+    # all at relative residual 1e-8: solutions agree far below the discretization error
+    for m in MODES[1:]:
+        assert _s0_rel(s0, xs[m], xs["f64"]) < 1e-7, m
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_benchmark_workload_solution_error_vs_oracle(mode):
+    # ||u - u*||_*0 / ||u*||_*0 <= 1e-6 against the oracle's u* (its FP64 MG-PCG to 1e-13)
+    F = _full_size()
+    ustar = _u_star()
+    x, st = F["h"].solve(_dev(F["b"]), solver="mgpcg", mode=mode, tol=1e-8)
+    assert st.status == 0
+    err = _s0_rel(F["lev"].star0, x.cpu().numpy(), ustar)
+    print(f"icosphere x8 {mode}: iters {st.iters}, rel_res {st.rel_res:.3e}, *0 error vs oracle u* {err:.3e}")
+    assert err <= 1e-6, err
 
 
 @pytest.mark.parametrize("solver", ["mg", "mgpcg"])
