@@ -252,6 +252,28 @@ int dec_mesh_copy_table(const dec_mesh *mesh, int what, void *host_out);
 int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t flags,
                  const double *star1_scale, const dec_mg_opts *opts, dec_mg **out);
 void dec_mg_destroy(dec_mg *mg);
+/* dec_mg_build_maps: a hierarchy on caller-given meshes related by
+ * caller-given geometric maps, for transfers beyond nested subdivision
+ * (Sec. 2.2: a PL map f from the fine mesh to the coarse one and its matrix
+ * M(f), whose column j holds the global barycentric coordinates of the image
+ * of fine vertex j; Sec. 2.2.1: interpolation is M(f)^T, restriction the
+ * transpose of the row-normalized M(f), or the *0-adjoint of interpolation
+ * with DEC_RESTRICT_STAR0).  meshes: host array of nlevels mesh handles,
+ * coarsest first (level 0), copied.  map_idx[l], map_w[l] (l = 0 ..
+ * nlevels-2; host arrays, copied): for each vertex v of level l+1, three
+ * vertices of level l at [3v .. 3v+2] and their weights -- the nonzeros of
+ * column v of M(f), padded with weight 0 -- the layout of DEC_TABLE_MAP_IDX /
+ * DEC_TABLE_MAP_W.  The operator is discretized on every mesh (Sec. 3.1.1,
+ * last paragraph); bc and star1_scale (finest edges) as for dec_mg_build;
+ * flags: DEC_HOST_ONLY or 0.  Interpolation leaves fixed (Dirichlet) fine
+ * vertices at 0.  Errors: DEC_ERR_ARG for a null pointer, an index outside
+ * level l, a non-finite weight, a vertex whose weights do not sum to 1
+ * (within 1e-9), or a coarse vertex that carries no weight (its restriction
+ * row would be empty); the errors of dec_mg_build otherwise.  The cycle runs
+ * on the general transfer kernels (as for DEC_SUBDIV_CUBIC). */
+int dec_mg_build_maps(const dec_mesh *const *meshes, int nlevels, const int32_t *const *map_idx,
+                      const double *const *map_w, int bc, uint32_t flags, const double *star1_scale,
+                      const dec_mg_opts *opts, dec_mg **out);
 int dec_mg_info(const dec_mg *mg, dec_mg_info_t *info);
 /* Copy a host-side table of one level (DEC_TABLE_*) into host_out. */
 int dec_mg_copy_table(const dec_mg *mg, int level, int what, void *host_out);

@@ -97,6 +97,18 @@ def barycentric_matrix(nc, parents):
     return sp.csr_matrix((vals, (rows, cols)), shape=(nc, nf))
 
 
+def map_matrix_from_table(nc, idx, w):
+    """M(f) (n_c x n_f) of a geometric map given per fine vertex j as up to three
+    coarse vertices idx[j] and the barycentric coordinates w[j] of f(v_j) in
+    their triangle (Sec. 2.2, Def. of M(f): column j holds the global
+    barycentric coordinates of the image of fine vertex j)."""
+    idx = np.asarray(idx).reshape(-1, 3)
+    w = np.asarray(w, dtype=np.float64).reshape(-1, 3)
+    nf = len(idx)
+    cols = np.repeat(np.arange(nf), 3)
+    return sp.csr_matrix((w.ravel(), (idx.ravel(), cols)), shape=(nc, nf))
+
+
 def _map_matrix(nc, parents):
     """M(f) from a binary parent table or an explicit map matrix (cubic subdivision)."""
     return parents if sp.issparse(parents) else barycentric_matrix(nc, parents)

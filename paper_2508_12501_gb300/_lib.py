@@ -104,6 +104,8 @@ _SIGS = {
     "dec_mesh_refine": (_i, [_p, _i, _u32, C.POINTER(_p)]),
     "dec_mesh_copy_table": (_i, [_p, _i, _p]),
     "dec_mg_build": (_i, [_p, _i, _i, _i, _u32, _p, C.POINTER(dec_mg_opts), C.POINTER(_p)]),
+    "dec_mg_build_maps": (_i, [C.POINTER(_p), _i, C.POINTER(_p), C.POINTER(_p), _i, _u32, _p,
+                              C.POINTER(dec_mg_opts), C.POINTER(_p)]),
     "dec_mg_destroy": (None, [_p]),
     "dec_mg_info": (_i, [_p, C.POINTER(dec_mg_info_t)]),
     "dec_mg_copy_table": (_i, [_p, _i, _i, _p]),

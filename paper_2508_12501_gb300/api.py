@@ -101,20 +101,9 @@ class Hierarchy:
                  fcycle=False, scheme="binary", fuse_max_rows=None):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
-        o = L.dec_mg_opts()
-        lib.dec_mg_default_opts(C.byref(o))
-        o.smoother = SMOOTHERS[smoother]
-        o.nu1, o.nu2, o.omega = nu1, nu2, omega
-        o.cheby_lo, o.cheby_hi = cheby_lo, cheby_hi
-        o.power_iters, o.gamma = power_iters, gamma
-        o.restriction = RESTRICTIONS[restriction]
-        if fuse is not None:  # None keeps the library default (the row-local fusions)
-            o.fuse = int(fuse) if not isinstance(fuse, bool) else (L.DEC_FUSE_ALL if fuse else 0)
+        o = self._opts(smoother, nu1, nu2, omega, cheby_lo, cheby_hi, power_iters, gamma, restriction, fuse,
+                       fuse_max_rows, coarse_max_rows, fcycle)
         self.fuse = int(o.fuse)
-        if fuse_max_rows is not None:  # None keeps the library default
-            o.fuse_max_rows = int(fuse_max_rows)
-        o.coarse_max_rows = int(coarse_max_rows)
-        o.fcycle = 1 if fcycle else 0
         flags = ((L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0) | ORDERS[order]
                  | SCHEMES[scheme])
         scale = None
@@ -128,6 +117,63 @@ class Hierarchy:
         check(lib.dec_mg_build(mesh._h, int(nsub), int(nlevels), BCS[bc], flags,
                                _np_ptr(scale) if scale is not None else None, C.byref(o), C.byref(h)),
               "dec_mg_build")
+        self._finish(h, bc, host_only)
+
+    @classmethod
+    def from_maps(cls, meshes, maps_idx, maps_w, bc="dirichlet", star1_scale=None, host_only=False, smoother="jacobi",
+                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
+                  restriction="rownorm", fuse=None, fcycle=False, fuse_max_rows=None):
+        """A hierarchy on given meshes (coarsest first) related by given geometric maps (dec_mg_build_maps):
+        maps_idx[l], maps_w[l] are [nv(l+1), 3] arrays -- the coarse vertices of level l and barycentric
+        weights of each vertex of level l+1."""
+        self = cls.__new__(cls)
+        if not all(isinstance(m, Mesh) for m in meshes):
+            raise TypeError("meshes must be Mesh objects")
+        nl = len(meshes)
+        if len(maps_idx) != nl - 1 or len(maps_w) != nl - 1:
+            raise ValueError("one map per pair of consecutive levels")
+        o = self._opts(smoother, nu1, nu2, omega, cheby_lo, cheby_hi, power_iters, gamma, restriction, fuse,
+                       fuse_max_rows, 0, fcycle)
+        self.fuse = int(o.fuse)
+        mi = [np.ascontiguousarray(a, dtype=np.int32).reshape(-1) for a in maps_idx]
+        mw = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in maps_w]
+        for l, (a, w) in enumerate(zip(mi, mw)):
+            if a.size != 3 * meshes[l + 1].nv or w.size != 3 * meshes[l + 1].nv:
+                raise ValueError(f"map {l} must have 3 entries per vertex of level {l + 1}")
+        hs = (C.c_void_p * nl)(*[m._h for m in meshes])
+        pi = (C.c_void_p * max(1, nl - 1))(*[C.c_void_p(a.ctypes.data) for a in mi])
+        pw = (C.c_void_p * max(1, nl - 1))(*[C.c_void_p(w.ctypes.data) for w in mw])
+        scale = None if star1_scale is None else np.ascontiguousarray(star1_scale, dtype=np.float64)
+        self.device = None
+        if not host_only:
+            torch = _torch()
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        h = C.c_void_p()
+        check(lib.dec_mg_build_maps(hs, nl, pi, pw, BCS[bc], L.DEC_HOST_ONLY if host_only else 0,
+                                    _np_ptr(scale) if scale is not None else None, C.byref(o), C.byref(h)),
+              "dec_mg_build_maps")
+        self._finish(h, bc, host_only)
+        return self
+
+    @staticmethod
+    def _opts(smoother, nu1, nu2, omega, cheby_lo, cheby_hi, power_iters, gamma, restriction, fuse, fuse_max_rows,
+              coarse_max_rows, fcycle):
+        o = L.dec_mg_opts()
+        lib.dec_mg_default_opts(C.byref(o))
+        o.smoother = SMOOTHERS[smoother]
+        o.nu1, o.nu2, o.omega = nu1, nu2, omega
+        o.cheby_lo, o.cheby_hi = cheby_lo, cheby_hi
+        o.power_iters, o.gamma = power_iters, gamma
+        o.restriction = RESTRICTIONS[restriction]
+        if fuse is not None:  # None keeps the library default (the row-local fusions)
+            o.fuse = int(fuse) if not isinstance(fuse, bool) else (L.DEC_FUSE_ALL if fuse else 0)
+        if fuse_max_rows is not None:  # None keeps the library default
+            o.fuse_max_rows = int(fuse_max_rows)
+        o.coarse_max_rows = int(coarse_max_rows)
+        o.fcycle = 1 if fcycle else 0
+        return o
+
+    def _finish(self, h, bc, host_only):
         self._h = h
         self.bc = bc
         self.host_only = host_only

@@ -659,7 +659,7 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
         return fail(Status::fail(DEC_ERR_ARG, "bad batch options (block 128/256/512, 1 <= nu <= 8, kgroup a power of two)"));
     for (int m = 0; m < nmesh; ++m) {
         if (!mgs[m] || mgs[m]->host_only) return fail(Status::fail(DEC_ERR_ARG, "a hierarchy is null or host-only"));
-        if (mgs[m]->H.cubic) return fail(Status::fail(DEC_ERR_ARG, "batched solves transfer along binary subdivision"));
+        if (mgs[m]->H.mapped) return fail(Status::fail(DEC_ERR_ARG, "batched solves transfer along binary subdivision (no general maps)"));
         if (nrhs[m] < 1) return fail(Status::fail(DEC_ERR_ARG, "every mesh needs at least one right-hand side"));
     }
     dec_batch *B = new (std::nothrow) dec_batch;

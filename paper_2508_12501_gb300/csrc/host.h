@@ -86,7 +86,8 @@ struct HostHierarchy {
     dec_mg_opts opts{};
     std::vector<HostLevel> levels;
     std::vector<std::vector<int32_t>> parents;  // parents[l]: level-l edges = parents of level l+1 midpoints
-    bool cubic = false;                         // 1->9 subdivision: general maps below instead of parents
+    bool mapped = false;                        // transfers by the general maps below instead of parents:
+                                                // cubic 1->9 subdivision or caller-supplied geometric maps
     std::vector<std::vector<int32_t>> map_idx;  // map_idx[l], map_w[l]: the map from level l to l+1,
     std::vector<std::vector<double>> map_w;     // 3 (coarse vertex, weight) pairs per level-(l+1) vertex
     std::vector<double> G;                      // [n0 * n0] coarse solution operator, row-major
@@ -94,6 +95,13 @@ struct HostHierarchy {
 
 Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton, bool cubic,
                        const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H);
+
+// A hierarchy on caller-given meshes (levels[0] coarsest) with caller-given
+// geometric maps between consecutive levels: maps_idx[l], maps_w[l] hold three
+// (level-l vertex, weight) slots per level-(l+1) vertex (Sec. 2.2, M(f)).
+Status build_hierarchy_maps(const std::vector<const HostMesh *> &meshes,
+                            const std::vector<const int32_t *> &maps_idx, const std::vector<const double *> &maps_w,
+                            int bc, const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H);
 
 // Rebuild ELL weights of one level from its (possibly new) star1.
 Status level_weights(HostLevel &L, int bc);

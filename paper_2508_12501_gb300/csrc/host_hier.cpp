@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <string>
 
 #include "host.h"
 
@@ -202,6 +203,29 @@ static Status coarse_operator(const HostLevel &L, int bc, std::vector<double> &G
     return Status::ok();
 }
 
+// One level: Hodge stars (scaled *1 when star1_scale is given), the free
+// mask, the ELL operator, lambda_max and the greedy colouring.
+static Status make_level(const HostMesh &mesh, int bc, const double *star1_scale, const dec_mg_opts &opts,
+                         HostLevel &L) {
+    L.mesh = mesh;
+    hodge_stars(L.mesh, L.star0, L.star1);
+    if (star1_scale)
+        for (int64_t e = 0; e < L.mesh.ne; ++e) L.star1[e] *= star1_scale[e];
+    if (bc == DEC_BC_DIRICHLET) {
+        L.free_ = boundary_vertices(L.mesh);
+        for (auto &f : L.free_) f = !f;
+    } else {
+        L.free_.assign(L.mesh.nv, 1);
+    }
+    Status st = build_ell(L);
+    if (!st.good()) return st;
+    st = level_weights(L, bc);
+    if (!st.good()) return st;
+    L.lmax = power_lmax(L, opts.power_iters);
+    greedy_colour(L);
+    return Status::ok();
+}
+
 Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool sphere, bool morton, bool cubic,
                        const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H) {
     if (nsub < 0 || nlevels < 1 || nlevels > nsub + 1 || nlevels > 16)
@@ -212,7 +236,7 @@ Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool
     H.opts = opts;
     H.levels.clear();
     H.parents.clear();
-    H.cubic = cubic;
+    H.mapped = cubic;  // cubic subdivision transfers by its geometric map
     H.map_idx.clear();
     H.map_w.clear();
     const int first = nsub + 1 - nlevels;
@@ -239,22 +263,63 @@ Status build_hierarchy(const HostMesh &base, int nsub, int nlevels, int bc, bool
         }
         if (i < first) continue;
         HostLevel L;
-        L.mesh = cur;
-        hodge_stars(L.mesh, L.star0, L.star1);
-        if (i == nsub && star1_scale)
-            for (int64_t e = 0; e < L.mesh.ne; ++e) L.star1[e] *= star1_scale[e];
-        if (bc == DEC_BC_DIRICHLET) {
-            L.free_ = boundary_vertices(L.mesh);
-            for (auto &f : L.free_) f = !f;
-        } else {
-            L.free_.assign(L.mesh.nv, 1);
+        Status st = make_level(cur, bc, i == nsub ? star1_scale : nullptr, opts, L);
+        if (!st.good()) return st;
+        H.levels.push_back(std::move(L));
+    }
+    return coarse_operator(H.levels[0], bc, H.G);
+}
+
+Status build_hierarchy_maps(const std::vector<const HostMesh *> &meshes,
+                            const std::vector<const int32_t *> &maps_idx, const std::vector<const double *> &maps_w,
+                            int bc, const double *star1_scale, const dec_mg_opts &opts, HostHierarchy &H) {
+    const int nl = (int)meshes.size();
+    if (nl < 1 || nl > 16) return Status::fail(DEC_ERR_ARG, "nlevels must be in 1..16");
+    if ((int)maps_idx.size() != nl - 1 || (int)maps_w.size() != nl - 1)
+        return Status::fail(DEC_ERR_ARG, "one map per pair of consecutive levels");
+    if (bc != DEC_BC_DIRICHLET && bc != DEC_BC_GAUGE) return Status::fail(DEC_ERR_ARG, "bad boundary condition");
+    H.bc = bc;
+    H.sphere = false;
+    H.opts = opts;
+    H.levels.clear();
+    H.parents.clear();
+    H.mapped = true;
+    H.map_idx.clear();
+    H.map_w.clear();
+    for (int l = 0; l + 1 < nl; ++l) {
+        // M(f) of Sec. 2.2: each fine vertex's image has barycentric coordinates in one
+        // coarse triangle, so its weights are finite, sum to 1, and name coarse vertices
+        const int64_t nf = meshes[l + 1]->nv, nc = meshes[l]->nv;
+        if (!maps_idx[l] || !maps_w[l]) return Status::fail(DEC_ERR_ARG, "null map");
+        std::vector<int32_t> mi(maps_idx[l], maps_idx[l] + 3 * nf);
+        std::vector<double> mw(maps_w[l], maps_w[l] + 3 * nf);
+        std::vector<uint8_t> hit(nc, 0);
+        for (int64_t v = 0; v < nf; ++v) {
+            double sum = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                const int32_t c = mi[3 * v + q];
+                const double w = mw[3 * v + q];
+                if (c < 0 || c >= nc || !std::isfinite(w))
+                    return Status::fail(DEC_ERR_ARG, "map " + std::to_string(l) + ": vertex " + std::to_string(v) +
+                                                         " has a coarse index out of range or a non-finite weight");
+                sum += w;
+                if (w != 0.0) hit[c] = 1;
+            }
+            if (!(std::fabs(sum - 1.0) <= 1e-9))
+                return Status::fail(DEC_ERR_ARG, "map " + std::to_string(l) + ": the weights of vertex " +
+                                                     std::to_string(v) + " do not sum to 1");
         }
-        Status st = build_ell(L);
+        for (int64_t c = 0; c < nc; ++c)
+            if (!hit[c])
+                return Status::fail(DEC_ERR_ARG, "map " + std::to_string(l) + ": coarse vertex " + std::to_string(c) +
+                                                     " carries no weight (its restriction row would be empty)");
+        H.map_idx.push_back(std::move(mi));
+        H.map_w.push_back(std::move(mw));
+    }
+    for (int l = 0; l < nl; ++l) {
+        HostLevel L;
+        Status st = make_level(*meshes[l], bc, l == nl - 1 ? star1_scale : nullptr, opts, L);
         if (!st.good()) return st;
-        st = level_weights(L, bc);
-        if (!st.good()) return st;
-        L.lmax = power_lmax(L, opts.power_iters);
-        greedy_colour(L);
         H.levels.push_back(std::move(L));
     }
     return coarse_operator(H.levels[0], bc, H.G);

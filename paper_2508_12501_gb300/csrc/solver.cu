@@ -299,15 +299,15 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     // the coarse level's first smoothing step rides on the restriction
     // (not into the shared-memory coarse cycle, which starts from b itself)
     const bool coarse_next = std::is_same<T, float>::value && (o.fuse & DEC_FUSE_COARSE) && l - 1 == mg->coarse_top;
-    const bool cubic = mg->H.cubic;  // general map transfers (k_restrict_map, k_prolong_map), unfused
+    const bool mapped = mg->H.mapped;  // general map transfers (k_restrict_map, k_prolong_map), unfused
     const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0 && !coarse_next &&
-                           o.smoother != DEC_SMOOTH_MCGS && !cubic;
+                           o.smoother != DEC_SMOOTH_MCGS && !mapped;
     bool coarse_pre0 = false;
     const int g = grid_for(mg, L.n);
     const T *w = P<T>::w(L);
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
-        if (fuse_here(o, DEC_FUSE_RESTRICT, L.n) && L.K <= 7 && !cubic) {
+        if (fuse_here(o, DEC_FUSE_RESTRICT, L.n) && L.K <= 7 && !mapped) {
             ProfScope ps(mg, DEC_PK_RESRESTRICT, l, s);
             const int gr = grid_for(mg, (int64_t)C.n * 8);
             const T *s0l = P<T>::s0(L), *s0c = P<T>::s0(C);
@@ -344,7 +344,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
         {
             ProfScope ps(mg, DEC_PK_RESTRICT, l, s);
             const int gc = grid_for(mg, C.n);
-            if (cubic) {
+            if (mapped) {
                 launch(mg, k_restrict_map<T>, gc, s, C.n, L.gKr, (const int32_t *)L.ridx, P<T>::rw(L),
                        (const T *)P<T>::r(L), P<T>::b(C), skip);
             } else if (restrict0) {
@@ -400,7 +400,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
             ec = P<T>::y(C);
         }
     }
-    if (fuse_here(o, DEC_FUSE_PROLONG, L.n) && o.nu2 > 0 && o.smoother != DEC_SMOOTH_MCGS && !cubic) {
+    if (fuse_here(o, DEC_FUSE_PROLONG, L.n) && o.nu2 > 0 && o.smoother != DEC_SMOOTH_MCGS && !mapped) {
         const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
         const T e0 = (T)(cheb ? L.e_post[0] : o.omega);
         const bool dout = cheb && 1 < o.nu2;
@@ -423,7 +423,7 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     }
     {
         ProfScope ps(mg, DEC_PK_PROLONG, l, s);
-        if (cubic)
+        if (mapped)
             launch(mg, k_prolong_map<T>, g, s, L.n, (const int32_t *)L.gidx, P<T>::gw(L), (const T *)ec,
                    P<T>::x(L, cur), skip);
         else
@@ -954,10 +954,13 @@ int upload_map(dec_mg *mg, int l, DevLevel &D) {
     const int nf = D.n, nc = (int)H.levels[l - 1].mesh.nv;
     std::vector<int32_t> gi(3 * (size_t)nf);
     std::vector<double> gw(3 * (size_t)nf);
+    // interpolation x_f += free_f * M(f)^T e_c: a fixed (Dirichlet) fine vertex gets no
+    // correction, whatever coarse vertices its image lies between
+    const std::vector<uint8_t> &ff = H.levels[l].free_;
     for (int v = 0; v < nf; ++v)
         for (int q = 0; q < 3; ++q) {
             gi[(size_t)q * nf + v] = mi[3 * (size_t)v + q];
-            gw[(size_t)q * nf + v] = mw[3 * (size_t)v + q];
+            gw[(size_t)q * nf + v] = ff[v] ? mw[3 * (size_t)v + q] : 0.0;
         }
     // restriction rows: every (fine v, weight) whose map slot points at coarse c, in increasing v
     std::vector<int> cnt(nc + 1, 0);
@@ -1010,7 +1013,7 @@ int setup_coarse_cycle(dec_mg *mg) {
     const dec_mg_opts &o = mg->H.opts;
     const int nl = (int)mg->lv.size();
     if (nl < 2 || o.gamma != 1 || o.fcycle || o.nu1 > kCoarseMaxNu || o.nu2 > kCoarseMaxNu ||
-        o.smoother == DEC_SMOOTH_MCGS || mg->H.cubic)
+        o.smoother == DEC_SMOOTH_MCGS || mg->H.mapped)
         return DEC_OK;
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, mg->device);
@@ -1106,14 +1109,10 @@ int setup_coarse_cycle(dec_mg *mg) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t flags, const double *star1_scale,
-                 const dec_mg_opts *opts, dec_mg **out) {
-    if (!base || !out) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
-    *out = nullptr;
-    if (nsub < 0 || nsub > 14) return fail(Status::fail(DEC_ERR_ARG, "nsub out of range"));
-    dec_mg_opts o;
+// Options of a build: the defaults when opts is null, validated.
+int build_opts(const dec_mg_opts *opts, dec_mg_opts &o) {
     if (opts)
         o = *opts;
     else
@@ -1129,6 +1128,140 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma < 1 || o.gamma > 4 || o.power_iters < 1 ||
         !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
         return fail(Status::fail(DEC_ERR_ARG, "bad multigrid options"));
+    return DEC_OK;
+}
+
+// Device part of a build: uploads every level's tables, allocates the work
+// vectors and the outer-iteration workspace, sets up the shared-memory coarse
+// cycle.  On failure the caller frees the handle.
+int device_build(dec_mg *mg) {
+    const dec_mg_opts &o = mg->H.opts;
+    int rc = DEC_OK;
+    cudaError_t ce = cudaGetDevice(&mg->device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    cudaDeviceGetAttribute(&mg->nsm, cudaDevAttrMultiProcessorCount, mg->device);
+    ce = cudaStreamCreateWithFlags(&mg->cap, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamCreate");
+    const int nl = (int)mg->H.levels.size();
+    mg->lv.resize(nl);
+    for (int l = 0; l < nl; ++l) {
+        decimpl::HostLevel &HL = mg->H.levels[l];
+        DevLevel &D = mg->lv[l];
+        D.n = (int)HL.mesh.nv;
+        D.K = HL.K;
+        D.ne = HL.mesh.ne;
+        D.nc = l > 0 ? (int)mg->H.levels[l - 1].mesh.nv : 0;
+        const size_t slots = (size_t)HL.K * D.n;
+        std::vector<float> w32(slots);
+        for (size_t i = 0; i < slots; ++i) w32[i] = (float)HL.w[i];
+        if ((rc = upload(mg, &D.col, HL.col.data(), slots))) return rc;
+        if ((rc = upload(mg, &D.w64, HL.w.data(), slots))) return rc;
+        if ((rc = upload(mg, &D.w32, w32.data(), slots))) return rc;
+        if ((rc = upload(mg, &D.star0, HL.star0.data(), D.n))) return rc;
+        {
+            std::vector<float> s32(HL.star0.begin(), HL.star0.end());
+            if ((rc = upload(mg, &D.star0_32, s32.data(), D.n))) return rc;
+        }
+        if ((rc = upload(mg, &D.freev, HL.free_.data(), D.n))) return rc;
+        if (l > 0 && !mg->H.mapped) {
+            const std::vector<int32_t> &par = mg->H.parents[l - 1];
+            if ((rc = upload(mg, &D.par, reinterpret_cast<const int2 *>(par.data()), par.size() / 2))) return rc;
+        }
+        if (l > 0 && mg->H.mapped) {
+            if ((rc = upload_map(mg, l, D))) return rc;
+        }
+        for (int i = 0; i < 2; ++i) {
+            if ((rc = dalloc(mg, &D.x32[i], D.n)) || (rc = dalloc(mg, &D.d32[i], D.n)) ||
+                (rc = dalloc(mg, &D.x64[i], D.n)) || (rc = dalloc(mg, &D.d64[i], D.n)))
+                return rc;
+        }
+        if ((rc = dalloc(mg, &D.r32, D.n)) || (rc = dalloc(mg, &D.b32, D.n)) || (rc = dalloc(mg, &D.r64, D.n)) ||
+            (rc = dalloc(mg, &D.b64, D.n)))
+            return rc;
+        if ((o.gamma > 1 || o.fcycle) && (((rc = dalloc(mg, &D.y32, D.n))) || (rc = dalloc(mg, &D.c32, D.n)) ||
+                            (rc = dalloc(mg, &D.y64, D.n)) || (rc = dalloc(mg, &D.c64, D.n))))
+            return rc;
+        cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu1, 1), D.c_pre, D.e_pre);
+        cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu2, 1), D.c_post, D.e_post);
+        if ((rc = dalloc(mg, &D.dg32, D.n)) || (rc = dalloc(mg, &D.dg64, D.n))) return rc;
+        update_diagonals(mg, D, nullptr);
+        if (o.smoother == DEC_SMOOTH_MCGS) {
+            // rows by colour, ascending row id within a colour (counting sort)
+            D.coff.assign(HL.ncolors + 1, 0);
+            for (int v = 0; v < D.n; ++v) D.coff[HL.colors[v] + 1] += 1;
+            for (int c = 0; c < HL.ncolors; ++c) D.coff[c + 1] += D.coff[c];
+            std::vector<int32_t> rows(D.n);
+            std::vector<int> fill(D.coff.begin(), D.coff.end() - 1);
+            for (int v = 0; v < D.n; ++v) rows[fill[HL.colors[v]]++] = v;
+            if ((rc = upload(mg, &D.crow, rows.data(), rows.size()))) return rc;
+        }
+    }
+    // coarsest dense operator
+    {
+        mg->n0 = mg->lv[0].n;
+        const std::vector<double> &G = mg->H.G;
+        std::vector<float> G32(G.size());
+        for (size_t i = 0; i < G.size(); ++i) G32[i] = (float)G[i];
+        if ((rc = upload(mg, &mg->G64, G.data(), G.size())) || (rc = upload(mg, &mg->G32, G32.data(), G32.size())))
+            return rc;
+    }
+    // finest extras and outer workspace
+    {
+        decimpl::HostLevel &HF = mg->H.levels.back();
+        const int n = (int)HF.mesh.nv;
+        if ((rc = upload(mg, &mg->slot_edge, HF.slot_edge.data(), HF.slot_edge.size()))) return rc;
+        if ((rc = upload(mg, &mg->edges, reinterpret_cast<const int2 *>(HF.mesh.edges.data()), (size_t)HF.mesh.ne)))
+            return rc;
+        mg->dim = HF.mesh.dim;
+        if ((rc = upload(mg, &mg->verts, HF.mesh.verts.data(), HF.mesh.verts.size()))) return rc;
+        if ((rc = dalloc(mg, &mg->pot, n)) || (rc = dalloc(mg, &mg->ptmp, n)) || (rc = dalloc(mg, &mg->prhs, n)))
+            return rc;
+        double **vecs[] = {&mg->ox, &mg->orr, &mg->op, &mg->oq, &mg->ozn, &mg->ozo, &mg->ob, &mg->tmp};
+        for (double **v : vecs)
+            if ((rc = dalloc(mg, v, n))) return rc;
+        if ((rc = dalloc(mg, &mg->zo32, n))) return rc;
+        float **fvecs[] = {&mg->fxh, &mg->fxl, &mg->frl, &mg->fqh, &mg->fql, &mg->fp, &mg->fbh, &mg->fbl};
+        for (float **v : fvecs)
+            if ((rc = dalloc(mg, v, n))) return rc;
+        {
+            DevLevel &DF = mg->lv.back();
+            const size_t slots = (size_t)HF.K * n;
+            std::vector<float> wlo(slots);
+            for (size_t i = 0; i < slots; ++i) wlo[i] = (float)(HF.w[i] - (double)(float)HF.w[i]);
+            if ((rc = upload(mg, &DF.wlo, wlo.data(), slots))) return rc;
+        }
+
+        if ((rc = dalloc(mg, &mg->partials, 8 * kMaxRedBlocks))) return rc;
+        if ((rc = dalloc(mg, &mg->counter, 1))) return rc;
+        if ((rc = dalloc(mg, &mg->scal, 1))) return rc;
+        ce = cudaMemset(mg->scal, 0, sizeof(Scal));
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemset");
+        ce = cudaMemset(mg->counter, 0, sizeof(unsigned));
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemset");
+        ce = cudaMallocHost((void **)&mg->scal_h, sizeof(Scal));
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMallocHost");
+        double s = 0.0;
+        for (int v = 0; v < n; ++v)
+            if (HF.free_[v]) s += HF.star0[v];
+        mg->star0_sum = s;
+    }
+    if ((rc = setup_coarse_cycle(mg))) return rc;
+    ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaDeviceSynchronize");
+    return DEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t flags, const double *star1_scale,
+                 const dec_mg_opts *opts, dec_mg **out) {
+    if (!base || !out) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    *out = nullptr;
+    if (nsub < 0 || nsub > 14) return fail(Status::fail(DEC_ERR_ARG, "nsub out of range"));
+    dec_mg_opts o;
+    if (int rc = build_opts(opts, o)) return rc;
     dec_mg *mg = new (std::nothrow) dec_mg;
     if (!mg) return fail(Status::fail(DEC_ERR_OOM, "host allocation"));
     int rc = DEC_OK;
@@ -1152,117 +1285,46 @@ int dec_mg_build(const dec_mesh *base, int nsub, int nlevels, int bc, uint32_t f
         *out = mg;
         return DEC_OK;
     }
-    cudaError_t ce = cudaGetDevice(&mg->device);
-    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
-    cudaDeviceGetAttribute(&mg->nsm, cudaDevAttrMultiProcessorCount, mg->device);
-    ce = cudaStreamCreateWithFlags(&mg->cap, cudaStreamNonBlocking);
-    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
-    const int nl = (int)mg->H.levels.size();
-    mg->lv.resize(nl);
-    for (int l = 0; l < nl; ++l) {
-        decimpl::HostLevel &HL = mg->H.levels[l];
-        DevLevel &D = mg->lv[l];
-        D.n = (int)HL.mesh.nv;
-        D.K = HL.K;
-        D.ne = HL.mesh.ne;
-        D.nc = l > 0 ? (int)mg->H.levels[l - 1].mesh.nv : 0;
-        const size_t slots = (size_t)HL.K * D.n;
-        std::vector<float> w32(slots);
-        for (size_t i = 0; i < slots; ++i) w32[i] = (float)HL.w[i];
-        if ((rc = upload(mg, &D.col, HL.col.data(), slots))) return bail(rc);
-        if ((rc = upload(mg, &D.w64, HL.w.data(), slots))) return bail(rc);
-        if ((rc = upload(mg, &D.w32, w32.data(), slots))) return bail(rc);
-        if ((rc = upload(mg, &D.star0, HL.star0.data(), D.n))) return bail(rc);
-        {
-            std::vector<float> s32(HL.star0.begin(), HL.star0.end());
-            if ((rc = upload(mg, &D.star0_32, s32.data(), D.n))) return bail(rc);
-        }
-        if ((rc = upload(mg, &D.freev, HL.free_.data(), D.n))) return bail(rc);
-        if (l > 0 && !mg->H.cubic) {
-            const std::vector<int32_t> &par = mg->H.parents[l - 1];
-            if ((rc = upload(mg, &D.par, reinterpret_cast<const int2 *>(par.data()), par.size() / 2))) return bail(rc);
-        }
-        if (l > 0 && mg->H.cubic) {
-            if ((rc = upload_map(mg, l, D))) return bail(rc);
-        }
-        for (int i = 0; i < 2; ++i) {
-            if ((rc = dalloc(mg, &D.x32[i], D.n)) || (rc = dalloc(mg, &D.d32[i], D.n)) ||
-                (rc = dalloc(mg, &D.x64[i], D.n)) || (rc = dalloc(mg, &D.d64[i], D.n)))
-                return bail(rc);
-        }
-        if ((rc = dalloc(mg, &D.r32, D.n)) || (rc = dalloc(mg, &D.b32, D.n)) || (rc = dalloc(mg, &D.r64, D.n)) ||
-            (rc = dalloc(mg, &D.b64, D.n)))
-            return bail(rc);
-        if ((o.gamma > 1 || o.fcycle) && (((rc = dalloc(mg, &D.y32, D.n))) || (rc = dalloc(mg, &D.c32, D.n)) ||
-                            (rc = dalloc(mg, &D.y64, D.n)) || (rc = dalloc(mg, &D.c64, D.n))))
-            return bail(rc);
-        cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu1, 1), D.c_pre, D.e_pre);
-        cheb_coeffs(HL.lmax, o.cheby_lo, o.cheby_hi, std::max(o.nu2, 1), D.c_post, D.e_post);
-        if ((rc = dalloc(mg, &D.dg32, D.n)) || (rc = dalloc(mg, &D.dg64, D.n))) return bail(rc);
-        update_diagonals(mg, D, nullptr);
-        if (o.smoother == DEC_SMOOTH_MCGS) {
-            // rows by colour, ascending row id within a colour (counting sort)
-            D.coff.assign(HL.ncolors + 1, 0);
-            for (int v = 0; v < D.n; ++v) D.coff[HL.colors[v] + 1] += 1;
-            for (int c = 0; c < HL.ncolors; ++c) D.coff[c + 1] += D.coff[c];
-            std::vector<int32_t> rows(D.n);
-            std::vector<int> fill(D.coff.begin(), D.coff.end() - 1);
-            for (int v = 0; v < D.n; ++v) rows[fill[HL.colors[v]]++] = v;
-            if ((rc = upload(mg, &D.crow, rows.data(), rows.size()))) return bail(rc);
-        }
-    }
-    // coarsest dense operator
-    {
-        mg->n0 = mg->lv[0].n;
-        const std::vector<double> &G = mg->H.G;
-        std::vector<float> G32(G.size());
-        for (size_t i = 0; i < G.size(); ++i) G32[i] = (float)G[i];
-        if ((rc = upload(mg, &mg->G64, G.data(), G.size())) || (rc = upload(mg, &mg->G32, G32.data(), G32.size())))
-            return bail(rc);
-    }
-    // finest extras and outer workspace
-    {
-        decimpl::HostLevel &HF = mg->H.levels.back();
-        const int n = (int)HF.mesh.nv;
-        if ((rc = upload(mg, &mg->slot_edge, HF.slot_edge.data(), HF.slot_edge.size()))) return bail(rc);
-        if ((rc = upload(mg, &mg->edges, reinterpret_cast<const int2 *>(HF.mesh.edges.data()), (size_t)HF.mesh.ne)))
-            return bail(rc);
-        mg->dim = HF.mesh.dim;
-        if ((rc = upload(mg, &mg->verts, HF.mesh.verts.data(), HF.mesh.verts.size()))) return bail(rc);
-        if ((rc = dalloc(mg, &mg->pot, n)) || (rc = dalloc(mg, &mg->ptmp, n)) || (rc = dalloc(mg, &mg->prhs, n)))
-            return bail(rc);
-        double **vecs[] = {&mg->ox, &mg->orr, &mg->op, &mg->oq, &mg->ozn, &mg->ozo, &mg->ob, &mg->tmp};
-        for (double **v : vecs)
-            if ((rc = dalloc(mg, v, n))) return bail(rc);
-        if ((rc = dalloc(mg, &mg->zo32, n))) return bail(rc);
-        float **fvecs[] = {&mg->fxh, &mg->fxl, &mg->frl, &mg->fqh, &mg->fql, &mg->fp, &mg->fbh, &mg->fbl};
-        for (float **v : fvecs)
-            if ((rc = dalloc(mg, v, n))) return bail(rc);
-        {
-            DevLevel &DF = mg->lv.back();
-            const size_t slots = (size_t)HF.K * n;
-            std::vector<float> wlo(slots);
-            for (size_t i = 0; i < slots; ++i) wlo[i] = (float)(HF.w[i] - (double)(float)HF.w[i]);
-            if ((rc = upload(mg, &DF.wlo, wlo.data(), slots))) return bail(rc);
-        }
+    if ((rc = device_build(mg))) return bail(rc);
+    *out = mg;
+    return DEC_OK;
+}
 
-        if ((rc = dalloc(mg, &mg->partials, 8 * kMaxRedBlocks))) return bail(rc);
-        if ((rc = dalloc(mg, &mg->counter, 1))) return bail(rc);
-        if ((rc = dalloc(mg, &mg->scal, 1))) return bail(rc);
-        ce = cudaMemset(mg->scal, 0, sizeof(Scal));
-        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
-        ce = cudaMemset(mg->counter, 0, sizeof(unsigned));
-        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
-        ce = cudaMallocHost((void **)&mg->scal_h, sizeof(Scal));
-        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMallocHost"));
-        double s = 0.0;
-        for (int v = 0; v < n; ++v)
-            if (HF.free_[v]) s += HF.star0[v];
-        mg->star0_sum = s;
+int dec_mg_build_maps(const dec_mesh *const *meshes, int nlevels, const int32_t *const *map_idx,
+                      const double *const *map_w, int bc, uint32_t flags, const double *star1_scale,
+                      const dec_mg_opts *opts, dec_mg **out) {
+    if (!meshes || !out || (nlevels > 1 && (!map_idx || !map_w))) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    *out = nullptr;
+    if (nlevels < 1 || nlevels > 16) return fail(Status::fail(DEC_ERR_ARG, "nlevels must be in 1..16"));
+    if (flags & ~(uint32_t)DEC_HOST_ONLY) return fail(Status::fail(DEC_ERR_ARG, "the only flag is DEC_HOST_ONLY"));
+    dec_mg_opts o;
+    if (int rc = build_opts(opts, o)) return rc;
+    dec_mg *mg = new (std::nothrow) dec_mg;
+    if (!mg) return fail(Status::fail(DEC_ERR_OOM, "host allocation"));
+    auto bail = [&](int code) {
+        free_all(mg);
+        delete mg;
+        return code;
+    };
+    try {
+        std::vector<const decimpl::HostMesh *> ms;
+        for (int l = 0; l < nlevels; ++l) {
+            if (!meshes[l]) return bail(fail(Status::fail(DEC_ERR_ARG, "null mesh")));
+            ms.push_back(dec_mesh_host(meshes[l]));
+        }
+        std::vector<const int32_t *> mi(map_idx ? map_idx : nullptr, map_idx ? map_idx + (nlevels - 1) : nullptr);
+        std::vector<const double *> mw(map_w ? map_w : nullptr, map_w ? map_w + (nlevels - 1) : nullptr);
+        Status st = decimpl::build_hierarchy_maps(ms, mi, mw, bc, star1_scale, o, mg->H);
+        if (!st.good()) return bail(fail(st));
+    } catch (const std::bad_alloc &) {
+        return bail(fail(Status::fail(DEC_ERR_OOM, "host allocation")));
     }
-    if ((rc = setup_coarse_cycle(mg))) return bail(rc);
-    ce = cudaDeviceSynchronize();
-    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceSynchronize"));
+    if (flags & DEC_HOST_ONLY) {
+        mg->host_only = true;
+        *out = mg;
+        return DEC_OK;
+    }
+    if (int rc = device_build(mg)) return bail(rc);
     *out = mg;
     return DEC_OK;
 }
@@ -1309,7 +1371,7 @@ int dec_mg_copy_table(const dec_mg *mg, int level, int what, void *out) {
             const int nf = (int)mg->H.levels[level + 1].mesh.nv, nc = (int)L.mesh.nv;
             std::vector<int32_t> mi;
             std::vector<double> mw;
-            if (mg->H.cubic) {
+            if (mg->H.mapped) {
                 mi = mg->H.map_idx[level];
                 mw = mg->H.map_w[level];
             } else {
@@ -1336,7 +1398,7 @@ int dec_mg_copy_table(const dec_mg *mg, int level, int what, void *out) {
             // the coarse edge of each new vertex of level + 1, in that level's vertex order
             if (level + 1 >= (int)mg->H.levels.size())
                 return fail(Status::fail(DEC_ERR_ARG, "the finest level has no parents table"));
-            if (mg->H.cubic) return fail(Status::fail(DEC_ERR_ARG, "cubic hierarchies store DEC_TABLE_MAP_*"));
+            if (mg->H.mapped) return fail(Status::fail(DEC_ERR_ARG, "hierarchies with general-map transfers store DEC_TABLE_MAP_*"));
             const std::vector<int32_t> &par = mg->H.parents[level];
             std::memcpy(out, par.data(), par.size() * 4);
             break;
@@ -1767,7 +1829,7 @@ extern "C" int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_s
         return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle is a V-cycle (gamma = 1)"));
     if (mg->H.opts.smoother == DEC_SMOOTH_MCGS)
         return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle smooths with Jacobi or Chebyshev"));
-    if (mg->H.cubic) return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle transfers along binary subdivision"));
+    if (mg->H.mapped) return fail(Status::fail(DEC_ERR_ARG, "the allocation-free cycle transfers along binary subdivision (no general maps)"));
     const size_t need = noalloc_floats(mg) * sizeof(float);
     if (need > DEC_NOALLOC_SCRATCH_BYTES)
         return fail(Status::fail(DEC_ERR_ARG, "hierarchy needs " + std::to_string(need) +

@@ -217,3 +217,36 @@ def test_host_only_handles_refuse_device_entry_points():
     ms, by = C.c_double(), C.c_double()
     assert L.lib.dec_mg_time_kernel(h._h, L.PROF_KINDS.index("spmv64"), -1, 5, C.byref(ms), C.byref(by),
                                     None) == L.DEC_ERR_ARG
+
+
+def test_mapped_hierarchy_host_tables_and_refusals():
+    # dec_mg_build_maps (host only): the caller's map comes back bit for bit and equals the oracle's M(f);
+    # the per-level tables match the oracle's levels; malformed maps are refused before any device work
+    ms, mi, mw = W.jittered_square_levels(3, 5)
+    meshes = [Mesh(v, t) for v, t in ms]
+    h = Hierarchy.from_maps(meshes, mi, mw, bc="dirichlet", host_only=True)
+    assert h.nv == [len(v) for v, _ in ms]
+    om = [omesh.build_mesh(v, t) for v, t in ms]
+    for l in range(2):
+        assert np.array_equal(h.table(l, "map_idx"), mi[l]) and np.array_equal(h.table(l, "map_w"), mw[l])
+        Mo = omg.map_matrix_from_table(om[l].nv, mi[l], mw[l]).toarray()
+        Ml = np.zeros_like(Mo)
+        for q in range(3):
+            np.add.at(Ml, (h.table(l, "map_idx")[:, q], np.arange(om[l + 1].nv)), h.table(l, "map_w")[:, q])
+        assert np.array_equal(Ml, Mo)
+    for l in range(3):
+        assert np.array_equal(h.table(l, "edges"), om[l].edges)
+        lev = omg.make_level(om[l], "dirichlet")
+        assert np.array_equal(h.table(l, "free").astype(bool), lev.free)
+    bad = [a.copy() for a in mi]
+    bad[0][0, 0] = -1
+    with pytest.raises(DecError) as ei:
+        Hierarchy.from_maps(meshes, bad, mw, host_only=True)
+    assert ei.value.code == lib_mod.DEC_ERR_ARG and "out of range" in str(ei.value)
+    badw = [a.copy() for a in mw]
+    badw[1][5, :] = [0.5, 0.5, 0.5]
+    with pytest.raises(DecError) as ei:
+        Hierarchy.from_maps(meshes, mi, badw, host_only=True)
+    assert ei.value.code == lib_mod.DEC_ERR_ARG and "sum to 1" in str(ei.value)
+    with pytest.raises(ValueError):
+        Hierarchy.from_maps(meshes, mi[:1], mw[:1], host_only=True)

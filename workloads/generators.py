@@ -27,6 +27,7 @@ __all__ = [
     "gaussian_initial_T",
     "random_directions",
     "heptagon_fan",
+    "jittered_square_levels",
     "WORKLOADS",
 ]
 
@@ -231,3 +232,60 @@ def heptagon_fan():
     verts = np.concatenate([[[0.0, 0.0]], np.stack([np.cos(ang), np.sin(ang)], axis=1)])
     tris = np.array([[0, 1 + k, 1 + (k + 1) % 7] for k in range(7)], dtype=np.int32)
     return verts, tris
+
+
+def jittered_square_levels(nlevels, seed, base=2, amp=0.15):
+    """Non-nested meshes of the unit square and the geometric maps between them.
+
+    Level l (0 = coarsest) is the (2^(base+l) + 1)^2 grid_mesh with each interior
+    vertex moved by amp * h * U[-1,1]^2 (h its grid spacing, seeded by seed + l),
+    so no level's vertices lie on the next coarser mesh's edges: the levels are
+    not related by subdivision.  The map from level l+1 to level l sends every
+    vertex to its own position; it is described, as a caller of a geometric-map
+    hierarchy supplies it, by the coarse triangle that contains the position and
+    the position's barycentric coordinates there: maps_idx[l], maps_w[l] are
+    [nv(l+1), 3] arrays (int32 coarse vertex ids, float64 weights).
+
+    Returns (meshes, maps_idx, maps_w), meshes a list of (verts, tris).
+    """
+    meshes = []
+    for lev in range(nlevels):
+        n = 2 ** (base + lev) + 1
+        v, t = grid_mesh(n, n)
+        h = 1.0 / (n - 1)
+        inner = (v[:, 0] > 0.0) & (v[:, 0] < 1.0) & (v[:, 1] > 0.0) & (v[:, 1] < 1.0)
+        d = np.random.default_rng(seed + lev).uniform(-1.0, 1.0, size=v.shape) * (amp * h)
+        meshes.append((v + d * inner[:, None], t))
+    maps_idx, maps_w = [], []
+    for lev in range(nlevels - 1):
+        cv, ct = meshes[lev]
+        fv, _ = meshes[lev + 1]
+        nc = 2 ** (base + lev) + 1
+        H = 1.0 / (nc - 1)
+        idx = np.zeros((len(fv), 3), dtype=np.int32)
+        wts = np.zeros((len(fv), 3))
+        for j, p in enumerate(fv):
+            ci = min(int(p[0] / H), nc - 2)
+            cj = min(int(p[1] / H), nc - 2)
+            best = None
+            # the containing triangle lies in this grid cell or a neighbouring one (jitter < H / 2)
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    i2, j2 = ci + di, cj + dj
+                    if not (0 <= i2 < nc - 1 and 0 <= j2 < nc - 1):
+                        continue
+                    for tri in ct[2 * (j2 * (nc - 1) + i2): 2 * (j2 * (nc - 1) + i2) + 2]:
+                        a, b, c = cv[tri[0]], cv[tri[1]], cv[tri[2]]
+                        m = np.array([[b[0] - a[0], c[0] - a[0]], [b[1] - a[1], c[1] - a[1]]])
+                        s, r = np.linalg.solve(m, p - a)
+                        lam = np.array([1.0 - s - r, s, r])
+                        if best is None or lam.min() > best[1].min():
+                            best = (tri, lam)
+            tri, lam = best
+            lam = np.where(np.abs(lam) < 1e-14, 0.0, lam)
+            idx[j] = tri
+            wts[j] = lam / lam.sum()
+        maps_idx.append(idx)
+        maps_w.append(wts)
+    return meshes, maps_idx, maps_w
+
