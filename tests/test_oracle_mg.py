@@ -189,7 +189,9 @@ def test_mg_and_pcg_reach_direct_solution(smoother, which):
     for r in (r1, r2):
         assert r.rel_res <= 1e-10
         assert mg.star0_norm(lev, r.x - xs) / mg.star0_norm(lev, xs) < 1e-8
-    band = {"jacobi": 0.35, "chebyshev": 0.3, "gs": 0.2, "mcgs": 0.2}[smoother]
+    # Jacobi: the spectral radius of the V(2,2) error propagator of this operator and these transfers is
+    # 0.31 (test_jacobi_v22_factor_is_the_dense_error_propagators_spectral_radius); the others converge faster
+    band = {"jacobi": 0.32, "chebyshev": 0.3, "gs": 0.2, "mcgs": 0.2}[smoother]
     assert mg.convergence_factor(r1.history) < band
     assert r2.iters <= r1.iters
 
@@ -273,3 +275,71 @@ def test_f_cycle_between_v_and_w():
         res[name] = mg.convergence_factor(r.history)
     assert res["W"] <= res["F"] * 1.05 and res["F"] <= res["V"] * 1.05, res
     assert res["F"] < res["V"], res
+
+
+def _dense_vcycle_propagator(n, nlev, omega, nu1, nu2):
+    """V-cycle error propagator on the interior of the (n+1)^2 grid of the unit square, built from the
+    textbook definitions alone (not from the oracle): the 5-point operator (4 u_i - sum of the 4 neighbours)
+    / h^2 -- the DEC operator on this triangulation, whose hypotenuses carry *1 = 0 -- damped Jacobi,
+    interpolation linear on the triangles (a midpoint takes the mean of its edge's ends, the diagonal edges
+    running (i,j)-(i+1,j+1)), restriction the row-normalized transpose of that map, the operator
+    rediscretized on every level and an exact solve on the coarsest:
+    E_l = S^nu2 (I - P (I - E_{l-1}) A_{l-1}^-1 R A_l) S^nu1."""
+    m = n - 1
+    A = np.zeros((m * m, m * m))
+    for j in range(1, n):
+        for i in range(1, n):
+            k = (j - 1) * m + (i - 1)
+            A[k, k] = 4.0 * n * n
+            for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                if 1 <= i + di <= n - 1 and 1 <= j + dj <= n - 1:
+                    A[k, (j + dj - 1) * m + (i + di - 1)] = -1.0 * n * n
+    if nlev == 1:
+        return np.zeros_like(A)
+    nc = n // 2 + 1
+    M = np.zeros((nc * nc, (n + 1) * (n + 1)))
+    for j in range(n + 1):
+        for i in range(n + 1):
+            if i % 2 == 0 and j % 2 == 0:
+                par = [(i // 2, j // 2, 1.0)]
+            elif j % 2 == 0:
+                par = [((i - 1) // 2, j // 2, 0.5), ((i + 1) // 2, j // 2, 0.5)]
+            elif i % 2 == 0:
+                par = [(i // 2, (j - 1) // 2, 0.5), (i // 2, (j + 1) // 2, 0.5)]
+            else:
+                par = [((i - 1) // 2, (j - 1) // 2, 0.5), ((i + 1) // 2, (j + 1) // 2, 0.5)]
+            for I, J, w in par:
+                M[J * nc + I, j * (n + 1) + i] = w
+    R = M / M.sum(axis=1, keepdims=True)
+    ic = [J * nc + I for J in range(1, nc - 1) for I in range(1, nc - 1)]
+    jf = [j * (n + 1) + i for j in range(1, n) for i in range(1, n)]
+    P, R = M[np.ix_(ic, jf)].T, R[np.ix_(ic, jf)]
+    Ec = _dense_vcycle_propagator(n // 2, nlev - 1, omega, nu1, nu2)
+    mc = n // 2 - 1
+    Ac = np.zeros((mc * mc, mc * mc))
+    nn = n // 2
+    for j in range(1, nn):
+        for i in range(1, nn):
+            k = (j - 1) * mc + (i - 1)
+            Ac[k, k] = 4.0 * nn * nn
+            for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                if 1 <= i + di <= nn - 1 and 1 <= j + dj <= nn - 1:
+                    Ac[k, (j + dj - 1) * mc + (i + di - 1)] = -1.0 * nn * nn
+    S = np.eye(m * m) - omega * A / (4.0 * n * n)
+    C = np.eye(m * m) - P @ (np.eye(mc * mc) - Ec) @ np.linalg.solve(Ac, R @ A)
+    return np.linalg.matrix_power(S, nu2) @ C @ np.linalg.matrix_power(S, nu1)
+
+
+def test_jacobi_v22_factor_is_the_dense_error_propagators_spectral_radius():
+    # The paper's transfers with damped Jacobi (omega = 2/3) V(2,2) on config 1's 5 levels: the asymptotic
+    # residual reduction per cycle is the spectral radius of the cycle's error propagator, 0.307 here (the
+    # smoothing factor alone, (2/3)^4 = 0.198, ignores the coarse-grid correction's own error)
+    E = _dense_vcycle_propagator(32, 5, 2.0 / 3.0, 2, 2)
+    rho = float(max(abs(np.linalg.eigvals(E))))
+    assert 0.30 < rho < 0.31
+    h = _square(5, 5)
+    r = mg.mg_solve(h, W.uniform_field(h.finest.mesh.nv, 13), 1e-13, 100)
+    assert r.iters >= 21
+    fac = (r.history[20] / r.history[15]) ** 0.2  # asymptotic rate: cycles 16-20, past the fast start
+    assert abs(fac - rho) < 0.02, (fac, rho)
+
