@@ -365,46 +365,67 @@ int dec_solve_backward(dec_mg *mg, const double *u, const double *grad_u, double
 
 /* ---- batched solves ------------------------------------------------------------
  * (Not in the paper: solves many right-hand sides on many hierarchies together.)
- * Each hierarchy's right-hand sides are split into groups of k (a power of
- * two, kgroup, or the smallest power of two >= the mesh's count when kgroup
- * = 0) whose vectors are interleaved, value j of vertex v at [v*k + j], so a
- * neighbour gather reads k contiguous values; every operation of the cycle
- * is one launch over all groups of all meshes.  The solver is FP32 cycles
- * inside FP64 iterative refinement, x += C(b - L x), until every right-hand
- * side has ||b - L x||_2 / ||b||_2 <= tol (Sec. 3.1.2); the refinement
- * loop runs on the device.  All hierarchies must use the same restriction;
- * the batch uses its own smoother and sweep count (nu1 = nu2 = nu) with each
- * hierarchy's Chebyshev interval and lambda_max.  The hierarchies must
- * outlive the batch and must not be solved concurrently with it. */
+ * The right-hand sides of every hierarchy -- of all entries that pass the
+ * same handle, in entry order -- are split into groups of k (a power of two,
+ * kgroup, or the smallest power of two >= their count, at most `block`, when
+ * kgroup = 0) whose vectors are interleaved, value j of vertex v at
+ * [v*k + j], so a neighbour gather reads k contiguous values and one read of
+ * the operator serves the group; every operation of the cycle is one launch
+ * over all groups of all meshes.  Solvers (Sec. 3.1.2 with the
+ * mixed-precision pattern): FP32 cycles inside an FP64 outer iteration per
+ * right-hand side -- flexible MG-PCG in the *0 inner product (FP64 residual,
+ * dot products, updates, gauge projection; DEC_SOLVER_MGPCG, the default) or
+ * iterative refinement x += C(b - L x) (DEC_SOLVER_MG) -- until every
+ * right-hand side has ||b - L x||_2 / ||b||_2 <= tol.  A right-hand side that
+ * converged stops moving (step 0) while the others continue.  The loop runs
+ * on the device.  Per-right-hand-side sums are formed in a fixed order, so
+ * results are bitwise reproducible.  All hierarchies must use the same
+ * restriction and live on the current device; the batch uses its own
+ * smoother and sweep count (nu1 = nu2 = nu) with each hierarchy's Chebyshev
+ * interval and lambda_max.  The hierarchies must outlive the batch and must
+ * not be solved concurrently with it. */
 typedef struct dec_batch dec_batch;
 typedef struct dec_batch_opts {
     int block;    /* threads per block of the batched kernels: 128, 256 or 512 */
-    int kgroup;   /* right-hand sides per interleaved group (power of two <= block), 0: per mesh */
+    int kgroup;   /* right-hand sides per interleaved group (power of two <= block), 0: per hierarchy */
     int nu;       /* smoothing sweeps before and after the coarse correction, 1..8 */
     int smoother; /* DEC_SMOOTH_JACOBI or DEC_SMOOTH_CHEBYSHEV */
+    int solver;   /* DEC_SOLVER_MGPCG (default) or DEC_SOLVER_MG (refinement) */
 } dec_batch_opts;
 typedef struct dec_batch_stats {
-    int iters;          /* refinement passes                                  */
+    int iters;          /* outer iterations (MG-PCG) or refinement passes      */
     double max_rel_res; /* largest final relative residual                     */
     int64_t launches;   /* libdec kernels launched by the call                 */
     int64_t dof;        /* finest vertices x right-hand sides over all meshes   */
 } dec_batch_stats;
 void dec_batch_default_opts(dec_batch_opts *opts);
-/* mgs: host array of nmesh hierarchies; nrhs: host array of right-hand-side
- * counts.  Allocates the batch's device vectors.  Errors: DEC_ERR_ARG,
- * DEC_ERR_OOM, DEC_ERR_CUDA. */
+/* mgs: host array of nmesh hierarchies (an entry may repeat a handle: its
+ * right-hand sides join that hierarchy's groups); nrhs: host array of
+ * right-hand-side counts.  Allocates the batch's device vectors.  Errors:
+ * DEC_ERR_ARG, DEC_ERR_OOM, DEC_ERR_CUDA. */
 int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_batch_opts *opts, dec_batch **out);
 void dec_batch_destroy(dec_batch *batch);
-/* b, x: host arrays of nmesh DEVICE pointers, mesh m's vectors being double
+/* b, x: host arrays of nmesh DEVICE pointers, entry m's vectors being double
  * [nv_finest(m) * nrhs(m)] in [v * nrhs + j] order.  Under DEC_BC_GAUGE each
  * right-hand side is projected to *0-weighted mean zero and so is its
  * solution.  Synchronizes `stream`.  Errors as for dec_solve. */
 int dec_batch_solve(dec_batch *batch, const double *const *b, double *const *x, double tol, int maxit,
                     dec_batch_stats *stats, dec_stream_t stream);
+/* dec_batch_solve_backward: the adjoint of every solve of the batch (as
+ * dec_solve_backward, per right-hand side).  Given u = L^-1 b and grad_u =
+ * dJ/du (host arrays of nmesh device pointers, layout as for dec_batch_solve),
+ * solves L mu = *0^-1 grad_u on the same batch, then writes grad_b = *0 mu
+ * and, where grad_star1 (nullable array; nullable entries) gives a device
+ * vector of [ne_finest(m) * nrhs(m)] doubles, grad_star1[e * nrhs + j] =
+ * -(d0 mu_j)_e (d0 u_j)_e.  Same options, tolerance and errors as
+ * dec_batch_solve. */
+int dec_batch_solve_backward(dec_batch *batch, const double *const *u, const double *const *grad_u,
+                             double *const *grad_b, double *const *grad_star1, double tol, int maxit,
+                             dec_batch_stats *stats, dec_stream_t stream);
 int dec_batch_info(const dec_batch *batch, int *ngroups, int *total_rhs, int64_t *dof, size_t *device_bytes);
 /* dec_batch_tune: the batch autotuner.  For each candidate setting (cands,
  * or when null a grid of block {128,256,512} x kgroup {0,8,16,32} x nu
- * {1,2,3}, Chebyshev) it builds a batch, solves once to warm up, times
+ * {1,2,3}, Chebyshev, MG-PCG) it builds a batch, solves once to warm up, times
  * `reps` solves of b with CUDA events on `stream`, and keeps the fastest
  * that converges.  times (nullable, one per candidate) receives the mean
  * milliseconds, -1 for a failed candidate.  x receives the last solution. */
@@ -414,9 +435,9 @@ int dec_batch_tune(dec_mg *const *mgs, const int *nrhs, int nmesh, const double 
 /* dec_batch_time_smooth: mean duration of one launch of the batched
  * finest-level smoothing sweep (every group), over `reps` back-to-back
  * launches timed with CUDA events on `stream`, and its algorithmic bytes
- * (each mesh's finest operator once -- K column indices and K weights per
- * row, shared by all its groups -- and per right-hand side x, b, the new x
- * and, for Chebyshev, a direction vector; padding columns not counted). */
+ * (each group's finest operator once -- K column indices and K weights per
+ * row -- and per right-hand side x, b, the new x and, for Chebyshev, a
+ * direction vector; padding columns not counted). */
 int dec_batch_time_smooth(dec_batch *batch, int reps, double *avg_ms, double *bytes, dec_stream_t stream);
 
 /* ---- porous convection (Sec. 3.2) -------------------------------------------

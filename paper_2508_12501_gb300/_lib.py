@@ -76,7 +76,8 @@ class dec_porous_params(C.Structure):
 
 
 class dec_batch_opts(C.Structure):
-    _fields_ = [("block", C.c_int), ("kgroup", C.c_int), ("nu", C.c_int), ("smoother", C.c_int)]
+    _fields_ = [("block", C.c_int), ("kgroup", C.c_int), ("nu", C.c_int), ("smoother", C.c_int),
+                ("solver", C.c_int)]
 
 
 class dec_batch_stats(C.Structure):
@@ -123,6 +124,8 @@ _SIGS = {
     "dec_batch_create": (_i, [C.POINTER(_p), C.POINTER(_i), _i, C.POINTER(dec_batch_opts), C.POINTER(_p)]),
     "dec_batch_destroy": (None, [_p]),
     "dec_batch_solve": (_i, [_p, C.POINTER(_p), C.POINTER(_p), C.c_double, _i, C.POINTER(dec_batch_stats), _p]),
+    "dec_batch_solve_backward": (_i, [_p, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.c_double, _i,
+                                      C.POINTER(dec_batch_stats), _p]),
     "dec_batch_info": (_i, [_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64), C.POINTER(C.c_size_t)]),
     "dec_batch_tune": (_i, [C.POINTER(_p), C.POINTER(_i), _i, C.POINTER(_p), C.POINTER(_p), C.c_double, _i,
                             C.POINTER(dec_batch_opts), _i, _i, C.POINTER(dec_batch_opts), C.POINTER(C.c_double),

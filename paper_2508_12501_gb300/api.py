@@ -488,15 +488,17 @@ class Batch:
     shape [nv, nrhs] (or flat [nv * nrhs]) in row-major order.
     """
 
-    def __init__(self, hierarchies, nrhs, block=256, kgroup=0, nu=2, smoother="chebyshev"):
+    def __init__(self, hierarchies, nrhs, block=256, kgroup=0, nu=2, smoother="chebyshev", solver="mgpcg"):
         self.h = list(hierarchies)
         self.nrhs = [int(k) for k in nrhs]
         if len(self.h) != len(self.nrhs) or not self.h:
             raise ValueError("one right-hand-side count per hierarchy")
+        if solver not in ("mg", "mgpcg"):
+            raise ValueError("batched solver must be 'mg' or 'mgpcg'")
         o = L.dec_batch_opts()
         lib.dec_batch_default_opts(C.byref(o))
-        o.block, o.kgroup, o.nu, o.smoother = block, kgroup, nu, SMOOTHERS[smoother]
-        self.opts = dict(block=block, kgroup=kgroup, nu=nu, smoother=smoother)
+        o.block, o.kgroup, o.nu, o.smoother, o.solver = block, kgroup, nu, SMOOTHERS[smoother], SOLVERS[solver]
+        self.opts = dict(block=block, kgroup=kgroup, nu=nu, smoother=smoother, solver=solver)
         arr = (C.c_void_p * len(self.h))(*[hh._h.value for hh in self.h])
         ks = (C.c_int * len(self.h))(*self.nrhs)
         bh = C.c_void_p()
@@ -529,6 +531,29 @@ class Batch:
             check(rc, "dec_batch_solve")
         return xs, BatchStats(st.iters, st.max_rel_res, st.launches, st.dof, rc)
 
+    def solve_backward(self, us, grad_us, want_star1=True, tol=1e-8, maxit=100, raise_on_fail=True):
+        """Adjoint of every solve (dec_batch_solve_backward): per entry, the solutions u and dJ/du in the
+        layout of solve(); returns (grad_b list, grad_star1 list or None, BatchStats)."""
+        torch = _torch()
+        gb, gs, pu, pg = [], [], [], []
+        for hh, k, u, g in zip(self.h, self.nrhs, us, grad_us):
+            pu.append(hh._vec(u.reshape(-1), hh.n * k, (torch.float64,), "u"))
+            pg.append(hh._vec(g.reshape(-1), hh.n * k, (torch.float64,), "grad_u"))
+            gb.append(torch.empty_like(u))
+            if want_star1:
+                ne = hh.ne[-1]
+                gs.append(torch.empty(ne, k, dtype=torch.float64, device=hh.device) if k > 1 else
+                          torch.empty(ne, dtype=torch.float64, device=hh.device))
+        arr = lambda ps: (C.c_void_p * len(ps))(*[p.value for p in ps])  # noqa: E731
+        pgb = [C.c_void_p(t.data_ptr()) for t in gb]
+        pgs = arr([C.c_void_p(t.data_ptr()) for t in gs]) if want_star1 else None
+        st = L.dec_batch_stats()
+        rc = lib.dec_batch_solve_backward(self._h, arr(pu), arr(pg), arr(pgb), pgs, float(tol), int(maxit),
+                                          C.byref(st), self.h[0]._stream())
+        if rc not in (L.DEC_OK, L.DEC_ERR_NOT_CONVERGED) or (raise_on_fail and rc != L.DEC_OK):
+            check(rc, "dec_batch_solve_backward")
+        return gb, (gs if want_star1 else None), BatchStats(st.iters, st.max_rel_res, st.launches, st.dof, rc)
+
     def time_smooth(self, reps=20):
         """(mean ms, algorithmic bytes) of one batched finest-level smoothing launch."""
         ms, by = C.c_double(), C.c_double()
@@ -553,10 +578,13 @@ def tune_batch(hierarchies, nrhs, bs, tol=1e-8, maxit=100, candidates=None, reps
     cands = (L.dec_batch_opts * len(candidates))()
     for c, o in zip(cands, candidates):
         c.block, c.kgroup, c.nu, c.smoother = o["block"], o["kgroup"], o["nu"], SMOOTHERS[o["smoother"]]
+        c.solver = SOLVERS[o.get("solver", "mgpcg")]
     times = (C.c_double * len(candidates))()
     best = L.dec_batch_opts()
     best_ms = C.c_double()
     check(lib.dec_batch_tune(arr, ks, len(hs), ab, ax, float(tol), int(maxit), cands, len(candidates), int(reps),
                              C.byref(best), C.byref(best_ms), times, hs[0]._stream()), "dec_batch_tune")
-    bo = dict(block=best.block, kgroup=best.kgroup, nu=best.nu, smoother=inv[best.smoother])
+    inv_solver = {v: k for k, v in SOLVERS.items()}
+    bo = dict(block=best.block, kgroup=best.kgroup, nu=best.nu, smoother=inv[best.smoother],
+              solver=inv_solver[best.solver])
     return bo, best_ms.value, [(o, t) for o, t in zip(candidates, times)]

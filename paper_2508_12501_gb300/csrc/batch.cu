@@ -1,18 +1,23 @@
 // Batched solves: many right-hand sides on many hierarchies of uneven size,
-// advanced together.  Each hierarchy's right-hand sides are split into
-// groups of k (a power of two) whose vectors are interleaved, value j of
-// vertex v at [v * k + j], so one gather of a neighbour reads k contiguous
-// values.  Every operation of the cycle is one launch over all groups of all
-// meshes: a tile list maps each block to (group level, item range), items
-// being (vertex, right-hand side) pairs.  Operations are aligned by depth
-// below each hierarchy's finest level, so the number of launches per cycle
-// follows the deepest hierarchy, not the number of meshes.
+// advanced together.  The right-hand sides of every hierarchy (entries that
+// share a hierarchy are merged) are split into groups of k (a power of two)
+// whose vectors are interleaved, value j of vertex v at [v * k + j], so one
+// gather of a neighbour reads k contiguous values and one read of the
+// operator serves the whole group.  Every operation of the cycle is one
+// launch over all groups of all meshes: a tile list maps each block to
+// (group level, item range), items being (vertex, right-hand side) pairs.
+// Operations are aligned by depth below each hierarchy's finest level, so the
+// number of launches per cycle follows the deepest hierarchy, not the number
+// of meshes.
 //
-// Solver: FP32 cycles (Sec. 2.2.1 transfers, Jacobi or Chebyshev smoothing,
-// dense coarsest solve) inside FP64 iterative refinement,
-// x += C(b - L x), until every right-hand side satisfies
-// ||b - L x||_2 / ||b||_2 <= tol (Sec. 3.1.2).  The refinement loop runs on
-// the device as a CUDA graph with a while node.
+// Solvers (Sec. 3.1.2, with the mixed-precision pattern): FP32 cycles
+// (Sec. 2.2.1 transfers, Jacobi or Chebyshev smoothing, dense coarsest solve)
+// inside an FP64 outer iteration per right-hand side -- flexible MG-PCG in the
+// *0 inner product (FP64 residual, dot products, updates and gauge
+// projection), or iterative refinement x += C(b - L x) -- until every
+// right-hand side satisfies ||b - L x||_2 / ||b||_2 <= tol.  The loop runs on
+// the device as a CUDA graph with a while node.  The adjoint solve
+// L mu = *0^-1 dJ/du shares the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,11 +50,12 @@ struct BLevel {
     int res_idx;  // buffer holding this level's cycle result
     float cpre[kBMaxNu], epre[kBMaxNu], cpost[kBMaxNu], epost[kBMaxNu];
     const float *G;  // level 0: dense solution operator
-    // finest level: FP64 outer refinement
+    // finest level: the FP64 outer iteration (refinement or MG-PCG)
     const double *w64;
     const uint8_t *freev;
     const double *star0;
     double *ox, *orr, *ob;
+    double *op, *oq, *ozo;  // MG-PCG: search direction, L p, previous shifted preconditioned vector
     int rhs_base;     // index of this group's first right-hand side in the batch
     int gauge;
     double s0sum;     // sum of *0 over free vertices
@@ -307,28 +313,61 @@ __global__ void k_b_prolong(const BLevel *__restrict__ lv, const BTile *__restri
         prolong_body<1>(L, C, t, dst);
 }
 
-// Per-right-hand-side sums: a thread's items all share j = threadIdx.x & (k-1)
-// (tiles start on vertex boundaries and blockDim is a multiple of k); the
-// block folds its threads per j in shared memory, then adds once per j.
-__device__ __forceinline__ void b_sum_per_rhs(double v, int k, int base, double *out) {
-    extern __shared__ double sh[];
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    if ((int)threadIdx.x < k) {
-        double a = 0.0;
-        for (int m = threadIdx.x; m < (int)blockDim.x; m += k) a += sh[m];
-        atomicAdd(out + base + threadIdx.x, a);
+// ---------------------------------------------------------------------------
+// Finest level: the FP64 outer iteration of every right-hand side.
+//
+// These kernels run on the finest tile list (block b works on tile b; a tile
+// belongs to one group and covers whole vertices), one item per thread.
+// Every thread's items share one right-hand side j = threadIdx.x & (k-1),
+// because tiles start on vertex boundaries and blockDim is a multiple of k.
+// Per-right-hand-side sums are deterministic: the block folds its threads per
+// j in a fixed order and writes one partial per (sum, tile, j); k_b_finalize
+// adds a right-hand side's partials over its group's tiles in tile order.
+// ---------------------------------------------------------------------------
+
+struct BSums {
+    double *part;  // [kBMaxSums][ntile][kmax]
+    int ntile, kmax;
+};
+constexpr int kBMaxSums = 4;
+
+// Per right-hand side: its group's finest tiles [tb, te), its column j, its
+// finest level descriptor and whether it is a caller's column (live) or padding.
+struct BRhs {
+    int tb, te, j, lev, live;
+};
+
+// Per right-hand side scalars of the outer iteration (FP64).
+struct BScal {
+    double rz, alpha, beta, c, rn2, bn2, thr2, rel, mean;
+    int done, stalled;
+};
+
+template <int NS>
+__device__ __forceinline__ void bsum_write(const double (&acc)[NS], int k, const BSums &P) {
+    extern __shared__ double sh[];  // blockDim.x doubles
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        sh[threadIdx.x] = acc[s];
+        __syncthreads();
+        if ((int)threadIdx.x < k) {
+            double a = 0.0;
+            for (int m = threadIdx.x; m < (int)blockDim.x; m += k) a += sh[m];
+            P.part[((size_t)s * P.ntile + blockIdx.x) * P.kmax + threadIdx.x] = a;
+        }
+        __syncthreads();
     }
 }
 
-// FP64 residual of the refinement: r = b - L x (free rows), r32 = cycle input, sums of r^2 (and b^2)
-__global__ void k_b_res64(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, double *rn2, double *bn2,
-                          const int *skip) {
+__device__ __forceinline__ int rhs_of(const BLevel &L, int i) { return L.rhs_base + (i & (L.k - 1)); }
+
+// Standalone refinement: r = b - L x (FP64, free rows), r32 = cycle input, sums of r^2 and b^2.
+__global__ void k_b_res64(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, BSums P, const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
-    double acc = 0.0, accb = 0.0;
+    double acc[2] = {0.0, 0.0};
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift, j = i & (L.k - 1);
         double ri = 0.0, bi = 0.0;
@@ -344,14 +383,10 @@ __global__ void k_b_res64(const BLevel *__restrict__ lv, const BTile *__restrict
         }
         L.orr[i] = ri;
         L.b[i] = (float)ri;
-        acc = fma(ri, ri, acc);
-        if (bn2) accb = fma(bi, bi, accb);
+        acc[0] = fma(ri, ri, acc[0]);
+        acc[1] = fma(bi, bi, acc[1]);
     }
-    b_sum_per_rhs(acc, L.k, L.rhs_base, rn2);
-    if (bn2) {
-        __syncthreads();
-        b_sum_per_rhs(accb, L.k, L.rhs_base, bn2);
-    }
+    bsum_write<2>(acc, L.k, P);
 }
 
 // x += (double) e
@@ -364,94 +399,257 @@ __global__ void k_b_add64(const BLevel *__restrict__ lv, const BTile *__restrict
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) L.ox[i] += (double)e[i];
 }
 
-// gauge: per-right-hand-side *0-weighted sums of v (ob or ox), then v -= sum / sum(*0)
-__global__ void k_b_mean(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int which, double *msum) {
+// gauge: per-right-hand-side sums of *0 v over free rows (v = ob or ox)
+__global__ void k_b_meansum(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int which, BSums P) {
     pdl_prologue();
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
-    if (!L.gauge) return;  // uniform over the block
     const double *v = which ? L.ox : L.ob;
-    double acc = 0.0;
+    double acc[1] = {0.0};
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int vv = i >> L.kshift;
-        if (L.freev[vv]) acc = fma(__ldg(L.star0 + vv), v[i], acc);
+        if (L.freev[vv]) acc[0] = fma(__ldg(L.star0 + vv), v[i], acc[0]);
     }
-    b_sum_per_rhs(acc, L.k, L.rhs_base, msum);
+    bsum_write<1>(acc, L.k, P);
 }
 
+// v -= mean (gauge groups; the mean is 0 for Dirichlet groups), 0 on fixed rows
 __global__ void k_b_shift(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int which,
-                          const double *msum) {
+                          const BScal *__restrict__ sc) {
     pdl_prologue();
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
-    if (!L.gauge) return;
     double *v = which ? L.ox : L.ob;
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
-        const int vv = i >> L.kshift, j = i & (L.k - 1);
-        v[i] = L.freev[vv] ? v[i] - msum[L.rhs_base + j] / L.s0sum : 0.0;
+        const int vv = i >> L.kshift;
+        v[i] = L.freev[vv] ? v[i] - sc[rhs_of(L, i)].mean : 0.0;
     }
 }
 
-// convergence of every right-hand side; resets the residual sums for the next pass
-__global__ void k_b_conv(int nrhs, double *rn2, const double *bn2, double *rel, Scal *S, int count_iter) {
+// MG-PCG, cold start: x = 0, r = b (free rows), r32 = (float) r; sums of r^2 and b^2.
+__global__ void k_bp_init(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, BSums P) {
     pdl_prologue();
-    __shared__ int all_ok;
-    __shared__ int bad;
-    __shared__ double worst;
-    if (threadIdx.x == 0) {
-        all_ok = 1;
-        bad = 0;
-        worst = 0.0;
+    const BTile t = tiles[blockIdx.x];
+    const BLevel &L = lv[t.lev];
+    double acc[2] = {0.0, 0.0};
+    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+        const int v = i >> L.kshift;
+        const double ri = L.freev[v] ? L.ob[i] : 0.0;
+        L.ox[i] = 0.0;
+        L.orr[i] = ri;
+        L.b[i] = (float)ri;
+        acc[0] = fma(ri, ri, acc[0]);
+        acc[1] = acc[0];
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < nrhs; j += blockDim.x) {
-        const double b2 = bn2[j], r2 = rn2[j];
-        double rr;
-        if (!isfinite(b2) || !isfinite(r2)) {
-            rr = (double)NAN;
-            atomicExch(&bad, 1);
-        } else {
-            rr = b2 > 0.0 ? sqrt(r2 / b2) : 0.0;
+    bsum_write<2>(acc, L.k, P);
+}
+
+// The four FP64 dot products of the preconditioned vector z (FP32 cycle
+// output) in the *0 inner product: sum *0 z, sum *0 r z, sum *0 r zo (zo the
+// previous shifted z, FP64) and sum *0 r, over free rows.
+__global__ void k_bp_zdots(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int first, BSums P,
+                           const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const BTile t = tiles[blockIdx.x];
+    const BLevel &L = lv[t.lev];
+    const float *z = L.x[L.res_idx];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+        const int v = i >> L.kshift;
+        if (L.freev[v]) {
+            const double s0 = __ldg(L.star0 + v), zi = (double)z[i];
+            const double sr = s0 * L.orr[i];
+            acc[0] = fma(s0, zi, acc[0]);
+            acc[1] = fma(sr, zi, acc[1]);
+            if (!first) acc[2] = fma(sr, L.ozo[i], acc[2]);
+            acc[3] += sr;
         }
-        rel[j] = rr;
-        if (!(rr <= S->tol)) atomicExch(&all_ok, 0);
-        rn2[j] = 0.0;
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < nrhs; j += blockDim.x) {
-        // max of the relative residuals (non-negative doubles compare like their bit patterns)
-        if (isfinite(rel[j])) atomicMax((unsigned long long *)&worst, (unsigned long long)__double_as_longlong(rel[j]));
+    bsum_write<4>(acc, L.k, P);
+}
+
+// zs = z - c (FP64, free rows; 0 on fixed rows), p = zs + beta p (p = zs on the first pass), zo = zs
+__global__ void k_bp_pupd(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int first,
+                          const BScal *__restrict__ sc, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const BTile t = tiles[blockIdx.x];
+    const BLevel &L = lv[t.lev];
+    const float *z = L.x[L.res_idx];
+    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+        const int v = i >> L.kshift;
+        const BScal &S = sc[rhs_of(L, i)];
+        const double zs = L.freev[v] ? (double)z[i] - S.c : 0.0;
+        L.ozo[i] = zs;
+        L.op[i] = first ? zs : fma(S.beta, L.op[i], zs);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (count_iter) S->iter += 1;
-        S->rel = worst;
-        if (bad) {
-            S->status = 1;
-            S->done = 1;
-        } else if (all_ok || S->iter >= S->maxit) {
-            S->done = 1;
+}
+
+// q = L p (FP64, difference form; fixed rows have weights 0 and give 0), sum *0 p q
+__global__ void k_bp_spmv(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, BSums P, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const BTile t = tiles[blockIdx.x];
+    const BLevel &L = lv[t.lev];
+    double acc[1] = {0.0};
+    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+        const int v = i >> L.kshift, j = i & (L.k - 1);
+        const double pi = L.op[i];
+        double s = 0.0;
+        for (int q = 0; q < L.K; ++q) {
+            const size_t o = (size_t)q * L.n + v;
+            s = fma(__ldg(L.w64 + o), pi - L.op[(__ldg(L.col + o) << L.kshift) + j], s);
+        }
+        L.oq[i] = s;
+        acc[0] = fma(__ldg(L.star0 + v) * pi, s, acc[0]);
+    }
+    bsum_write<1>(acc, L.k, P);
+}
+
+// x += alpha p, r -= alpha q (FP64), r32 = (float) r, sum r^2
+__global__ void k_bp_update(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, const BScal *__restrict__ sc,
+                            BSums P, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const BTile t = tiles[blockIdx.x];
+    const BLevel &L = lv[t.lev];
+    double acc[1] = {0.0};
+    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+        const double a = sc[rhs_of(L, i)].alpha;
+        L.ox[i] = fma(a, L.op[i], L.ox[i]);
+        const double ri = fma(-a, L.oq[i], L.orr[i]);
+        L.orr[i] = ri;
+        L.b[i] = (float)ri;
+        acc[0] = fma(ri, ri, acc[0]);
+    }
+    bsum_write<1>(acc, L.k, P);
+}
+
+enum { kFinMean = 0, kFinInit = 1, kFinZdots = 2, kFinAlpha = 3, kFinConv = 4 };
+
+// One warp per right-hand side: add its partials over its group's tiles (lane
+// strided, then a fixed butterfly), then the scalars of `kind`.  kFinInit and
+// kFinConv also decide convergence: the last block to finish sets the batch's
+// done flag once every right-hand side has converged (or maxit is reached),
+// counts the pass (kFinConv) and records the largest relative residual.
+__global__ void k_b_finalize(int nrhs, const BRhs *__restrict__ rinfo, const BLevel *__restrict__ lv, BSums P,
+                             BScal *__restrict__ sc, int kind, int first, Scal *S, int *pending, unsigned *counter,
+                             const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    const int warp = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int ns = kind == kFinZdots ? 4 : (kind == kFinInit ? 2 : 1);
+    if (warp < nrhs) {
+        const BRhs R = rinfo[warp];
+        double tot[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int s = 0; s < ns; ++s) {
+            double a = 0.0;
+            for (int tt = R.tb + lane; tt < R.te; tt += 32) a += P.part[((size_t)s * P.ntile + tt) * P.kmax + R.j];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            tot[s] = a;
+        }
+        if (lane == 0) {
+            BScal &C = sc[warp];
+            const BLevel &L = lv[R.lev];
+            if (kind == kFinMean) {
+                C.mean = L.gauge ? tot[0] / L.s0sum : 0.0;
+            } else if (kind == kFinInit) {
+                C.bn2 = tot[1];
+                C.rn2 = tot[0];
+                C.thr2 = tot[1] > 0.0 ? S->tol * S->tol * tot[1] : (double)INFINITY;
+                C.stalled = 0;
+                C.done = !R.live || C.rn2 <= C.thr2;
+                C.rz = 0.0;
+                C.c = 0.0;
+            } else if (kind == kFinZdots) {
+                const double c = L.gauge ? tot[0] / L.s0sum : 0.0;
+                const double rz_new = tot[1] - c * tot[3];
+                C.beta = (first || C.done) ? 0.0 : (rz_new - tot[2]) / C.rz;
+                C.rz = rz_new;
+                C.c = c;
+            } else if (kind == kFinAlpha) {
+                double a = C.done ? 0.0 : C.rz / tot[0];
+                if (!C.done && (!(tot[0] > 0.0) || !isfinite(a))) {
+                    a = 0.0;  // the iteration cannot move this right-hand side any further
+                    C.stalled = 1;
+                    C.done = 1;
+                }
+                C.alpha = a;
+            } else {  // kFinConv
+                C.rn2 = tot[0];
+                if (!C.done && C.rn2 <= C.thr2) C.done = 1;
+            }
+            if (kind == kFinInit || kind == kFinConv) {
+                const bool bad = !isfinite(C.rn2) || !isfinite(C.bn2);
+                C.rel = bad ? (double)NAN : (C.bn2 > 0.0 ? sqrt(C.rn2 / C.bn2) : 0.0);
+                if (bad) {
+                    C.done = 1;
+                    atomicExch(&S->status, 1);
+                }
+                if (!C.done) atomicAdd(pending, 1);
+                if (R.live && isfinite(C.rel))
+                    atomicMax((unsigned long long *)&S->rel, (unsigned long long)__double_as_longlong(C.rel));
+            }
         }
     }
-}
-
-// user layout [n][nrhs] <-> group layout [n][k] for columns [col0, col0 + kk),
-// kk <= k; the padding columns of a partial last group hold zeros
-__global__ void k_b_gather(int n, int k, int kk, int nrhs, int col0, const double *__restrict__ src,
-                           double *__restrict__ dst) {
-    pdl_prologue();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * k; i += gridDim.x * blockDim.x) {
-        const int j = i % k;
-        dst[i] = j < kk ? src[(size_t)(i / k) * nrhs + col0 + j] : 0.0;
+    if (kind != kFinInit && kind != kFinConv) return;
+    if (!decdev::last_block(counter)) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int left = atomicAdd(pending, 0);
+        if (kind == kFinConv) S->iter += 1;
+        if (left == 0 || S->status != 0 || S->iter >= S->maxit) S->done = 1;
+        *pending = 0;
+        *counter = 0u;
     }
 }
 
-__global__ void k_b_scatter(int n, int k, int kk, int nrhs, int col0, const double *__restrict__ src,
-                            double *__restrict__ dst) {
+// Clear the largest relative residual before a convergence pass.
+__global__ void k_b_relzero(Scal *S, const int *skip) {
     pdl_prologue();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * k; i += gridDim.x * blockDim.x) {
-        const int j = i % k;
-        if (j < kk) dst[(size_t)(i / k) * nrhs + col0 + j] = src[i];
+    if (skipped(skip)) return;
+    if (threadIdx.x == 0) S->rel = 0.0;
+}
+
+// user layout [n][nrhs] -> group layout [n][k], columns [src0, src0 + cnt) to [dst0, ...);
+// inv != nullptr: divide by inv[v] on free rows, 0 on fixed rows
+__global__ void k_b_gather(int n, int k, int nrhs, int src0, int dst0, int cnt, const double *__restrict__ src,
+                           double *__restrict__ dst, const double *__restrict__ inv, const uint8_t *__restrict__ freev) {
+    pdl_prologue();
+    const int64_t tot = (int64_t)n * cnt;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(i / cnt), c = (int)(i % cnt);
+        double val = src[(size_t)v * nrhs + src0 + c];
+        if (inv) val = freev[v] ? val / inv[v] : 0.0;
+        dst[(size_t)v * k + dst0 + c] = val;
+    }
+}
+
+// group layout -> user layout; mul != nullptr: multiply by mul[v]
+__global__ void k_b_scatter(int n, int k, int nrhs, int src0, int dst0, int cnt, const double *__restrict__ src,
+                            double *__restrict__ dst, const double *__restrict__ mul) {
+    pdl_prologue();
+    const int64_t tot = (int64_t)n * cnt;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(i / cnt), c = (int)(i % cnt);
+        const double val = src[(size_t)v * k + src0 + c];
+        dst[(size_t)v * nrhs + dst0 + c] = mul ? val * mul[v] : val;
+    }
+}
+
+// dJ/d*1_e = -(d0 mu)_e (d0 u)_e per right-hand side, mu and u in group layout,
+// written to the user layout [ne][nrhs]
+__global__ void k_b_edge_grad(int64_t ne, int k, int nrhs, int src0, int dst0, int cnt, const int2 *__restrict__ edges,
+                              const double *__restrict__ mu, const double *__restrict__ u, double *__restrict__ g) {
+    pdl_prologue();
+    const int64_t tot = ne * cnt;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / cnt;
+        const int c = (int)(i % cnt);
+        const int2 ab = __ldg(edges + e);
+        const size_t lo = (size_t)ab.x * k + src0 + c, hi = (size_t)ab.y * k + src0 + c;
+        g[(size_t)e * nrhs + dst0 + c] = -(mu[hi] - mu[lo]) * (u[hi] - u[lo]);
     }
 }
 
@@ -464,26 +662,39 @@ __global__ void k_b_scatter(int n, int k, int kk, int nrhs, int col0, const doub
 struct dec_batch {
     dec_batch_opts opts;
     int device = 0;
-    std::vector<dec_mg *> mgs;
+    std::vector<dec_mg *> mgs;  // one per caller entry
     std::vector<int> nrhs;
+    // A run of caller columns [src0, src0 + cnt) of entry `entry` that fill group
+    // columns [dst0, dst0 + cnt).
+    struct Run {
+        int entry, src0, dst0, cnt;
+    };
+    // A group: up to k right-hand sides of one hierarchy (entries that share a
+    // hierarchy are merged), interleaved; descriptors [first_lev, first_lev + nlev),
+    // coarsest first; kk caller columns, k - kk padding columns.
     struct Group {
-        int mesh, col0, k, first_lev, nlev;  // descriptors [first_lev, first_lev + nlev), coarsest first
+        dec_mg *mg;
+        int k, kk, first_lev, nlev, rhs_base;
+        std::vector<Run> runs;
     };
     std::vector<Group> groups;
     std::vector<BLevel> hlv;   // host copy of the descriptors
     BLevel *dlv = nullptr;     // device descriptors
     int total_rhs = 0;
-    int64_t dof = 0;           // finest vertices x right-hand sides, summed
-    // tile lists per operation
+    int64_t dof = 0;           // finest vertices x caller right-hand sides, summed
     struct Op {
-        int kind;   // 0 smooth0, 1 smooth, 2 residual, 3 restrict, 4 coarse, 5 prolong, 6 add64, 7 res64
+        int kind;  // 0 smooth0, 1 smooth, 2 residual, 3 restrict, 4 coarse, 5 prolong
         int off, cnt;
         int sweep, post, src, din, dout;
     };
     std::vector<Op> cycle_ops;
-    int res_off = 0, res_cnt = 0;      // finest items of every group (FP64 residual, add, gauge)
+    int res_off = 0, res_cnt = 0;  // finest items of every group (the outer iteration)
     BTile *dtiles = nullptr;
-    double *rn2 = nullptr, *bn2 = nullptr, *rel = nullptr, *msum = nullptr;
+    BSums sums{};
+    BRhs *rinfo = nullptr;
+    BScal *bsc = nullptr;
+    int *pending = nullptr;
+    unsigned *counter = nullptr;
     Scal *scal = nullptr;
     Scal *scal_h = nullptr;
     cudaStream_t cap = nullptr;
@@ -556,9 +767,11 @@ void blaunch(const dec_batch *B, void (*kernel)(KArgs...), int grid, size_t smem
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// One refinement pass: cycle on the current residual, x += e, new residual, convergence.
-void enqueue_pass(dec_batch *B, cudaStream_t s) {
-    const int *skip = &B->scal->done;
+int fin_grid(const dec_batch *B) { return (B->total_rhs * 32 + B->opts.block - 1) / B->opts.block; }
+
+// One multigrid cycle of every group on its finest level's r32 (L.b); the
+// result is the finest level's x[res_idx].
+void enqueue_cycle(dec_batch *B, cudaStream_t s, const int *skip) {
     const auto &o = B->opts;
     const int cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
     const float omega = (float)(2.0 / 3.0);
@@ -576,11 +789,42 @@ void enqueue_pass(dec_batch *B, cudaStream_t s) {
             case 5: blaunch(B, k_b_prolong, op.cnt, 0, s, (const BLevel *)B->dlv, t, op.src, skip); break;
         }
     }
+}
+
+void enqueue_finalize(dec_batch *B, cudaStream_t s, int kind, int first, const int *skip) {
+    blaunch(B, k_b_finalize, fin_grid(B), 0, s, B->total_rhs, (const BRhs *)B->rinfo, (const BLevel *)B->dlv, B->sums,
+            B->bsc, kind, first, B->scal, B->pending, B->counter, skip);
+}
+
+// The preconditioned vector's dot products, the new search direction.
+void enqueue_precondition(dec_batch *B, cudaStream_t s, int first, const int *skip) {
     const BTile *rt = B->dtiles + B->res_off;
-    blaunch(B, k_b_add64, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, skip);
-    blaunch(B, k_b_res64, B->res_cnt, sizeof(double) * o.block, s, (const BLevel *)B->dlv, rt, B->rn2, (double *)nullptr,
-            skip);
-    blaunch(B, k_b_conv, 1, 0, s, B->total_rhs, B->rn2, (const double *)B->bn2, B->rel, B->scal, 1);
+    const size_t sm = sizeof(double) * B->opts.block;
+    enqueue_cycle(B, s, skip);
+    blaunch(B, k_bp_zdots, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, first, B->sums, skip);
+    enqueue_finalize(B, s, kFinZdots, first, skip);
+    blaunch(B, k_bp_pupd, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, first, (const BScal *)B->bsc, skip);
+}
+
+// One pass of the loop: a refinement pass (x += C(b - L x)) or an MG-PCG iteration.
+void enqueue_pass(dec_batch *B, cudaStream_t s) {
+    const int *skip = &B->scal->done;
+    const BTile *rt = B->dtiles + B->res_off;
+    const size_t sm = sizeof(double) * B->opts.block;
+    if (B->opts.solver == DEC_SOLVER_MG) {
+        enqueue_cycle(B, s, skip);
+        blaunch(B, k_b_add64, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, skip);
+        blaunch(B, k_b_res64, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, B->sums, skip);
+        blaunch(B, k_b_relzero, 1, 0, s, B->scal, skip);
+        enqueue_finalize(B, s, kFinConv, 0, skip);
+        return;
+    }
+    blaunch(B, k_bp_spmv, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, B->sums, skip);
+    enqueue_finalize(B, s, kFinAlpha, 0, skip);
+    blaunch(B, k_bp_update, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, (const BScal *)B->bsc, B->sums, skip);
+    blaunch(B, k_b_relzero, 1, 0, s, B->scal, skip);
+    enqueue_finalize(B, s, kFinConv, 0, skip);
+    enqueue_precondition(B, s, 0, skip);
 }
 
 int count_kernels(cudaGraph_t g) {
@@ -633,6 +877,94 @@ int build_loop(dec_batch *B) {
     return DEC_OK;
 }
 
+int check_batch_device(const dec_batch *B) {
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != B->device)
+        return fail(Status::fail(DEC_ERR_ARG, "the batch lives on device " + std::to_string(B->device) + " but device " +
+                                                  std::to_string(cur) + " is current"));
+    return DEC_OK;
+}
+
+// Solve with the right-hand sides already in every group's finest ob (caller
+// columns, zero padding): the gauge projection, x = 0, the loop, the gauge
+// shift of x.  The result is in every group's finest ox.
+int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &launches) {
+    Scal *h = B->scal_h;
+    std::memset(h, 0, offsetof(Scal, hist));
+    h->tol = tol;
+    h->maxit = maxit;
+    h->max_loops = maxit + 1;
+    CK(cudaMemcpyAsync(B->scal, h, offsetof(Scal, hist), cudaMemcpyHostToDevice, s));
+    const BTile *rt = B->dtiles + B->res_off;
+    const size_t sm = sizeof(double) * B->opts.block;
+    bool any_gauge = false;
+    for (auto &L : B->hlv)
+        if (L.ox && L.gauge) any_gauge = true;
+    if (any_gauge) {
+        blaunch(B, k_b_meansum, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, 0, B->sums);
+        enqueue_finalize(B, s, kFinMean, 0, nullptr);
+        blaunch(B, k_b_shift, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, 0, (const BScal *)B->bsc);
+        launches += 3;
+    }
+    if (B->opts.solver == DEC_SOLVER_MG) {
+        for (const auto &G : B->groups) {
+            const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
+            CK(cudaMemsetAsync(L.ox, 0, sizeof(double) * (size_t)L.n * G.k, s));
+        }
+        blaunch(B, k_b_res64, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, B->sums, (const int *)nullptr);
+        enqueue_finalize(B, s, kFinInit, 0, nullptr);
+        launches += 2;
+    } else {
+        blaunch(B, k_bp_init, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, B->sums);
+        enqueue_finalize(B, s, kFinInit, 0, nullptr);
+        launches += 2;
+    }
+    CK(cudaGetLastError());
+    if (maxit > 0) {
+        if (B->opts.solver != DEC_SOLVER_MG) {
+            enqueue_precondition(B, s, 1, &B->scal->done);
+            launches += (int64_t)B->cycle_ops.size() + 3;
+        }
+        if (!B->loop) {
+            int rc = build_loop(B);
+            if (rc) return rc;
+        }
+        CK(cudaGraphLaunch(B->loop, s));
+    }
+    if (any_gauge) {
+        blaunch(B, k_b_meansum, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, 1, B->sums);
+        enqueue_finalize(B, s, kFinMean, 0, nullptr);
+        blaunch(B, k_b_shift, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, 1, (const BScal *)B->bsc);
+        launches += 3;
+    }
+    CK(cudaGetLastError());
+    return DEC_OK;
+}
+
+// Statistics and status of the last batch_run (synchronizes s).
+int batch_finish(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t launches, dec_batch_stats *stats) {
+    Scal *h = B->scal_h;
+    CK(cudaMemcpyAsync(h, B->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->iters = h->iter;
+        stats->max_rel_res = h->rel;
+        stats->launches = launches + (maxit > 0 ? (int64_t)h->loops * B->loop_kernels : 0);
+        stats->dof = B->dof;
+    }
+    if (h->status == 1) return fail(Status::fail(DEC_ERR_NONFINITE, "non-finite residual in a batched solve"));
+    if (!(h->rel <= tol))
+        return fail(Status::fail(DEC_ERR_NOT_CONVERGED, "maxit reached (or an iteration stalled) before every "
+                                                        "right-hand side converged"));
+    return DEC_OK;
+}
+
+int gather_grid(const dec_batch *B, int64_t items) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (items + B->opts.block - 1) / B->opts.block));
+}
+
 }  // namespace
 
 extern "C" {
@@ -643,6 +975,7 @@ void dec_batch_default_opts(dec_batch_opts *o) {
     o->kgroup = 0;
     o->nu = 2;
     o->smoother = DEC_SMOOTH_CHEBYSHEV;
+    o->solver = DEC_SOLVER_MGPCG;
 }
 
 int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_batch_opts *opts, dec_batch **out) {
@@ -655,13 +988,24 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
         dec_batch_default_opts(&o);
     if ((o.block != 128 && o.block != 256 && o.block != 512) || o.nu < 1 || o.nu > kBMaxNu ||
         (o.smoother != DEC_SMOOTH_JACOBI && o.smoother != DEC_SMOOTH_CHEBYSHEV) || o.kgroup < 0 ||
-        (o.kgroup & (o.kgroup - 1)) != 0 || o.kgroup > o.block)
-        return fail(Status::fail(DEC_ERR_ARG, "bad batch options (block 128/256/512, 1 <= nu <= 8, kgroup a power of two)"));
+        (o.kgroup & (o.kgroup - 1)) != 0 || o.kgroup > o.block ||
+        (o.solver != DEC_SOLVER_MG && o.solver != DEC_SOLVER_MGPCG))
+        return fail(Status::fail(DEC_ERR_ARG, "bad batch options (block 128/256/512, 1 <= nu <= 8, kgroup a power of "
+                                              "two, solver MG or MGPCG)"));
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(Status::fail(DEC_ERR_CUDA, "cudaGetDevice"));
     for (int m = 0; m < nmesh; ++m) {
         if (!mgs[m] || mgs[m]->host_only) return fail(Status::fail(DEC_ERR_ARG, "a hierarchy is null or host-only"));
-        if (mgs[m]->H.mapped) return fail(Status::fail(DEC_ERR_ARG, "batched solves transfer along binary subdivision (no general maps)"));
+        if (mgs[m]->device != dev) return fail(Status::fail(DEC_ERR_ARG, "a hierarchy lives on another device"));
+        if (mgs[m]->H.mapped)
+            return fail(Status::fail(DEC_ERR_ARG, "batched solves transfer along binary subdivision (no general maps)"));
         if (nrhs[m] < 1) return fail(Status::fail(DEC_ERR_ARG, "every mesh needs at least one right-hand side"));
     }
+    // restriction: every hierarchy in a batch must use the same one
+    const int star0 = mgs[0]->H.opts.restriction == DEC_RESTRICT_STAR0;
+    for (int m = 1; m < nmesh; ++m)
+        if ((mgs[m]->H.opts.restriction == DEC_RESTRICT_STAR0) != (star0 != 0))
+            return fail(Status::fail(DEC_ERR_ARG, "all hierarchies of a batch must use the same restriction"));
     dec_batch *B = new (std::nothrow) dec_batch;
     if (!B) return fail(Status::fail(DEC_ERR_OOM, "host allocation"));
     auto bail = [&](int code) {
@@ -672,24 +1016,40 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
     B->opts = o;
     B->mgs.assign(mgs, mgs + nmesh);
     B->nrhs.assign(nrhs, nrhs + nmesh);
-    cudaGetDevice(&B->device);
+    B->device = dev;
     cudaError_t ce = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
     int rc;
-    // groups and their level descriptors
+    // Groups: the right-hand sides of all entries that share a hierarchy, in
+    // entry order, cut into groups of k (one operator read serves the group).
+    std::vector<dec_mg *> uniq;
+    for (int m = 0; m < nmesh; ++m)
+        if (std::find(uniq.begin(), uniq.end(), mgs[m]) == uniq.end()) uniq.push_back(mgs[m]);
     int rhs_base = 0;
-    for (int m = 0; m < nmesh; ++m) {
-        dec_mg *mg = mgs[m];
+    for (dec_mg *mg : uniq) {
+        std::vector<std::pair<int, int>> cols;  // (entry, column)
+        for (int m = 0; m < nmesh; ++m)
+            if (mgs[m] == mg)
+                for (int c = 0; c < nrhs[m]; ++c) cols.emplace_back(m, c);
+        const int total = (int)cols.size();
         int kg = o.kgroup ? o.kgroup : 1;
         if (!o.kgroup)
-            while (kg < nrhs[m] && kg < o.block) kg <<= 1;
-        for (int c0 = 0; c0 < nrhs[m]; c0 += kg) {
-            const int k = kg;  // the last group of a mesh is padded with zero right-hand sides
+            while (kg < total && kg < o.block) kg <<= 1;
+        for (int c0 = 0; c0 < total; c0 += kg) {
+            const int k = kg;  // the last group of a hierarchy is padded with zero right-hand sides
             if ((int64_t)mg->lv.back().n * k >= ((int64_t)1 << 31))
                 return bail(fail(Status::fail(DEC_ERR_ARG, "vertices x group size must stay below 2^31")));
             int ks = 0;
             while ((1 << ks) < k) ++ks;
-            dec_batch::Group G{m, c0, k, (int)B->hlv.size(), (int)mg->lv.size()};
+            dec_batch::Group G{mg, k, std::min(k, total - c0), (int)B->hlv.size(), (int)mg->lv.size(), rhs_base, {}};
+            for (int j = 0; j < G.kk; ++j) {
+                const auto &pc = cols[c0 + j];
+                if (!G.runs.empty() && G.runs.back().entry == pc.first &&
+                    G.runs.back().src0 + G.runs.back().cnt == pc.second && G.runs.back().dst0 + G.runs.back().cnt == j)
+                    G.runs.back().cnt += 1;
+                else
+                    G.runs.push_back(dec_batch::Run{pc.first, pc.second, j, 1});
+            }
             for (int l = 0; l < G.nlev; ++l) {
                 const DevLevel &D = mg->lv[l];
                 const decimpl::HostLevel &HL = mg->H.levels[l];
@@ -716,10 +1076,13 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
                     L.star0 = D.star0;
                     if ((rc = balloc(B, &L.ox, nv)) || (rc = balloc(B, &L.orr, nv)) || (rc = balloc(B, &L.ob, nv)))
                         return bail(rc);
+                    if (o.solver == DEC_SOLVER_MGPCG &&
+                        ((rc = balloc(B, &L.op, nv)) || (rc = balloc(B, &L.oq, nv)) || (rc = balloc(B, &L.ozo, nv))))
+                        return bail(rc);
                     L.rhs_base = rhs_base;
                     L.gauge = mg->H.bc == DEC_BC_GAUGE;
                     L.s0sum = mg->star0_sum;
-                    B->dof += (int64_t)D.n * std::min(k, nrhs[m] - c0);
+                    B->dof += (int64_t)D.n * G.kk;
                 }
                 B->hlv.push_back(L);
             }
@@ -740,73 +1103,65 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
         if (op.cnt > 0) B->cycle_ops.push_back(op);
     };
     const int cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
-    for (int d = 0; d < dmax; ++d) {
-        auto at_depth = [&](const dec_batch::Group &G) { return G.nlev - 1 - d; };  // level index, -1 if none
-        // pre-smoothing: sweep 0 from zero, then ping-pong
-        op_tiles(0, 0, 0, 0, 0, (cheb && o.nu > 1), [&](const dec_batch::Group &G, std::vector<BTile> &t) {
-            int l = at_depth(G);
+    auto level_tiles = [&](int d) {
+        return [&, d](const dec_batch::Group &G, std::vector<BTile> &t) {
+            const int l = G.nlev - 1 - d;
             if (l >= 1) add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l].n, B->hlv[G.first_lev + l].kshift, target);
-        });
+        };
+    };
+    for (int d = 0; d < dmax; ++d) {
+        // pre-smoothing: sweep 0 from zero, then ping-pong
+        op_tiles(0, 0, 0, 0, 0, (cheb && o.nu > 1), level_tiles(d));
         int cur = 0;
         for (int sw = 1; sw < o.nu; ++sw) {
-            op_tiles(1, sw, 0, cur, cheb, (cheb && sw + 1 < o.nu), [&](const dec_batch::Group &G, std::vector<BTile> &t) {
-                int l = at_depth(G);
-                if (l >= 1) add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l].n, B->hlv[G.first_lev + l].kshift, target);
-            });
+            op_tiles(1, sw, 0, cur, cheb, (cheb && sw + 1 < o.nu), level_tiles(d));
             cur = 1 - cur;
         }
-        op_tiles(2, 0, 0, cur, 0, 0, [&](const dec_batch::Group &G, std::vector<BTile> &t) {
-            int l = at_depth(G);
-            if (l >= 1) add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l].n, B->hlv[G.first_lev + l].kshift, target);
-        });
-        op_tiles(3, 0, 0, 0, 0, 0, [&](const dec_batch::Group &G, std::vector<BTile> &t) {
-            int l = at_depth(G);
+        op_tiles(2, 0, 0, cur, 0, 0, level_tiles(d));
+        op_tiles(3, 0, 0, star0, 0, 0, [&](const dec_batch::Group &G, std::vector<BTile> &t) {
+            const int l = G.nlev - 1 - d;
             if (l >= 1) add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l - 1].n, B->hlv[G.first_lev + l].kshift, target);
         });
     }
-    // restriction flag per op: every hierarchy in a batch must use the same restriction
-    const int star0 = mgs[0]->H.opts.restriction == DEC_RESTRICT_STAR0;
-    for (int m = 1; m < nmesh; ++m)
-        if ((mgs[m]->H.opts.restriction == DEC_RESTRICT_STAR0) != (star0 != 0))
-            return bail(fail(Status::fail(DEC_ERR_ARG, "all hierarchies of a batch must use the same restriction")));
-    for (auto &op : B->cycle_ops)
-        if (op.kind == 3) op.src = star0;
     // coarsest solves of every group
     op_tiles(4, 0, 0, 0, 0, 0, [&](const dec_batch::Group &G, std::vector<BTile> &t) {
         add_tiles(t, G.first_lev, B->hlv[G.first_lev].n, B->hlv[G.first_lev].kshift, target);
     });
     const int after_pre = (o.nu - 1) % 2;
     for (int d = dmax - 1; d >= 0; --d) {
-        auto at_depth = [&](const dec_batch::Group &G) { return G.nlev - 1 - d; };
-        op_tiles(5, 0, 0, after_pre, 0, 0, [&](const dec_batch::Group &G, std::vector<BTile> &t) {
-            int l = at_depth(G);
-            if (l >= 1) add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l].n, B->hlv[G.first_lev + l].kshift, target);
-        });
+        op_tiles(5, 0, 0, after_pre, 0, 0, level_tiles(d));
         int cur = after_pre;
         for (int sw = 0; sw < o.nu; ++sw) {
-            op_tiles(1, sw, 1, cur, (cheb && sw > 0), (cheb && sw + 1 < o.nu),
-                     [&](const dec_batch::Group &G, std::vector<BTile> &t) {
-                         int l = at_depth(G);
-                         if (l >= 1)
-                             add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l].n, B->hlv[G.first_lev + l].kshift, target);
-                     });
+            op_tiles(1, sw, 1, cur, (cheb && sw > 0), (cheb && sw + 1 < o.nu), level_tiles(d));
             cur = 1 - cur;
         }
     }
-    // finest items of every group, in larger tiles (fewer per-RHS atomics)
+    // finest items of every group, in larger tiles; the per-right-hand-side tile ranges
     B->res_off = (int)tiles.size();
+    std::vector<BRhs> rinfo;
+    int kmax = 1;
     for (auto &G : B->groups) {
         const int l = G.first_lev + G.nlev - 1;
+        const int tb = (int)tiles.size() - B->res_off;
         add_tiles(tiles, l, B->hlv[l].n, B->hlv[l].kshift, o.block * 32);
+        const int te = (int)tiles.size() - B->res_off;
+        for (int j = 0; j < G.k; ++j) rinfo.push_back(BRhs{tb, te, j, l, j < G.kk ? 1 : 0});
+        kmax = std::max(kmax, G.k);
     }
     B->res_cnt = (int)tiles.size() - B->res_off;
+    B->sums.ntile = B->res_cnt;
+    B->sums.kmax = kmax;
     if ((rc = balloc(B, &B->dtiles, tiles.size())) || (rc = balloc(B, &B->dlv, B->hlv.size())) ||
-        (rc = balloc(B, &B->rn2, B->total_rhs)) || (rc = balloc(B, &B->bn2, B->total_rhs)) ||
-        (rc = balloc(B, &B->rel, B->total_rhs)) || (rc = balloc(B, &B->msum, B->total_rhs)) ||
-        (rc = balloc(B, &B->scal, 1)))
+        (rc = balloc(B, &B->sums.part, (size_t)kBMaxSums * B->res_cnt * kmax)) ||
+        (rc = balloc(B, &B->rinfo, rinfo.size())) || (rc = balloc(B, &B->bsc, (size_t)B->total_rhs)) ||
+        (rc = balloc(B, &B->pending, 1)) || (rc = balloc(B, &B->counter, 1)) || (rc = balloc(B, &B->scal, 1)))
         return bail(rc);
     ce = cudaMemcpy(B->dtiles, tiles.data(), tiles.size() * sizeof(BTile), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(B->dlv, B->hlv.data(), B->hlv.size() * sizeof(BLevel), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(B->rinfo, rinfo.data(), rinfo.size() * sizeof(BRhs), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(B->bsc, 0, sizeof(BScal) * B->total_rhs);
+    if (ce == cudaSuccess) ce = cudaMemset(B->pending, 0, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMemset(B->counter, 0, sizeof(unsigned));
     if (ce == cudaSuccess) ce = cudaMemset(B->scal, 0, sizeof(Scal));
     if (ce == cudaSuccess) ce = cudaMallocHost((void **)&B->scal_h, sizeof(Scal));
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "batch upload"));
@@ -824,84 +1179,76 @@ int dec_batch_solve(dec_batch *B, const double *const *b, double *const *x, doub
                     dec_batch_stats *stats, dec_stream_t stream) {
     if (!B || !b || !x) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
     if (!(tol >= 0.0) || maxit < 0 || maxit >= decdev::kHist) return fail(Status::fail(DEC_ERR_ARG, "bad tol or maxit"));
-    {
-        int cur = -1;
-        CK(cudaGetDevice(&cur));
-        if (cur != B->device)
-            return fail(Status::fail(DEC_ERR_ARG, "the batch lives on device " + std::to_string(B->device) +
-                                                      " but device " + std::to_string(cur) + " is current"));
-    }
+    if (int rc = check_batch_device(B)) return rc;
     for (size_t m = 0; m < B->mgs.size(); ++m)
         if (!b[m] || !x[m]) return fail(Status::fail(DEC_ERR_ARG, "null vector"));
     cudaStream_t s = (cudaStream_t)stream;
     int64_t launches = 0;
-    // inputs into group layout, x = 0
+    // inputs into group layout (padding columns zero)
     for (auto &G : B->groups) {
         const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
-        const int nr = B->nrhs[G.mesh];
-        const int kk = std::min(G.k, nr - G.col0);
-        CK(cudaMemsetAsync(L.ox, 0, sizeof(double) * (size_t)L.n * G.k, s));
-        blaunch(B, k_b_gather, (int)std::min<int64_t>(4096, ((int64_t)L.n * G.k + B->opts.block - 1) / B->opts.block), 0,
-                s, L.n, G.k, kk, nr, G.col0, b[G.mesh], L.ob);
-        ++launches;
-    }
-    Scal *h = B->scal_h;
-    std::memset(h, 0, offsetof(Scal, hist));
-    h->tol = tol;
-    h->maxit = maxit;
-    h->max_loops = maxit + 1;
-    CK(cudaMemcpyAsync(B->scal, h, offsetof(Scal, hist), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(B->rn2, 0, sizeof(double) * B->total_rhs, s));
-    CK(cudaMemsetAsync(B->bn2, 0, sizeof(double) * B->total_rhs, s));
-    const BTile *rt = B->dtiles + B->res_off;
-    bool any_gauge = false;
-    for (auto &L : B->hlv)
-        if (L.ox && L.gauge) any_gauge = true;
-    if (any_gauge) {
-        // (every group's mean is formed; Dirichlet groups are not shifted)
-        CK(cudaMemsetAsync(B->msum, 0, sizeof(double) * B->total_rhs, s));
-        blaunch(B, k_b_mean, B->res_cnt, sizeof(double) * B->opts.block, s, (const BLevel *)B->dlv, rt, 0, B->msum);
-        blaunch(B, k_b_shift, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, 0, (const double *)B->msum);
-        launches += 2;
-    }
-    blaunch(B, k_b_res64, B->res_cnt, sizeof(double) * B->opts.block, s, (const BLevel *)B->dlv, rt, B->rn2, B->bn2,
-            (const int *)nullptr);
-    blaunch(B, k_b_conv, 1, 0, s, B->total_rhs, B->rn2, (const double *)B->bn2, B->rel, B->scal, 0);
-    launches += 2;
-    CK(cudaGetLastError());
-    if (maxit > 0) {
-        if (!B->loop) {
-            int rc = build_loop(B);
-            if (rc) return rc;
+        if (G.kk < G.k) CK(cudaMemsetAsync(L.ob, 0, sizeof(double) * (size_t)L.n * G.k, s));
+        for (const auto &R : G.runs) {
+            blaunch(B, k_b_gather, gather_grid(B, (int64_t)L.n * R.cnt), 0, s, L.n, G.k, B->nrhs[R.entry], R.src0, R.dst0,
+                    R.cnt, b[R.entry], L.ob, (const double *)nullptr, (const uint8_t *)nullptr);
+            ++launches;
         }
-        CK(cudaGraphLaunch(B->loop, s));
     }
-    if (any_gauge) {
-        CK(cudaMemsetAsync(B->msum, 0, sizeof(double) * B->total_rhs, s));
-        blaunch(B, k_b_mean, B->res_cnt, sizeof(double) * B->opts.block, s, (const BLevel *)B->dlv, rt, 1, B->msum);
-        blaunch(B, k_b_shift, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, 1, (const double *)B->msum);
-        launches += 2;
-    }
+    if (int rc = batch_run(B, tol, maxit, s, launches)) return rc;
     for (auto &G : B->groups) {
         const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
-        const int nr = B->nrhs[G.mesh];
-        const int kk = std::min(G.k, nr - G.col0);
-        blaunch(B, k_b_scatter, (int)std::min<int64_t>(4096, ((int64_t)L.n * G.k + B->opts.block - 1) / B->opts.block), 0,
-                s, L.n, G.k, kk, nr, G.col0, (const double *)L.ox, x[G.mesh]);
-        ++launches;
+        for (const auto &R : G.runs) {
+            blaunch(B, k_b_scatter, gather_grid(B, (int64_t)L.n * R.cnt), 0, s, L.n, G.k, B->nrhs[R.entry], R.dst0,
+                    R.src0, R.cnt, (const double *)L.ox, x[R.entry], (const double *)nullptr);
+            ++launches;
+        }
     }
-    CK(cudaMemcpyAsync(h, B->scal, offsetof(Scal, hist), cudaMemcpyDeviceToHost, s));
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(s));
-    if (stats) {
-        stats->iters = h->iter;
-        stats->max_rel_res = h->rel;
-        stats->launches = launches + (maxit > 0 ? (int64_t)h->loops * B->loop_kernels : 0);
-        stats->dof = B->dof;
+    return batch_finish(B, tol, maxit, s, launches, stats);
+}
+
+int dec_batch_solve_backward(dec_batch *B, const double *const *u, const double *const *grad_u, double *const *grad_b,
+                             double *const *grad_star1, double tol, int maxit, dec_batch_stats *stats,
+                             dec_stream_t stream) {
+    if (!B || !u || !grad_u || !grad_b) return fail(Status::fail(DEC_ERR_ARG, "null pointer"));
+    if (!(tol >= 0.0) || maxit < 0 || maxit >= decdev::kHist) return fail(Status::fail(DEC_ERR_ARG, "bad tol or maxit"));
+    if (int rc = check_batch_device(B)) return rc;
+    for (size_t m = 0; m < B->mgs.size(); ++m)
+        if (!u[m] || !grad_u[m] || !grad_b[m]) return fail(Status::fail(DEC_ERR_ARG, "null vector"));
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t launches = 0;
+    // L mu = *0^-1 grad_u for every right-hand side
+    for (auto &G : B->groups) {
+        const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
+        if (G.kk < G.k) CK(cudaMemsetAsync(L.ob, 0, sizeof(double) * (size_t)L.n * G.k, s));
+        for (const auto &R : G.runs) {
+            blaunch(B, k_b_gather, gather_grid(B, (int64_t)L.n * R.cnt), 0, s, L.n, G.k, B->nrhs[R.entry], R.src0, R.dst0,
+                    R.cnt, grad_u[R.entry], L.ob, (const double *)L.star0, (const uint8_t *)L.freev);
+            ++launches;
+        }
     }
-    if (h->status == 1) return fail(Status::fail(DEC_ERR_NONFINITE, "non-finite residual in a batched solve"));
-    if (!(h->rel <= tol)) return fail(Status::fail(DEC_ERR_NOT_CONVERGED, "maxit reached before every right-hand side converged"));
-    return DEC_OK;
+    if (int rc = batch_run(B, tol, maxit, s, launches)) return rc;
+    for (auto &G : B->groups) {
+        const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
+        // dJ/db = *0 mu
+        for (const auto &R : G.runs) {
+            blaunch(B, k_b_scatter, gather_grid(B, (int64_t)L.n * R.cnt), 0, s, L.n, G.k, B->nrhs[R.entry], R.dst0,
+                    R.src0, R.cnt, (const double *)L.ox, grad_b[R.entry], (const double *)L.star0);
+            ++launches;
+        }
+        if (!grad_star1) continue;
+        // dJ/d*1 = -(d0 mu)(d0 u) on the finest edges, u gathered into the group layout (ob)
+        const dec_mg *mg = G.mg;
+        const int64_t ne = mg->lv.back().ne;
+        for (const auto &R : G.runs) {
+            if (!grad_star1[R.entry]) continue;
+            blaunch(B, k_b_gather, gather_grid(B, (int64_t)L.n * R.cnt), 0, s, L.n, G.k, B->nrhs[R.entry], R.src0,
+                    R.dst0, R.cnt, u[R.entry], L.ob, (const double *)nullptr, (const uint8_t *)nullptr);
+            blaunch(B, k_b_edge_grad, gather_grid(B, ne * R.cnt), 0, s, ne, G.k, B->nrhs[R.entry], R.dst0, R.src0,
+                    R.cnt, (const int2 *)mg->edges, (const double *)L.ox, (const double *)L.ob, grad_star1[R.entry]);
+            launches += 2;
+        }
+    }
+    return batch_finish(B, tol, maxit, s, launches, stats);
 }
 
 int dec_batch_info(const dec_batch *B, int *ngroups, int *total_rhs, int64_t *dof, size_t *device_bytes) {
@@ -931,7 +1278,14 @@ extern "C" int dec_batch_tune(dec_mg *const *mgs, const int *nrhs, int nmesh, co
     } else {
         for (int blk : {128, 256, 512})
             for (int kg : {0, 8, 16, 32})
-                for (int nu : {1, 2, 3}) grid.push_back(dec_batch_opts{blk, kg, nu, DEC_SMOOTH_CHEBYSHEV});
+                for (int nu : {1, 2, 3}) {
+                    dec_batch_opts c;
+                    dec_batch_default_opts(&c);
+                    c.block = blk;
+                    c.kgroup = kg;
+                    c.nu = nu;
+                    grid.push_back(c);
+                }
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
@@ -976,6 +1330,7 @@ extern "C" int dec_batch_tune(dec_mg *const *mgs, const int *nrhs, int nmesh, co
 // with CUDA events on `stream`; reports the average and the algorithmic bytes.
 extern "C" int dec_batch_time_smooth(dec_batch *B, int reps, double *avg_ms, double *bytes, dec_stream_t stream) {
     if (!B || reps < 1 || !avg_ms || !bytes) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    if (int rc = check_batch_device(B)) return rc;
     // the first post-smoothing sweep on depth 0 (every group's finest level)
     const dec_batch::Op *op = nullptr;
     for (const auto &o : B->cycle_ops)
@@ -983,20 +1338,14 @@ extern "C" int dec_batch_time_smooth(dec_batch *B, int reps, double *avg_ms, dou
     if (!op) return fail(Status::fail(DEC_ERR_ARG, "batch has no smoothing sweep"));
     cudaStream_t s = (cudaStream_t)stream;
     const int cheb = B->opts.smoother == DEC_SMOOTH_CHEBYSHEV;
-    // Algorithmic bytes: the finest operator of each mesh once (K columns + K
-    // weights per row, whatever the number of its groups: the groups of a mesh
-    // share one table), then per item x, b, x_out (+ direction) for the
-    // right-hand sides the mesh actually has (padding columns excluded).
+    // Algorithmic bytes: each group's finest operator once (K columns + K
+    // weights per row; a group holds every right-hand side of its hierarchy
+    // up to k), then per item x, b, x_out (+ direction) for the caller's
+    // right-hand sides (padding columns not counted).
     double by = 0.0;
-    std::vector<const int32_t *> seen;
     for (auto &G : B->groups) {
         const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
-        if (std::find(seen.begin(), seen.end(), L.col) == seen.end()) {
-            seen.push_back(L.col);
-            by += (double)L.n * (8.0 * L.K);
-        }
-        const int kk = std::min(G.k, B->nrhs[G.mesh] - G.col0);
-        by += (double)L.n * kk * 4.0 * (3 + (cheb ? 1 : 0));
+        by += (double)L.n * (8.0 * L.K) + (double)L.n * G.kk * 4.0 * (3 + (cheb ? 1 : 0));
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

@@ -1241,6 +1241,22 @@ __global__ void __launch_bounds__(kThreads, 8) k_mg_residual_m(int n, int K, con
 // Scalars (alpha, beta, the gauge shift) are FP64 quotients of FP64 sums.
 // ---------------------------------------------------------------------------
 
+// FP32 -> FP64 conversion by integer instructions.  Widening a binary32 to
+// binary64 is exact: the sign carries over, the exponent is rebiased by
+// 1023 - 127 = 896 and the 23 fraction bits move up by 29.  Zero, subnormal,
+// infinite and NaN inputs take the hardware conversion.  (GB300 issues the
+// hardware conversion on its narrow FP64 pipe; these bit operations run on
+// the integer pipe.)
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 // x += alpha p, r -= alpha q, r32 = (float) r, ||r||^2 -> convergence test.
 // s0mode > 0 also runs the next cycle's first smoothing step on the finest
 // level from zero, as k_smooth0 does on b = r32 (x0 = e0 r32 / dg, and d0 =
@@ -1277,26 +1293,24 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_d(int n, cons
 }
 
 // After the four FP64 sums of the preconditioned vector z: sum *0 z, sum *0 r z,
-// sum *0 r z_prev and sum *0 r over free rows, z and z_prev being the cycle
-// outputs before their gauge shifts c and c_prev (S->c until it is replaced
-// here).  Shift c = sum *0 z / sum *0, <r, z - c> = tot1 - c tot3,
-// <r, z_prev - c_prev> = tot2 - c_prev tot3, and the Polak-Ribiere
-// beta = (<r, z> - <r, z_prev>) / <r_prev, z_prev>.
+// sum *0 r zo and sum *0 r over free rows, z being the cycle output before its
+// gauge shift and zo the previous preconditioned vector after its shift.
+// Shift c = sum *0 z / sum *0, <r, z - c> = tot1 - c tot3, <r, zo> = tot2, and
+// the Polak-Ribiere beta = (<r, z - c> - <r, zo>) / <r_prev, zo>.
 __device__ __forceinline__ void zdots_epilogue_d(Scal *S, const double (&tot)[4], int first, int gauge) {
     const double c = gauge ? tot[0] / S->star0_sum : 0.0;
     const double rz_new = tot[1] - c * tot[3];
-    const double rzo = tot[2] - S->c * tot[3];
-    S->beta = first ? 0.0 : (rz_new - rzo) / S->rz;
+    S->beta = first ? 0.0 : (rz_new - tot[2]) / S->rz;
     S->rz = rz_new;
     S->c = c;
 }
 
 // The four FP64 dot products of z (FP32 cycle output, unshifted) with *0 and
-// the FP64 residual r; zo is the previous unshifted z (FP32).
+// the FP64 residual r; zo is the previous shifted z (FP64).
 static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_d(int n, const double *__restrict__ star0,
                                                          const uint8_t *__restrict__ freev,
                                                          const float *__restrict__ z, const double *__restrict__ r,
-                                                         const float *__restrict__ zo, int first, int gauge,
+                                                         const double *__restrict__ zo, int first, int gauge,
                                                          double *partials, unsigned *counter, Scal *S,
                                                          const int *skip) {
     pdl_prologue();
@@ -1304,11 +1318,11 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_d(int n, const
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     GRID_STRIDE(i, n) {
         if (freev[i]) {
-            const double s0 = ldg(star0 + i), zi = (double)ldg(z + i);
+            const double s0 = ldg(star0 + i), zi = f2d(ldg(z + i));
             const double sr = s0 * ldg(r + i);
             acc[0] = fma(s0, zi, acc[0]);
             acc[1] = fma(sr, zi, acc[1]);
-            if (!first) acc[2] = fma(sr, (double)ldg(zo + i), acc[2]);
+            if (!first) acc[2] = fma(sr, ldg(zo + i), acc[2]);
             acc[3] += sr;
         }
     }
@@ -1328,7 +1342,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots_d(int n, int K, co
                                                             float c, float e, const double *__restrict__ star0,
                                                             const uint8_t *__restrict__ freev,
                                                             const double *__restrict__ r64,
-                                                            const float *__restrict__ zo, int first, int gauge,
+                                                            const double *__restrict__ zo, int first, int gauge,
                                                             double *partials, unsigned *counter, Scal *S,
                                                             const int *skip) {
     pdl_prologue_ell<KT>(n, K, col, w);
@@ -1342,11 +1356,11 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots_d(int n, int K, co
         const float zf = add_rn(ldg(x_in + i), delta);
         x_out[i] = zf;
         if (freev[i]) {
-            const double s0 = ldg(star0 + i), zi = (double)zf;
+            const double s0 = ldg(star0 + i), zi = f2d(zf);
             const double sr = s0 * ldg(r64 + i);
             acc[0] = fma(s0, zi, acc[0]);
             acc[1] = fma(sr, zi, acc[1]);
-            if (!first) acc[2] = fma(sr, (double)ldg(zo + i), acc[2]);
+            if (!first) acc[2] = fma(sr, ldg(zo + i), acc[2]);
             acc[3] += sr;
         }
     }
@@ -1354,20 +1368,18 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots_d(int n, int K, co
     if (grid_reduce<4>(acc, partials, counter, tot) && threadIdx.x == 0) zdots_epilogue_d(S, tot, first, gauge);
 }
 
-// zo = z (unshifted, FP32; 0 on fixed rows), p = (z - c) + beta p in FP64
-// (p = z - c on the first pass).
+// zs = z - c in FP64 (free rows; 0 on fixed rows), zo = zs, p = zs + beta p
+// (p = zs on the first pass).
 static __global__ void __launch_bounds__(kThreads, 8) k_pcg_pupd_d(int n, const uint8_t *__restrict__ freev,
-                                                        const float *__restrict__ z, float *__restrict__ zo,
+                                                        const float *__restrict__ z, double *__restrict__ zo,
                                                         double *__restrict__ p, int first, const Scal *S,
                                                         const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
     const double c = S->c, beta = S->beta;
     GRID_STRIDE(i, n) {
-        const bool f = freev[i] != 0;
-        const float zr = f ? ldg(z + i) : 0.f;
-        zo[i] = zr;
-        const double zi = f ? (double)zr - c : 0.0;
+        const double zi = freev[i] ? f2d(ldg(z + i)) - c : 0.0;
+        zo[i] = zi;
         p[i] = first ? zi : fma(beta, p[i], zi);
     }
 }

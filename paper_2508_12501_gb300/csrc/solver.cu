@@ -217,12 +217,12 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
                         if (din)
                             launch(mg, k_smooth_zdots_d<KT, true>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
                                    (const float *)xi, (const float *)di, xo, c, e, (const double *)F.star0,
-                                   (const uint8_t *)F.freev, (const double *)mg->orr, (const float *)mg->zo32,
+                                   (const uint8_t *)F.freev, (const double *)mg->orr, (const double *)mg->ozo,
                                    da->first, da->gauge, mg->partials, mg->counter, mg->scal, skip);
                         else
                             launch(mg, k_smooth_zdots_d<KT, false>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
                                    (const float *)xi, (const float *)nullptr, xo, c, e, (const double *)F.star0,
-                                   (const uint8_t *)F.freev, (const double *)mg->orr, (const float *)mg->zo32,
+                                   (const uint8_t *)F.freev, (const double *)mg->orr, (const double *)mg->ozo,
                                    da->first, da->gauge, mg->partials, mg->counter, mg->scal, skip);
                     } else if (din)
                         launch(mg, k_smooth_zdots<KT, true>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
@@ -495,7 +495,7 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
             ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
             if (d64)
                 launch(mg, k_pcg_zdots_d, rg, s, F.n, (const double *)F.star0, (const uint8_t *)F.freev,
-                       (const float *)z, (const double *)mg->orr, (const float *)mg->zo32, first ? 1 : 0, gauge,
+                       (const float *)z, (const double *)mg->orr, (const double *)mg->ozo, first ? 1 : 0, gauge,
                        mg->partials, mg->counter, mg->scal, skip);
             else
                 launch(mg, k_pcg_zdots_m, rg, s, F.n, (const float *)F.star0_32, (const uint8_t *)F.freev,
@@ -507,7 +507,7 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
             launch(mg, k_pcg_pupd_f, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
                    mg->fp, first ? 1 : 0, (const Scal *)mg->scal, skip);
         else if (d64)
-            launch(mg, k_pcg_pupd_d, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,
+            launch(mg, k_pcg_pupd_d, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->ozo,
                    mg->op, first ? 1 : 0, (const Scal *)mg->scal, skip);
         else
             launch(mg, k_pcg_pupd_m, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, (const float *)z, mg->zo32,

@@ -44,8 +44,9 @@ def _check(oh, x, b, tol):
         assert omg.star0_norm(lev, xj - xs) / omg.star0_norm(lev, xs) < 1e-6
 
 
+@pytest.mark.parametrize("solver", ["mgpcg", "mg"])
 @pytest.mark.parametrize("kgroup", [0, 1, 2, 4, 8])
-def test_uneven_batch_matches_oracle(kgroup):
+def test_uneven_batch_matches_oracle(kgroup, solver):
     import paper_2508_12501_gb300 as P
     cases = [("ico", 4, 3, 5), ("square", 5, 5, 1), ("square", 4, 3, 3), ("fan", 3, 3, 2)]
     hs, ohs, bs = [], [], []
@@ -53,7 +54,7 @@ def test_uneven_batch_matches_oracle(kgroup):
         h, oh = _mesh(kind, nsub, nl)
         hs.append(h); ohs.append(oh)
         bs.append(_rhs(h.n, k, 10 * i))
-    B = P.Batch(hs, [c[3] for c in cases], kgroup=kgroup, nu=2)
+    B = P.Batch(hs, [c[3] for c in cases], kgroup=kgroup, nu=2, solver=solver)
     xs, st = B.solve([torch.as_tensor(b, device="cuda") for b in bs], tol=1e-10, maxit=100)
     assert st.status == 0 and st.max_rel_res <= 1e-10
     assert st.dof == sum(h.n * c[3] for h, c in zip(hs, cases))
@@ -73,6 +74,54 @@ def test_batch_smoother_options(smoother, nu):
     assert st.max_rel_res <= 1e-10
     _check(o1, xs[0].cpu().numpy(), b1, 1e-10)
     _check(o2, xs[1].cpu().numpy(), b2, 1e-10)
+
+
+def test_entries_sharing_a_hierarchy_are_one_group_and_match_the_oracle():
+    # the same hierarchy passed three times (2 + 1 + 3 right-hand sides) and another once: the shared one's
+    # six columns form one interleaved group of 8 (two padding columns); every column matches the oracle
+    import paper_2508_12501_gb300 as P
+    h1, o1 = _mesh("square", 5, 4)
+    h2, o2 = _mesh("ico", 4, 3)
+    ks = [2, 3, 1, 3]
+    hs, ohs = [h1, h2, h1, h1], [o1, o2, o1, o1]
+    bs = [_rhs(h.n, k, 40 + 10 * i) for i, (h, k) in enumerate(zip(hs, ks))]
+    B = P.Batch(hs, ks)
+    assert B.ngroups == 2 and B.total_rhs == 8 + 4
+    xs, st = B.solve([torch.as_tensor(b.reshape(-1), device="cuda") for b in bs], tol=1e-10)
+    assert st.max_rel_res <= 1e-10
+    for oh, x, b, k in zip(ohs, xs, bs, ks):
+        _check(oh, x.reshape(-1, k).cpu().numpy(), b, 1e-10)
+    # bitwise reproducible: the per-right-hand-side sums have a fixed order
+    xs2, _ = B.solve([torch.as_tensor(b.reshape(-1), device="cuda") for b in bs], tol=1e-10)
+    assert all(torch.equal(a, c) for a, c in zip(xs, xs2))
+
+
+@pytest.mark.parametrize("solver", ["mgpcg", "mg"])
+def test_batched_adjoint_matches_oracle_gradients(solver):
+    # dJ/db = *0 mu and dJ/d*1 = -(d0 mu)(d0 u) per right-hand side, mu = L^-1 (*0^-1 dJ/du), against the
+    # oracle's adjoint formulas with its direct solves
+    import paper_2508_12501_gb300 as P
+    from oracle import adjoint as oadj
+    h1, o1 = _mesh("square", 5, 4)
+    h2, o2 = _mesh("ico", 4, 3)
+    ks = [3, 2]
+    bs = [_rhs(h1.n, 3, 61), _rhs(h2.n, 2, 62)]
+    B = P.Batch([h1, h2], ks, solver=solver)
+    xs, _ = B.solve([torch.as_tensor(b.reshape(-1), device="cuda") for b in bs], tol=1e-11, maxit=200)
+    gus = [torch.as_tensor(_rhs(h1.n, 3, 71), device="cuda"), torch.as_tensor(_rhs(h2.n, 2, 72), device="cuda")]
+    gbs, gss, st = B.solve_backward([x.reshape(h.n, -1) for x, h in zip(xs, (h1, h2))], gus, tol=1e-11, maxit=200)
+    assert st.max_rel_res <= 1e-11
+    for oh, x, gu, gb, gs, k in zip((o1, o2), xs, gus, gbs, gss, ks):
+        lev = oh.finest
+        bc = oh.bc
+        for j in range(k):
+            u = x.reshape(lev.mesh.nv, k)[:, j].cpu().numpy()
+            g = gu[:, j].cpu().numpy()
+            rb, rs = oadj.gradients(lev, bc, u, g)
+            ab = gb.reshape(lev.mesh.nv, k)[:, j].cpu().numpy()
+            as1 = gs.reshape(-1, k)[:, j].cpu().numpy()
+            assert np.linalg.norm(ab - rb) <= 1e-8 * np.linalg.norm(rb), j
+            assert np.linalg.norm(as1 - rs) <= 1e-8 * np.linalg.norm(rs), j
 
 
 def test_batch_error_paths():
