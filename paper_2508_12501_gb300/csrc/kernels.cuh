@@ -664,35 +664,79 @@ __device__ __forceinline__ bool last_block(unsigned *counter) {
     return last;
 }
 
+// Warp sums of NS doubles (NS = 1, 2 or 4) with few FP64 additions.  GB300
+// issues FP64 on a narrow pipe where a warp-wide addition takes 32 lane
+// slots, so NS independent butterflies (5 NS additions per lane) would cost
+// more than the rows themselves.  For NS > 1 the first levels of the
+// butterfly exchange half of the sums a lane holds; after log2(NS) levels a
+// lane holds one sum and finishes with a plain butterfly: NS = 4 takes 6
+// additions per lane instead of 20.  Returns the total of sum (lane >> 3) & 3
+// (NS = 4), lane >> 4 (NS = 2) or sum 0 (NS = 1): sum s is held by the lanes
+// s * 32 / NS ... (s + 1) * 32 / NS - 1.  The order of the additions is fixed.
+template <int NS>
+__device__ __forceinline__ double warp_sums(const double (&v)[NS], int lane) {
+    static_assert(NS == 1 || NS == 2 || NS == 4, "warp_sums: NS must be 1, 2 or 4");
+    double a;
+    int o = 16;
+    if constexpr (NS == 4) {
+        const bool h16 = (lane & 16) != 0;
+        const double a0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, h16 ? v[0] : v[2], 16);
+        const double a1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, h16 ? v[1] : v[3], 16);
+        const bool h8 = (lane & 8) != 0;
+        a = (h8 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, h8 ? a0 : a1, 8);
+        o = 4;
+    } else if constexpr (NS == 2) {
+        const bool h16 = (lane & 16) != 0;
+        a = (h16 ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, h16 ? v[0] : v[1], 16);
+        o = 8;
+    } else {
+        a = v[0];
+    }
+#pragma unroll
+    for (; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// Combine per-warp totals sh[s][w] (s < NS, w < kWarps) in warp 0: lane
+// s * kWarps + w holds one of them, a butterfly over the kWarps lanes of each
+// sum leaves sum s in lane s * kWarps.  Needs NS * kWarps <= 32.
+template <int NS>
+__device__ __forceinline__ double warps_sums(const double (&sh)[NS][kWarps], int lane) {
+    static_assert(NS * kWarps <= 32, "warps_sums: too many sums");
+    const int s = lane / kWarps, w = lane % kWarps;
+    double a = s < NS ? sh[s][w] : 0.0;
+#pragma unroll
+    for (int o = kWarps / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
 // Grid-wide sums.  Returns true in every thread of the last block to finish;
 // thread 0 of that block then holds the sums in tot[].  Requires blockDim.x ==
 // kThreads and gridDim.x <= kMaxRedBlocks.  The last block issues all its
 // partial loads first (one L2 round trip), then adds them in a fixed order,
 // so results do not depend on scheduling.
 //
-// FP64 per-thread values: warp and block sums in FP64.  GB300 issues FP64 at
-// a small fraction of its FP32 rate, so the tail adds only the partials a
-// warp actually holds (a warp-uniform bound) and combines warps over 8 lanes.
+// FP64 per-thread values: sums in FP64 throughout, with the few-addition warp
+// and block combinations above (FP64 kernels launch fewer blocks, see
+// red_grid64, so each thread adds several rows before the warp sums).
 template <int NS>
 __device__ bool grid_reduce(double (&v)[NS], double *partials, unsigned *counter, double (&tot)[NS]) {
     __shared__ double sh[NS][kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        const double x = warp_sum(v[s]);
-        if (lane == 0) sh[s][warp] = x;
+    constexpr int kPerSum = 32 / NS;  // lanes that hold one warp sum
+    {
+        const double x = warp_sums<NS>(v, lane);
+        if ((lane & (kPerSum - 1)) == 0) sh[lane / kPerSum][warp] = x;
     }
     __syncthreads();
     if (warp == 0) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const double x = warps_sum(lane < kWarps ? sh[s][lane] : 0.0);
-            if (lane == 0) partials[s * kMaxRedBlocks + blockIdx.x] = x;
-        }
+        const double x = warps_sums<NS>(sh, lane);
+        if (lane % kWarps == 0 && lane / kWarps < NS) partials[(lane / kWarps) * kMaxRedBlocks + blockIdx.x] = x;
     }
     if (!last_block(counter)) return false;
     constexpr int kPer = kMaxRedBlocks / kThreads;
     const int nj = ((int)gridDim.x - warp * 32 + kThreads - 1) / kThreads;  // rounds with a live lane in this warp
+    double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         double part[kPer];
@@ -701,16 +745,21 @@ __device__ bool grid_reduce(double (&v)[NS], double *partials, unsigned *counter
             const int b = threadIdx.x + j * kThreads;
             part[j] = b < (int)gridDim.x ? __ldcg(partials + s * kMaxRedBlocks + b) : 0.0;
         }
-        double acc = part[0];
+        double a = part[0];
 #pragma unroll
         for (int j = 1; j < kPer; ++j)
-            if (j < nj) acc += part[j];
-        acc = warp_sum(acc);
-        __syncthreads();
-        if (lane == 0) sh[s][warp] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            const double t = warps_sum(lane < kWarps ? sh[s][lane] : 0.0);
+            if (j < nj) a += part[j];
+        acc[s] = a;
+    }
+    const double x = warp_sums<NS>(acc, lane);
+    __syncthreads();  // every warp of warp 0's block-level read of sh is done (last_block's barriers)
+    if ((lane & (kPerSum - 1)) == 0) sh[lane / kPerSum][warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const double y = warps_sums<NS>(sh, lane);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double t = __shfl_sync(0xffffffffu, y, s * kWarps);
             if (lane == 0) tot[s] = t;
         }
     }

@@ -212,7 +212,7 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
                 if (da && post && k == nu - 1) {
                     DevLevel &F = mg->lv.back();
                     ProfScope ps(mg, DEC_PK_SMOOTHDOTS, l, s);
-                    const int rg = red_grid(mg, L.n);
+                    const int rg = da->d64 ? red_grid64(mg, L.n) : red_grid(mg, L.n);
                     if (da->d64) {
                         if (din)
                             launch(mg, k_smooth_zdots_d<KT, true>, rg, s, L.n, L.K, (const int32_t *)L.col, w, b,
@@ -445,10 +445,10 @@ void enqueue_outer_init(dec_mg *mg, TV *rv, cudaStream_t s, bool x0) {
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (x0)
-            launch(mg, k_outer_init<KT, TV, true>, red_grid(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob,
+            launch(mg, k_outer_init<KT, TV, true>, red_grid64(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob,
                    mg->ox, mg->orr, rv, mg->partials, mg->counter, mg->scal);
         else
-            launch(mg, k_outer_init<KT, TV, false>, red_grid(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob,
+            launch(mg, k_outer_init<KT, TV, false>, red_grid64(mg, F.n), s, F.n, F.K, F.col, F.w64, F.freev, mg->ob,
                    mg->ox, mg->orr, rv, mg->partials, mg->counter, mg->scal);
     });
 }
@@ -457,7 +457,7 @@ void enqueue_mean_shift(dec_mg *mg, double *v, cudaStream_t s, const int *skip) 
     DevLevel &F = mg->lv.back();
     const int top = (int)mg->lv.size() - 1;
     ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
-    launch(mg, k_mean, red_grid(mg, F.n), s, F.n, F.star0, F.freev, v, mg->partials, mg->counter, mg->scal, skip);
+    launch(mg, k_mean, red_grid64(mg, F.n), s, F.n, F.star0, F.freev, v, mg->partials, mg->counter, mg->scal, skip);
     launch(mg, k_shift, grid_for(mg, F.n), s, F.n, F.freev, v, mg->scal, skip);
 }
 
@@ -468,11 +468,11 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
                           bool first_pre0 = false) {
     DevLevel &F = mg->lv.back();
     const int gauge = mg->H.bc == DEC_BC_GAUGE;
-    const int rg = red_grid(mg, F.n);
+    const int rg = red_grid(mg, F.n), rg64 = red_grid64(mg, F.n);
     const int top = (int)mg->lv.size() - 1;
     if (solver == DEC_SOLVER_CG) {
         ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
-        launch(mg, k_pcg_zdots<double>, rg, s, F.n, F.star0, F.freev, mg->orr, mg->ozn, mg->orr, mg->ozo, first,
+        launch(mg, k_pcg_zdots<double>, rg64, s, F.n, F.star0, F.freev, mg->orr, mg->ozn, mg->orr, mg->ozo, first,
                                                     gauge, mg->partials, mg->counter, mg->scal, skip);
     } else if (mode != DEC_MODE_F64) {
         // z is the FP32 cycle output.  DEC_MODE_MIXED: FP64 dot products with
@@ -494,7 +494,7 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
         if (!da.done) {
             ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
             if (d64)
-                launch(mg, k_pcg_zdots_d, rg, s, F.n, (const double *)F.star0, (const uint8_t *)F.freev,
+                launch(mg, k_pcg_zdots_d, rg64, s, F.n, (const double *)F.star0, (const uint8_t *)F.freev,
                        (const float *)z, (const double *)mg->orr, (const double *)mg->ozo, first ? 1 : 0, gauge,
                        mg->partials, mg->counter, mg->scal, skip);
             else
@@ -516,7 +516,7 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
     } else {
         double *z = cycle<double>(mg, top, mg->orr, s, skip);
         ProfScope ps(mg, DEC_PK_ZDOTS, top, s);
-        launch(mg, k_pcg_zdots<double>, rg, s, F.n, F.star0, F.freev, z, mg->ozn, mg->orr, mg->ozo, first, gauge,
+        launch(mg, k_pcg_zdots<double>, rg64, s, F.n, F.star0, F.freev, z, mg->ozn, mg->orr, mg->ozo, first, gauge,
                                                     mg->partials, mg->counter, mg->scal, skip);
     }
     ProfScope ps(mg, DEC_PK_PUPD, top, s);
@@ -527,7 +527,7 @@ void enqueue_precondition(dec_mg *mg, int solver, int mode, bool first, cudaStre
 void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
     DevLevel &F = mg->lv.back();
     const int *skip = &mg->scal->done;
-    const int rg = red_grid(mg, F.n);
+    const int rg = red_grid(mg, F.n), rg64 = red_grid64(mg, F.n);
     const int top = (int)mg->lv.size() - 1;
     if (mode == DEC_MODE_MIXED_FF && solver != DEC_SOLVER_CG) {
         dispatch_k(F.K, [&](auto kt) {
@@ -557,7 +557,7 @@ void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         ProfScope ps(mg, DEC_PK_SPMV64, top, s);
-        launch(mg, k_pcg_spmv_d<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
+        launch(mg, k_pcg_spmv_d<KT>, rg64, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
                (const double *)F.star0, (const double *)mg->op, mg->oq, mg->partials, mg->counter, mg->scal, skip);
     });
     {
@@ -571,13 +571,13 @@ void enqueue_pcg_iteration(dec_mg *mg, int solver, int mode, cudaStream_t s) {
             s0mode = cheb && 1 < o.nu1 ? 2 : 1;
             e0 = (float)(cheb ? F.e_pre[0] : o.omega);
         }
-        launch(mg, k_pcg_update_d, rg, s, F.n, (const double *)mg->op, (const double *)mg->oq, mg->ox, mg->orr, F.b32,
+        launch(mg, k_pcg_update_d, rg64, s, F.n, (const double *)mg->op, (const double *)mg->oq, mg->ox, mg->orr, F.b32,
                mg->partials, mg->counter, mg->scal, skip, s0mode, (const float *)F.dg32, F.x32[0], F.d32[0], e0);
     } else if (mode == DEC_MODE_MIXED_F32DOT && solver != DEC_SOLVER_CG)
         launch(mg, k_pcg_update_m, rg, s, F.n, (const double *)mg->op, (const double *)mg->oq, mg->ox, mg->orr, F.b32,
                mg->partials, mg->counter, mg->scal, skip);
     else
-        launch(mg, k_pcg_update<double>, rg, s, F.n, mg->op, mg->oq, mg->ox, mg->orr, nullptr, mg->partials,
+        launch(mg, k_pcg_update<double>, rg64, s, F.n, mg->op, mg->oq, mg->ox, mg->orr, nullptr, mg->partials,
                                                      mg->counter, mg->scal, skip);
     }
     enqueue_precondition(mg, solver, mode, false, s, skip);
@@ -587,7 +587,7 @@ void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
     DevLevel &F = mg->lv.back();
     const int *skip = &mg->scal->done;
     const int top = (int)mg->lv.size() - 1;
-    const int rg = red_grid(mg, F.n);
+    const int rg = red_grid(mg, F.n), rg64 = red_grid64(mg, F.n);
     if (mode == DEC_MODE_MIXED_FF) {
         float *e = cycle<float>(mg, top, F.b32, s, skip);
         {
@@ -612,7 +612,7 @@ void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
             constexpr int KT = decltype(kt)::value;
             ProfScope ps(mg, DEC_PK_MGRES, top, s);
             if (mode == DEC_MODE_MIXED)
-                launch(mg, k_mg_residual_d<KT>, rg, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
+                launch(mg, k_mg_residual_d<KT>, rg64, s, F.n, F.K, (const int32_t *)F.col, (const double *)F.w64,
                        (const uint8_t *)F.freev, (const double *)mg->ob, (const double *)mg->ox, mg->orr, F.b32,
                        mg->partials, mg->counter, mg->scal, skip);
             else
@@ -629,7 +629,7 @@ void enqueue_mg_iteration(dec_mg *mg, int mode, cudaStream_t s) {
         dispatch_k(F.K, [&](auto kt) {
             constexpr int KT = decltype(kt)::value;
             ProfScope ps(mg, DEC_PK_MGRES, top, s);
-            launch(mg, k_mg_residual<KT, double>, rg, s, F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox, mg->orr,
+            launch(mg, k_mg_residual<KT, double>, rg64, s, F.n, F.K, F.col, F.w64, F.freev, mg->ob, mg->ox, mg->orr,
                                                               (double *)nullptr, mg->partials, mg->counter, mg->scal,
                                                               skip);
         });
@@ -797,7 +797,7 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         ProfScope p1(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s), p2(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
         const bool mg_solver = o.solver == DEC_SOLVER_MG;
         const int rg = red_grid(mg, F.n);
-        launch(mg, k_b_stats, rg, s, F.n, (const double *)F.star0, (const uint8_t *)F.freev, (const double *)mg->ob,
+        launch(mg, k_b_stats, red_grid64(mg, F.n), s, F.n, (const double *)F.star0, (const uint8_t *)F.freev, (const double *)mg->ob,
                gauge ? 1 : 0, mg->partials, mg->counter, mg->scal);
         launch(mg, k_init_ff, rg, s, F.n, (const uint8_t *)F.freev, mg->ob, mg->fxh, mg->fxl, F.b32, mg->frl,
                mg_solver ? mg->fbh : nullptr, mg_solver ? mg->fbl : nullptr, s0mode, (const float *)F.dg32,
@@ -863,7 +863,7 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         const int top = (int)mg->lv.size() - 1;
         if (gauge) {
             ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
-            launch(mg, k_ff_join_mean, red_grid(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl,
+            launch(mg, k_ff_join_mean, red_grid64(mg, F.n), s, F.n, (const float *)mg->fxh, (const float *)mg->fxl,
                    mg->ox, (const double *)F.star0, (const uint8_t *)F.freev, mg->partials, mg->counter, mg->scal);
             launch(mg, k_shift_out, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, mg->ox,
                    x_host ? nullptr : x, (const Scal *)mg->scal);
@@ -876,7 +876,7 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         // the mean shift writes the caller's x as it goes
         const int top = (int)mg->lv.size() - 1;
         ProfScope p1(mg, DEC_PK_AUX, top, s), p2(mg, DEC_PK_AUX, top, s);
-        launch(mg, k_mean, red_grid(mg, F.n), s, F.n, F.star0, F.freev, (const double *)mg->ox, mg->partials,
+        launch(mg, k_mean, red_grid64(mg, F.n), s, F.n, F.star0, F.freev, (const double *)mg->ox, mg->partials,
                mg->counter, mg->scal, (const int *)nullptr);
         launch(mg, k_shift_out, grid_for(mg, F.n), s, F.n, (const uint8_t *)F.freev, mg->ox,
                x_host ? nullptr : x, (const Scal *)mg->scal);
@@ -2100,7 +2100,7 @@ int dec_porous_rk(dec_mg *mg, double *T, double *P, const uint8_t *fixed, const 
     double *esum = work + (size_t)10 * n;
     dec_rk_stats out{};
     double t = 0.0, dt = dt0;  // time reached and next step (reported on every return)
-    const int g = grid_for(mg, n), rg = red_grid(mg, n);
+    const int g = grid_for(mg, n), rg = red_grid64(mg, n);
     auto finish = [&](int code) {
         out.t = t;
         out.dt = dt;
