@@ -99,6 +99,20 @@ def bytes_per_row(kind, K, mode, cheb, outer=False):
     return None
 
 
+def fp64_per_row(kind, mode):
+    """FP64 instructions per row of the FP64-pipe-bound outer kernels (0: not FP64-bound).  Mode mixed:
+    q = L p in the difference form (6 subtractions, 6 FMAs) with <p, q>*0 (a product, an FMA); the update
+    (x, r, ||r||^2: 3 FMAs, the FP32 rounding of r); the four *0 dot products of z (a product, 3 FMAs, an
+    add; z widened by integer instructions); the direction (a subtraction, an FMA)."""
+    if mode == "mixed":
+        return {"spmv64": 14, "update": 4, "smoothdots": 5, "zdots": 5, "pupd": 2}.get(kind, 0)
+    if mode == "mixed_f32dot":
+        return {"spmv64": 14, "update": 3, "pupd": 1}.get(kind, 0)
+    if mode == "f64":
+        return {"spmv64": 21, "update": 3, "zdots": 6, "pupd": 2}.get(kind, 0)
+    return 0
+
+
 def restrict_bytes(n_f, n_c, K, f):
     return n_c * K * 4 + n_f * f + n_c * f
 
@@ -143,7 +157,7 @@ def peaks():
 
 def kernels_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "coarse_cycle.cuh"):  # the device code the counters were taken on
+    for f in ("kernels.cuh", "coarse_cycle.cuh", "batch.cu"):  # the device code the counters were taken on
         with open(os.path.join(ROOT, "paper_2508_12501_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -732,36 +746,58 @@ def main():
     # ---- live per-kernel timing of the same solves (event pairs on the solve stream)
     mixed = args.mode != "f64"
     cheb = args.smoother == "chebyshev"
-    rows, roof = [], None
+    rows, roof, vroof = [], None, None
     try:
         _, _, _, prof = timed_solves(args.steps, args.mode, profile=2 if args.profile_all_levels else 1)
         for e in prof or []:
             by = kernel_bytes(e, h, args.mode, cheb)
             avg = e["total_ms"] / max(1, e["launches"])
             rows.append(dict(e, avg_ms=avg, bytes=by, gbs=(by / (avg * 1e-3) / 1e9) if by else None))
-        top = max(rows, key=lambda r: r["total_ms"]) if rows else None
         peak, peak_src = peaks()
-        if top and top["bytes"]:
-            tr = ncu_traffic(top["kind"])
+        tot_ms = sum(r["total_ms"] for r in rows) or 1.0
+
+        def hbm_roof(r):
             # achieved: algorithmic bytes over the kernel's own duration inside the solve (an event pair around
             # each launch in the captured iteration graph, on the solve stream, L2 flushed before every solve)
-            avg_ms, by = top["avg_ms"], top["bytes"]
-            gbs = by / (avg_ms * 1e-3) / 1e9
-            roof = {"bound": "hbm", "kernel": f"{top['kind']} (level {top['level']}, {top['rows']} rows)",
-                    "achieved": gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                    "frac": gbs / peak, "traffic": tr, "algorithmic_bytes": by,
-                    "traffic_over_algorithmic": (tr / by) if tr else None,
-                    "avg_launch_ms": avg_ms,
+            tr = ncu_traffic(r["kind"])
+            gbs = r["bytes"] / (r["avg_ms"] * 1e-3) / 1e9
+            out = {"bound": "hbm", "kernel": f"{r['kind']} (level {r['level']}, {r['rows']} rows)",
+                   "achieved": gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": gbs / peak,
+                   "traffic": tr, "algorithmic_bytes": r["bytes"],
+                   "traffic_over_algorithmic": (tr / r["bytes"]) if tr else None, "avg_launch_ms": r["avg_ms"],
+                   "timing": "event pair around each launch inside the solve's iteration graph (in-solve)",
+                   "share_of_profiled_time": r["total_ms"] / tot_ms}
+            if r["kind"] == "smooth":
+                # the same kernel and launch shape back to back on the solve stream (no event between
+                # launches); the level's working set stays in L2, so this is an L2-assisted figure
+                bb_ms, bb_by = h.time_kernel("smooth", level=r["level"], reps=200)
+                out["l2_assisted"] = {"achieved": bb_by / (bb_ms * 1e-3) / 1e9,
+                                      "frac": bb_by / (bb_ms * 1e-3) / 1e9 / peak, "avg_launch_ms": bb_ms,
+                                      "timing": "200 back-to-back launches between two CUDA events"}
+            return out
+
+        def alu_roof(r):
+            # FP64-pipe-bound outer kernels: FP64 instructions per row (fp64_per_row) over the in-solve duration,
+            # against GB300's FP64 issue rate: 2 lanes per SM per cycle (ncu: dfma peak_sustained 2/cycle/SM)
+            # x 152 SMs x the maximum SM clock
+            per = fp64_per_row(r["kind"], args.mode)
+            sm_clk = (clk or {}).get("sm_max_mhz") or 2070.0
+            pk = 2.0 * 152 * sm_clk * 1e6 / 1e9
+            ach = per * r["rows"] / (r["avg_ms"] * 1e-3) / 1e9
+            return {"bound": "alu", "pipe": "fp64", "kernel": f"{r['kind']} (level {r['level']}, {r['rows']} rows)",
+                    "achieved": ach, "peak": pk, "peak_source": "FP64 issue rate (2 lanes/SM/cycle x 152 SMs x "
+                    f"{sm_clk:.0f} MHz)", "unit": "G FP64 instructions/s", "frac": ach / pk,
+                    "fp64_instructions_per_row": per, "avg_launch_ms": r["avg_ms"], "traffic": None,
                     "timing": "event pair around each launch inside the solve's iteration graph (in-solve)",
-                    "share_of_profiled_time": top["total_ms"] / sum(r["total_ms"] for r in rows)}
-            if top["kind"] == "smooth" or (top["kind"] in ("smoothdots", "spmv64", "update")
-                                           and args.mode == "mixed_ff"):
-                # the same kernel and launch shape back to back on the solve stream (no event between launches);
-                # the level's working set stays in L2, so this is an L2-assisted figure, not an HBM one
-                bb_ms, bb_by = h.time_kernel(top["kind"], level=top["level"], reps=200)
-                roof["l2_assisted"] = {"achieved": bb_by / (bb_ms * 1e-3) / 1e9,
-                                       "frac": bb_by / (bb_ms * 1e-3) / 1e9 / peak, "avg_launch_ms": bb_ms,
-                                       "timing": "200 back-to-back launches between two CUDA events"}
+                    "share_of_profiled_time": r["total_ms"] / tot_ms}
+
+        top = max(rows, key=lambda r: r["total_ms"]) if rows else None
+        if top is not None:
+            roof = alu_roof(top) if fp64_per_row(top["kind"], args.mode) else (hbm_roof(top) if top["bytes"] else None)
+        # the dominant kernel of the FP32 V-cycle (HBM-bound), whatever the outer iteration's precision
+        cyc = [r for r in rows if r["kind"] in ("smooth", "smooth0", "residual", "restrict", "prolong") and r["bytes"]]
+        if cyc:
+            vroof = hbm_roof(max(cyc, key=lambda r: r["total_ms"]))
     except Exception as ex:  # noqa: BLE001
         errors["profile"] = repr(ex)
 
@@ -876,7 +912,8 @@ def main():
                       "mixed_f32dot": "f32 cycles + f64 outer with f32 dot products", "f64": "f64"}[args.mode],
             "data": "synthetic",
             "config": workload_config(args, n, world),
-            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "roofline_vcycle": vroof, "cpu_baseline": cpu,
+            "clocks": clk,
             "iters": st.iters, "rel_res": st.rel_res, "true_rel_res": modes[args.mode]["true_rel_res"],
             "modes": modes, "fp64_solves_per_s": v64,
             "speedup_vs_fp64": (value / world / v64) if v64 else None, "mode_vs_fp64_rel_err_star0": err,
