@@ -106,13 +106,36 @@ __device__ __forceinline__ void vst(float *p, int i, const VecT<VW> &a) {
         p[i] = a.v[0];
 }
 
-// s = sum_q w_q (x_i - x_col(q)), d = sum_q w_q for VW adjacent right-hand sides
+// s = sum_q w_q (x_i - x_col(q)), d = sum_q w_q for VW adjacent right-hand sides.
+// Rows of 6 slots (interior valence 6) issue all their table loads, then all
+// six neighbour gathers, before the first FMA: the gathers are in flight
+// together.  The slot order of the sums is the same either way.
 template <int VW>
 __device__ __forceinline__ void brow(const BLevel &L, int v, int j, const float *x, VecT<VW> &s, float &d) {
     const VecT<VW> xi = vld<VW>(x, (v << L.kshift) + j);
 #pragma unroll
     for (int c = 0; c < VW; ++c) s.v[c] = 0.f;
     d = 0.f;
+    if (L.K == 6) {
+        const int n = L.n, ks = L.kshift;
+        int cq[6];
+        float wq[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            cq[q] = __ldg(L.col + (size_t)q * n + v);
+            wq[q] = __ldg(L.w + (size_t)q * n + v);
+        }
+        VecT<VW> xn[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) xn[q] = vld<VW>(x, (cq[q] << ks) + j);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+#pragma unroll
+            for (int c = 0; c < VW; ++c) s.v[c] = fmaf(wq[q], xi.v[c] - xn[q].v[c], s.v[c]);
+            d += wq[q];
+        }
+        return;
+    }
     for (int q = 0; q < L.K; ++q) {
         const size_t o = (size_t)q * L.n + v;
         const float wk = __ldg(L.w + o);
@@ -139,16 +162,18 @@ __device__ __forceinline__ void smooth0_body(const BLevel &L, const BTile &t, fl
 }
 
 __global__ void k_b_smooth0(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int cheb, float omega,
-                            int dout, const int *skip) {
+                            int dout, const int *skip, int ntiles) {
     pdl_prologue();
     if (skipped(skip)) return;
-    const BTile t = tiles[blockIdx.x];
-    const BLevel &L = lv[t.lev];
-    const float e = cheb ? L.epre[0] : omega;
-    if ((L.k & 3) == 0)
-        smooth0_body<4>(L, t, e, dout);
-    else
-        smooth0_body<1>(L, t, e, dout);
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const BTile t = tiles[tb];
+        const BLevel &L = lv[t.lev];
+        const float e = cheb ? L.epre[0] : omega;
+        if ((L.k & 3) == 0)
+            smooth0_body<4>(L, t, e, dout);
+        else
+            smooth0_body<1>(L, t, e, dout);
+    }
 }
 
 template <int VW>
@@ -177,17 +202,19 @@ __device__ __forceinline__ void smooth_body(const BLevel &L, const BTile &t, flo
 }
 
 __global__ void k_b_smooth(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int cheb, float omega,
-                           int sweep, int post, int src, int din, int dout, const int *skip) {
+                           int sweep, int post, int src, int din, int dout, const int *skip, int ntiles) {
     pdl_prologue();
     if (skipped(skip)) return;
-    const BTile t = tiles[blockIdx.x];
-    const BLevel &L = lv[t.lev];
-    const float e = cheb ? (post ? L.epost[sweep] : L.epre[sweep]) : omega;
-    const float c = cheb ? (post ? L.cpost[sweep] : L.cpre[sweep]) : 0.f;
-    if ((L.k & 3) == 0)
-        smooth_body<4>(L, t, e, c, src, din, dout);
-    else
-        smooth_body<1>(L, t, e, c, src, din, dout);
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const BTile t = tiles[tb];
+        const BLevel &L = lv[t.lev];
+        const float e = cheb ? (post ? L.epost[sweep] : L.epre[sweep]) : omega;
+        const float c = cheb ? (post ? L.cpost[sweep] : L.cpre[sweep]) : 0.f;
+        if ((L.k & 3) == 0)
+            smooth_body<4>(L, t, e, c, src, din, dout);
+        else
+            smooth_body<1>(L, t, e, c, src, din, dout);
+    }
 }
 
 template <int VW>
@@ -206,15 +233,17 @@ __device__ __forceinline__ void residual_body(const BLevel &L, const BTile &t, i
 }
 
 __global__ void k_b_residual(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int src,
-                             const int *skip) {
+                             const int *skip, int ntiles) {
     pdl_prologue();
     if (skipped(skip)) return;
-    const BTile t = tiles[blockIdx.x];
-    const BLevel &L = lv[t.lev];
-    if ((L.k & 3) == 0)
-        residual_body<4>(L, t, src);
-    else
-        residual_body<1>(L, t, src);
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const BTile t = tiles[tb];
+        const BLevel &L = lv[t.lev];
+        if ((L.k & 3) == 0)
+            residual_body<4>(L, t, src);
+        else
+            residual_body<1>(L, t, src);
+    }
 }
 
 // tiles range over the coarse items; t.lev is the fine level (the coarse one is t.lev - 1)
@@ -252,29 +281,33 @@ __device__ __forceinline__ void restrict_body(const BLevel &L, const BLevel &C, 
 }
 
 __global__ void k_b_restrict(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int star0,
-                             const int *skip) {
+                             const int *skip, int ntiles) {
     pdl_prologue();
     if (skipped(skip)) return;
-    const BTile t = tiles[blockIdx.x];
-    const BLevel &L = lv[t.lev];
-    const BLevel &C = lv[t.lev - 1];
-    if ((L.k & 3) == 0)
-        restrict_body<4>(L, C, t, star0);
-    else
-        restrict_body<1>(L, C, t, star0);
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const BTile t = tiles[tb];
+        const BLevel &L = lv[t.lev];
+        const BLevel &C = lv[t.lev - 1];
+        if ((L.k & 3) == 0)
+            restrict_body<4>(L, C, t, star0);
+        else
+            restrict_body<1>(L, C, t, star0);
+    }
 }
 
 // coarsest level: x = G b for each right-hand side
-__global__ void k_b_coarse(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, const int *skip) {
+__global__ void k_b_coarse(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, const int *skip, int ntiles) {
     pdl_prologue();
     if (skipped(skip)) return;
-    const BTile t = tiles[blockIdx.x];
-    const BLevel &L = lv[t.lev];
-    for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
-        const int row = i >> L.kshift, j = i & (L.k - 1);
-        float acc = 0.f;
-        for (int c = 0; c < L.n; ++c) acc = fmaf(__ldg(L.G + (size_t)row * L.n + c), L.b[(c << L.kshift) + j], acc);
-        L.x[0][i] = acc;
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const BTile t = tiles[tb];
+        const BLevel &L = lv[t.lev];
+        for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+            const int row = i >> L.kshift, j = i & (L.k - 1);
+            float acc = 0.f;
+            for (int c = 0; c < L.n; ++c) acc = fmaf(__ldg(L.G + (size_t)row * L.n + c), L.b[(c << L.kshift) + j], acc);
+            L.x[0][i] = acc;
+        }
     }
 }
 
@@ -301,16 +334,18 @@ __device__ __forceinline__ void prolong_body(const BLevel &L, const BLevel &C, c
 }
 
 __global__ void k_b_prolong(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, int dst,
-                            const int *skip) {
+                            const int *skip, int ntiles) {
     pdl_prologue();
     if (skipped(skip)) return;
-    const BTile t = tiles[blockIdx.x];
-    const BLevel &L = lv[t.lev];
-    const BLevel &C = lv[t.lev - 1];
-    if ((L.k & 3) == 0)
-        prolong_body<4>(L, C, t, dst);
-    else
-        prolong_body<1>(L, C, t, dst);
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const BTile t = tiles[tb];
+        const BLevel &L = lv[t.lev];
+        const BLevel &C = lv[t.lev - 1];
+        if ((L.k & 3) == 0)
+            prolong_body<4>(L, C, t, dst);
+        else
+            prolong_body<1>(L, C, t, dst);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -688,6 +723,9 @@ struct dec_batch {
         int sweep, post, src, din, dout;
     };
     std::vector<Op> cycle_ops;
+    // blocks of one wave of each cycle kernel (SMs x resident blocks): a
+    // launch over more tiles loops, each block taking every wave-th tile
+    int wave[6] = {0, 0, 0, 0, 0, 0};
     int res_off = 0, res_cnt = 0;  // finest items of every group (the outer iteration)
     BTile *dtiles = nullptr;
     BSums sums{};
@@ -777,16 +815,17 @@ void enqueue_cycle(dec_batch *B, cudaStream_t s, const int *skip) {
     const float omega = (float)(2.0 / 3.0);
     for (const auto &op : B->cycle_ops) {
         const BTile *t = B->dtiles + op.off;
+        const int g = std::min(op.cnt, B->wave[op.kind]);
         switch (op.kind) {
-            case 0: blaunch(B, k_b_smooth0, op.cnt, 0, s, (const BLevel *)B->dlv, t, cheb, omega, op.dout, skip); break;
+            case 0: blaunch(B, k_b_smooth0, g, 0, s, (const BLevel *)B->dlv, t, cheb, omega, op.dout, skip, op.cnt); break;
             case 1:
-                blaunch(B, k_b_smooth, op.cnt, 0, s, (const BLevel *)B->dlv, t, cheb, omega, op.sweep, op.post, op.src,
-                        op.din, op.dout, skip);
+                blaunch(B, k_b_smooth, g, 0, s, (const BLevel *)B->dlv, t, cheb, omega, op.sweep, op.post, op.src,
+                        op.din, op.dout, skip, op.cnt);
                 break;
-            case 2: blaunch(B, k_b_residual, op.cnt, 0, s, (const BLevel *)B->dlv, t, op.src, skip); break;
-            case 3: blaunch(B, k_b_restrict, op.cnt, 0, s, (const BLevel *)B->dlv, t, op.src, skip); break;
-            case 4: blaunch(B, k_b_coarse, op.cnt, 0, s, (const BLevel *)B->dlv, t, skip); break;
-            case 5: blaunch(B, k_b_prolong, op.cnt, 0, s, (const BLevel *)B->dlv, t, op.src, skip); break;
+            case 2: blaunch(B, k_b_residual, g, 0, s, (const BLevel *)B->dlv, t, op.src, skip, op.cnt); break;
+            case 3: blaunch(B, k_b_restrict, g, 0, s, (const BLevel *)B->dlv, t, op.src, skip, op.cnt); break;
+            case 4: blaunch(B, k_b_coarse, g, 0, s, (const BLevel *)B->dlv, t, skip, op.cnt); break;
+            case 5: blaunch(B, k_b_prolong, g, 0, s, (const BLevel *)B->dlv, t, op.src, skip, op.cnt); break;
         }
     }
 }
@@ -1017,6 +1056,22 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
     B->mgs.assign(mgs, mgs + nmesh);
     B->nrhs.assign(nrhs, nrhs + nmesh);
     B->device = dev;
+    {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+        auto wave_of = [&](auto kernel) {
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, o.block, 0) != cudaSuccess || nb < 1) nb = 1;
+            return nsm * nb;
+        };
+        B->wave[0] = wave_of(k_b_smooth0);
+        B->wave[1] = wave_of(k_b_smooth);
+        B->wave[2] = wave_of(k_b_residual);
+        B->wave[3] = wave_of(k_b_restrict);
+        B->wave[4] = wave_of(k_b_coarse);
+        B->wave[5] = wave_of(k_b_prolong);
+        (void)cudaGetLastError();
+    }
     cudaError_t ce = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
     int rc;
@@ -1351,13 +1406,14 @@ extern "C" int dec_batch_time_smooth(dec_batch *B, int reps, double *avg_ms, dou
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int *noskip = nullptr;
+    const int g = std::min(op->cnt, B->wave[1]);
     for (int r = 0; r < 2; ++r)
-        blaunch(B, k_b_smooth, op->cnt, 0, s, (const BLevel *)B->dlv, (const BTile *)(B->dtiles + op->off), cheb,
-                (float)(2.0 / 3.0), 0, 1, op->src, 0, op->dout, noskip);
+        blaunch(B, k_b_smooth, g, 0, s, (const BLevel *)B->dlv, (const BTile *)(B->dtiles + op->off), cheb,
+                (float)(2.0 / 3.0), 0, 1, op->src, 0, op->dout, noskip, op->cnt);
     CK(cudaEventRecord(e0, s));
     for (int r = 0; r < reps; ++r)
-        blaunch(B, k_b_smooth, op->cnt, 0, s, (const BLevel *)B->dlv, (const BTile *)(B->dtiles + op->off), cheb,
-                (float)(2.0 / 3.0), 0, 1, op->src, 0, op->dout, noskip);
+        blaunch(B, k_b_smooth, g, 0, s, (const BLevel *)B->dlv, (const BTile *)(B->dtiles + op->off), cheb,
+                (float)(2.0 / 3.0), 0, 1, op->src, 0, op->dout, noskip, op->cnt);
     CK(cudaEventRecord(e1, s));
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
