@@ -606,6 +606,20 @@ def other_configs(torch, dev, stream):
 # our arm
 # ----------------------------------------------------------------------------
 
+def replica_throughput(local_s, steps, world, device):
+    """Whole-job throughput of `world` independent replicas that each ran `steps` solves in local_s seconds:
+    all ranks' solves over the slowest rank's time (max over ranks by all_reduce; no data moves between
+    replicas).  Returns (value, max seconds)."""
+    tot = local_s
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([local_s], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot = float(tt.item())
+    return steps * world / tot, tot
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -702,13 +716,8 @@ def main():
     ms, st, launches, _ = timed_solves(args.steps, args.mode)
     barrier()
     clk = clocks.stop()
-    tot_s = sum(ms) / 1e3
     x_mixed = x.clone()
-    if world > 1:
-        tt = torch.tensor([tot_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_s = float(tt.item())
-    value = args.steps * world / tot_s
+    value, tot_s = replica_throughput(sum(ms) / 1e3, args.steps, world, dev)
     errors = {}
     if args.only_solves:
         if rank == 0:
@@ -836,11 +845,8 @@ def main():
             t0 = time.perf_counter()
             xh, _ = h.solve(b_pin, x_pin, solver="mgpcg", mode=args.mode, tol=TOL)  # returns with x on the host
             e2e_s += time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e = {"value": args.steps * world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+        e2e_value, e2e_s = replica_throughput(e2e_s, args.steps, world, dev)
+        e2e = {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
                "d2h_bytes_per_step": 8 * n,
                "note": "host wall clock around each dec_solve_host call (pinned b and x; H2D, solve, D2H); "
                        "a 256 MB L2 flush before each call, outside the clock"}
