@@ -461,15 +461,17 @@ __global__ void k_b_shift(const BLevel *__restrict__ lv, const BTile *__restrict
     }
 }
 
-// MG-PCG, cold start: x = 0, r = b (free rows), r32 = (float) r; sums of r^2 and b^2.
-__global__ void k_bp_init(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, BSums P) {
+// MG-PCG, cold start: x = 0, r = b - mean (free rows; the gauge mean when sc is
+// given, 0 for Dirichlet groups), r32 = (float) r; sums of r^2 and b^2.
+__global__ void k_bp_init(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, const BScal *__restrict__ sc,
+                          BSums P) {
     pdl_prologue();
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
     double acc[2] = {0.0, 0.0};
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift;
-        const double ri = L.freev[v] ? L.ob[i] : 0.0;
+        const double ri = L.freev[v] ? L.ob[i] - (sc ? sc[rhs_of(L, i)].mean : 0.0) : 0.0;
         L.ox[i] = 0.0;
         L.orr[i] = ri;
         L.b[i] = (float)ri;
@@ -493,7 +495,7 @@ __global__ void k_bp_zdots(const BLevel *__restrict__ lv, const BTile *__restric
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift;
         if (L.freev[v]) {
-            const double s0 = __ldg(L.star0 + v), zi = (double)z[i];
+            const double s0 = __ldg(L.star0 + v), zi = decdev::f2d(z[i]);
             const double sr = s0 * L.orr[i];
             acc[0] = fma(s0, zi, acc[0]);
             acc[1] = fma(sr, zi, acc[1]);
@@ -515,7 +517,7 @@ __global__ void k_bp_pupd(const BLevel *__restrict__ lv, const BTile *__restrict
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift;
         const BScal &S = sc[rhs_of(L, i)];
-        const double zs = L.freev[v] ? (double)z[i] - S.c : 0.0;
+        const double zs = L.freev[v] ? decdev::f2d(z[i]) - S.c : 0.0;
         L.ozo[i] = zs;
         L.op[i] = first ? zs : fma(S.beta, L.op[i], zs);
     }
@@ -563,69 +565,74 @@ __global__ void k_bp_update(const BLevel *__restrict__ lv, const BTile *__restri
 
 enum { kFinMean = 0, kFinInit = 1, kFinZdots = 2, kFinAlpha = 3, kFinConv = 4 };
 
-// One warp per right-hand side: add its partials over its group's tiles (lane
-// strided, then a fixed butterfly), then the scalars of `kind`.  kFinInit and
-// kFinConv also decide convergence: the last block to finish sets the batch's
-// done flag once every right-hand side has converged (or maxit is reached),
-// counts the pass (kFinConv) and records the largest relative residual.
+// One block per right-hand side (block b = right-hand side b): add its
+// partials over its group's tiles (thread-strided, then a fixed-order warp
+// butterfly and a fixed-order sum of the warps), then the scalars of `kind`.
+// kFinInit and kFinConv also decide convergence: the last block to finish
+// sets the batch's done flag once every right-hand side has converged (or
+// maxit is reached), counts the pass (kFinConv) and records the largest
+// relative residual.
 __global__ void k_b_finalize(int nrhs, const BRhs *__restrict__ rinfo, const BLevel *__restrict__ lv, BSums P,
                              BScal *__restrict__ sc, int kind, int first, Scal *S, int *pending, unsigned *counter,
                              const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
-    const int warp = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    __shared__ double wsum[kBMaxSums][16];  // per-warp totals (blockDim <= 512)
+    const int q = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ns = kind == kFinZdots ? 4 : (kind == kFinInit ? 2 : 1);
-    if (warp < nrhs) {
-        const BRhs R = rinfo[warp];
+    const BRhs R = rinfo[q];
+    for (int s = 0; s < ns; ++s) {
+        double a = 0.0;
+        for (int tt = R.tb + threadIdx.x; tt < R.te; tt += blockDim.x)
+            a += P.part[((size_t)s * P.ntile + tt) * P.kmax + R.j];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) wsum[s][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double tot[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int s = 0; s < ns; ++s) {
-            double a = 0.0;
-            for (int tt = R.tb + lane; tt < R.te; tt += 32) a += P.part[((size_t)s * P.ntile + tt) * P.kmax + R.j];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            tot[s] = a;
+        for (int s = 0; s < ns; ++s)
+            for (int w = 0; w < nw; ++w) tot[s] += wsum[s][w];
+        BScal &C = sc[q];
+        const BLevel &L = lv[R.lev];
+        if (kind == kFinMean) {
+            C.mean = L.gauge ? tot[0] / L.s0sum : 0.0;
+        } else if (kind == kFinInit) {
+            C.bn2 = tot[1];
+            C.rn2 = tot[0];
+            C.thr2 = tot[1] > 0.0 ? S->tol * S->tol * tot[1] : (double)INFINITY;
+            C.stalled = 0;
+            C.done = !R.live || C.rn2 <= C.thr2;
+            C.rz = 0.0;
+            C.c = 0.0;
+        } else if (kind == kFinZdots) {
+            const double c = L.gauge ? tot[0] / L.s0sum : 0.0;
+            const double rz_new = tot[1] - c * tot[3];
+            C.beta = (first || C.done) ? 0.0 : (rz_new - tot[2]) / C.rz;
+            C.rz = rz_new;
+            C.c = c;
+        } else if (kind == kFinAlpha) {
+            double a = C.done ? 0.0 : C.rz / tot[0];
+            if (!C.done && (!(tot[0] > 0.0) || !isfinite(a))) {
+                a = 0.0;  // the iteration cannot move this right-hand side any further
+                C.stalled = 1;
+                C.done = 1;
+            }
+            C.alpha = a;
+        } else {  // kFinConv
+            C.rn2 = tot[0];
+            if (!C.done && C.rn2 <= C.thr2) C.done = 1;
         }
-        if (lane == 0) {
-            BScal &C = sc[warp];
-            const BLevel &L = lv[R.lev];
-            if (kind == kFinMean) {
-                C.mean = L.gauge ? tot[0] / L.s0sum : 0.0;
-            } else if (kind == kFinInit) {
-                C.bn2 = tot[1];
-                C.rn2 = tot[0];
-                C.thr2 = tot[1] > 0.0 ? S->tol * S->tol * tot[1] : (double)INFINITY;
-                C.stalled = 0;
-                C.done = !R.live || C.rn2 <= C.thr2;
-                C.rz = 0.0;
-                C.c = 0.0;
-            } else if (kind == kFinZdots) {
-                const double c = L.gauge ? tot[0] / L.s0sum : 0.0;
-                const double rz_new = tot[1] - c * tot[3];
-                C.beta = (first || C.done) ? 0.0 : (rz_new - tot[2]) / C.rz;
-                C.rz = rz_new;
-                C.c = c;
-            } else if (kind == kFinAlpha) {
-                double a = C.done ? 0.0 : C.rz / tot[0];
-                if (!C.done && (!(tot[0] > 0.0) || !isfinite(a))) {
-                    a = 0.0;  // the iteration cannot move this right-hand side any further
-                    C.stalled = 1;
-                    C.done = 1;
-                }
-                C.alpha = a;
-            } else {  // kFinConv
-                C.rn2 = tot[0];
-                if (!C.done && C.rn2 <= C.thr2) C.done = 1;
+        if (kind == kFinInit || kind == kFinConv) {
+            const bool bad = !isfinite(C.rn2) || !isfinite(C.bn2);
+            C.rel = bad ? (double)NAN : (C.bn2 > 0.0 ? sqrt(C.rn2 / C.bn2) : 0.0);
+            if (bad) {
+                C.done = 1;
+                atomicExch(&S->status, 1);
             }
-            if (kind == kFinInit || kind == kFinConv) {
-                const bool bad = !isfinite(C.rn2) || !isfinite(C.bn2);
-                C.rel = bad ? (double)NAN : (C.bn2 > 0.0 ? sqrt(C.rn2 / C.bn2) : 0.0);
-                if (bad) {
-                    C.done = 1;
-                    atomicExch(&S->status, 1);
-                }
-                if (!C.done) atomicAdd(pending, 1);
-                if (R.live && isfinite(C.rel))
-                    atomicMax((unsigned long long *)&S->rel, (unsigned long long)__double_as_longlong(C.rel));
-            }
+            if (!C.done) atomicAdd(pending, 1);
+            if (R.live && isfinite(C.rel))
+                atomicMax((unsigned long long *)&S->rel, (unsigned long long)__double_as_longlong(C.rel));
         }
     }
     if (kind != kFinInit && kind != kFinConv) return;
@@ -661,14 +668,17 @@ __global__ void k_b_gather(int n, int k, int nrhs, int src0, int dst0, int cnt, 
     }
 }
 
-// group layout -> user layout; mul != nullptr: multiply by mul[v]
+// group layout -> user layout; sc != nullptr: subtract each right-hand side's
+// mean (rhs0 = batch index of group column 0); mul != nullptr: then multiply by mul[v]
 __global__ void k_b_scatter(int n, int k, int nrhs, int src0, int dst0, int cnt, const double *__restrict__ src,
-                            double *__restrict__ dst, const double *__restrict__ mul) {
+                            double *__restrict__ dst, const double *__restrict__ mul, const BScal *__restrict__ sc,
+                            int rhs0) {
     pdl_prologue();
     const int64_t tot = (int64_t)n * cnt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int v = (int)(i / cnt), c = (int)(i % cnt);
-        const double val = src[(size_t)v * k + src0 + c];
+        double val = src[(size_t)v * k + src0 + c];
+        if (sc) val -= sc[rhs0 + src0 + c].mean;
         dst[(size_t)v * nrhs + dst0 + c] = mul ? val * mul[v] : val;
     }
 }
@@ -805,7 +815,7 @@ void blaunch(const dec_batch *B, void (*kernel)(KArgs...), int grid, size_t smem
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-int fin_grid(const dec_batch *B) { return (B->total_rhs * 32 + B->opts.block - 1) / B->opts.block; }
+int fin_grid(const dec_batch *B) { return B->total_rhs; }
 
 // One multigrid cycle of every group on its finest level's r32 (L.b); the
 // result is the finest level's x[res_idx].
@@ -927,8 +937,9 @@ int check_batch_device(const dec_batch *B) {
 
 // Solve with the right-hand sides already in every group's finest ob (caller
 // columns, zero padding): the gauge projection, x = 0, the loop, the gauge
-// shift of x.  The result is in every group's finest ox.
-int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &launches) {
+// mean of x.  The result is in every group's finest ox; when gauge is set on
+// return, the callers' scatter subtracts each right-hand side's mean (BScal::mean).
+int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &launches, bool &gauge) {
     Scal *h = B->scal_h;
     std::memset(h, 0, offsetof(Scal, hist));
     h->tol = tol;
@@ -940,11 +951,16 @@ int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &laun
     bool any_gauge = false;
     for (auto &L : B->hlv)
         if (L.ox && L.gauge) any_gauge = true;
+    gauge = any_gauge;
     if (any_gauge) {
+        // the mean of b; refinement shifts b itself (its residuals read b), MG-PCG shifts r = b in k_bp_init
         blaunch(B, k_b_meansum, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, 0, B->sums);
         enqueue_finalize(B, s, kFinMean, 0, nullptr);
-        blaunch(B, k_b_shift, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, 0, (const BScal *)B->bsc);
-        launches += 3;
+        launches += 2;
+        if (B->opts.solver == DEC_SOLVER_MG) {
+            blaunch(B, k_b_shift, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, 0, (const BScal *)B->bsc);
+            ++launches;
+        }
     }
     if (B->opts.solver == DEC_SOLVER_MG) {
         for (const auto &G : B->groups) {
@@ -955,7 +971,8 @@ int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &laun
         enqueue_finalize(B, s, kFinInit, 0, nullptr);
         launches += 2;
     } else {
-        blaunch(B, k_bp_init, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, B->sums);
+        blaunch(B, k_bp_init, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt,
+                any_gauge ? (const BScal *)B->bsc : (const BScal *)nullptr, B->sums);
         enqueue_finalize(B, s, kFinInit, 0, nullptr);
         launches += 2;
     }
@@ -972,10 +989,10 @@ int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &laun
         CK(cudaGraphLaunch(B->loop, s));
     }
     if (any_gauge) {
+        // the mean of x, subtracted by the scatter into the callers' vectors
         blaunch(B, k_b_meansum, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, 1, B->sums);
         enqueue_finalize(B, s, kFinMean, 0, nullptr);
-        blaunch(B, k_b_shift, B->res_cnt, 0, s, (const BLevel *)B->dlv, rt, 1, (const BScal *)B->bsc);
-        launches += 3;
+        launches += 2;
     }
     CK(cudaGetLastError());
     return DEC_OK;
@@ -1249,12 +1266,14 @@ int dec_batch_solve(dec_batch *B, const double *const *b, double *const *x, doub
             ++launches;
         }
     }
-    if (int rc = batch_run(B, tol, maxit, s, launches)) return rc;
+    bool gauge = false;
+    if (int rc = batch_run(B, tol, maxit, s, launches, gauge)) return rc;
+    const BScal *msc = gauge ? (const BScal *)B->bsc : (const BScal *)nullptr;
     for (auto &G : B->groups) {
         const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
         for (const auto &R : G.runs) {
             blaunch(B, k_b_scatter, gather_grid(B, (int64_t)L.n * R.cnt), 0, s, L.n, G.k, B->nrhs[R.entry], R.dst0,
-                    R.src0, R.cnt, (const double *)L.ox, x[R.entry], (const double *)nullptr);
+                    R.src0, R.cnt, (const double *)L.ox, x[R.entry], (const double *)nullptr, msc, G.rhs_base);
             ++launches;
         }
     }
@@ -1281,13 +1300,15 @@ int dec_batch_solve_backward(dec_batch *B, const double *const *u, const double 
             ++launches;
         }
     }
-    if (int rc = batch_run(B, tol, maxit, s, launches)) return rc;
+    bool gauge = false;
+    if (int rc = batch_run(B, tol, maxit, s, launches, gauge)) return rc;
+    const BScal *msc = gauge ? (const BScal *)B->bsc : (const BScal *)nullptr;
     for (auto &G : B->groups) {
         const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
-        // dJ/db = *0 mu
+        // dJ/db = *0 mu (mu with its gauge mean removed)
         for (const auto &R : G.runs) {
             blaunch(B, k_b_scatter, gather_grid(B, (int64_t)L.n * R.cnt), 0, s, L.n, G.k, B->nrhs[R.entry], R.dst0,
-                    R.src0, R.cnt, (const double *)L.ox, grad_b[R.entry], (const double *)L.star0);
+                    R.src0, R.cnt, (const double *)L.ox, grad_b[R.entry], (const double *)L.star0, msc, G.rhs_base);
             ++launches;
         }
         if (!grad_star1) continue;
