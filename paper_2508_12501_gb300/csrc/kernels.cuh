@@ -129,6 +129,12 @@ __device__ __forceinline__ void row_apply(int i, int n, int K, const int32_t *__
     _Pragma("unroll 2") for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 // The same loop not unrolled, for kernels whose two rows do not fit in 32 registers.
 #define GRID_STRIDE_1(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+// The loop unrolled by four, for the kernels whose per-row work and sums are
+// FP64: they run kFp64Blocks blocks per SM (a wave of them, red_grid64) with
+// up to 64 registers, so four rows' loads are in flight per thread.
+#define GRID_STRIDE_4(i, n) \
+    _Pragma("unroll 4") for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+constexpr int kFp64Blocks = 4;
 
 // y = L x
 template <typename T, int KT>
@@ -906,13 +912,13 @@ __device__ __forceinline__ void record_residual(Scal *S, double rnorm2) {
 }
 
 // mean = sum(*0 v) / sum(*0) over free rows (mask: free != 0)
-static __global__ void __launch_bounds__(kThreads, 8) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+static __global__ void __launch_bounds__(kThreads, kFp64Blocks) k_mean(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                   const double *__restrict__ v, double *partials, unsigned *counter,
                                                   Scal *S, const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
     double acc[1] = {0.0};
-    GRID_STRIDE(i, n) if (freev[i]) acc[0] += ldg(star0 + i) * ldg(v + i);
+    GRID_STRIDE_4(i, n) if (freev[i]) acc[0] += ldg(star0 + i) * ldg(v + i);
     double tot[1];
     if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) S->mean = tot[0] / S->star0_sum;
 }
@@ -930,14 +936,14 @@ static __global__ void __launch_bounds__(kThreads, 8) k_shift(int n, const uint8
 // also writes the cycle's input rv (cast) when rv != nullptr.  X0: x = 0, so
 // r = b without the operator apply.
 template <int KT, typename TV, bool X0 = false>
-__global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, kFp64Blocks) k_outer_init(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w, const uint8_t *__restrict__ freev,
                                                         const double *__restrict__ b, const double *__restrict__ x,
                                                         double *__restrict__ r, TV *__restrict__ rv, double *partials,
                                                         unsigned *counter, Scal *S) {
     pdl_prologue();
     double acc[2] = {0.0, 0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         double s = 0.0;
         if (!X0) {
             double d;
@@ -969,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_outer_init(int n, int K, const 
 // After a cycle produced z (type TZ): zn = (double) z; sums of *0 z, *0 r zn, *0 r zo, *0 r;
 // epilogue: gauge shift c, new <r,z>, Polak-Ribiere beta.
 template <typename TZ>
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
+__global__ void __launch_bounds__(kThreads, kFp64Blocks) k_pcg_zdots(int n, const double *__restrict__ star0, const uint8_t *__restrict__ freev,
                                                        const TZ *__restrict__ z, double *__restrict__ zn,
                                                        const double *__restrict__ r, const double *__restrict__ zo,
                                                        int first, int gauge, double *partials, unsigned *counter,
@@ -977,7 +983,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots(int n, const double *
     pdl_prologue();
     if (skipped(skip)) return;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         double zi = (double)ldg(z + i);
         if ((void *)zn != (void *)z) zn[i] = zi;
         if (freev[i]) {
@@ -1035,14 +1041,14 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv(int n, int K, const in
 
 // x += alpha p, r -= alpha q, rv = (TV) r, ||r||^2 -> convergence test
 template <typename TV>
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
+__global__ void __launch_bounds__(kThreads, kFp64Blocks) k_pcg_update(int n, const double *__restrict__ p, const double *__restrict__ q,
                                                         double *__restrict__ x, double *__restrict__ r, TV *__restrict__ rv,
                                                         double *partials, unsigned *counter, Scal *S, const int *skip) {
     pdl_prologue();
     if (skipped(skip)) return;
     const double a = S->alpha;
     double acc[1] = {0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         x[i] = fma(a, ldg(p + i), x[i]);
         double ri = fma(-a, ldg(q + i), r[i]);
         r[i] = ri;
@@ -1058,7 +1064,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_update(int n, const double 
 
 // Standalone MG / iterative refinement: x += e; r = b - L x; ||r||^2 -> convergence test.
 template <int KT, typename TV>
-__global__ void __launch_bounds__(kThreads, 8) k_mg_residual(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, kFp64Blocks) k_mg_residual(int n, int K, const int32_t *__restrict__ col,
                                                          const double *__restrict__ w, const uint8_t *__restrict__ freev,
                                                          const double *__restrict__ b, const double *__restrict__ x,
                                                          double *__restrict__ r, TV *__restrict__ rv, double *partials,
@@ -1066,7 +1072,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_mg_residual(int n, int K, const
     pdl_prologue();
     if (skipped(skip)) return;
     double acc[1] = {0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         double s, d;
         row_apply<double, KT>(i, n, K, col, w, x, s, d);
         double ri = freev[i] ? ldg(b + i) - s : 0.0;
@@ -1110,7 +1116,7 @@ __device__ __forceinline__ double row_apply_nod(int i, int n, int K, const int32
 
 // q = L p, <p, q> (*0) -> alpha
 template <int KT>
-__global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_d(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, kFp64Blocks) k_pcg_spmv_d(int n, int K, const int32_t *__restrict__ col,
                                                         const double *__restrict__ w,
                                                         const double *__restrict__ star0, const double *__restrict__ p,
                                                         double *__restrict__ q, double *partials, unsigned *counter,
@@ -1118,7 +1124,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_pcg_spmv_d(int n, int K, const 
     pdl_prologue();
     if (skipped(skip)) return;
     double acc[1] = {0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         const double qi = row_apply_nod<KT>(i, n, K, col, w, p);
         q[i] = qi;
         acc[0] = fma(ldg(star0 + i) * ldg(p + i), qi, acc[0]);
@@ -1310,7 +1316,7 @@ __device__ __forceinline__ double f2d(float f) {
 // s0mode > 0 also runs the next cycle's first smoothing step on the finest
 // level from zero, as k_smooth0 does on b = r32 (x0 = e0 r32 / dg, and d0 =
 // x0 when s0mode == 2); it is row-local.
-static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_d(int n, const double *__restrict__ p,
+static __global__ void __launch_bounds__(kThreads, kFp64Blocks) k_pcg_update_d(int n, const double *__restrict__ p,
                                                           const double *__restrict__ q, double *__restrict__ x,
                                                           double *__restrict__ r, float *__restrict__ r32,
                                                           double *partials, unsigned *counter, Scal *S,
@@ -1320,7 +1326,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_update_d(int n, cons
     if (skipped(skip)) return;
     const double a = S->alpha;
     double acc[1] = {0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         x[i] = fma(a, ldg(p + i), x[i]);
         const double ri = fma(-a, ldg(q + i), r[i]);
         r[i] = ri;
@@ -1356,7 +1362,7 @@ __device__ __forceinline__ void zdots_epilogue_d(Scal *S, const double (&tot)[4]
 
 // The four FP64 dot products of z (FP32 cycle output, unshifted) with *0 and
 // the FP64 residual r; zo is the previous shifted z (FP64).
-static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_d(int n, const double *__restrict__ star0,
+static __global__ void __launch_bounds__(kThreads, kFp64Blocks) k_pcg_zdots_d(int n, const double *__restrict__ star0,
                                                          const uint8_t *__restrict__ freev,
                                                          const float *__restrict__ z, const double *__restrict__ r,
                                                          const double *__restrict__ zo, int first, int gauge,
@@ -1365,7 +1371,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_d(int n, const
     pdl_prologue();
     if (skipped(skip)) return;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         if (freev[i]) {
             const double s0 = ldg(star0 + i), zi = f2d(ldg(z + i));
             const double sr = s0 * ldg(r + i);
@@ -1384,7 +1390,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_zdots_d(int n, const
 // are row-local.  Launched on the reduction grid so that rows map to threads
 // as in k_pcg_zdots_d (bitwise equal sums).
 template <int KT, bool DIN>
-__global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots_d(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, kFp64Blocks) k_smooth_zdots_d(int n, int K, const int32_t *__restrict__ col,
                                                             const float *__restrict__ w, const float *__restrict__ b,
                                                             const float *__restrict__ x_in,
                                                             const float *__restrict__ d_in, float *__restrict__ x_out,
@@ -1397,7 +1403,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth_zdots_d(int n, int K, co
     pdl_prologue_ell<KT>(n, K, col, w);
     if (skipped(skip)) return;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    GRID_STRIDE_1(i, n) {
+    GRID_STRIDE_4(i, n) {
         float s, d;
         row_apply<float, KT>(i, n, K, col, w, x_in, s, d);
         const float q = d != 0.f ? (ldg(b + i) - s) / d : 0.f;
@@ -1436,7 +1442,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_pcg_pupd_d(int n, const 
 // Standalone MG / iterative refinement with the FP64 outer loop: r = b - L x
 // (FP64), r32 = (float) r, ||r||^2 in FP64 -> convergence test.
 template <int KT>
-__global__ void __launch_bounds__(kThreads, 8) k_mg_residual_d(int n, int K, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, kFp64Blocks) k_mg_residual_d(int n, int K, const int32_t *__restrict__ col,
                                                            const double *__restrict__ w,
                                                            const uint8_t *__restrict__ freev,
                                                            const double *__restrict__ b, const double *__restrict__ x,
@@ -1446,7 +1452,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_mg_residual_d(int n, int K, con
     pdl_prologue();
     if (skipped(skip)) return;
     double acc[1] = {0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         const double s = row_apply_nod<KT>(i, n, K, col, w, x);
         const double ri = freev[i] ? ldg(b + i) - s : 0.0;
         r[i] = ri;
@@ -1554,7 +1560,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_ff_join(int n, const flo
 
 // The same with the gauge: x = (hi + lo) / scale and the *0-weighted mean of x
 // over free rows, for k_shift_out.
-static __global__ void __launch_bounds__(kThreads, 8) k_ff_join_mean(int n, const float *__restrict__ xh,
+static __global__ void __launch_bounds__(kThreads, kFp64Blocks) k_ff_join_mean(int n, const float *__restrict__ xh,
                                                           const float *__restrict__ xl, double *__restrict__ x,
                                                           const double *__restrict__ star0,
                                                           const uint8_t *__restrict__ freev, double *partials,
@@ -1562,7 +1568,7 @@ static __global__ void __launch_bounds__(kThreads, 8) k_ff_join_mean(int n, cons
     pdl_prologue();
     const double is = S->iscale;
     double acc[1] = {0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         const double v = ((double)ldg(xh + i) + (double)ldg(xl + i)) * is;
         x[i] = v;
         if (freev[i]) acc[0] = fma(ldg(star0 + i), v, acc[0]);
@@ -1587,13 +1593,13 @@ static __global__ void __launch_bounds__(kThreads, 8) k_shift_out(int n, const u
 // Start of a cold-start (x = 0) float-float solve, pass 1: the *0-weighted
 // mean of b over free rows (gauge) and ||b||^2 over free rows, whose size
 // fixes the power-of-two scale of the ff iteration (ff_scale).
-static __global__ void __launch_bounds__(kThreads, 8) k_b_stats(int n, const double *__restrict__ star0,
+static __global__ void __launch_bounds__(kThreads, kFp64Blocks) k_b_stats(int n, const double *__restrict__ star0,
                                                      const uint8_t *__restrict__ freev,
                                                      const double *__restrict__ b, int gauge, double *partials,
                                                      unsigned *counter, Scal *S) {
     pdl_prologue();
     double acc[2] = {0.0, 0.0};
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE_4(i, n) {
         if (freev[i]) {
             const double bi = ldg(b + i);
             if (gauge) acc[0] = fma(ldg(star0 + i), bi, acc[0]);
@@ -1955,14 +1961,14 @@ static __global__ void __launch_bounds__(kThreads) k_rk_combine(int n, const dou
 
 // Embedded error estimate err = dt * sum_j e_j k_j, scaled componentwise by
 // atol + rtol max(|T|, |T_new|); *out = the sum of the squares (FP64).
-static __global__ void __launch_bounds__(kThreads, 8) k_rk_error(int n, const double *__restrict__ T,
+static __global__ void __launch_bounds__(kThreads, kFp64Blocks) k_rk_error(int n, const double *__restrict__ T,
                                                           const double *__restrict__ Tn,
                                                           const __grid_constant__ RkStages e, double dt,
                                                           double rtol, double atol, double *partials,
                                                           unsigned *counter, double *out) {
     pdl_prologue();
     double acc[1] = {0.0};
-    GRID_STRIDE(v, n) {
+    GRID_STRIDE_4(v, n) {
         double s = 0.0;
         for (int j = 0; j < e.nk; ++j) s = fma(e.a[j], ldg(e.k[j] + v), s);
         const double err = dt * s;

@@ -236,13 +236,14 @@ inline int red_grid(const dec_mg *mg, int64_t n) {
     return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
-// Grid of a kernel whose per-row work and sums are FP64: half a wave (4
-// blocks per SM), so every thread adds about twice the rows before its FP64
-// warp and block sums -- on GB300's narrow FP64 pipe those sums cost more
-// than the rows at one or two rows per thread.
+// Grid of a kernel whose per-row work and sums are FP64: one wave of
+// decdev::kFp64Blocks blocks per SM (half the blocks of the FP32 kernels), so
+// every thread adds about twice the rows before its FP64 warp and block sums
+// -- on GB300's narrow FP64 pipe those sums cost more than the rows at one or
+// two rows per thread -- and, with 64 registers, keeps four rows' loads in flight.
 inline int red_grid64(const dec_mg *mg, int64_t n) {
     int64_t g = (n + kThreads - 1) / kThreads;
-    int64_t cap = std::min<int64_t>(kMaxRedBlocks, (int64_t)mg->nsm * 4);
+    int64_t cap = std::min<int64_t>(kMaxRedBlocks, (int64_t)mg->nsm * decdev::kFp64Blocks);
     return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
