@@ -1665,6 +1665,49 @@ static __global__ void __launch_bounds__(kThreads, 8) k_init_ff(int n, const uin
     }
 }
 
+// Start of a cold-start (x = 0) MG-PCG solve with an FP64 outer iteration
+// (DEC_MODE_MIXED, DEC_MODE_MIXED_F32DOT), after k_b_stats gave the gauge
+// mean: b <- b - mean on free rows, 0 on fixed rows (written back), r = b,
+// r32 = (float) r, x = 0, and ||r||^2 = ||b||^2 (FP64) starts the stopping
+// test.  s0mode > 0 also runs the first cycle's first smoothing step on the
+// finest level from zero, as k_smooth0 does (x0 = e0 r32 / dg, d0 = x0 when
+// s0mode == 2).
+static __global__ void __launch_bounds__(kThreads, kFp64Blocks) k_init_d(int n, const uint8_t *__restrict__ freev,
+                                                               double *b, double *__restrict__ x,
+                                                               double *__restrict__ r, float *__restrict__ r32,
+                                                               int s0mode, const float *__restrict__ dg,
+                                                               float *__restrict__ x0, float *__restrict__ d0,
+                                                               float e0, double *partials, unsigned *counter, Scal *S) {
+    pdl_prologue();
+    const double m = S->mean;
+    double acc[1] = {0.0};
+    GRID_STRIDE_4(i, n) {
+        const double v = freev[i] ? b[i] - m : 0.0;
+        b[i] = v;
+        x[i] = 0.0;
+        r[i] = v;
+        const float rf = (float)v;
+        r32[i] = rf;
+        acc[0] = fma(v, v, acc[0]);
+        if (s0mode > 0) {
+            const float di = ldg(dg + i);
+            const float x1 = di != 0.f ? e0 * (rf / di) : 0.f;
+            x0[i] = x1;
+            if (s0mode == 2) d0[i] = x1;
+        }
+    }
+    double tot[1];
+    if (grid_reduce<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        S->bnorm2 = tot[0];
+        S->thr2 = tot[0] > 0.0 ? S->tol * S->tol * tot[0] : (double)INFINITY;
+        S->iter = 0;
+        S->done = 0;
+        S->status = 0;
+        S->rnorm2_0 = tot[0];
+        record_residual(S, tot[0]);
+    }
+}
+
 // z = z - c (free rows), zo = z, p = z + beta p, all FP32.
 static __global__ void __launch_bounds__(kThreads, 8) k_pcg_pupd_f(int n, const uint8_t *__restrict__ freev,
                                                         const float *__restrict__ z, float *__restrict__ zo,

@@ -770,10 +770,15 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     // gauge mean and the ff scale from one pass over b, then the shifted b as
     // ff pairs with x = 0 and the first cycle's first smoothing step.
     const bool cold_ff = ff && !o.warm_start;
+    // A cold MG-PCG solve with an FP64 outer iteration starts the same way: the
+    // gauge mean from one pass over b, then r = b - mean, x = 0, ||r||^2 and the
+    // first cycle's first smoothing step in one pass.
+    const bool cold_d = (o.mode == DEC_MODE_MIXED || o.mode == DEC_MODE_MIXED_F32DOT) && !o.warm_start &&
+                        o.solver == DEC_SOLVER_MGPCG;
     const dec_mg_opts &mo = mg->H.opts;
     int s0mode = 0;
     float e0 = 0.f;
-    if (cold_ff && o.solver == DEC_SOLVER_MGPCG && (mo.fuse & DEC_FUSE_OUTER) && mo.nu1 > 0 &&
+    if ((cold_ff || cold_d) && o.solver == DEC_SOLVER_MGPCG && (mo.fuse & DEC_FUSE_OUTER) && mo.nu1 > 0 &&
         mo.smoother != DEC_SMOOTH_MCGS) {
         const bool cheb = mo.smoother == DEC_SMOOTH_CHEBYSHEV;
         s0mode = cheb && 1 < mo.nu1 ? 2 : 1;
@@ -782,7 +787,7 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
     CK(cudaMemcpyAsync(mg->ob, b, vb, b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     if (o.warm_start)
         CK(cudaMemcpyAsync(mg->ox, x, vb, x_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
-    else if (!cold_ff)
+    else if (!cold_ff && !cold_d)
         CK(cudaMemsetAsync(mg->ox, 0, vb, s));
     // scalar header (everything before the history)
     Scal *h = mg->scal_h;
@@ -802,6 +807,13 @@ int solve_impl(dec_mg *mg, const double *b, double *x, const dec_solve_opts *po,
         launch(mg, k_init_ff, rg, s, F.n, (const uint8_t *)F.freev, mg->ob, mg->fxh, mg->fxl, F.b32, mg->frl,
                mg_solver ? mg->fbh : nullptr, mg_solver ? mg->fbl : nullptr, s0mode, (const float *)F.dg32,
                F.x32[0], F.d32[0], e0, mg->partials, mg->counter, mg->scal);
+    } else if (cold_d) {
+        ProfScope p1(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s), p2(mg, DEC_PK_AUX, (int)mg->lv.size() - 1, s);
+        const int rg64 = red_grid64(mg, F.n);
+        launch(mg, k_b_stats, rg64, s, F.n, (const double *)F.star0, (const uint8_t *)F.freev, (const double *)mg->ob,
+               gauge ? 1 : 0, mg->partials, mg->counter, mg->scal);
+        launch(mg, k_init_d, rg64, s, F.n, (const uint8_t *)F.freev, mg->ob, mg->ox, mg->orr, F.b32, s0mode,
+               (const float *)F.dg32, F.x32[0], F.d32[0], e0, mg->partials, mg->counter, mg->scal);
     } else {
     if (gauge) {
         enqueue_mean_shift(mg, mg->ob, s, nullptr);
