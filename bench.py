@@ -155,9 +155,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernels_hash():
+# Device sources each measured kernel is compiled from (single-right-hand-side kernels: kernels.cuh and
+# coarse_cycle.cuh; batched kernels: batch.cu and the kernels.cuh helpers it includes).
+KERNEL_SOURCES = {"single": ("kernels.cuh", "coarse_cycle.cuh"), "batched": ("batch.cu", "kernels.cuh")}
+
+
+def kernels_hash(group="single"):
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "coarse_cycle.cuh", "batch.cu"):  # the device code the counters were taken on
+    for f in KERNEL_SOURCES[group]:  # the device code the counters were taken on
         with open(os.path.join(ROOT, "paper_2508_12501_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -170,10 +175,10 @@ def ncu_traffic(kind):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    if d.get("kernels_hash") != kernels_hash():
-        return None
     ent = d.get("kernels", {}).get(kind)
-    return None if ent is None else float(ent["dram_bytes_per_launch"])
+    if ent is None or ent.get("kernels_hash") != kernels_hash(ent.get("sources", "single")):
+        return None
+    return float(ent["dram_bytes_per_launch"])
 
 
 # ----------------------------------------------------------------------------
