@@ -287,11 +287,12 @@ int dec_mg_set_star1(dec_mg *mg, const double *star1, dec_stream_t stream);
  * dec_laplace0_apply: y = L_level x (Sec. 3.1.1, Eq. hodge0-laplacian, as
  * -Delta_0), i.e. y_v = (1 / star0_v) sum_{e=(v,w)} *1_e (x_v - x_w); rows of
  * Dirichlet vertices are 0.  prec = DEC_F64 (double x, y) or DEC_F32 (float
- * x, y, weights rounded to float).  k: right-hand sides, interleaved.
- * x and y must not overlap. */
+ * x, y, weights rounded to float).  k >= 1: right-hand sides, interleaved
+ * ([v * k + j]).  x and y must not overlap. */
 int dec_laplace0_apply(const dec_mg *mg, int level, const void *x, void *y, int k,
                        int prec, dec_stream_t stream);
-/* dec_residual: r = b - L_level x on free vertices, 0 on Dirichlet vertices. */
+/* dec_residual: r = b - L_level x on free vertices, 0 on Dirichlet vertices;
+ * k >= 1 interleaved right-hand sides as for dec_laplace0_apply. */
 int dec_residual(const dec_mg *mg, int level, const void *b, const void *x, void *r, int k,
                  int prec, dec_stream_t stream);
 
@@ -301,7 +302,11 @@ int dec_residual(const dec_mg *mg, int level, const void *b, const void *x, void
  * restriction by the row-normalized transpose of the subdivision matrix,
  * recursion (gamma times), interpolation by the subdivision matrix,
  * post-smoothing (Sec. 2.2.1; Sec. 3.1.1 last paragraph), and a dense
- * direct solve on the coarsest level.  prec as for dec_laplace0_apply. */
+ * direct solve on the coarsest level.  prec as for dec_laplace0_apply.  With
+ * k > 1 interleaved right-hand sides every column gets its own cycle, one
+ * after the other through contiguous copies (three finest-level vectors
+ * allocated on the first such call); the batch (dec_batch_*) advances many
+ * right-hand sides together. */
 int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_stream_t stream);
 
 /* dec_mg_vcycle_noalloc: the same FP32 cycle as dec_mg_vcycle(prec =
@@ -339,14 +344,17 @@ int dec_mg_vcycle_noalloc(dec_mg *mg, const float *b, float *x, dec_stream_t str
  * plain CG.  DEC_MODE_MIXED runs the cycles in FP32 inside the FP64 outer
  * iteration (residuals and updates in FP64); DEC_MODE_MIXED_FF inside a
  * float-float one (see the DEC_MODE_* enum).  b and x are
- * double device vectors of nv(finest) * k entries.  Under DEC_BC_GAUGE, b is
- * projected to *0-weighted mean zero and so is x.  Synchronizes `stream`
- * while iterating.  Returns DEC_ERR_NOT_CONVERGED (x holds the last iterate)
- * or DEC_ERR_NONFINITE; stats may be null. */
+ * double device vectors of nv(finest) * k entries, interleaved for k > 1; each
+ * column is then solved on its own, one after the other (stats: the largest
+ * iteration count and residuals; launches summed); the batch
+ * (dec_batch_*) solves many right-hand sides together.  Under DEC_BC_GAUGE,
+ * b is projected to *0-weighted mean zero and so is x.  Synchronizes
+ * `stream` while iterating.  Returns DEC_ERR_NOT_CONVERGED (x holds the last
+ * iterate) or DEC_ERR_NONFINITE; stats may be null. */
 int dec_solve(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts,
               dec_stats *stats, dec_stream_t stream);
-/* dec_solve_host: dec_solve with b and x in HOST memory (nv(finest) doubles
- * each, pinned or pageable; pinned memory lets the copies run as DMA).  b is
+/* dec_solve_host: dec_solve with b and x in HOST memory (k = 1; nv(finest)
+ * doubles each, pinned or pageable; pinned memory lets the copies run as DMA).  b is
  * copied straight into the solver's own right-hand side and the result out
  * of its own iterate (x is read first when opts->warm_start), so the call
  * makes no device copy of either; it returns once x holds the result.  Same

@@ -165,6 +165,42 @@ __global__ void __launch_bounds__(kThreads, 8) k_residual(int n, int K, const in
     }
 }
 
+// Several right-hand sides interleaved, value j of vertex v at [v k + j]:
+// y = L x (RES = false) or r = b - L x on free rows, 0 on fixed rows (RES).
+template <typename T, bool RES>
+__global__ void __launch_bounds__(kThreads, 8) k_apply_k(int n, int K, int k, const int32_t *__restrict__ col,
+                                                     const T *__restrict__ w, const T *__restrict__ x,
+                                                     const T *__restrict__ b, T *__restrict__ y) {
+    pdl_prologue();
+    const int64_t items = (int64_t)n * k;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < items; it += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(it / k), j = (int)(it % k);
+        const T xi = ldg(x + it);
+        T s = T(0), d = T(0);
+        for (int q = 0; q < K; ++q) {
+            const size_t o = (size_t)q * n + i;
+            const T wq = ldg(w + o);
+            s = fma(wq, xi - ldg(x + (size_t)ldg(col + o) * k + j), s);
+            d += wq;
+        }
+        y[it] = RES ? (d != T(0) ? ldg(b + it) - s : T(0)) : s;
+    }
+}
+
+// Column j of an interleaved [n][k] vector to a contiguous one (gather) and back (scatter).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8) k_col_gather(int n, int k, int j, const T *__restrict__ src,
+                                                        T *__restrict__ dst) {
+    pdl_prologue();
+    GRID_STRIDE(i, n) dst[i] = src[(size_t)i * k + j];
+}
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8) k_col_scatter(int n, int k, int j, const T *__restrict__ src,
+                                                         T *__restrict__ dst) {
+    pdl_prologue();
+    GRID_STRIDE(i, n) dst[(size_t)i * k + j] = src[i];
+}
+
 // One smoothing step from a nonzero iterate:
 //   q = D^-1 (b - L x);  delta = c * d_in + e * q;  x_out = x_in + delta;  d_out = delta.
 // Damped Jacobi: DIN = DOUT = false, e = omega.  Chebyshev: the first step of

@@ -115,6 +115,9 @@ struct dec_mg {
     float *fxh = nullptr, *fxl = nullptr, *frl = nullptr, *fqh = nullptr, *fql = nullptr, *fp = nullptr;
     float *fbh = nullptr, *fbl = nullptr;
     double *tmp = nullptr;
+    // contiguous columns for calls with several interleaved right-hand sides (allocated on first use)
+    double *kx64 = nullptr;
+    float *kb32 = nullptr, *kx32 = nullptr;
     double *partials = nullptr;
     unsigned *counter = nullptr;
     decdev::Scal *scal = nullptr;

@@ -1123,6 +1123,17 @@ int setup_coarse_cycle(dec_mg *mg) {
 
 namespace {
 
+// Contiguous column buffers for calls with k > 1 interleaved right-hand
+// sides, allocated on the first such call.
+int column_buffers(dec_mg *mg) {
+    const int n = mg->lv.back().n;
+    int rc;
+    if (!mg->kx64 && (rc = dalloc(mg, &mg->kx64, n))) return rc;
+    if (!mg->kb32 && (rc = dalloc(mg, &mg->kb32, n))) return rc;
+    if (!mg->kx32 && (rc = dalloc(mg, &mg->kx32, n))) return rc;
+    return DEC_OK;
+}
+
 // Options of a build: the defaults when opts is null, validated.
 int build_opts(const dec_mg_opts *opts, dec_mg_opts &o) {
     if (opts)
@@ -1442,10 +1453,21 @@ int dec_mg_set_star1(dec_mg *mg, const double *star1, dec_stream_t stream) {
 int dec_laplace0_apply(const dec_mg *mgc, int level, const void *x, void *y, int k, int prec, dec_stream_t stream) {
     if (int rc = check_dev(mgc)) return rc;
     dec_mg *mg = const_cast<dec_mg *>(mgc);
-    if (!x || !y || level < 0 || level >= (int)mg->lv.size() || k != 1 || (prec != DEC_F64 && prec != DEC_F32))
+    if (!x || !y || level < 0 || level >= (int)mg->lv.size() || k < 1 || (prec != DEC_F64 && prec != DEC_F32))
         return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
     cudaStream_t s = (cudaStream_t)stream;
     DevLevel &L = mg->lv[level];
+    if (k > 1) {
+        const int g = grid_for(mg, (int64_t)L.n * k);
+        if (prec == DEC_F64)
+            launch(mg, k_apply_k<double, false>, g, s, L.n, L.K, k, (const int32_t *)L.col, (const double *)L.w64,
+                   (const double *)x, (const double *)nullptr, (double *)y);
+        else
+            launch(mg, k_apply_k<float, false>, g, s, L.n, L.K, k, (const int32_t *)L.col, (const float *)L.w32,
+                   (const float *)x, (const float *)nullptr, (float *)y);
+        CK(cudaGetLastError());
+        return DEC_OK;
+    }
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64)
@@ -1463,10 +1485,21 @@ int dec_residual(const dec_mg *mgc, int level, const void *b, const void *x, voi
                  dec_stream_t stream) {
     if (int rc = check_dev(mgc)) return rc;
     dec_mg *mg = const_cast<dec_mg *>(mgc);
-    if (!b || !x || !r || level < 0 || level >= (int)mg->lv.size() || k != 1 || (prec != DEC_F64 && prec != DEC_F32))
+    if (!b || !x || !r || level < 0 || level >= (int)mg->lv.size() || k < 1 || (prec != DEC_F64 && prec != DEC_F32))
         return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
     cudaStream_t s = (cudaStream_t)stream;
     DevLevel &L = mg->lv[level];
+    if (k > 1) {
+        const int g = grid_for(mg, (int64_t)L.n * k);
+        if (prec == DEC_F64)
+            launch(mg, k_apply_k<double, true>, g, s, L.n, L.K, k, (const int32_t *)L.col, (const double *)L.w64,
+                   (const double *)x, (const double *)b, (double *)r);
+        else
+            launch(mg, k_apply_k<float, true>, g, s, L.n, L.K, k, (const int32_t *)L.col, (const float *)L.w32,
+                   (const float *)x, (const float *)b, (float *)r);
+        CK(cudaGetLastError());
+        return DEC_OK;
+    }
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64)
@@ -1482,11 +1515,33 @@ int dec_residual(const dec_mg *mgc, int level, const void *b, const void *x, voi
 
 int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_stream_t stream) {
     if (int rc = check_dev(mg)) return rc;
-    if (!b || !x || k != 1 || (prec != DEC_F64 && prec != DEC_F32)) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    if (!b || !x || k < 1 || (prec != DEC_F64 && prec != DEC_F32)) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
     cudaStream_t s = (cudaStream_t)stream;
     const int top = (int)mg->lv.size() - 1;
     DevLevel &F = mg->lv[top];
     const int g = grid_for(mg, F.n);
+    if (k > 1) {
+        // one column at a time through contiguous copies
+        if (int rc = column_buffers(mg)) return rc;
+        for (int j = 0; j < k; ++j) {
+            if (prec == DEC_F64) {
+                launch(mg, k_col_gather<double>, g, s, F.n, k, j, (const double *)b, mg->tmp);
+                launch(mg, k_col_gather<double>, g, s, F.n, k, j, (const double *)x, mg->kx64);
+            } else {
+                launch(mg, k_col_gather<float>, g, s, F.n, k, j, (const float *)b, mg->kb32);
+                launch(mg, k_col_gather<float>, g, s, F.n, k, j, (const float *)x, mg->kx32);
+            }
+            const int rc = dec_mg_vcycle(mg, prec == DEC_F64 ? (const void *)mg->tmp : (const void *)mg->kb32,
+                                         prec == DEC_F64 ? (void *)mg->kx64 : (void *)mg->kx32, 1, prec, stream);
+            if (rc) return rc;
+            if (prec == DEC_F64)
+                launch(mg, k_col_scatter<double>, g, s, F.n, k, j, (const double *)mg->kx64, (double *)x);
+            else
+                launch(mg, k_col_scatter<float>, g, s, F.n, k, j, (const float *)mg->kx32, (float *)x);
+        }
+        CK(cudaGetLastError());
+        return DEC_OK;
+    }
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64) {
@@ -1674,14 +1729,40 @@ int dec_mg_time_kernel(dec_mg *mg, int kind, int level, int reps, double *avg_ms
 int dec_solve(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts, dec_stats *stats,
               dec_stream_t stream) {
     if (int rc = check_dev(mg)) return rc;
-    if (!b || !x || k != 1) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
-    return solve_impl(mg, b, x, opts, stats, (cudaStream_t)stream);
+    if (!b || !x || k < 1) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    if (k == 1) return solve_impl(mg, b, x, opts, stats, (cudaStream_t)stream);
+    // several interleaved right-hand sides: one solve per column through contiguous copies
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = column_buffers(mg)) return rc;
+    const DevLevel &F = mg->lv.back();
+    const int g = grid_for(mg, F.n);
+    const bool warm = opts && opts->warm_start;
+    dec_stats tot{}, one{};
+    int worst = DEC_OK;
+    for (int j = 0; j < k; ++j) {
+        launch(mg, k_col_gather<double>, g, s, F.n, k, j, b, mg->tmp);
+        if (warm) launch(mg, k_col_gather<double>, g, s, F.n, k, j, (const double *)x, mg->kx64);
+        const int rc = solve_impl(mg, mg->tmp, mg->kx64, opts, &one, s);
+        if (rc != DEC_OK && rc != DEC_ERR_NOT_CONVERGED) return rc;
+        if (rc != DEC_OK) worst = rc;
+        launch(mg, k_col_scatter<double>, g, s, F.n, k, j, (const double *)mg->kx64, x);
+        tot.iters = std::max(tot.iters, one.iters);
+        tot.rel_res = std::max(tot.rel_res, one.rel_res);
+        tot.rel_res0 = std::max(tot.rel_res0, one.rel_res0);
+        tot.launches += one.launches + (warm ? 3 : 2);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    if (stats) *stats = tot;
+    if (worst != DEC_OK) return fail(Status::fail(worst, "a right-hand side did not reach tol within maxit"));
+    return DEC_OK;
 }
 
 int dec_solve_host(dec_mg *mg, const double *b, double *x, int k, const dec_solve_opts *opts, dec_stats *stats,
                    dec_stream_t stream) {
     if (int rc = check_dev(mg)) return rc;
-    if (!b || !x || k != 1) return fail(Status::fail(DEC_ERR_ARG, "bad argument"));
+    if (!b || !x || k != 1)
+        return fail(Status::fail(DEC_ERR_ARG, "host-buffer solves take one right-hand side (k = 1)"));
     return solve_impl(mg, b, x, opts, stats, (cudaStream_t)stream, true, true);
 }
 

@@ -395,3 +395,48 @@ def test_cubic_square_closed_form():
     s0 = h.table(-1, "star0")
     d = x.cpu().numpy() - u_h
     assert np.sqrt(np.sum(s0 * d * d) / np.sum(s0 * u_h * u_h)) < 1e-10
+
+
+def test_interleaved_right_hand_sides_match_single_calls():
+    # k = 3 interleaved columns ([v * k + j]): the operator and residual per column equal the single-column
+    # calls bitwise (same per-row arithmetic); cycles and solves per column equal single-column ones
+    import ctypes as C
+    from paper_2508_12501_gb300 import _lib as L
+    h, oh = _pair("ico5")
+    lev = oh.finest
+    n, k = lev.mesh.nv, 3
+    X = np.stack([W.uniform_field(n, 300 + j) for j in range(k)], axis=1)
+    Bm = np.stack([omg.prepare_rhs(oh, W.uniform_field(n, 310 + j)) for j in range(k)], axis=1)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for dt, prec in ((torch.float64, L.DEC_F64), (torch.float32, L.DEC_F32)):
+        x = torch.as_tensor(X, dtype=dt, device="cuda").contiguous()
+        b = torch.as_tensor(Bm, dtype=dt, device="cuda").contiguous()
+        y = torch.empty_like(x)
+        r = torch.empty_like(x)
+        assert L.lib.dec_laplace0_apply(h._h, h.nlevels - 1, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), k,
+                                        prec, st) == 0
+        assert L.lib.dec_residual(h._h, h.nlevels - 1, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                  C.c_void_p(r.data_ptr()), k, prec, st) == 0
+        xv = x.clone()
+        assert L.lib.dec_mg_vcycle(h._h, C.c_void_p(b.data_ptr()), C.c_void_p(xv.data_ptr()), k, prec, st) == 0
+        for j in range(k):
+            xj = x[:, j].contiguous()
+            assert torch.equal(y[:, j], h.laplace0_apply(xj))
+            rj = torch.empty_like(xj)
+            assert L.lib.dec_residual(h._h, h.nlevels - 1, C.c_void_p(b[:, j].contiguous().data_ptr()),
+                                      C.c_void_p(xj.data_ptr()), C.c_void_p(rj.data_ptr()), 1, prec, st) == 0
+            assert torch.equal(r[:, j], rj)
+            h.vcycle(b[:, j].contiguous(), xj)
+            assert torch.equal(xv[:, j], xj)
+    b = torch.as_tensor(np.stack([W.uniform_field(n, 320 + j) for j in range(k)], axis=1), device="cuda")
+    x = torch.empty_like(b)
+    o = L.dec_solve_opts()
+    L.lib.dec_solve_default_opts(C.byref(o))
+    o.tol = 1e-10
+    sts = L.dec_stats()
+    assert L.lib.dec_solve(h._h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), k, C.byref(o), C.byref(sts),
+                           st) == 0
+    assert sts.rel_res <= 1e-10
+    for j in range(k):
+        xs = omg.direct_solve(oh, b[:, j].cpu().numpy())
+        assert _s0_rel(lev, x[:, j].cpu().numpy(), xs) < 1e-7
