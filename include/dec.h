@@ -117,12 +117,18 @@ typedef struct dec_mg_opts {
     int coarse_max_rows; /* DEC_FUSE_COARSE: largest level (rows) run in the shared-memory
                             block; 0 (default): the library's choice */
     int fuse;         /* DEC_FUSE_* mask of fused cycle kernels, each bitwise equal to
-                         the two separate kernels it replaces; default
-                         DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE (those that
+                         the separate kernels it replaces; default DEC_FUSE_RESTRICT0 |
+                         DEC_FUSE_OUTER | DEC_FUSE_COARSE | DEC_FUSE_PATCH (the fusions that
                          gather a second vector measured slower on GB300) */
     int fuse_max_rows; /* the gathering fusions (DEC_FUSE_SMOOTH01, _RESTRICT, _PROLONG) run
                           on levels of at most this many rows, the separate kernels on larger
                           ones; 0 (default): every level */
+    int patch_max_rows; /* DEC_FUSE_PATCH: largest level (rows) run as halo tiles; 0 (default):
+                           every level between the coarsest and the finest */
+    int patch_chunk;    /* DEC_FUSE_PATCH: coarse vertices per tile (consecutive in Z-order);
+                           0 (default): 24 */
+    int patch_threads;  /* DEC_FUSE_PATCH: threads per tile block, a multiple of 32 up to 256;
+                           0 (default): 256 */
 } dec_mg_opts;
 /* Fused cycle kernels.  Gathering a second vector per neighbour:
  *   DEC_FUSE_SMOOTH01  the first two pre-smoothing steps from zero;
@@ -135,10 +141,17 @@ typedef struct dec_mg_opts {
  *                      step with the dot products of the preconditioned vector. */
 /*   DEC_FUSE_COARSE    the coarsest levels whose operators fit in one SM's shared memory
  *                      (FP32 V-cycles) run as one 1024-thread block, __syncthreads between
- *                      phases instead of kernel boundaries. */
+ *                      phases instead of kernel boundaries.
+ *   DEC_FUSE_PATCH     halo tiles: on the levels between the coarsest and the finest (binary
+ *                      subdivision, V-cycles, Jacobi or Chebyshev, 1 to 3 steps per smoothing
+ *                      call) one block per tile runs the pre-smoothing, residual and restriction
+ *                      (one launch) and the interpolation, correction and post-smoothing (one
+ *                      launch) out of shared memory, recomputing the values of the vertices
+ *                      within nu edges of its own.  Takes precedence over the three gathering
+ *                      fusions on those levels. */
 enum {
     DEC_FUSE_SMOOTH01 = 1, DEC_FUSE_RESTRICT = 2, DEC_FUSE_PROLONG = 4, DEC_FUSE_RESTRICT0 = 8,
-    DEC_FUSE_OUTER = 16, DEC_FUSE_COARSE = 32, DEC_FUSE_ALL = 63
+    DEC_FUSE_OUTER = 16, DEC_FUSE_COARSE = 32, DEC_FUSE_PATCH = 64, DEC_FUSE_ALL = 127
 };
 
 /* Solver options.  dec_solve_default_opts(): MG-PCG, mixed precision,
@@ -174,6 +187,7 @@ typedef struct dec_mg_info_t {
     int bc;               /* DEC_BC_*                                             */
     int dim;              /* coordinate dimension of the vertices (2 or 3)        */
     size_t device_bytes;  /* device memory held by the handle                     */
+    int tiles[16];        /* halo tiles per level (DEC_FUSE_PATCH); 0: per-step kernels */
 } dec_mg_info_t;
 
 /* What dec_mg_copy_table copies (host output, element type in brackets). */
@@ -569,6 +583,8 @@ enum {
     DEC_PK_PROLSMOOTH,  /* fused interpolation, correction and first post-smoothing step */
     DEC_PK_SMOOTHDOTS,  /* fused last post-smoothing step and preconditioned-vector dot products */
     DEC_PK_COARSECYCLE, /* the coarsest levels' whole sub-cycle in one block (launched on its top level) */
+    DEC_PK_PATCHDOWN,   /* halo tiles: pre-smoothing, residual and restriction of one level */
+    DEC_PK_PATCHUP,     /* halo tiles: interpolation, correction and post-smoothing of one level */
     DEC_PK_COUNT
 };
 typedef struct dec_prof_entry {

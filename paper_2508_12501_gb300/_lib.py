@@ -30,7 +30,8 @@ DEC_SOLVER_MG, DEC_SOLVER_MGPCG, DEC_SOLVER_CG = 0, 1, 2
 DEC_MODE_F64, DEC_MODE_MIXED, DEC_MODE_MIXED_FF, DEC_MODE_MIXED_F32DOT = 0, 1, 2, 3
 DEC_FUSE_SMOOTH01, DEC_FUSE_RESTRICT, DEC_FUSE_PROLONG, DEC_FUSE_RESTRICT0, DEC_FUSE_OUTER = 1, 2, 4, 8, 16
 DEC_FUSE_COARSE = 32
-DEC_FUSE_ALL = 63
+DEC_FUSE_PATCH = 64
+DEC_FUSE_ALL = 127
 (DEC_TABLE_VERTS, DEC_TABLE_TRIS, DEC_TABLE_EDGES, DEC_TABLE_STAR0, DEC_TABLE_STAR1,
  DEC_TABLE_FREE, DEC_TABLE_PARENTS, DEC_TABLE_COLORS, DEC_TABLE_MAP_IDX, DEC_TABLE_MAP_W) = range(10)
 
@@ -42,7 +43,8 @@ class dec_mg_opts(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("cheby_lo", C.c_double), ("cheby_hi", C.c_double), ("power_iters", C.c_int), ("gamma", C.c_int),
                 ("restriction", C.c_int), ("fcycle", C.c_int), ("coarse_max_rows", C.c_int), ("fuse", C.c_int),
-                ("fuse_max_rows", C.c_int)]
+                ("fuse_max_rows", C.c_int), ("patch_max_rows", C.c_int), ("patch_chunk", C.c_int),
+                ("patch_threads", C.c_int)]
 
 
 class dec_solve_opts(C.Structure):
@@ -61,7 +63,7 @@ class dec_prof_entry(C.Structure):
 
 PROF_KINDS = ["smooth0", "smooth", "residual", "restrict", "prolong", "coarse", "spmv64", "update", "zdots",
               "pupd", "mgres", "add", "aux", "smooth01", "resrestrict", "prolsmooth",
-              "smoothdots", "coarsecycle"]
+              "smoothdots", "coarsecycle", "patchdown", "patchup"]
 
 
 class dec_rk_stats(C.Structure):
@@ -87,7 +89,7 @@ class dec_batch_stats(C.Structure):
 class dec_mg_info_t(C.Structure):
     _fields_ = [("nlevels", C.c_int), ("nv", C.c_int64 * 16), ("ne", C.c_int64 * 16), ("nt", C.c_int64 * 16),
                 ("ell_width", C.c_int * 16), ("lmax", C.c_double * 16), ("ncolors", C.c_int * 16),
-                ("bc", C.c_int), ("dim", C.c_int), ("device_bytes", C.c_size_t)]
+                ("bc", C.c_int), ("dim", C.c_int), ("device_bytes", C.c_size_t), ("tiles", C.c_int * 16)]
 
 
 _p = C.c_void_p

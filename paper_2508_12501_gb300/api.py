@@ -98,11 +98,12 @@ class Hierarchy:
     def __init__(self, mesh, nsub, nlevels, bc="dirichlet", sphere=False, star1_scale=None, smoother="jacobi",
                  nu1=2, nu2=2, omega=2.0 / 3.0, cheby_lo=0.3, cheby_hi=1.1, power_iters=10, gamma=1,
                  restriction="rownorm", host_only=False, fuse=None, order="edge", coarse_max_rows=0,
-                 fcycle=False, scheme="binary", fuse_max_rows=None):
+                 fcycle=False, scheme="binary", fuse_max_rows=None, patch_max_rows=0, patch_chunk=0,
+                 patch_threads=0):
         if not isinstance(mesh, Mesh):
             raise TypeError("mesh must be a Mesh")
         o = self._opts(smoother, nu1, nu2, omega, cheby_lo, cheby_hi, power_iters, gamma, restriction, fuse,
-                       fuse_max_rows, coarse_max_rows, fcycle)
+                       fuse_max_rows, coarse_max_rows, fcycle, patch_max_rows, patch_chunk, patch_threads)
         self.fuse = int(o.fuse)
         flags = ((L.DEC_SPHERE_PROJECT if sphere else 0) | (L.DEC_HOST_ONLY if host_only else 0) | ORDERS[order]
                  | SCHEMES[scheme])
@@ -157,7 +158,7 @@ class Hierarchy:
 
     @staticmethod
     def _opts(smoother, nu1, nu2, omega, cheby_lo, cheby_hi, power_iters, gamma, restriction, fuse, fuse_max_rows,
-              coarse_max_rows, fcycle):
+              coarse_max_rows, fcycle, patch_max_rows=0, patch_chunk=0, patch_threads=0):
         o = L.dec_mg_opts()
         lib.dec_mg_default_opts(C.byref(o))
         o.smoother = SMOOTHERS[smoother]
@@ -171,6 +172,9 @@ class Hierarchy:
             o.fuse_max_rows = int(fuse_max_rows)
         o.coarse_max_rows = int(coarse_max_rows)
         o.fcycle = 1 if fcycle else 0
+        o.patch_max_rows = int(patch_max_rows)
+        o.patch_chunk = int(patch_chunk)
+        o.patch_threads = int(patch_threads)
         return o
 
     def _finish(self, h, bc, host_only):
@@ -188,6 +192,7 @@ class Hierarchy:
         self.ncolors = [info.ncolors[i] for i in range(self.nlevels)]
         self.dim = info.dim
         self.device_bytes = info.device_bytes
+        self.tiles = [info.tiles[i] for i in range(self.nlevels)]  # halo tiles per level (DEC_FUSE_PATCH)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libdec.so")
 
-HOST_SOURCES = ["host_mesh.cpp", "host_hier.cpp", "capi_host.cpp"]
+HOST_SOURCES = ["host_mesh.cpp", "host_hier.cpp", "host_patch.cpp", "capi_host.cpp"]
 CUDA_SOURCES = ["solver.cu", "batch.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -36,9 +36,12 @@ void dec_mg_default_opts(dec_mg_opts *o) {
     o->gamma = 1;
     o->restriction = DEC_RESTRICT_ROWNORM;
     o->fcycle = 0;
-    o->fuse = DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE;
+    o->fuse = DEC_FUSE_RESTRICT0 | DEC_FUSE_OUTER | DEC_FUSE_COARSE | DEC_FUSE_PATCH;
     o->coarse_max_rows = 0;
     o->fuse_max_rows = 0;
+    o->patch_max_rows = 0;
+    o->patch_chunk = 0;
+    o->patch_threads = 0;
 }
 
 void dec_solve_default_opts(dec_solve_opts *o) {

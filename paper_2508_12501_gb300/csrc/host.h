@@ -109,4 +109,38 @@ Status level_weights(HostLevel &L, int bc);
 // lambda_max(D^-1 L) by power iteration on the free vertices.
 double power_lmax(const HostLevel &L, int iters);
 
+// Z-order keys of points [n x dim] on their bounding box (host_mesh.cpp).
+void morton_keys(const double *pts, int64_t n, int dim, std::vector<uint64_t> &keys);
+
+// Halo tiles of one level of binary subdivision for the tiled cycle kernels
+// (DEC_FUSE_PATCH).  Per tile, kPatchHdr ints:
+//   [0] offset of its local vertices in gid, [1] offset of its local ELL in
+//   lcol / lw, [2] owned vertices (locals 0 .. nown-1, written back),
+//   [3] coarse rows (down tiles: locals 0 .. ncoarse-1 are the fine copies of
+//   the tile's coarse vertices), [4 + k] |ring 0 .. ring k| for k = 0..3
+//   (cumulative; entries past the depth repeat the last).
+// Locals are numbered ring by ring.  The local ELL covers the rows of rings
+// 0 .. depth-1 (m = entry [4 + depth - 1]): slot k of local row i at
+// [row offset + k m + i], its column a local index, its weight the level's.
+constexpr int kPatchHdr = 8;
+constexpr int kPatchMaxDepth = 3;
+struct HostPatch {
+    int ntiles = 0, depth = 0;
+    int cap = 0;                 // most locals of one tile
+    std::vector<int32_t> hdr;    // [ntiles * kPatchHdr]
+    std::vector<int32_t> gid;    // local -> level vertex, all tiles
+    std::vector<int32_t> lcol;   // local ELL columns, all tiles
+    std::vector<double> lw;      // local ELL weights (the level's w), all tiles
+};
+
+// Down tiles: chunks of `chunk` coarse vertices in Z-order; ring 0 is the
+// fine closed neighbourhood of those vertices (what the restriction reads),
+// rings 1..depth_down what the pre-smoothing steps and the residual read.
+// Up tiles: ring 0 is the fine vertices the matching down tile owns (its
+// coarse vertices' fine copies and the midpoints whose first parent is one of
+// them: a partition of the fine level), rings 1..depth_up what the
+// post-smoothing steps read.  parents: coarse edge endpoints of each midpoint.
+Status build_patches(const HostLevel &F, const HostMesh &coarse, const std::vector<int32_t> &parents, int chunk,
+                     int depth_down, int depth_up, HostPatch &down, HostPatch &up);
+
 }  // namespace decimpl

@@ -103,8 +103,6 @@ Status build_mesh(std::vector<double> verts, int dim, std::vector<int32_t> tris,
     return Status::ok();
 }
 
-namespace {
-
 // Z-order keys of points [n x dim]: per axis q = floor((x - lo) * ((2^B - 1)/(hi - lo)))
 // on the points' bounding box, clamped to [0, 2^B - 1], bits interleaved (axis 0 lowest).
 void morton_keys(const double *pts, int64_t n, int dim, std::vector<uint64_t> &keys) {
@@ -128,8 +126,6 @@ void morton_keys(const double *pts, int64_t n, int dim, std::vector<uint64_t> &k
         }
     }
 }
-
-}  // namespace
 
 Status subdivide(const HostMesh &c, bool sphere, bool morton, HostMesh &f, std::vector<int32_t> *parents) {
     if (sphere && c.dim != 3) return Status::fail(DEC_ERR_ARG, "sphere projection needs 3-D vertices");

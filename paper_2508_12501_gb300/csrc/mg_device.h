@@ -13,6 +13,7 @@
 #include "coarse_cycle.cuh"
 #include "host.h"
 #include "kernels.cuh"
+#include "patch.cuh"
 
 namespace decimpl {
 
@@ -49,6 +50,14 @@ struct DevLevel {
     double *y64 = nullptr, *c64 = nullptr;
     // Chebyshev coefficients (c_k, e_k) of one smoothing call of nu1 and nu2 steps
     std::vector<double> c_pre, e_pre, c_post, e_post;
+    // halo tiles of this level (DEC_FUSE_PATCH, host_patch.cpp): ntiles == 0 if none
+    struct Tiles {
+        int ntiles = 0, depth = 0, threads = 0, smem32 = 0, smem64 = 0;  // smem: bytes per block, FP32 / FP64
+        int32_t *hdr = nullptr, *gid = nullptr, *lcol = nullptr;
+        float *lw32 = nullptr;
+        double *lw64 = nullptr;
+    };
+    Tiles tdown, tup;
 };
 
 template <typename T> struct P;
@@ -64,6 +73,8 @@ template <> struct P<float> {
     static const float *rw(const DevLevel &L) { return L.rw32; }
     static float *y(DevLevel &L) { return L.y32; }
     static float *c(DevLevel &L) { return L.c32; }
+    static const float *lw(const DevLevel::Tiles &t) { return t.lw32; }
+    static int smem(const DevLevel::Tiles &t) { return t.smem32; }
 };
 template <> struct P<double> {
     static double *x(DevLevel &L, int i) { return L.x64[i]; }
@@ -77,6 +88,8 @@ template <> struct P<double> {
     static const double *rw(const DevLevel &L) { return L.rw64; }
     static double *y(DevLevel &L) { return L.y64; }
     static double *c(DevLevel &L) { return L.c64; }
+    static const double *lw(const DevLevel::Tiles &t) { return t.lw64; }
+    static int smem(const DevLevel::Tiles &t) { return t.smem64; }
 };
 
 template <typename F>

@@ -263,6 +263,10 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
 // for gamma = 1, W), a single V, or F (an F-cycle, then a V-cycle); -1 takes
 // the hierarchy's option.
 enum { kCycGamma = 0, kCycV = 1, kCycF = 2 };
+// Level l runs as halo tiles (DEC_FUSE_PATCH; tiles exist only where setup_patches built them).
+inline bool patch_at(const dec_mg *mg, int l) {
+    return (mg->H.opts.fuse & DEC_FUSE_PATCH) && l >= 1 && l < (int)mg->lv.size() && mg->lv[l].tdown.ntiles > 0;
+}
 template <typename T>
 T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pre0_done = false,
          DotsArgs *da = nullptr, int kind = -1) {
@@ -290,6 +294,54 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
             return L.x32[0];
         }
     }
+    if (patch_at(mg, l)) {
+        // halo tiles: pre-smoothing, residual and restriction in one launch; interpolation,
+        // correction and post-smoothing in another (patch.cuh), bitwise the per-step kernels
+        DevLevel &C = mg->lv[l - 1];
+        const bool cheb = o.smoother == DEC_SMOOTH_CHEBYSHEV;
+        decdev::PatchArgs<T> A{};
+        A.K = L.K;
+        A.cheb = cheb ? 1 : 0;
+        A.b = b;
+        auto tiles = [&](const DevLevel::Tiles &t, const std::vector<double> &cc, const std::vector<double> &ee) {
+            A.hdr = t.hdr;
+            A.gid = t.gid;
+            A.lcol = t.lcol;
+            A.lw = P<T>::lw(t);
+            A.depth = t.depth;
+            for (int k = 0; k < t.depth; ++k) {
+                A.c[k] = (T)(cheb ? cc[k] : 0.0);
+                A.e[k] = (T)(cheb ? ee[k] : o.omega);
+            }
+        };
+        tiles(L.tdown, L.c_pre, L.e_pre);
+        A.x_out = P<T>::x(L, 0);
+        A.dg = P<T>::dg(L);
+        A.bc = P<T>::b(C);
+        A.star0 = o.restriction == DEC_RESTRICT_STAR0 ? 1 : 0;
+        A.s0f = P<T>::s0(L);
+        A.s0c = P<T>::s0(C);
+        dispatch_k(L.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            ProfScope ps(mg, DEC_PK_PATCHDOWN, l, s);
+            launch_block(mg, decdev::k_patch_down<T, KT>, L.tdown.ntiles, L.tdown.threads, P<T>::smem(L.tdown),
+                         s, A, skip);
+        });
+        T *ec = cycle<T>(mg, l - 1, P<T>::b(C), s, skip, false, nullptr, kind);
+        tiles(L.tup, L.c_post, L.e_post);
+        A.x_in = P<T>::x(L, 0);
+        A.ec = ec;
+        A.par = L.par;
+        A.nc = C.n;
+        A.x_out = P<T>::x(L, 1);
+        dispatch_k(L.K, [&](auto kt) {
+            constexpr int KT = decltype(kt)::value;
+            ProfScope ps(mg, DEC_PK_PATCHUP, l, s);
+            launch_block(mg, decdev::k_patch_up<T, KT>, L.tup.ntiles, L.tup.threads, P<T>::smem(L.tup), s, A,
+                         skip);
+        });
+        return P<T>::x(L, 1);
+    }
     DevLevel &C = mg->lv[l - 1];
     int cur = 0;
     if (o.nu1 > 0)
@@ -300,8 +352,9 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
     // (not into the shared-memory coarse cycle, which starts from b itself)
     const bool coarse_next = std::is_same<T, float>::value && (o.fuse & DEC_FUSE_COARSE) && l - 1 == mg->coarse_top;
     const bool mapped = mg->H.mapped;  // general map transfers (k_restrict_map, k_prolong_map), unfused
+    // (nor into halo tiles, which recompute it on their rings)
     const bool restrict0 = (o.fuse & DEC_FUSE_RESTRICT0) && l - 1 > 0 && o.nu1 > 0 && !coarse_next &&
-                           o.smoother != DEC_SMOOTH_MCGS && !mapped;
+                           o.smoother != DEC_SMOOTH_MCGS && !mapped && !patch_at(mg, l - 1);
     bool coarse_pre0 = false;
     const int g = grid_for(mg, L.n);
     const T *w = P<T>::w(L);
@@ -1125,6 +1178,78 @@ namespace {
 
 // Contiguous column buffers for calls with k > 1 interleaved right-hand
 // sides, allocated on the first such call.
+static_assert(decdev::kPatchDepth == decimpl::kPatchMaxDepth && decdev::kPatchHdrInts == decimpl::kPatchHdr,
+              "tile header layout");
+
+constexpr int kPatchChunk = 24;
+
+int upload_tiles(dec_mg *mg, const decimpl::HostPatch &H, int threads, DevLevel::Tiles &T) {
+    int rc;
+    std::vector<float> w32(H.lw.size());
+    for (size_t i = 0; i < w32.size(); ++i) w32[i] = (float)H.lw[i];
+    if ((rc = upload(mg, &T.hdr, H.hdr.data(), H.hdr.size())) || (rc = upload(mg, &T.gid, H.gid.data(), H.gid.size())) ||
+        (rc = upload(mg, &T.lcol, H.lcol.data(), H.lcol.size())) ||
+        (rc = upload(mg, &T.lw64, H.lw.data(), H.lw.size())) || (rc = upload(mg, &T.lw32, w32.data(), w32.size())))
+        return rc;
+    T.ntiles = H.ntiles;
+    T.depth = H.depth;
+    T.threads = threads;
+    T.smem32 = decdev::patch_smem_bytes<float>(H.cap);
+    T.smem64 = decdev::patch_smem_bytes<double>(H.cap);
+    return DEC_OK;
+}
+
+// Halo tiles (DEC_FUSE_PATCH) for the levels strictly between the coarsest and
+// the finest, up to patch_max_rows rows: binary subdivision, V-cycles, Jacobi
+// or Chebyshev with 1 to 3 steps per smoothing call.  A level whose largest
+// FP64 tile would not fit in a block's shared memory keeps the per-step kernels.
+int setup_patches(dec_mg *mg) {
+    const dec_mg_opts &o = mg->H.opts;
+    const int nl = (int)mg->lv.size();
+    if (!(o.fuse & DEC_FUSE_PATCH) || mg->H.mapped || o.gamma != 1 || o.fcycle ||
+        (o.smoother != DEC_SMOOTH_JACOBI && o.smoother != DEC_SMOOTH_CHEBYSHEV) || o.nu1 < 1 || o.nu2 < 1 ||
+        o.nu1 > decimpl::kPatchMaxDepth || o.nu2 > decimpl::kPatchMaxDepth)
+        return DEC_OK;
+    int smem_optin = 0;
+    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, mg->device));
+    int need32 = 0, need64 = 0;
+    for (int l = 1; l + 1 < nl; ++l) {
+        DevLevel &D = mg->lv[l];
+        if (o.patch_max_rows > 0 && D.n > o.patch_max_rows) continue;
+        const decimpl::HostMesh &HC = mg->H.levels[l - 1].mesh;
+        const int64_t nc = HC.nv;
+        // 24 coarse vertices per tile (about 180 locals with two rings): the fastest of 12 to 48
+        // in whole solves on the icosphere benchmark (FP32 and FP64 cycles)
+        const int chunk = o.patch_chunk > 0 ? o.patch_chunk : kPatchChunk;
+        decimpl::HostPatch pd, pu;
+        Status st = decimpl::build_patches(mg->H.levels[l], HC, mg->H.parents[l - 1], chunk, o.nu1, o.nu2, pd, pu);
+        if (!st.good()) return fail(st);
+        if ((int64_t)decdev::patch_smem_bytes<double>(1) * std::max(pd.cap, pu.cap) > smem_optin) continue;
+        int rc;
+        const int threads = o.patch_threads > 0 ? o.patch_threads : decdev::kPatchThreads;
+        if ((rc = upload_tiles(mg, pd, threads, D.tdown)) || (rc = upload_tiles(mg, pu, threads, D.tup))) return rc;
+        need32 = std::max({need32, D.tdown.smem32, D.tup.smem32});
+        need64 = std::max({need64, D.tdown.smem64, D.tup.smem64});
+    }
+    // blocks above the default 48 KB of dynamic shared memory need the opt-in
+    bool ok = true;
+    if (need32 > 48 * 1024)
+        ok = ok && cudaFuncSetAttribute(decdev::k_patch_down<float, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, need32) == cudaSuccess &&
+             cudaFuncSetAttribute(decdev::k_patch_down<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, need32) == cudaSuccess &&
+             cudaFuncSetAttribute(decdev::k_patch_up<float, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, need32) == cudaSuccess &&
+             cudaFuncSetAttribute(decdev::k_patch_up<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, need32) == cudaSuccess;
+    if (need64 > 48 * 1024)
+        ok = ok && cudaFuncSetAttribute(decdev::k_patch_down<double, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, need64) == cudaSuccess &&
+             cudaFuncSetAttribute(decdev::k_patch_down<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, need64) == cudaSuccess &&
+             cudaFuncSetAttribute(decdev::k_patch_up<double, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, need64) == cudaSuccess &&
+             cudaFuncSetAttribute(decdev::k_patch_up<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, need64) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        for (DevLevel &D : mg->lv) D.tdown.ntiles = D.tup.ntiles = 0;  // keep the per-step kernels
+    }
+    return DEC_OK;
+}
+
 int column_buffers(dec_mg *mg) {
     const int n = mg->lv.back().n;
     int rc;
@@ -1147,6 +1272,10 @@ int build_opts(const dec_mg_opts *opts, dec_mg_opts &o) {
     if (o.fuse < 0 || o.fuse > DEC_FUSE_ALL) return fail(Status::fail(DEC_ERR_ARG, "fuse must be a DEC_FUSE_* mask"));
     if (o.fuse_max_rows < 0) return fail(Status::fail(DEC_ERR_ARG, "fuse_max_rows must be >= 0"));
     if (o.coarse_max_rows < 0) return fail(Status::fail(DEC_ERR_ARG, "coarse_max_rows must be >= 0"));
+    if (o.patch_max_rows < 0 || o.patch_chunk < 0)
+        return fail(Status::fail(DEC_ERR_ARG, "patch_max_rows and patch_chunk must be >= 0"));
+    if (o.patch_threads < 0 || o.patch_threads % 32 != 0 || o.patch_threads > decdev::kPatchThreads)
+        return fail(Status::fail(DEC_ERR_ARG, "patch_threads must be a multiple of 32 up to 256"));
     if (o.fcycle != 0 && o.fcycle != 1) return fail(Status::fail(DEC_ERR_ARG, "fcycle must be 0 or 1"));
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.gamma < 1 || o.gamma > 4 || o.power_iters < 1 ||
         !(o.cheby_hi > o.cheby_lo) || !(o.cheby_lo > 0.0))
@@ -1269,6 +1398,7 @@ int device_build(dec_mg *mg) {
         mg->star0_sum = s;
     }
     if ((rc = setup_coarse_cycle(mg))) return rc;
+    if ((rc = setup_patches(mg))) return rc;
     ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaDeviceSynchronize");
     return DEC_OK;
@@ -1375,6 +1505,7 @@ int dec_mg_info(const dec_mg *mg, dec_mg_info_t *info) {
     info->bc = mg->H.bc;
     info->dim = mg->H.levels.back().mesh.dim;
     info->device_bytes = mg->bytes;
+    for (int l = 0; l < (int)mg->lv.size() && l < 16; ++l) info->tiles[l] = mg->lv[l].tdown.ntiles;
     return DEC_OK;
 }
 

@@ -195,13 +195,23 @@ def test_binary_map_tables_are_the_parents():
 def test_option_defaults_and_fuse_max_rows_validation():
     o = lib_mod.dec_mg_opts()
     lib_mod.lib.dec_mg_default_opts(C.byref(o))
-    assert o.fuse == lib_mod.DEC_FUSE_RESTRICT0 | lib_mod.DEC_FUSE_OUTER | lib_mod.DEC_FUSE_COARSE
+    assert o.fuse == (lib_mod.DEC_FUSE_RESTRICT0 | lib_mod.DEC_FUSE_OUTER | lib_mod.DEC_FUSE_COARSE
+                      | lib_mod.DEC_FUSE_PATCH)
+    assert (o.patch_max_rows, o.patch_chunk, o.patch_threads) == (0, 0, 0)
     assert o.fuse_max_rows == 0 and o.coarse_max_rows == 0 and o.fcycle == 0
     v, t = W.unit_square()
     Hierarchy(Mesh(v, t), 3, 2, bc="dirichlet", host_only=True, fuse=63, fuse_max_rows=100)
     with pytest.raises(DecError) as ei:
         Hierarchy(Mesh(v, t), 3, 2, bc="dirichlet", host_only=True, fuse_max_rows=-1)
     assert ei.value.code == lib_mod.DEC_ERR_ARG
+    # halo tiles: every fusion bit, block sizes in warps up to 256 threads, non-negative sizes
+    Hierarchy(Mesh(v, t), 3, 2, bc="dirichlet", host_only=True, fuse=lib_mod.DEC_FUSE_ALL, patch_chunk=7,
+              patch_threads=64, patch_max_rows=10)
+    for kw in (dict(patch_threads=48), dict(patch_threads=288), dict(patch_chunk=-1), dict(patch_max_rows=-5),
+               dict(fuse=lib_mod.DEC_FUSE_ALL + 1)):
+        with pytest.raises(DecError) as ei:
+            Hierarchy(Mesh(v, t), 3, 2, bc="dirichlet", host_only=True, **kw)
+        assert ei.value.code == lib_mod.DEC_ERR_ARG
 
 
 def test_host_only_handles_refuse_device_entry_points():
