@@ -142,6 +142,11 @@ def kernel_bytes(entry, hier, mode, cheb):
     if kind == "prolsmooth":
         # operator, diagonal, b, x in and out, the direction (Chebyshev), the coarse correction and parents
         return n * (K * 4 + K * f + 4 * f + (f if cheb else 0)) + nc * f + (n - nc) * 8
+    if kind in ("patchdown", "patchup"):
+        # halo tiles, per row of the level once (the ring rows a tile recomputes are not counted): the
+        # operator, b, the diagonal (down) or the uncorrected iterate (up), the new iterate; the coarse
+        # right-hand side (down) or the coarse correction and the midpoint parents (up)
+        return n * (K * 4 + K * f + 3 * f) + nc * f + ((n - nc) * 8 if kind == "patchup" else 0)
     per = bytes_per_row(kind, K, mode, cheb, outer=bool(getattr(hier, "fuse", 0) & 16))
     return None if per is None else per * n
 
