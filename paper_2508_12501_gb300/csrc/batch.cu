@@ -16,8 +16,10 @@
 // *0 inner product (FP64 residual, dot products, updates and gauge
 // projection), or iterative refinement x += C(b - L x) -- until every
 // right-hand side satisfies ||b - L x||_2 / ||b||_2 <= tol.  The loop runs on
-// the device as a CUDA graph with a while node.  The adjoint solve
-// L mu = *0^-1 dJ/du shares the batch.
+// the device as a CUDA graph with a while node; a group whose right-hand sides
+// have all converged drops out of the loop's kernels (its blocks return at
+// once) while the others go on.  The adjoint solve L mu = *0^-1 dJ/du shares
+// the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,7 +61,14 @@ struct BLevel {
     int rhs_base;     // index of this group's first right-hand side in the batch
     int gauge;
     double s0sum;     // sum of *0 over free vertices
+    int group;        // index of the group
+    const int *live;  // the group's flag: 0 once every right-hand side of the group has converged
+    int *gpend;       // the group's count of right-hand sides still iterating (k_b_finalize)
 };
+
+// A group that has converged skips the loop's kernels: its blocks return at
+// once.  (The flag changes only in k_b_finalize's last block, between passes.)
+__device__ __forceinline__ bool group_done(const BLevel &L) { return *L.live == 0; }
 
 struct BTile {
     int lev;          // index into the level descriptor array
@@ -168,6 +177,7 @@ __global__ void k_b_smooth0(const BLevel *__restrict__ lv, const BTile *__restri
     for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
         const BTile t = tiles[tb];
         const BLevel &L = lv[t.lev];
+        if (group_done(L)) continue;
         const float e = cheb ? L.epre[0] : omega;
         if ((L.k & 3) == 0)
             smooth0_body<4>(L, t, e, dout);
@@ -208,6 +218,7 @@ __global__ void k_b_smooth(const BLevel *__restrict__ lv, const BTile *__restric
     for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
         const BTile t = tiles[tb];
         const BLevel &L = lv[t.lev];
+        if (group_done(L)) continue;
         const float e = cheb ? (post ? L.epost[sweep] : L.epre[sweep]) : omega;
         const float c = cheb ? (post ? L.cpost[sweep] : L.cpre[sweep]) : 0.f;
         if ((L.k & 3) == 0)
@@ -239,6 +250,7 @@ __global__ void k_b_residual(const BLevel *__restrict__ lv, const BTile *__restr
     for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
         const BTile t = tiles[tb];
         const BLevel &L = lv[t.lev];
+        if (group_done(L)) continue;
         if ((L.k & 3) == 0)
             residual_body<4>(L, t, src);
         else
@@ -288,6 +300,7 @@ __global__ void k_b_restrict(const BLevel *__restrict__ lv, const BTile *__restr
         const BTile t = tiles[tb];
         const BLevel &L = lv[t.lev];
         const BLevel &C = lv[t.lev - 1];
+        if (group_done(L)) continue;
         if ((L.k & 3) == 0)
             restrict_body<4>(L, C, t, star0);
         else
@@ -302,6 +315,7 @@ __global__ void k_b_coarse(const BLevel *__restrict__ lv, const BTile *__restric
     for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
         const BTile t = tiles[tb];
         const BLevel &L = lv[t.lev];
+        if (group_done(L)) continue;
         for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
             const int row = i >> L.kshift, j = i & (L.k - 1);
             float acc = 0.f;
@@ -341,6 +355,7 @@ __global__ void k_b_prolong(const BLevel *__restrict__ lv, const BTile *__restri
         const BTile t = tiles[tb];
         const BLevel &L = lv[t.lev];
         const BLevel &C = lv[t.lev - 1];
+        if (group_done(L)) continue;
         if ((L.k & 3) == 0)
             prolong_body<4>(L, C, t, dst);
         else
@@ -402,6 +417,7 @@ __global__ void k_b_res64(const BLevel *__restrict__ lv, const BTile *__restrict
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
+    if (group_done(L)) return;  // block-uniform: the tile is one group's
     double acc[2] = {0.0, 0.0};
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift, j = i & (L.k - 1);
@@ -430,6 +446,7 @@ __global__ void k_b_add64(const BLevel *__restrict__ lv, const BTile *__restrict
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
+    if (group_done(L)) return;  // block-uniform: the tile is one group's
     const float *e = L.x[L.res_idx];
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) L.ox[i] += (double)e[i];
 }
@@ -490,6 +507,7 @@ __global__ void k_bp_zdots(const BLevel *__restrict__ lv, const BTile *__restric
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
+    if (group_done(L)) return;  // block-uniform: the tile is one group's
     const float *z = L.x[L.res_idx];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
@@ -513,6 +531,7 @@ __global__ void k_bp_pupd(const BLevel *__restrict__ lv, const BTile *__restrict
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
+    if (group_done(L)) return;  // block-uniform: the tile is one group's
     const float *z = L.x[L.res_idx];
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift;
@@ -529,6 +548,7 @@ __global__ void k_bp_spmv(const BLevel *__restrict__ lv, const BTile *__restrict
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
+    if (group_done(L)) return;  // block-uniform: the tile is one group's
     double acc[1] = {0.0};
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift, j = i & (L.k - 1);
@@ -551,6 +571,7 @@ __global__ void k_bp_update(const BLevel *__restrict__ lv, const BTile *__restri
     if (skipped(skip)) return;
     const BTile t = tiles[blockIdx.x];
     const BLevel &L = lv[t.lev];
+    if (group_done(L)) return;  // block-uniform: the tile is one group's
     double acc[1] = {0.0};
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const double a = sc[rhs_of(L, i)].alpha;
@@ -570,11 +591,13 @@ enum { kFinMean = 0, kFinInit = 1, kFinZdots = 2, kFinAlpha = 3, kFinConv = 4 };
 // butterfly and a fixed-order sum of the warps), then the scalars of `kind`.
 // kFinInit and kFinConv also decide convergence: the last block to finish
 // sets the batch's done flag once every right-hand side has converged (or
-// maxit is reached), counts the pass (kFinConv) and records the largest
-// relative residual.
+// maxit is reached), counts the pass (kFinConv), records the largest
+// relative residual and sets each group's live flag for the next pass.  The
+// right-hand sides of a group that skipped this pass keep their scalars (the
+// group's partials were not written).
 __global__ void k_b_finalize(int nrhs, const BRhs *__restrict__ rinfo, const BLevel *__restrict__ lv, BSums P,
                              BScal *__restrict__ sc, int kind, int first, Scal *S, int *pending, unsigned *counter,
-                             const int *skip) {
+                             const int *skip, int *glive, int *gpend, int ngroups) {
     pdl_prologue();
     if (skipped(skip)) return;
     __shared__ double wsum[kBMaxSums][16];  // per-warp totals (blockDim <= 512)
@@ -595,7 +618,10 @@ __global__ void k_b_finalize(int nrhs, const BRhs *__restrict__ rinfo, const BLe
             for (int w = 0; w < nw; ++w) tot[s] += wsum[s][w];
         BScal &C = sc[q];
         const BLevel &L = lv[R.lev];
-        if (kind == kFinMean) {
+        const bool dead = (kind == kFinZdots || kind == kFinAlpha || kind == kFinConv) && group_done(L);
+        if (dead) {
+            // this group's kernels skipped the pass: every scalar stays as it was
+        } else if (kind == kFinMean) {
             C.mean = L.gauge ? tot[0] / L.s0sum : 0.0;
         } else if (kind == kFinInit) {
             C.bn2 = tot[1];
@@ -623,14 +649,19 @@ __global__ void k_b_finalize(int nrhs, const BRhs *__restrict__ rinfo, const BLe
             C.rn2 = tot[0];
             if (!C.done && C.rn2 <= C.thr2) C.done = 1;
         }
-        if (kind == kFinInit || kind == kFinConv) {
+        if ((kind == kFinInit || kind == kFinConv) && !dead) {
             const bool bad = !isfinite(C.rn2) || !isfinite(C.bn2);
             C.rel = bad ? (double)NAN : (C.bn2 > 0.0 ? sqrt(C.rn2 / C.bn2) : 0.0);
             if (bad) {
                 C.done = 1;
                 atomicExch(&S->status, 1);
             }
-            if (!C.done) atomicAdd(pending, 1);
+        }
+        if (kind == kFinInit || kind == kFinConv) {
+            if (!C.done) {
+                atomicAdd(pending, 1);
+                atomicAdd(L.gpend, 1);
+            }
             if (R.live && isfinite(C.rel))
                 atomicMax((unsigned long long *)&S->rel, (unsigned long long)__double_as_longlong(C.rel));
         }
@@ -643,6 +674,7 @@ __global__ void k_b_finalize(int nrhs, const BRhs *__restrict__ rinfo, const BLe
         if (kind == kFinConv) S->iter += 1;
         if (left == 0 || S->status != 0 || S->iter >= S->maxit) S->done = 1;
         *pending = 0;
+        for (int g = 0; g < ngroups; ++g) glive[g] = atomicExch(gpend + g, 0) > 0 ? 1 : 0;
         *counter = 0u;
     }
 }
@@ -743,6 +775,7 @@ struct dec_batch {
     BScal *bsc = nullptr;
     int *pending = nullptr;
     unsigned *counter = nullptr;
+    int *glive = nullptr, *gpend = nullptr;  // per group: live flag, right-hand sides still iterating
     Scal *scal = nullptr;
     Scal *scal_h = nullptr;
     cudaStream_t cap = nullptr;
@@ -842,7 +875,13 @@ void enqueue_cycle(dec_batch *B, cudaStream_t s, const int *skip) {
 
 void enqueue_finalize(dec_batch *B, cudaStream_t s, int kind, int first, const int *skip) {
     blaunch(B, k_b_finalize, fin_grid(B), 0, s, B->total_rhs, (const BRhs *)B->rinfo, (const BLevel *)B->dlv, B->sums,
-            B->bsc, kind, first, B->scal, B->pending, B->counter, skip);
+            B->bsc, kind, first, B->scal, B->pending, B->counter, skip, B->glive, B->gpend, (int)B->groups.size());
+}
+
+// Every group live again (between solves: kernels run outside the loop, such as the smoother timer, see all).
+int all_groups_live(dec_batch *B, cudaStream_t s) {
+    CK(cudaMemsetAsync(B->glive, 1, sizeof(int) * B->groups.size(), s));  // int 0x01010101: nonzero
+    return DEC_OK;
 }
 
 // The preconditioned vector's dot products, the new search direction.
@@ -988,6 +1027,7 @@ int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &laun
         }
         CK(cudaGraphLaunch(B->loop, s));
     }
+    if (int rc = all_groups_live(B, s)) return rc;
     if (any_gauge) {
         // the mean of x, subtracted by the scatter into the callers' vectors
         blaunch(B, k_b_meansum, B->res_cnt, sm, s, (const BLevel *)B->dlv, rt, 1, B->sums);
@@ -1156,6 +1196,7 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
                     L.s0sum = mg->star0_sum;
                     B->dof += (int64_t)D.n * G.kk;
                 }
+                L.group = (int)B->groups.size();
                 B->hlv.push_back(L);
             }
             B->groups.push_back(G);
@@ -1223,6 +1264,12 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
     B->res_cnt = (int)tiles.size() - B->res_off;
     B->sums.ntile = B->res_cnt;
     B->sums.kmax = kmax;
+    if ((rc = balloc(B, &B->glive, B->groups.size())) || (rc = balloc(B, &B->gpend, B->groups.size())))
+        return bail(rc);
+    for (BLevel &L : B->hlv) {
+        L.live = B->glive + L.group;
+        L.gpend = B->gpend + L.group;
+    }
     if ((rc = balloc(B, &B->dtiles, tiles.size())) || (rc = balloc(B, &B->dlv, B->hlv.size())) ||
         (rc = balloc(B, &B->sums.part, (size_t)kBMaxSums * B->res_cnt * kmax)) ||
         (rc = balloc(B, &B->rinfo, rinfo.size())) || (rc = balloc(B, &B->bsc, (size_t)B->total_rhs)) ||
@@ -1233,6 +1280,8 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
     if (ce == cudaSuccess) ce = cudaMemcpy(B->rinfo, rinfo.data(), rinfo.size() * sizeof(BRhs), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset(B->bsc, 0, sizeof(BScal) * B->total_rhs);
     if (ce == cudaSuccess) ce = cudaMemset(B->pending, 0, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMemset(B->gpend, 0, sizeof(int) * B->groups.size());
+    if (ce == cudaSuccess) ce = cudaMemset(B->glive, 1, sizeof(int) * B->groups.size());
     if (ce == cudaSuccess) ce = cudaMemset(B->counter, 0, sizeof(unsigned));
     if (ce == cudaSuccess) ce = cudaMemset(B->scal, 0, sizeof(Scal));
     if (ce == cudaSuccess) ce = cudaMallocHost((void **)&B->scal_h, sizeof(Scal));
@@ -1413,6 +1462,7 @@ extern "C" int dec_batch_time_smooth(dec_batch *B, int reps, double *avg_ms, dou
         if (o.kind == 1 && o.post == 1 && o.sweep == 0) op = &o;  // the last such op is depth 0
     if (!op) return fail(Status::fail(DEC_ERR_ARG, "batch has no smoothing sweep"));
     cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = all_groups_live(B, s)) return rc;
     const int cheb = B->opts.smoother == DEC_SMOOTH_CHEBYSHEV;
     // Algorithmic bytes: each group's finest operator once (K columns + K
     // weights per row; a group holds every right-hand side of its hierarchy

@@ -97,6 +97,42 @@ def test_entries_sharing_a_hierarchy_are_one_group_and_match_the_oracle():
 
 
 @pytest.mark.parametrize("solver", ["mgpcg", "mg"])
+def test_converged_groups_drop_out_without_changing_results(solver):
+    # a quickly converging group (icosphere, gauge) beside slower ones (squares, Dirichlet): once a group
+    # has converged its kernels return at once, so the batch gives every group exactly the bits of that
+    # group solved on its own, and takes the slowest group's pass count
+    import paper_2508_12501_gb300 as P
+    h1, o1 = _mesh("ico", 5, 4)
+    h2, o2 = _mesh("square", 7, 6)
+    h3, o3 = _mesh("square", 6, 5)
+    hs, ks = [h1, h2, h3], [8, 1, 2]
+    bs = [torch.as_tensor(_rhs(h.n, k, 70 + 10 * i).reshape(-1), device="cuda")
+          for i, (h, k) in enumerate(zip(hs, ks))]
+    B = P.Batch(hs, ks, solver=solver)
+    xs, st = B.solve(bs, tol=1e-9)
+    iters = []
+    for i, (h, k) in enumerate(zip(hs, ks)):
+        Bi = P.Batch([h], [k], solver=solver)
+        xi, sti = Bi.solve([bs[i]], tol=1e-9)
+        assert torch.equal(xs[i], xi[0]), i
+        iters.append(sti.iters)
+    assert st.iters == max(iters) and min(iters) < max(iters), iters
+    assert st.max_rel_res <= 1e-9
+    for oh, x, b, k in zip((o1, o2, o3), xs, bs, ks):
+        _check(oh, x.reshape(-1, k).cpu().numpy(), b.reshape(-1, k).cpu().numpy(), 1e-9)
+    # the adjoint shares the loop: the same per-group bits
+    us = [x.reshape(h.n, -1) for x, h in zip(xs, hs)]
+    gb, gs, _ = B.solve_backward(us, us, tol=1e-9)
+    for i, (h, k) in enumerate(zip(hs, ks)):
+        Bi = P.Batch([h], [k], solver=solver)
+        gbi, gsi, _ = Bi.solve_backward([us[i]], [us[i]], tol=1e-9)
+        assert torch.equal(gb[i], gbi[0]) and torch.equal(gs[i], gsi[0]), i
+    # the smoother timer after a solve sees every group again
+    ms, by = B.time_smooth(2)
+    assert ms > 0 and by > 0
+
+
+@pytest.mark.parametrize("solver", ["mgpcg", "mg"])
 def test_batched_adjoint_matches_oracle_gradients(solver):
     # dJ/db = *0 mu and dJ/d*1 = -(d0 mu)(d0 u) per right-hand side, mu = L^-1 (*0^-1 dJ/du), against the
     # oracle's adjoint formulas with its direct solves
