@@ -411,6 +411,33 @@ __device__ __forceinline__ void bsum_write(const double (&acc)[NS], int k, const
 
 __device__ __forceinline__ int rhs_of(const BLevel &L, int i) { return L.rhs_base + (i & (L.k - 1)); }
 
+// (L x)_v of right-hand side j in FP64, difference form, slots in order.  Rows
+// of 6 slots issue their table loads and their six gathers before the first
+// FMA (the same sum, in the same order, as the loop).
+__device__ __forceinline__ double brow64(const BLevel &L, int v, int j, const double *x, double xi) {
+    double s = 0.0;
+    if (L.K == 6) {
+        const int n = L.n, ks = L.kshift;
+        int cq[6];
+        double wq[6], xq[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            cq[q] = __ldg(L.col + (size_t)q * n + v);
+            wq[q] = __ldg(L.w64 + (size_t)q * n + v);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) xq[q] = x[(cq[q] << ks) + j];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s = fma(wq[q], xi - xq[q], s);
+        return s;
+    }
+    for (int q = 0; q < L.K; ++q) {
+        const size_t o = (size_t)q * L.n + v;
+        s = fma(__ldg(L.w64 + o), xi - x[(__ldg(L.col + o) << L.kshift) + j], s);
+    }
+    return s;
+}
+
 // Standalone refinement: r = b - L x (FP64, free rows), r32 = cycle input, sums of r^2 and b^2.
 __global__ void k_b_res64(const BLevel *__restrict__ lv, const BTile *__restrict__ tiles, BSums P, const int *skip) {
     pdl_prologue();
@@ -423,12 +450,7 @@ __global__ void k_b_res64(const BLevel *__restrict__ lv, const BTile *__restrict
         const int v = i >> L.kshift, j = i & (L.k - 1);
         double ri = 0.0, bi = 0.0;
         if (L.freev[v]) {
-            const double xi = L.ox[i];
-            double s = 0.0;
-            for (int q = 0; q < L.K; ++q) {
-                const size_t o = (size_t)q * L.n + v;
-                s = fma(__ldg(L.w64 + o), xi - L.ox[(__ldg(L.col + o) << L.kshift) + j], s);
-            }
+            const double s = brow64(L, v, j, L.ox, L.ox[i]);
             bi = L.ob[i];
             ri = bi - s;
         }
@@ -553,11 +575,7 @@ __global__ void k_bp_spmv(const BLevel *__restrict__ lv, const BTile *__restrict
     for (int i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
         const int v = i >> L.kshift, j = i & (L.k - 1);
         const double pi = L.op[i];
-        double s = 0.0;
-        for (int q = 0; q < L.K; ++q) {
-            const size_t o = (size_t)q * L.n + v;
-            s = fma(__ldg(L.w64 + o), pi - L.op[(__ldg(L.col + o) << L.kshift) + j], s);
-        }
+        const double s = brow64(L, v, j, L.op, pi);
         L.oq[i] = s;
         acc[0] = fma(__ldg(L.star0 + v) * pi, s, acc[0]);
     }
