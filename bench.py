@@ -822,7 +822,8 @@ def main():
             return {"bound": "alu", "pipe": "fp64", "kernel": f"{r['kind']} (level {r['level']}, {r['rows']} rows)",
                     "achieved": ach, "peak": pk, "peak_source": "FP64 issue rate (2 lanes/SM/cycle x 152 SMs x "
                     f"{sm_clk:.0f} MHz)", "unit": "G FP64 instructions/s", "frac": ach / pk,
-                    "fp64_instructions_per_row": per, "avg_launch_ms": r["avg_ms"], "traffic": None,
+                    "fp64_instructions_per_row": per, "avg_launch_ms": r["avg_ms"],
+                    "traffic": ncu_traffic(r["kind"]), "algorithmic_bytes": r["bytes"],
                     "timing": "event pair around each launch inside the solve's iteration graph (in-solve)",
                     "share_of_profiled_time": r["total_ms"] / tot_ms}
 
