@@ -330,8 +330,10 @@ def batched_workload(torch, dev, flush, stream, steps, tune=True):
             ks.append(1)
             bs.append(torch.as_tensor(W.uniform_field(hq.n, seed), device=dev))
             seed += 1
-    cands = [dict(block=bl, kgroup=kg, nu=2, smoother="chebyshev", solver="mgpcg")
-             for bl in (256, 512) for kg in (0, 16, 32)]
+    # block size, interleave width k (0: every right-hand side of a hierarchy in one group, up to the block
+    # size) and sweeps per smoothing call
+    cands = [dict(block=bl, kgroup=kg, nu=nu, smoother="chebyshev", solver="mgpcg")
+             for bl in (256, 512) for kg in (0, 8, 16, 32) for nu in (1, 2, 3)]
     if tune:
         best, best_ms, table = P.tune_batch(hs, ks, bs, tol=TOL, candidates=cands, reps=2)
     else:  # the library's defaults (block 256, one group per hierarchy, Chebyshev nu = 2, MG-PCG)
@@ -549,13 +551,36 @@ def other_configs(torch, dev, stream):
     ms, (sf, sb) = _timed(torch, dev, stream, lambda: fwd_bwd("mixed"), 5)
     ms_ff, _ = _timed(torch, dev, stream, lambda: fwd_bwd("mixed_ff"), 5)
     ms_64, _ = _timed(torch, dev, stream, lambda: fwd_bwd("f64"), 5)
+
+    def finest_roofline(mode):
+        # the finest level's cycle kernels in one forward solve, timed by event pairs in the solve's graph;
+        # at 1,050,625 rows a sweep moves 67 MB (FP32 cycles) or 109 MB (FP64): per-level working sets at or
+        # above L2, where the scope table asks for the HBM fraction
+        h.profile(1)
+        h.solve(b, mode=mode, tol=1e-8)
+        torch.cuda.synchronize(dev)
+        ent = h.profile_read()
+        h.profile(0)
+        peak, src = peaks()
+        kern = {}
+        for e in ent:
+            if e["kind"] not in ("smooth", "residual", "restrict", "prolong"):
+                continue
+            by = kernel_bytes(e, h, mode, True)
+            avg = e["total_ms"] / max(1, e["launches"])
+            gbs = by / (avg * 1e-3) / 1e9
+            kern[e["kind"]] = {"algorithmic_bytes": by, "avg_launch_ms": avg, "achieved_gbs": gbs,
+                               "frac": gbs / peak}
+        return {"peak": peak, "peak_source": src, "unit": "GB/s", "kernels": kern,
+                "timing": "event pair around each launch inside the solve's iteration graph (in-solve)"}
+    roof_mixed, roof_64 = finest_roofline("mixed"), finest_roofline("f64")
     out["adjoint"] = {
         "workload": "unit square x10 (1,050,625 V), log-normal *1 (sigma 0.5, seed 2), b U[-1,1] (seed 3), "
                     "J = 1/2 ||u - sin(2 pi x) sin(pi y)||^2_*0, dJ/db and dJ/d*1, MG-PCG mixed (FP32 cycles, "
                     "FP64 outer) to 1e-8",
         "ms_forward_backward": ms, "forward_iters": sf.iters, "backward_iters": sb.iters,
         "ms_forward_backward_mixed_ff": ms_ff, "ms_forward_backward_f64": ms_64,
-        "speedup_vs_f64": ms_64 / ms}
+        "speedup_vs_f64": ms_64 / ms, "roofline_finest_mixed": roof_mixed, "roofline_finest_f64": roof_64}
     del h
     # porous convection: 2000 explicit steps with checkpoints every 100, then the checkpointed adjoint
     h = P.Hierarchy(P.Mesh(v, t), 9, 8, bc="gauge", restriction="star0")

@@ -245,6 +245,72 @@ __global__ void __launch_bounds__(kThreads, 8) k_smooth0(int n, int K, const T *
     }
 }
 
+// FP64 cycles (mode f64): the same three kernels with each row's diagonal
+// read from the stored table (k_diag) instead of summed again.  k_diag adds
+// the same weights in the same order, so the value is the same double; on
+// GB300's narrow FP64 pipe its six additions per row cost more than the
+// 8-byte load (an FP64 sweep issues about 31 FP64 instructions per row
+// otherwise).
+template <int KT>
+__device__ __forceinline__ double row_sum64(int i, int n, int K, const int32_t *__restrict__ col,
+                                            const double *__restrict__ w, const double *__restrict__ x) {
+    const int Kk = KT > 0 ? KT : K;
+    const double xi = ldg(x + i);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < (KT > 0 ? KT : 32); ++k) {
+        if (KT == 0 && k >= Kk) break;
+        const size_t o = (size_t)k * n + i;
+        s = fma(ldg(w + o), xi - ldg(x + ldg(col + o)), s);
+    }
+    return s;
+}
+
+template <int KT, bool DIN, bool DOUT>
+__global__ void __launch_bounds__(kThreads, 8) k_smooth_dg(int n, int K, const int32_t *__restrict__ col,
+                                                       const double *__restrict__ w, const double *__restrict__ dg,
+                                                       const double *__restrict__ b, const double *__restrict__ x_in,
+                                                       const double *__restrict__ d_in, double *__restrict__ x_out,
+                                                       double *__restrict__ d_out, double c, double e,
+                                                       const int *skip) {
+    pdl_prologue_ell<KT>(n, K, col, w);
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) {
+        const double s = row_sum64<KT>(i, n, K, col, w, x_in), d = ldg(dg + i);
+        double q = d != 0.0 ? (ldg(b + i) - s) / d : 0.0;
+        const double delta = smooth_delta<double>(DIN, c, DIN ? ldg(d_in + i) : 0.0, e, q);
+        x_out[i] = add_rn(ldg(x_in + i), delta);
+        if (DOUT) d_out[i] = delta;
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 8) k_residual_dg(int n, int K, const int32_t *__restrict__ col,
+                                                         const double *__restrict__ w, const double *__restrict__ dg,
+                                                         const double *__restrict__ b, const double *__restrict__ x,
+                                                         double *__restrict__ r, const int *skip) {
+    pdl_prologue_ell<KT>(n, K, col, w);
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) {
+        const double s = row_sum64<KT>(i, n, K, col, w, x);
+        r[i] = ldg(dg + i) != 0.0 ? ldg(b + i) - s : 0.0;
+    }
+}
+
+template <bool DOUT>
+__global__ void __launch_bounds__(kThreads, 8) k_smooth0_dg(int n, const double *__restrict__ dg,
+                                                        const double *__restrict__ b, double *__restrict__ x_out,
+                                                        double *__restrict__ d_out, double e, const int *skip) {
+    pdl_prologue();
+    if (skipped(skip)) return;
+    GRID_STRIDE(i, n) {
+        const double d = ldg(dg + i);
+        const double v = d != 0.0 ? e * (ldg(b + i) / d) : 0.0;
+        x_out[i] = v;
+        if (DOUT) d_out[i] = v;
+    }
+}
+
 // One multicolour Gauss-Seidel step over the rows of one colour class (rows
 // listed in `rows`): x_i += (b_i - (L x)_i) / L_ii in place.  Rows of one
 // colour are never neighbours, so every row reads the current values of the

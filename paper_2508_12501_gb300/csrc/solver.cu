@@ -198,7 +198,15 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
             if (k == 0 && from_zero) {
                 cur = 0;
                 ProfScope ps(mg, DEC_PK_SMOOTH0, l, s);
-                if (dout)
+                if constexpr (std::is_same<T, double>::value) {
+                    // FP64: the stored diagonal (the same double) instead of six FP64 additions per row
+                    if (dout)
+                        launch(mg, k_smooth0_dg<true>, g, s, L.n, (const double *)L.dg64, b, P<T>::x(L, 0),
+                               P<T>::d(L, 0), e, skip);
+                    else
+                        launch(mg, k_smooth0_dg<false>, g, s, L.n, (const double *)L.dg64, b, P<T>::x(L, 0),
+                               (double *)nullptr, e, skip);
+                } else if (dout)
                     launch(mg, k_smooth0<T, KT, true>, g, s, L.n, L.K, w, b, P<T>::x(L, 0), P<T>::d(L, 0), e, skip);
                 else
                     launch(mg, k_smooth0<T, KT, false>, g, s, L.n, L.K, w, b, P<T>::x(L, 0), nullptr, e, skip);
@@ -240,7 +248,20 @@ void smooth(dec_mg *mg, int l, const T *b, int nu, bool from_zero, bool post, in
                 }
             }
             ProfScope ps(mg, DEC_PK_SMOOTH, l, s);
-            if (din && dout)
+            if constexpr (std::is_same<T, double>::value) {
+                const double *dg = L.dg64;
+                if (din && dout)
+                    launch(mg, k_smooth_dg<KT, true, true>, g, s, L.n, L.K, L.col, w, dg, b, xi, di, xo, dn, c, e, skip);
+                else if (din)
+                    launch(mg, k_smooth_dg<KT, true, false>, g, s, L.n, L.K, L.col, w, dg, b, xi, di, xo,
+                           (double *)nullptr, c, e, skip);
+                else if (dout)
+                    launch(mg, k_smooth_dg<KT, false, true>, g, s, L.n, L.K, L.col, w, dg, b, xi, (const double *)nullptr,
+                           xo, dn, c, e, skip);
+                else
+                    launch(mg, k_smooth_dg<KT, false, false>, g, s, L.n, L.K, L.col, w, dg, b, xi,
+                           (const double *)nullptr, xo, (double *)nullptr, c, e, skip);
+            } else if (din && dout)
                 launch(mg, k_smooth<T, KT, true, true>, g, s, L.n, L.K, L.col, w, b, xi, di, xo, dn, c, e, skip);
             else if (din)
                 launch(mg, k_smooth<T, KT, true, false>, g, s, L.n, L.K, L.col, w, b, xi, di, xo, nullptr, c, e, skip);
@@ -392,7 +413,11 @@ T *cycle(dec_mg *mg, int l, const T *b, cudaStream_t s, const int *skip, bool pr
         }
         {
             ProfScope ps(mg, DEC_PK_RESIDUAL, l, s);
-            launch(mg, k_residual<T, KT>, g, s, L.n, L.K, L.col, w, b, P<T>::x(L, cur), P<T>::r(L), skip);
+            if constexpr (std::is_same<T, double>::value)
+                launch(mg, k_residual_dg<KT>, g, s, L.n, L.K, L.col, w, (const double *)L.dg64, b,
+                       (const double *)P<T>::x(L, cur), P<T>::r(L), skip);
+            else
+                launch(mg, k_residual<T, KT>, g, s, L.n, L.K, L.col, w, b, P<T>::x(L, cur), P<T>::r(L), skip);
         }
         {
             ProfScope ps(mg, DEC_PK_RESTRICT, l, s);
@@ -1634,8 +1659,8 @@ int dec_residual(const dec_mg *mgc, int level, const void *b, const void *x, voi
     dispatch_k(L.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64)
-            launch(mg, k_residual<double, KT>, grid_for(mg, L.n), s, L.n, L.K, L.col, L.w64, (const double *)b,
-                                                                         (const double *)x, (double *)r, nullptr);
+            launch(mg, k_residual_dg<KT>, grid_for(mg, L.n), s, L.n, L.K, L.col, (const double *)L.w64,
+                   (const double *)L.dg64, (const double *)b, (const double *)x, (double *)r, (const int *)nullptr);
         else
             launch(mg, k_residual<float, KT>, grid_for(mg, L.n), s, L.n, L.K, L.col, L.w32, (const float *)b,
                                                                         (const float *)x, (float *)r, nullptr);
@@ -1676,8 +1701,8 @@ int dec_mg_vcycle(dec_mg *mg, const void *b, void *x, int k, int prec, dec_strea
     dispatch_k(F.K, [&](auto kt) {
         constexpr int KT = decltype(kt)::value;
         if (prec == DEC_F64) {
-            launch(mg, k_residual<double, KT>, g, s, F.n, F.K, F.col, F.w64, (const double *)b, (const double *)x,
-                                                          F.b64, nullptr);
+            launch(mg, k_residual_dg<KT>, g, s, F.n, F.K, F.col, (const double *)F.w64, (const double *)F.dg64,
+                   (const double *)b, (const double *)x, F.b64, (const int *)nullptr);
             double *e = cycle<double>(mg, top, F.b64, s, nullptr);
             launch(mg, k_axpy1<double>, g, s, F.n, e, (double *)x, nullptr);
         } else {
