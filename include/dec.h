@@ -457,9 +457,10 @@ int dec_batch_tune(dec_mg *const *mgs, const int *nrhs, int nmesh, const double 
 /* dec_batch_time_smooth: mean duration of one launch of the batched
  * finest-level smoothing sweep (every group), over `reps` back-to-back
  * launches timed with CUDA events on `stream`, and its algorithmic bytes
- * (each group's finest operator once -- K column indices and K weights per
- * row -- and per right-hand side x, b, the new x and, for Chebyshev, a
- * direction vector; padding columns not counted). */
+ * (each hierarchy's finest operator once, however many groups share it --
+ * K column indices and K weights per row -- and per right-hand side x, b,
+ * the new x and, for Chebyshev, a direction vector; padding columns not
+ * counted). */
 int dec_batch_time_smooth(dec_batch *batch, int reps, double *avg_ms, double *bytes, dec_stream_t stream);
 
 /* ---- porous convection (Sec. 3.2) -------------------------------------------

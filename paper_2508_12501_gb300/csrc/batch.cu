@@ -1482,14 +1482,19 @@ extern "C" int dec_batch_time_smooth(dec_batch *B, int reps, double *avg_ms, dou
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = all_groups_live(B, s)) return rc;
     const int cheb = B->opts.smoother == DEC_SMOOTH_CHEBYSHEV;
-    // Algorithmic bytes: each group's finest operator once (K columns + K
-    // weights per row; a group holds every right-hand side of its hierarchy
-    // up to k), then per item x, b, x_out (+ direction) for the caller's
-    // right-hand sides (padding columns not counted).
+    // Algorithmic bytes: each hierarchy's finest operator once (K columns + K
+    // weights per row), however many groups of k right-hand sides share it,
+    // then per item x, b, x_out (+ direction) for the caller's right-hand
+    // sides (padding columns not counted).
     double by = 0.0;
+    std::vector<const dec_mg *> seen;
     for (auto &G : B->groups) {
         const BLevel &L = B->hlv[G.first_lev + G.nlev - 1];
-        by += (double)L.n * (8.0 * L.K) + (double)L.n * G.kk * 4.0 * (3 + (cheb ? 1 : 0));
+        if (std::find(seen.begin(), seen.end(), G.mg) == seen.end()) {
+            by += (double)L.n * (8.0 * L.K);
+            seen.push_back(G.mg);
+        }
+        by += (double)L.n * G.kk * 4.0 * (3 + (cheb ? 1 : 0));
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
