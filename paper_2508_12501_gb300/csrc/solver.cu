@@ -1242,7 +1242,6 @@ int setup_patches(dec_mg *mg) {
         DevLevel &D = mg->lv[l];
         if (o.patch_max_rows > 0 && D.n > o.patch_max_rows) continue;
         const decimpl::HostMesh &HC = mg->H.levels[l - 1].mesh;
-        const int64_t nc = HC.nv;
         // 24 coarse vertices per tile (about 180 locals with two rings): the fastest of 12 to 48
         // in whole solves on the icosphere benchmark (FP32 and FP64 cycles)
         const int chunk = o.patch_chunk > 0 ? o.patch_chunk : kPatchChunk;
