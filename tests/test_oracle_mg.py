@@ -100,6 +100,22 @@ def test_gauss_seidel_matches_sequential_sweep():
     assert np.allclose(got, x, rtol=1e-13, atol=1e-13)
 
 
+def test_greedy_colouring_worked_example():
+    # Heptagon fan: centre 0, rim 1..7 in cyclic order.  First fit in vertex order, worked by hand: the
+    # centre takes 0; rim vertex 1 sees {0} -> 1; 2 sees {0, 1} -> 2; 3 sees {0, 2} -> 1; 4 -> 2; 5 -> 1;
+    # 6 -> 2; 7 touches 0, 6 and 1, sees {0, 2, 1} -> 3 (an odd rim needs a third rim colour).  Any other
+    # order (largest first, by degree, by colour class size) colours this fan differently.
+    from oracle import mesh as om
+    v, t = W.heptagon_fan()
+    m = om.build_mesh(v, t)
+    assert mg.greedy_colors(m).tolist() == [0, 1, 2, 1, 2, 1, 2, 3]
+    # the same fan renumbered (rim starting one step later) moves the third rim colour with the numbering
+    perm = np.array([0, 2, 3, 4, 5, 6, 7, 1])  # new vertex k is old vertex perm[k]
+    inv = np.argsort(perm)
+    m2 = om.build_mesh(v[perm], inv[t])
+    assert mg.greedy_colors(m2).tolist() == [0, 1, 2, 1, 2, 1, 2, 3]
+
+
 @pytest.mark.parametrize("mk", [lambda: _square(3, 2, smoother="mcgs"), lambda: _ico(2, 2, smoother="mcgs")])
 def test_multicolour_gs_is_gs_in_colour_order(mk):
     h = mk()
