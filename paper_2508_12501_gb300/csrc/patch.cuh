@@ -8,8 +8,10 @@
 //     writes the corrected, smoothed iterate on the owned vertices.
 //
 // Every tile recomputes its ring vertices (the vertices within nu edges of its
-// own, see host_patch.cpp): step k runs on rings 0 .. depth-1-k of the ring
-// counts, reading neighbours from the ring outside.  Each row takes the same
+// own, see host_patch.cpp).  Each phase computes exactly the rings the next
+// phase reads: down, the first step (from zero, row-local) covers every ring,
+// step k of nu covers rings 0 .. nu-k, and the residual ring 0; up, the
+// interpolation covers every ring and step k rings 0 .. nu-1-k.  Each row takes the same
 // operations in the same order as k_smooth0 / k_smooth / k_residual /
 // k_restrict / k_prolong, so the results are bitwise those of the per-step
 // kernels, with two launches per level and cycle instead of 2 nu + 2 or more.
