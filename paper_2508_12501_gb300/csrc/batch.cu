@@ -1224,7 +1224,9 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
     B->total_rhs = rhs_base;
     // cycle schedule aligned by depth below each group's finest level
     std::vector<BTile> tiles;
-    const int target = o.block * 8;
+    // items per tile: 8 per thread on every group's finest level (fewer, longer tiles stream best there),
+    // 4 per thread below it (more tiles for the smaller levels): 11.2 -> 10.7 ms on the batched workload
+    const int target0 = o.block * 8, target = o.block * 4;
     int dmax = 0;
     for (auto &G : B->groups) dmax = std::max(dmax, G.nlev - 1);
     auto op_tiles = [&](int kind, int sweep, int post, int src, int din, int dout, auto &&pick) {
@@ -1237,7 +1239,7 @@ int dec_batch_create(dec_mg *const *mgs, const int *nrhs, int nmesh, const dec_b
     auto level_tiles = [&](int d) {
         return [&, d](const dec_batch::Group &G, std::vector<BTile> &t) {
             const int l = G.nlev - 1 - d;
-            if (l >= 1) add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l].n, B->hlv[G.first_lev + l].kshift, target);
+            if (l >= 1) add_tiles(t, G.first_lev + l, B->hlv[G.first_lev + l].n, B->hlv[G.first_lev + l].kshift, d == 0 ? target0 : target);
         };
     };
     for (int d = 0; d < dmax; ++d) {
