@@ -430,7 +430,9 @@ void dec_batch_destroy(dec_batch *batch);
 /* b, x: host arrays of nmesh DEVICE pointers, entry m's vectors being double
  * [nv_finest(m) * nrhs(m)] in [v * nrhs + j] order.  Under DEC_BC_GAUGE each
  * right-hand side is projected to *0-weighted mean zero and so is its
- * solution.  Synchronizes `stream`.  Errors as for dec_solve. */
+ * solution.  A group whose right-hand sides have all converged stops
+ * iterating while the others go on: every group's result is the one it gets
+ * solved alone.  Synchronizes `stream`.  Errors as for dec_solve. */
 int dec_batch_solve(dec_batch *batch, const double *const *b, double *const *x, double tol, int maxit,
                     dec_batch_stats *stats, dec_stream_t stream);
 /* dec_batch_solve_backward: the adjoint of every solve of the batch (as
