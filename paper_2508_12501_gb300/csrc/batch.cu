@@ -1003,6 +1003,8 @@ int batch_run(dec_batch *B, double tol, int maxit, cudaStream_t s, int64_t &laun
     h->maxit = maxit;
     h->max_loops = maxit + 1;
     CK(cudaMemcpyAsync(B->scal, h, offsetof(Scal, hist), cudaMemcpyHostToDevice, s));
+    // every group live for the set-up kernels (also after a run that returned early)
+    if (int rc = all_groups_live(B, s)) return rc;
     const BTile *rt = B->dtiles + B->res_off;
     const size_t sm = sizeof(double) * B->opts.block;
     bool any_gauge = false;
