@@ -161,15 +161,21 @@ def peaks():
 
 
 # Device sources each measured kernel is compiled from (single-right-hand-side kernels: kernels.cuh and
-# coarse_cycle.cuh; batched kernels: batch.cu and the kernels.cuh helpers it includes).
+# coarse_cycle.cuh; batched kernels: the device part of batch.cu, everything before its host-side section,
+# and the kernels.cuh helpers it includes).
 KERNEL_SOURCES = {"single": ("kernels.cuh", "coarse_cycle.cuh"), "batched": ("batch.cu", "kernels.cuh")}
+DEVICE_PART_END = {"batch.cu": b"// host side\n"}
 
 
 def kernels_hash(group="single"):
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[group]:  # the device code the counters were taken on
         with open(os.path.join(ROOT, "paper_2508_12501_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+            data = fh.read()
+        end = DEVICE_PART_END.get(f)
+        if end is not None and end in data:
+            data = data[:data.index(end)]
+        h.update(data)
     return h.hexdigest()[:16]
 
 
